@@ -1,0 +1,226 @@
+/*
+ * hqr.h -- C ABI of the GB300 hierarchical tile Householder QR library.
+ *
+ * Method: Dongarra, Faverge, Herault, Langou, Robert, "Hierarchical QR
+ * factorization algorithms for multi-core cluster systems" (arXiv 1110.1553).
+ * A tile QR of an m x n tile matrix (tiles b x b, M = m b, N = n b) is fully
+ * determined by its elimination list (Sec. 2, Alg. 1); each elimination is
+ * carried out by the tile kernels GEQRT, TSQRT/TTQRT and UNMQR, TSMQR/TTMQR
+ * (Alg. 2). HQR builds the list from TS domains of a tiles, a low-level tree
+ * inside each of p virtual domains and a high-level tree over the domains
+ * (Sec. 4.1-4.2). Q is applied by replaying the trees (Sec. 5.1).
+ *
+ * Conventions shared by every call:
+ *  - Matrices passed by the caller are column-major with a leading dimension
+ *    (LAPACK style). "d" pointers are device pointers, "h" pointers host
+ *    pointers. The caller owns every buffer it passes; the library never
+ *    frees or keeps them.
+ *  - The library copies A into its own tile-major workspace (zero padded to
+ *    whole tiles, Sec. 2 assumes M and N are multiples of b); the caller's A
+ *    is never written.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). All device
+ *    work of a call is ordered on it; calls that return a host result
+ *    synchronize the stream first, and say so.
+ *  - Return value: 0 on success; -k when argument k (1-based) is invalid;
+ *    a positive HQR_ERR_* code otherwise. No call aborts the process and no
+ *    kernel traps: device-side waits have a time limit and report
+ *    HQR_ERR_TIMEOUT. hqr_strerror() turns a code into text; for
+ *    HQR_ERR_CUDA, hqr_last_error() gives the CUDA error text.
+ */
+#ifndef HQR_H
+#define HQR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Reduction tree shapes (Sec. 3.1-3.3): FLAT and BINARY of Sec. 3.1, GREEDY
+ * of Sec. 3.2 (Table 4), FIBONACCI = the Modi-Clarke order-1 scheme named in
+ * Sec. 3.3 (its definition is not printed in the paper; see hqr_elim_list). */
+typedef enum { HQR_FLAT = 0, HQR_BINARY = 1, HQR_GREEDY = 2, HQR_FIBONACCI = 3 } hqr_tree_t;
+
+/* Kernel kind of an elimination (Sec. 2, Alg. 2). */
+typedef enum { HQR_KIND_TS = 0, HQR_KIND_TT = 1 } hqr_kind_t;
+
+/* One elimination elim(i, killer, k) of Sec. 2: tile (i, k) is zeroed by
+ * tile (killer, k). level: 0 = TS level, 1 = low level, 3 = high level
+ * (Sec. 4.2; level 2, the domino level, is not generated). step: time step
+ * of the unit-time model of Sec. 3.1-3.2. 24 bytes, no padding surprises. */
+typedef struct {
+  int32_t k;
+  int32_t i;
+  int32_t killer;
+  int32_t kind;
+  int32_t level;
+  int32_t step;
+} hqr_elim_t;
+
+/* Arithmetic of the factorization. HQR_FP64: FP64 storage and arithmetic
+ * everywhere (the paper's setting, Sec. 5.1). */
+typedef enum { HQR_FP64 = 0 } hqr_prec_t;
+
+enum {
+  HQR_SUCCESS = 0,
+  HQR_ERR_CUDA = 1,      /* a CUDA runtime call failed; see hqr_last_error() */
+  HQR_ERR_TIMEOUT = 2,   /* a device-side wait reached its time limit */
+  HQR_ERR_NOMEM = 3,     /* device or host allocation failed */
+  HQR_ERR_CAPACITY = 4,  /* output array too small; *count holds the size needed */
+  HQR_ERR_INVALID_LIST = 5, /* elimination list breaks a rule of Sec. 2 */
+  HQR_ERR_SINGULAR = 6,  /* exact zero on the diagonal of R (hqr_gels) */
+  HQR_ERR_INTERNAL = 7   /* internal consistency check failed */
+};
+
+/* Opaque factorization: owns the tile workspace (V and R), the T factors,
+ * a copy of the elimination list and the device task graphs. */
+typedef struct hqr_factors hqr_factors;
+
+/*
+ * hqr_elim_list -- HQR elimination list (Sec. 4.1-4.2, trees of Sec. 3.1-3.3).
+ * Host only, integer only, deterministic.
+ *   m, n      tile rows and tile columns, m >= n >= 1.
+ *   a         TS domain size (a = 1: no TS kernels), a >= 1.
+ *   p         number of virtual domains; tile row i is in domain i mod p.
+ *   low_tree  tree over the TS heads of each domain (level 1).
+ *   high_tree tree over the p domain tops (level 3).
+ *   out, cap  caller array of cap records (out may be NULL when cap == 0).
+ *   count     receives the number of records, sum_{k<n} (m-k-1).
+ * Records are written sorted by (k, step, i). If cap is too small nothing is
+ * written, *count is set and HQR_ERR_CAPACITY is returned.
+ * Readings of the paper (also in the design notes): heads are every a-th
+ * active row counted from the domain top; GREEDY takes readiness into account
+ * (a row is a candidate at step t once its last elimination is before t);
+ * FIBONACCI cuts the leaves below the survivor into groups of 1, 2, 3, ...
+ * killed by the same number of leaves right above them, bottom group first.
+ */
+int hqr_elim_list(int m, int n, int a, int p, int low_tree, int high_tree,
+                  hqr_elim_t *out, size_t cap, size_t *count);
+
+/*
+ * hqr_validate_list -- check a list against the validity rules of Sec. 2:
+ * every tile (i, k), i > k, killed exactly once; both rows ready (zeroed in
+ * every earlier panel before this record); the killer not yet zeroed in this
+ * panel; a TS kill only of a square tile (a row that has not killed before in
+ * this panel) and no kill by a TS-zeroed row. Host only.
+ * Returns 0 if valid, HQR_ERR_INVALID_LIST otherwise, -k for bad arguments.
+ */
+int hqr_validate_list(int m, int n, const hqr_elim_t *list, size_t count);
+
+/*
+ * hqr_geqrf -- tile QR factorization A = Q R driven by an elimination list
+ * (Alg. 1 with the eliminations of Alg. 2), executed by a persistent device
+ * kernel that starts each tile task as soon as its inputs are final
+ * (Sec. 4.2, "Execution scheme").
+ *   dA      device, M x N column-major, lda >= M; read only.
+ *   M, N    matrix size, M >= N >= 1. Padded with zeros to whole tiles.
+ *   prec    hqr_prec_t.
+ *   nb      tile size b: multiple of 8, 8 <= nb <= 256.
+ *   ib      inner block of the compact-WY T factors: even, divides nb.
+ *   list    host array of `count` records for m = ceil(M/nb), n = ceil(N/nb)
+ *           tiles, or NULL for the default list (flat TS domains of a = 4,
+ *           p = 1, greedy low tree).
+ *   F       receives the new factorization (free with hqr_factors_free).
+ * The stream is synchronized before return (the device reports its status).
+ */
+int hqr_geqrf(const void *dA, int M, int N, int lda, int prec, int nb, int ib,
+              const hqr_elim_t *list, size_t count, hqr_factors **F, void *stream);
+
+/*
+ * hqr_refactor -- factor a new matrix of the same shape with an existing
+ * factorization object (same list, tile size and task graph; no allocation).
+ * Used for repeated factorizations. Synchronizes the stream.
+ */
+int hqr_refactor(hqr_factors *F, const void *dA, int lda, void *stream);
+
+/*
+ * hqr_refactor_async -- as hqr_refactor but does not synchronize: the device
+ * status is left in the factorization and read by hqr_status(). No host
+ * synchronization, so it can be captured in a CUDA graph.
+ */
+int hqr_refactor_async(hqr_factors *F, const void *dA, int lda, void *stream);
+
+/* hqr_status -- synchronize `stream` and return the device status of the
+ * last asynchronous call on F (0, HQR_ERR_TIMEOUT or HQR_ERR_INTERNAL). */
+int hqr_status(hqr_factors *F, void *stream);
+
+/*
+ * hqr_get_r -- copy the N x N upper triangular factor R into dR (device,
+ * column-major, ldr >= N). The strict lower part of dR is set to zero.
+ */
+int hqr_get_r(const hqr_factors *F, void *dR, int ldr, void *stream);
+
+/*
+ * hqr_get_tiles -- copy the factored tile workspace, Mp x Np (padded sizes,
+ * see hqr_factors_info), into dOut (device, column-major, ld >= Mp): R in the
+ * upper triangles of the tiles on the diagonal and above, GEQRT V below the
+ * diagonal of each triangle tile, TSQRT V2 in TS-killed tiles, TTQRT V2 in
+ * the upper triangle of TT-killed tiles (Sec. 2 storage of the kernels).
+ */
+int hqr_get_tiles(const hqr_factors *F, void *dOut, int ld, void *stream);
+
+/*
+ * hqr_get_t -- copy all T factors into dT (device). Layout: for tile (i, k)
+ * of the m x n tile grid and which = 0 (GEQRT T) or 1 (TSQRT/TTQRT T), an
+ * ib x nb column-major array at element offset ((k*m + i)*2 + which)*ib*nb.
+ * Block q of reflectors owns columns q*ib .. q*ib+ib-1 (an upper triangle).
+ */
+int hqr_get_t(const hqr_factors *F, void *dT, void *stream);
+
+/* hqr_factors_info -- sizes of a factorization: padded rows/cols, tiles,
+ * tile size, inner block, number of tasks in the factorization graph. */
+int hqr_factors_info(const hqr_factors *F, int *Mp, int *Np, int *m, int *n,
+                     int *nb, int *ib, int64_t *ntasks);
+
+/*
+ * hqr_apply_q -- B <- Q^T B (trans = 1) or B <- Q B (trans = 0), replaying
+ * the elimination list forward or in reverse (Sec. 5.1: Q is formed by
+ * applying the reverse trees to the identity).
+ *   dB      device, M x nrhs column-major (M = the factorization's rows),
+ *           ldb >= M; overwritten with the result.
+ */
+int hqr_apply_q(hqr_factors *F, int trans, void *dB, int ldb, int nrhs, void *stream);
+
+/*
+ * hqr_gels -- least squares min ||b - A x||_2 for M >= N, full rank:
+ * factor, c = Q^T b, x = R^{-1} c[0:N] (problem of Sec. 2 with the
+ * application of Sec. 5.1).
+ *   db      device, M x nrhs, ldb >= M; read only.
+ *   dx      device, N x nrhs, ldx >= N; receives x.
+ *   list    as in hqr_geqrf (NULL = default).
+ * Returns HQR_ERR_SINGULAR if a diagonal entry of R is exactly zero.
+ */
+int hqr_gels(const void *dA, int M, int N, int lda, const void *db, int ldb, int nrhs,
+             void *dx, int ldx, int prec, int nb, int ib, const hqr_elim_t *list,
+             size_t count, void *stream);
+
+/*
+ * hqr_debug_block_task -- testing aid for the device-side time limits: add
+ * `extra` never-satisfied inputs to task `task` of F's factorization graph,
+ * so the next hqr_refactor cannot finish and must return HQR_ERR_TIMEOUT
+ * (after hqr_set_timeout_ms) instead of hanging. extra = 0 restores it.
+ */
+int hqr_debug_block_task(hqr_factors *F, int64_t task, int extra);
+
+/* hqr_factors_free -- release a factorization (NULL is allowed). */
+void hqr_factors_free(hqr_factors *F);
+
+/* hqr_set_timeout_ms -- time limit of every device-side wait (default 20000). */
+void hqr_set_timeout_ms(int64_t ms);
+
+/* hqr_strerror -- static text of a status code. */
+const char *hqr_strerror(int status);
+
+/* hqr_last_error -- text of the last CUDA error seen by this thread. */
+const char *hqr_last_error(void);
+
+/* hqr_last_launch -- kernel launches made by the last factorization or apply
+ * call on this thread (for launch accounting). */
+int64_t hqr_last_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HQR_H */

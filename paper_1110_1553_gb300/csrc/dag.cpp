@@ -1,0 +1,208 @@
+// Host construction of the tile task graphs (Alg. 1 and Alg. 2 expanded into
+// tasks with data dependencies). Each task lists the pieces of tile storage
+// it reads and writes; an edge is added for every read-after-write,
+// write-after-write and write-after-read between tasks taken in the
+// sequential order of Alg. 1, so any order the device scheduler picks gives
+// the same arithmetic as the sequential algorithm (Sec. 4.2 "Execution
+// scheme": tasks fire as soon as their dependencies are met).
+#include <algorithm>
+#include <stdexcept>
+
+#include "hqr_internal.h"
+
+namespace hqr {
+
+std::vector<PanelOp> expand_ops(const hqr_elim_t *list, size_t count, int m, int n) {
+  std::vector<PanelOp> ops;
+  const int K = std::min(m, n);
+  // records grouped by panel, keeping the list order inside a panel
+  std::vector<std::vector<size_t>> by_panel(K);
+  for (size_t q = 0; q < count; ++q) by_panel[list[q].k].push_back(q);
+  std::vector<int> triangle(m, -1);  // panel in which the row last got GEQRT
+  for (int k = 0; k < K; ++k) {
+    for (size_t q : by_panel[k]) {
+      const hqr_elim_t &e = list[q];
+      if (triangle[e.killer] != k) {
+        ops.push_back({0, k, e.killer, e.killer});
+        triangle[e.killer] = k;
+      }
+      if (e.kind == HQR_KIND_TT && triangle[e.i] != k) {
+        ops.push_back({0, k, e.i, e.i});
+        triangle[e.i] = k;
+      }
+      ops.push_back({(int8_t)(e.kind == HQR_KIND_TS ? 1 : 2), k, e.i, e.killer});
+    }
+    if (by_panel[k].empty()) ops.push_back({0, k, k, k});
+  }
+  return ops;
+}
+
+namespace {
+
+// Last writer and readers-since-last-write per storage piece.
+class Tracker {
+ public:
+  explicit Tracker(size_t nres) : writer_(nres, -1), readers_(nres) {}
+  void read(size_t res, std::vector<int32_t> &deps) {
+    if (writer_[res] >= 0) deps.push_back(writer_[res]);
+    pending_reads_.push_back(res);
+  }
+  void write(size_t res, std::vector<int32_t> &deps) {
+    if (writer_[res] >= 0) deps.push_back(writer_[res]);
+    for (int32_t r : readers_[res]) deps.push_back(r);
+    pending_writes_.push_back(res);
+  }
+  // Record the task's accesses after all its dependencies were collected.
+  void commit(int32_t task) {
+    for (size_t res : pending_writes_) {
+      writer_[res] = task;
+      readers_[res].clear();
+    }
+    for (size_t res : pending_reads_) readers_[res].push_back(task);
+    pending_reads_.clear();
+    pending_writes_.clear();
+  }
+
+ private:
+  std::vector<int32_t> writer_;
+  std::vector<std::vector<int32_t>> readers_;
+  std::vector<size_t> pending_reads_, pending_writes_;
+};
+
+class Builder {
+ public:
+  explicit Builder(size_t nres) : tr_(nres) {}
+  Tracker &tr() { return tr_; }
+  std::vector<int32_t> &deps() { return deps_; }
+  void add(const Task &t) {
+    const int32_t id = (int32_t)g_.tasks.size();
+    std::sort(deps_.begin(), deps_.end());
+    deps_.erase(std::unique(deps_.begin(), deps_.end()), deps_.end());
+    for (int32_t d : deps_) edges_.push_back({d, id});
+    g_.indeg.push_back((int32_t)deps_.size());
+    g_.tasks.push_back(t);
+    tr_.commit(id);
+    deps_.clear();
+  }
+  Graph finish() {
+    const size_t nt = g_.tasks.size();
+    std::vector<int32_t> cnt(nt + 1, 0);
+    for (auto &e : edges_) cnt[e.first + 1]++;
+    for (size_t q = 0; q < nt; ++q) cnt[q + 1] += cnt[q];
+    g_.succ.assign(edges_.size(), 0);
+    std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
+    for (auto &e : edges_) g_.succ[fill[e.first]++] = e.second;
+    for (size_t q = 0; q < nt; ++q) {
+      g_.tasks[q].succ_begin = cnt[q];
+      g_.tasks[q].succ_end = cnt[q + 1];
+    }
+    g_.nedges = (int64_t)edges_.size();
+    return std::move(g_);
+  }
+
+ private:
+  Tracker tr_;
+  std::vector<int32_t> deps_;
+  std::vector<std::pair<int32_t, int32_t>> edges_;
+  Graph g_;
+};
+
+Task make_task(int op, int prio, int i, int r, int k, int j, int c0, int cw, int trans) {
+  Task t;
+  t.op = (int8_t)op;
+  t.prio = (int8_t)prio;
+  t.trans = (int8_t)trans;
+  t.pad = 0;
+  t.i = i;
+  t.r = r;
+  t.k = k;
+  t.j = j;
+  t.c0 = c0;
+  t.cw = cw;
+  t.succ_begin = t.succ_end = 0;
+  return t;
+}
+
+}  // namespace
+
+Graph build_factor_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int w) {
+  const int S = (nb + w - 1) / w;  // column slabs per tile
+  const size_t per_tile = (size_t)S + 2;
+  // storage pieces of tile (i, j): S column slabs, then U (upper triangle
+  // with the diagonal: R, or TTQRT's V2) and L (strict lower: GEQRT's V)
+  auto slab = [&](int i, int j, int s) { return ((size_t)j * m + i) * per_tile + (size_t)s; };
+  auto upart = [&](int i, int j) { return ((size_t)j * m + i) * per_tile + (size_t)S; };
+  auto lpart = [&](int i, int j) { return ((size_t)j * m + i) * per_tile + (size_t)S + 1; };
+  Builder b((size_t)m * n * per_tile);
+  Tracker &tr = b.tr();
+  std::vector<int32_t> &d = b.deps();
+  for (const PanelOp &o : ops) {
+    const int k = o.k;
+    if (o.kind == 0) {  // GEQRT(i, k) and UNMQR(i, k, j) for j > k
+      for (int s = 0; s < S; ++s) tr.write(slab(o.i, k, s), d);
+      tr.write(upart(o.i, k), d);
+      tr.write(lpart(o.i, k), d);
+      b.add(make_task(OP_GEQRT, 0, o.i, o.i, k, k, 0, nb, 1));
+      for (int j = k + 1; j < n; ++j)
+        for (int s = 0; s < S; ++s) {
+          tr.read(lpart(o.i, k), d);
+          tr.write(slab(o.i, j, s), d);
+          b.add(make_task(OP_UNMQR, j == k + 1 ? 1 : 2, o.i, o.i, k, j, s * w,
+                          std::min(w, nb - s * w), 1));
+        }
+    } else if (o.kind == 1) {  // TSQRT(i, r, k), TSMQR(i, r, k, j)
+      tr.write(upart(o.r, k), d);
+      for (int s = 0; s < S; ++s) tr.write(slab(o.i, k, s), d);
+      tr.write(upart(o.i, k), d);
+      tr.write(lpart(o.i, k), d);
+      b.add(make_task(OP_TSQRT, 0, o.i, o.r, k, k, 0, nb, 1));
+      for (int j = k + 1; j < n; ++j)
+        for (int s = 0; s < S; ++s) {
+          tr.read(upart(o.i, k), d);
+          tr.read(lpart(o.i, k), d);
+          tr.write(slab(o.r, j, s), d);
+          tr.write(slab(o.i, j, s), d);
+          b.add(make_task(OP_TSMQR, j == k + 1 ? 1 : 2, o.i, o.r, k, j, s * w,
+                          std::min(w, nb - s * w), 1));
+        }
+    } else {  // TTQRT(i, r, k), TTMQR(i, r, k, j)
+      tr.write(upart(o.r, k), d);
+      tr.write(upart(o.i, k), d);
+      b.add(make_task(OP_TTQRT, 0, o.i, o.r, k, k, 0, nb, 1));
+      for (int j = k + 1; j < n; ++j)
+        for (int s = 0; s < S; ++s) {
+          tr.read(upart(o.i, k), d);
+          tr.write(slab(o.r, j, s), d);
+          tr.write(slab(o.i, j, s), d);
+          b.add(make_task(OP_TTMQR, j == k + 1 ? 1 : 2, o.i, o.r, k, j, s * w,
+                          std::min(w, nb - s * w), 1));
+        }
+    }
+  }
+  return b.finish();
+}
+
+Graph build_apply_graph(const std::vector<PanelOp> &ops, int m, int nslab, int w, int trans) {
+  // storage pieces: (row tile, column slab) of the right-hand side
+  auto piece = [&](int r, int s) { return (size_t)r * nslab + (size_t)s; };
+  Builder b((size_t)m * nslab);
+  Tracker &tr = b.tr();
+  std::vector<int32_t> &d = b.deps();
+  const size_t nops = ops.size();
+  for (size_t q = 0; q < nops; ++q) {
+    const PanelOp &o = trans ? ops[q] : ops[nops - 1 - q];
+    for (int s = 0; s < nslab; ++s) {
+      if (o.kind == 0) {
+        tr.write(piece(o.i, s), d);
+        b.add(make_task(OP_UNMQR, 1, o.i, o.i, o.k, s, 0, w, trans));
+      } else {
+        tr.write(piece(o.r, s), d);
+        tr.write(piece(o.i, s), d);
+        b.add(make_task(o.kind == 1 ? OP_TSMQR : OP_TTMQR, 1, o.i, o.r, o.k, s, 0, w, trans));
+      }
+    }
+  }
+  return b.finish();
+}
+
+}  // namespace hqr

@@ -1,0 +1,633 @@
+// FP64 tile kernels of tile Householder QR and the persistent task
+// scheduler that runs them (sm_103a).
+//
+// Every task of the graph (GEQRT, TSQRT, TTQRT and the UNMQR, TSMQR, TTMQR
+// updates of Alg. 2) is executed by one CTA of a persistent kernel. A CTA
+// takes the highest-priority ready task from device queues, stages its tile
+// data in shared memory with bulk copies (the TMA engine; one copy per tile
+// column, completion counted on an mbarrier), computes, writes the tiles back
+// and releases its successors: each successor whose count of missing inputs
+// drops to zero is pushed to a queue (Sec. 4.2, "Execution scheme": each
+// kernel fires as soon as its dependencies are satisfied).
+//
+// Arithmetic (compact-WY Householder, reflectors grouped ib at a time):
+//   column j of (alpha, x2): s = ||x2|| (sum of squares; a max-scaled second
+//   pass when the sum under- or overflows), beta = -sign(alpha) hypot(alpha,
+//   s) with sign(+-0) = +1, tau = (beta - alpha) / beta, v = (1, x2/(alpha -
+//   beta)); s == 0 gives the identity (tau = 0, beta = alpha).
+//   T of a block: T[j,j] = tau_j, T[:j,j] = -tau_j T[:j,:j] (V[:,:j]^T v_j).
+//   Q^T C = C - V T^T V^T C (blocks in ascending order); Q C uses T and the
+//   descending order.
+// Norm reductions use warp shuffles and a per-warp shared-memory stage.
+#pragma once
+
+#include <cstdint>
+
+#include "hqr_internal.h"
+#include "ptx.cuh"
+
+namespace hqr {
+
+constexpr int NT = 256;         // threads per CTA
+constexpr int NWARP = NT / 32;  // warps per CTA
+constexpr int VCMAX = 16;       // V columns staged per chunk in the updates
+constexpr int IBMAX = 32;       // largest inner block
+
+// Device control words of one graph run.
+struct Ctl {
+  unsigned head[kNumQueues];
+  unsigned tail[kNumQueues];
+  unsigned done;
+  int status;
+  int err_task;
+  int pad[3];
+};
+
+struct EngineParams {
+  double *A;           // tile workspace: tile (i, j) at ((j*m + i)*nb*nb), column-major
+  double *T;           // T factors: ((k*m + i)*2 + which)*ib*nb, ib x nb column-major
+  double *C;           // update targets: A for the factorization, RHS blocks for apply-Q
+  long long cstride;   // elements between target blocks of consecutive rows
+  int m, n, nb, ib;
+  int w;               // width of an update task's column slab (max)
+  int wt;              // slab width of the trailing update inside panel tasks
+  int vc;              // V columns staged per chunk in update tasks (divides ib)
+  int lds;             // shared-memory column stride (nb + 2)
+  const Task *tasks;
+  int ntasks;
+  const int *succ;
+  int *indeg;
+  int *slots;          // kNumQueues x ntasks ready slots (task id + 1, 0 = empty)
+  Ctl *ctl;
+  long long timeout_ns;
+};
+
+struct Shared {
+  uint64_t bar;
+  int task;
+  int abort;
+  double red[2 * NWARP];
+  double tau[IBMAX];
+  double wv[IBMAX];
+  double bc[4];
+};
+
+// ---------------------------------------------------------------- helpers --
+
+__device__ __forceinline__ double *tile_ptr(const EngineParams &p, int i, int j) {
+  return p.A + ((size_t)j * p.m + i) * (size_t)p.nb * p.nb;
+}
+__device__ __forceinline__ double *t_ptr(const EngineParams &p, int which, int i, int k) {
+  return p.T + (((size_t)k * p.m + i) * 2 + which) * (size_t)p.ib * p.nb;
+}
+__device__ __forceinline__ double *target_ptr(const EngineParams &p, const Task &t, int row) {
+  return p.C + ((size_t)t.j * p.m + row) * (size_t)p.cstride + (size_t)t.c0 * p.nb;
+}
+
+__device__ __forceinline__ void set_error(const EngineParams &p, int code, int task) {
+  if (atomicCAS(&p.ctl->status, 0, code) == 0) p.ctl->err_task = task;
+}
+
+struct Copy {
+  double *dst;
+  int ldd;
+  const double *src;
+  long long lds;
+  int nrows, ncols;
+};
+
+// Stage up to 3 column-blocks global -> shared with bulk copies, one copy per
+// column, and wait for them (bounded). Callers sync before (dst free).
+__device__ void stage(const EngineParams &p, Shared &sh, const Copy *cp, int ncp, uint32_t &phase) {
+  uint32_t total = 0;
+  for (int q = 0; q < ncp; ++q)
+    if (cp[q].nrows > 0 && cp[q].ncols > 0) total += (uint32_t)cp[q].nrows * 8u * (uint32_t)cp[q].ncols;
+  if (total == 0) return;
+  if (threadIdx.x < 32) {
+    ptx::fence_proxy_async();
+    if (threadIdx.x == 0) ptx::mbar_arrive_expect_tx(&sh.bar, total);
+    __syncwarp();
+    for (int q = 0; q < ncp; ++q) {
+      if (cp[q].nrows <= 0) continue;
+      const uint32_t bytes = (uint32_t)cp[q].nrows * 8u;
+      for (int c = threadIdx.x; c < cp[q].ncols; c += 32)
+        ptx::bulk_g2s(cp[q].dst + (size_t)c * cp[q].ldd, cp[q].src + (long long)c * cp[q].lds, bytes,
+                      &sh.bar);
+    }
+  }
+  if (!ptx::mbar_try_wait(&sh.bar, phase)) {
+    const uint64_t t0 = ptx::globaltimer();
+    while (!ptx::mbar_try_wait(&sh.bar, phase)) {
+      if (sh.abort || ptx::globaltimer() - t0 > (uint64_t)p.timeout_ns) {
+        sh.abort = 1;
+        break;
+      }
+    }
+  }
+  phase ^= 1u;
+  __syncthreads();
+  if (sh.abort && threadIdx.x == 0) set_error(p, HQR_ERR_TIMEOUT, -1);
+}
+
+// Write an nrows x ncols block from shared to global (coalesced along rows).
+// mode 0: all; 1: only rows <= roff + col (upper part incl. diagonal).
+__device__ void store_cols(double *g, long long ldg, const double *s, int ldsm, int nrows, int ncols,
+                           int mode, int roff) {
+  const int total = nrows * ncols;
+  for (int e = threadIdx.x; e < total; e += NT) {
+    const int c = e / nrows, r = e - c * nrows;
+    if (mode == 1 && r > roff + c) continue;
+    g[(long long)c * ldg + r] = s[(size_t)c * ldsm + r];
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the CTA; every thread gets the same value (fixed order).
+__device__ double block_sum(double v, Shared &sh) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int q = 0; q < NWARP; ++q) t += sh.red[q];
+  __syncthreads();
+  return t;
+}
+
+__device__ double block_max(double v, Shared &sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int q = 0; q < NWARP; ++q) t = fmax(t, sh.red[q]);
+  __syncthreads();
+  return t;
+}
+
+// W(i,j) = [Cinit(i,j)] + sum_{k<K} V(k,i) C(k,j), i < Mi, j < Nj.
+// Short output sets split K among thread groups; partial sums are combined
+// in a fixed order through `scr` (>= NT doubles).
+__device__ void gemm_tn(double *W, int ldw, const double *V, int ldv, const double *Cm, int ldc, int K,
+                        int Mi, int Nj, const double *Cinit, int ldi, double *scr) {
+  const int O = Mi * Nj;
+  if (O <= 0) return;
+  const int tid = threadIdx.x;
+  if (O >= NT / 2 || K < 64) {
+    for (int o = tid; o < O; o += NT) {
+      const int i = o % Mi, j = o / Mi;
+      const double *v = V + (size_t)i * ldv;
+      const double *c = Cm + (size_t)j * ldc;
+      double s0 = 0.0, s1 = 0.0;
+      int k = 0;
+      for (; k + 1 < K; k += 2) {
+        s0 = fma(v[k], c[k], s0);
+        s1 = fma(v[k + 1], c[k + 1], s1);
+      }
+      if (k < K) s0 = fma(v[k], c[k], s0);
+      const double base = Cinit ? Cinit[i + (size_t)j * ldi] : 0.0;
+      W[i + (size_t)j * ldw] = base + (s0 + s1);
+    }
+    __syncthreads();
+    return;
+  }
+  int G = NT / O;
+  if (G > 16) G = 16;
+  const int Kc = (K + G - 1) / G;
+  const int o = tid % O, g = tid / O;
+  if (g < G) {
+    const int i = o % Mi, j = o / Mi;
+    const double *v = V + (size_t)i * ldv;
+    const double *c = Cm + (size_t)j * ldc;
+    const int k0 = g * Kc, k1 = min(K, k0 + Kc);
+    double s = 0.0;
+    for (int k = k0; k < k1; ++k) s = fma(v[k], c[k], s);
+    scr[g * O + o] = s;
+  }
+  __syncthreads();
+  if (tid < O) {
+    const int i = tid % Mi, j = tid / Mi;
+    double s = 0.0;
+    for (int q = 0; q < G; ++q) s += scr[q * O + tid];
+    const double base = Cinit ? Cinit[i + (size_t)j * ldi] : 0.0;
+    W[i + (size_t)j * ldw] = base + s;
+  }
+  __syncthreads();
+}
+
+// C(k,j) -= sum_{i<Mi} V(k,i) W(i,j), k < K, j < Nj. Threads run along k.
+__device__ void gemm_nn_sub(double *Cm, int ldc, const double *V, int ldv, const double *W, int ldw, int K,
+                            int Mi, int Nj) {
+  const int nchunk = (Nj + 7) / 8;
+  const int total = K * nchunk;
+  for (int it = threadIdx.x; it < total; it += NT) {
+    const int k = it % K, jc = it / K;
+    const int j0 = jc * 8, jn = min(8, Nj - j0);
+    double acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    for (int i = 0; i < Mi; ++i) {
+      const double v = V[k + (size_t)i * ldv];
+      const double *w = W + i + (size_t)j0 * ldw;
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (q < jn) acc[q] = fma(v, w[(size_t)q * ldw], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (q < jn) Cm[k + (size_t)(j0 + q) * ldc] -= acc[q];
+  }
+  __syncthreads();
+}
+
+// W <- T^T W (trans) or T W, T an ib x ib upper triangle (ld ib).
+__device__ void trmm_tw(double *W, int ldw, const double *Tq, int ib, int Nj, int trans, double *tmp) {
+  const int O = ib * Nj;
+  for (int o = threadIdx.x; o < O; o += NT) {
+    const int i = o % ib, j = o / ib;
+    const double *w = W + (size_t)j * ldw;
+    double s = 0.0;
+    if (trans) {
+      for (int l = 0; l <= i; ++l) s = fma(Tq[l + (size_t)i * ib], w[l], s);
+    } else {
+      for (int l = i; l < ib; ++l) s = fma(Tq[i + (size_t)l * ib], w[l], s);
+    }
+    tmp[o] = s;
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < O; o += NT) {
+    const int i = o % ib, j = o / ib;
+    W[i + (size_t)j * ldw] = tmp[o];
+  }
+  __syncthreads();
+}
+
+// Ct(i,j) -= W(i,j): the identity top block of TS/TT reflectors.
+__device__ void sub_top(double *Ct, int ldt, const double *W, int ldw, int Mi, int Nj) {
+  for (int o = threadIdx.x; o < Mi * Nj; o += NT) {
+    const int i = o % Mi, j = o / Mi;
+    Ct[i + (size_t)j * ldt] -= W[i + (size_t)j * ldw];
+  }
+  __syncthreads();
+}
+
+enum { PANEL_GE = 0, PANEL_TS = 1, PANEL_TT = 2 };
+
+// Householder factorization of one block of ib columns held in shared memory.
+//  GE: P is L x ib, column jj has alpha = P(jj,jj) and x2 = P(jj+1:L, jj).
+//  TS: alpha = Rt(jj,jj), x2 = P(0:L, jj) (the killed square tile).
+//  TT: alpha = Rt(jj,jj), x2 = P(0:q0+jj+1, jj) (upper-triangular tile).
+// On return P holds the reflectors' lower parts (GE: R above) and sh.tau the
+// scalars; Rt's upper triangle holds the updated R rows of the block.
+__device__ void factor_block(int mode, double *P, int ld, int L, int ib, double *Rt, int ldt, int q0,
+                             Shared &sh) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int jj = 0; jj < ib; ++jj) {
+    const int r0 = (mode == PANEL_GE) ? jj + 1 : 0;
+    const int r1 = (mode == PANEL_TT) ? min(L, q0 + jj + 1) : L;
+    double *col = P + (size_t)jj * ld;
+    double ss = 0.0;
+    for (int k = r0 + tid; k < r1; k += NT) ss = fma(col[k], col[k], ss);
+    ss = block_sum(ss, sh);
+    double snorm;
+    if (ss > 1e-280 && ss < 1e280) {
+      snorm = sqrt(ss);
+    } else {
+      double am = 0.0;
+      for (int k = r0 + tid; k < r1; k += NT) am = fmax(am, fabs(col[k]));
+      am = block_max(am, sh);
+      if (am == 0.0) {
+        snorm = 0.0;
+      } else {
+        const double inv = 1.0 / am;
+        double s2 = 0.0;
+        for (int k = r0 + tid; k < r1; k += NT) {
+          const double x = col[k] * inv;
+          s2 = fma(x, x, s2);
+        }
+        s2 = block_sum(s2, sh);
+        snorm = am * sqrt(s2);
+      }
+    }
+    double *diag = (mode == PANEL_GE) ? &col[jj] : &Rt[jj + (size_t)jj * ldt];
+    if (tid == 0) {
+      const double alpha = *diag;
+      double beta = alpha, t = 0.0, scale = 0.0;
+      if (snorm != 0.0) {
+        const double h = hypot(alpha, snorm);
+        beta = (alpha >= 0.0) ? -h : h;
+        t = (beta - alpha) / beta;
+        scale = 1.0 / (alpha - beta);
+      }
+      *diag = beta;
+      sh.tau[jj] = t;
+      sh.bc[0] = t;
+      sh.bc[1] = scale;
+    }
+    __syncthreads();
+    const double t = sh.bc[0], scale = sh.bc[1];
+    for (int k = r0 + tid; k < r1; k += NT) col[k] *= scale;
+    __syncthreads();
+    if (t == 0.0) continue;  // identity reflector: nothing to apply
+    // w_c = top(jj,c) + v^T P(:,c) for the block's later columns
+    for (int c = jj + 1 + warp; c < ib; c += NWARP) {
+      const double *pc = P + (size_t)c * ld;
+      double s = 0.0;
+      for (int k = r0 + lane; k < r1; k += 32) s = fma(col[k], pc[k], s);
+      s = warp_sum(s);
+      if (lane == 0) {
+        const double top = (mode == PANEL_GE) ? pc[jj] : Rt[jj + (size_t)c * ldt];
+        sh.wv[c] = t * (top + s);
+      }
+    }
+    __syncthreads();
+    const int nr = r1 - r0, ncl = ib - jj - 1;
+    for (int e = tid; e < nr * ncl; e += NT) {
+      const int c = jj + 1 + e / nr, k = r0 + e % nr;
+      double *pc = P + (size_t)c * ld;
+      pc[k] = fma(-col[k], sh.wv[c], pc[k]);
+    }
+    if (tid > jj && tid < ib) {
+      if (mode == PANEL_GE)
+        P[jj + (size_t)tid * ld] -= sh.wv[tid];
+      else
+        Rt[jj + (size_t)tid * ldt] -= sh.wv[tid];
+    }
+    __syncthreads();
+  }
+}
+
+// T of a block from the Gram matrix G = V^T V (only G(l, j), l < j, used).
+__device__ void build_t(double *Tq, const double *G, int ib, const Shared &sh) {
+  for (int e = threadIdx.x; e < ib * ib; e += NT) Tq[e] = 0.0;
+  __syncthreads();
+  for (int jj = 0; jj < ib; ++jj) {
+    const int tid = threadIdx.x;
+    if (tid < jj) {
+      double y = 0.0;
+      for (int l = tid; l < jj; ++l) y = fma(Tq[tid + (size_t)l * ib], G[l + (size_t)jj * ib], y);
+      Tq[tid + (size_t)jj * ib] = -sh.tau[jj] * y;
+    } else if (tid == jj) {
+      Tq[jj + (size_t)jj * ib] = sh.tau[jj];
+    }
+    __syncthreads();
+  }
+}
+
+// Set the structural zeros (and unit diagonal) of a staged V chunk.
+//  GE: unit lower; chunk column cc is global block column coff + cc, local
+//      row kl is block row kl: zero above, one on the diagonal.
+//  TT: upper triangular: zero below row roff + coff + cc.
+__device__ void shape_v(double *V, int ld, int L, int ncols, int mode, int coff, int roff) {
+  for (int e = threadIdx.x; e < L * ncols; e += NT) {
+    const int c = e / L, k = e - c * L;
+    double *x = V + (size_t)c * ld + k;
+    if (mode == PANEL_GE) {
+      if (k < coff + c)
+        *x = 0.0;
+      else if (k == coff + c)
+        *x = 1.0;
+    } else if (mode == PANEL_TT) {
+      if (k > roff + coff + c) *x = 0.0;
+    }
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------- task bodies --
+
+// Updates UNMQR / TSMQR / TTMQR of one column slab (also used for Q and Q^T
+// applied to right-hand-side blocks).
+__device__ void task_update(const EngineParams &p, const Task &t, Shared &sh, double *dyn,
+                            uint32_t &phase) {
+  const int nb = p.nb, ib = p.ib, lds = p.lds, cw = t.cw;
+  const int VC = p.vc;
+  const int nchunk = ib / VC;
+  double *C1 = dyn;
+  double *C2 = C1 + (size_t)lds * p.w;
+  double *Vc = C2 + (size_t)lds * p.w;
+  double *Tq = Vc + (size_t)lds * VC;
+  double *W = Tq + (size_t)ib * ib;
+  double *scr = W + (size_t)ib * p.w;
+  const int op = t.op;
+  const bool pair = op != OP_UNMQR;
+  const int mode = op == OP_UNMQR ? PANEL_GE : (op == OP_TSMQR ? PANEL_TS : PANEL_TT);
+  double *g1 = target_ptr(p, t, pair ? t.r : t.i);
+  double *g2 = pair ? target_ptr(p, t, t.i) : nullptr;
+  const double *Vt = tile_ptr(p, t.i, t.k);
+  const double *Tt = t_ptr(p, pair ? 1 : 0, t.i, t.k);
+  {
+    Copy cp[2] = {{C1, lds, g1, nb, nb, cw}, {C2, lds, g2, nb, pair ? nb : 0, cw}};
+    stage(p, sh, cp, 2, phase);
+  }
+  const int nq = nb / ib;
+  for (int qq = 0; qq < nq; ++qq) {
+    const int q = t.trans ? qq : nq - 1 - qq;
+    const int q0 = q * ib;
+    const int vr0 = (mode == PANEL_GE) ? q0 : 0;
+    const int L = (mode == PANEL_GE) ? nb - q0 : (mode == PANEL_TS ? nb : q0 + ib);
+    double *Cb = (mode == PANEL_GE) ? C1 + q0 : C2;
+    double *Ct = C1 + q0;
+    for (int c = 0; c < nchunk; ++c) {
+      __syncthreads();
+      Copy cp[2] = {{Vc, lds, Vt + (size_t)(q0 + c * VC) * nb + vr0, nb, L, VC},
+                    {Tq, ib, Tt + (size_t)q * ib * ib, ib, c == 0 ? ib : 0, ib}};
+      stage(p, sh, cp, 2, phase);
+      shape_v(Vc, lds, L, VC, mode, c * VC, q0);
+      gemm_tn(W + c * VC, ib, Vc, lds, Cb, lds, L, VC, cw, pair ? Ct + c * VC : nullptr, lds, scr);
+    }
+    trmm_tw(W, ib, Tq, ib, cw, t.trans, scr);
+    if (pair) sub_top(Ct, lds, W, ib, ib, cw);
+    for (int c = 0; c < nchunk; ++c) {
+      if (nchunk > 1) {
+        __syncthreads();
+        Copy cp[1] = {{Vc, lds, Vt + (size_t)(q0 + c * VC) * nb + vr0, nb, L, VC}};
+        stage(p, sh, cp, 1, phase);
+        shape_v(Vc, lds, L, VC, mode, c * VC, q0);
+      }
+      gemm_nn_sub(Cb, lds, Vc, lds, W + c * VC, ib, L, VC, cw);
+    }
+  }
+  store_cols(g1, nb, C1, lds, nb, cw, 0, 0);
+  if (pair) store_cols(g2, nb, C2, lds, nb, cw, 0, 0);
+}
+
+// GEQRT (mode GE), TSQRT (TS) and TTQRT (TT) of one tile (pair).
+__device__ void task_panel(const EngineParams &p, const Task &t, Shared &sh, double *dyn,
+                           uint32_t &phase) {
+  const int nb = p.nb, ib = p.ib, lds = p.lds, wt = p.wt;
+  const int ldt = ib + 2;
+  const int mode = t.op == OP_GEQRT ? PANEL_GE : (t.op == OP_TSQRT ? PANEL_TS : PANEL_TT);
+  double *P = dyn;
+  double *Rt = P + (size_t)lds * ib;
+  double *Tq = Rt + (size_t)ldt * ib;
+  double *Ct = Tq + (size_t)ib * ib;
+  double *Cb = Ct + (size_t)ldt * wt;
+  double *G = Cb;  // the Gram matrix is dead before the trailing slabs use Cb
+  double *W = Cb + (size_t)(lds * wt > ib * ib ? lds * wt : ib * ib);
+  double *scr = W + (size_t)ib * wt;
+  double *XR = tile_ptr(p, t.r, t.k);  // GE: the tile itself (r == i)
+  double *XB = tile_ptr(p, t.i, t.k);
+  double *Tg = t_ptr(p, mode == PANEL_GE ? 0 : 1, t.i, t.k);
+  const int nq = nb / ib;
+  for (int q = 0; q < nq; ++q) {
+    const int q0 = q * ib;
+    const int L = (mode == PANEL_GE) ? nb - q0 : (mode == PANEL_TS ? nb : q0 + ib);
+    const int br0 = (mode == PANEL_GE) ? q0 : 0;  // first tile row held in P
+    __syncthreads();
+    {
+      Copy cp[2] = {{P, lds, XB + (size_t)q0 * nb + br0, nb, L, ib},
+                    {Rt, ldt, XR + (size_t)q0 * nb + q0, nb, mode == PANEL_GE ? 0 : ib, ib}};
+      stage(p, sh, cp, 2, phase);
+    }
+    if (mode == PANEL_TT) {  // the strict lower part of R2's tile is GEQRT's V, not data
+      for (int e = threadIdx.x; e < L * ib; e += NT) {
+        const int c = e / L, k = e - c * L;
+        if (k > q0 + c) P[(size_t)c * lds + k] = 0.0;
+      }
+      __syncthreads();
+    }
+    factor_block(mode, P, lds, L, ib, Rt, ldt, q0, sh);
+    // write back the factored block
+    if (mode == PANEL_GE) {
+      store_cols(XB + (size_t)q0 * nb + q0, nb, P, lds, L, ib, 0, 0);
+    } else {
+      store_cols(XR + (size_t)q0 * nb + q0, nb, Rt, ldt, ib, ib, 1, 0);
+      store_cols(XB + (size_t)q0 * nb, nb, P, lds, L, ib, mode == PANEL_TT ? 1 : 0, q0);
+    }
+    __syncthreads();
+    if (mode == PANEL_GE) shape_v(P, lds, L, ib, PANEL_GE, 0, 0);
+    gemm_tn(G, ib, P, lds, P, lds, L, ib, ib, nullptr, 0, scr);
+    build_t(Tq, G, ib, sh);
+    store_cols(Tg + (size_t)q * ib * ib, ib, Tq, ib, ib, ib, 0, 0);
+    // trailing columns of the tile(s): block reflector applied with Q^T
+    for (int c0 = q0 + ib; c0 < nb; c0 += wt) {
+      const int wc = min(wt, nb - c0);
+      __syncthreads();
+      if (mode == PANEL_GE) {
+        Copy cp[1] = {{Cb, lds, XB + (size_t)c0 * nb + q0, nb, L, wc}};
+        stage(p, sh, cp, 1, phase);
+        gemm_tn(W, ib, P, lds, Cb, lds, L, ib, wc, nullptr, 0, scr);
+        trmm_tw(W, ib, Tq, ib, wc, 1, scr);
+        gemm_nn_sub(Cb, lds, P, lds, W, ib, L, ib, wc);
+        store_cols(XB + (size_t)c0 * nb + q0, nb, Cb, lds, L, wc, 0, 0);
+      } else {
+        Copy cp[2] = {{Ct, ldt, XR + (size_t)c0 * nb + q0, nb, ib, wc},
+                      {Cb, lds, XB + (size_t)c0 * nb, nb, L, wc}};
+        stage(p, sh, cp, 2, phase);
+        gemm_tn(W, ib, P, lds, Cb, lds, L, ib, wc, Ct, ldt, scr);
+        trmm_tw(W, ib, Tq, ib, wc, 1, scr);
+        sub_top(Ct, ldt, W, ib, ib, wc);
+        gemm_nn_sub(Cb, lds, P, lds, W, ib, L, ib, wc);
+        store_cols(XR + (size_t)c0 * nb + q0, nb, Ct, ldt, ib, wc, 0, 0);
+        store_cols(XB + (size_t)c0 * nb, nb, Cb, lds, L, wc, 0, 0);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------- scheduler --
+
+__device__ __forceinline__ void push_ready(const EngineParams &p, int task) {
+  const int q = p.tasks[task].prio;
+  const unsigned idx = atomicAdd(&p.ctl->tail[q], 1u);
+  ptx::st_release(&p.slots[(size_t)q * p.ntasks + idx], task + 1);
+}
+
+// Claim the next ready task (thread 0 only). -1: finished or failed.
+__device__ int pop_ready(const EngineParams &p) {
+  const uint64_t t0 = ptx::globaltimer();
+  unsigned sleep_ns = 64;
+  while (true) {
+    if (ptx::ld_relaxed(&p.ctl->status) != 0) return -1;
+    for (int q = 0; q < kNumQueues; ++q) {
+      unsigned h = ptx::ld_relaxed_u32(&p.ctl->head[q]);
+      while (h < ptx::ld_relaxed_u32(&p.ctl->tail[q])) {
+        const unsigned old = atomicCAS(&p.ctl->head[q], h, h + 1);
+        if (old == h) {
+          const int *slot = &p.slots[(size_t)q * p.ntasks + h];
+          int v = ptx::ld_acquire(slot);
+          const uint64_t t1 = ptx::globaltimer();
+          while (v == 0) {
+            if (ptx::globaltimer() - t1 > (uint64_t)p.timeout_ns) {
+              set_error(p, HQR_ERR_TIMEOUT, -1);
+              return -1;
+            }
+            __nanosleep(32);
+            v = ptx::ld_acquire(slot);
+          }
+          __threadfence();
+          return v - 1;
+        }
+        h = old;
+      }
+    }
+    if (ptx::ld_relaxed_u32(&p.ctl->done) >= (unsigned)p.ntasks) return -1;
+    if (ptx::globaltimer() - t0 > (uint64_t)p.timeout_ns) {
+      set_error(p, HQR_ERR_TIMEOUT, -1);
+      return -1;
+    }
+    __nanosleep(sleep_ns);
+    if (sleep_ns < 2048) sleep_ns *= 2;
+  }
+}
+
+__global__ void __launch_bounds__(NT, 2) hqr_sched_fp64(EngineParams p) {
+  extern __shared__ __align__(16) double dyn[];
+  __shared__ Shared sh;
+  if (threadIdx.x == 0) {
+    ptx::mbar_init(&sh.bar, 1);
+    sh.abort = 0;
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  while (true) {
+    if (threadIdx.x == 0) sh.task = pop_ready(p);
+    __syncthreads();
+    const int tid = sh.task;
+    if (tid < 0) break;
+    const Task t = p.tasks[tid];
+    if (t.op == OP_GEQRT || t.op == OP_TSQRT || t.op == OP_TTQRT)
+      task_panel(p, t, sh, dyn, phase);
+    else
+      task_update(p, t, sh, dyn, phase);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      ptx::fence_proxy_async();
+      __threadfence();
+      for (int e = t.succ_begin; e < t.succ_end; ++e) {
+        const int s = p.succ[e];
+        if (atomicSub(&p.indeg[s], 1) == 1) push_ready(p, s);
+      }
+      __threadfence();
+      atomicAdd(&p.ctl->done, 1u);
+    }
+    if (sh.abort) break;
+  }
+  // a bulk copy that outlived its wait must land before the CTA exits
+  if (sh.abort && threadIdx.x == 0) {
+    const uint64_t t0 = ptx::globaltimer();
+    while (!ptx::mbar_try_wait(&sh.bar, phase) && ptx::globaltimer() - t0 < 1000000000ull) {
+    }
+  }
+}
+
+// Shared memory (bytes) of the scheduler kernel for a configuration.
+inline size_t engine_smem_bytes(int nb, int ib, int w, int wt, int vc) {
+  const int lds = nb + 2, ldt = ib + 2;
+  const size_t scr_u = (size_t)(ib * w > NT ? ib * w : NT);
+  const size_t scr_p = (size_t)(ib * wt > NT ? ib * wt : NT);
+  const size_t upd = (size_t)lds * (2 * w + vc) + (size_t)ib * ib + (size_t)ib * w + scr_u;
+  const size_t cbg = (size_t)(lds * wt > ib * ib ? lds * wt : ib * ib);
+  const size_t pan = (size_t)lds * ib + (size_t)ldt * (ib + wt) + (size_t)ib * ib + cbg +
+                     (size_t)ib * wt + scr_p;
+  return 8 * (upd > pan ? upd : pan);
+}
+
+}  // namespace hqr

@@ -1,0 +1,73 @@
+// Internal declarations shared by the host task-graph builder and the CUDA
+// engine. Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/hqr.h"
+
+namespace hqr {
+
+// Tile task opcodes (Alg. 2). The update opcodes also serve Q / Q^T
+// application to a right-hand side (Sec. 5.1).
+enum Op : int8_t {
+  OP_GEQRT = 0,
+  OP_UNMQR = 1,
+  OP_TSQRT = 2,
+  OP_TSMQR = 3,
+  OP_TTQRT = 4,
+  OP_TTMQR = 5,
+};
+
+// Scheduling classes, highest first: panel kernels (on the critical path),
+// updates of the next panel's column (look-ahead), other updates.
+constexpr int kNumQueues = 3;
+
+// One task of the device task graph. For update tasks, columns
+// [c0, c0 + cw) of the target tiles are updated (a column slab).
+struct Task {
+  int8_t op;
+  int8_t prio;
+  int8_t trans;   // apply Q^T (1) or Q (0); factorization tasks use 1
+  int8_t pad;
+  int32_t i;      // killed row (TS/TT), or the row of GEQRT/UNMQR
+  int32_t r;      // killer row (TS/TT); equals i for GEQRT/UNMQR
+  int32_t k;      // panel
+  int32_t j;      // target tile column (updates) or right-hand-side block
+  int32_t c0;     // first column of the slab inside the target tile
+  int32_t cw;     // slab width
+  int32_t succ_begin, succ_end;  // successor range in the CSR array
+};
+static_assert(sizeof(Task) == 36, "Task layout");
+
+// A task graph ready for upload: tasks in a topological order, successor
+// lists (CSR), in-degrees and per-queue initial ready lists.
+struct Graph {
+  std::vector<Task> tasks;
+  std::vector<int32_t> succ;
+  std::vector<int32_t> indeg;
+  int64_t nedges = 0;
+};
+
+// One step of the factorization in execution order, replayed by apply-Q.
+struct PanelOp {
+  int8_t kind;  // 0 geqrt(row i), 1 ts(i, r), 2 tt(i, r)
+  int32_t k, i, r;
+};
+
+// Operation sequence of Alg. 1/Alg. 2 for a validated list, one panel after
+// the other: a GEQRT the first time a row acts as a triangle in a panel, then
+// the TS or TT elimination. A panel without eliminations gets GEQRT(k, k).
+std::vector<PanelOp> expand_ops(const hqr_elim_t *list, size_t count, int m, int n);
+
+// Factorization graph: every op expanded into its panel task and its update
+// tasks over the tile columns j > k, each split into column slabs of width w.
+Graph build_factor_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int w);
+
+// Q^T (trans = 1) or Q (trans = 0) applied to a right-hand side split into
+// row tiles and `nslab` column slabs of width w: the update kernels replayed
+// forward or backwards.
+Graph build_apply_graph(const std::vector<PanelOp> &ops, int m, int nslab, int w, int trans);
+
+}  // namespace hqr

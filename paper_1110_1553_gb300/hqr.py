@@ -1,0 +1,280 @@
+"""Thin Python binding of the C ABI in include/hqr.h (argument marshalling only).
+
+Every computation runs in ``libhqr.so`` (host C++ for the elimination lists,
+sm_103a CUDA kernels for everything numeric). PyTorch supplies device memory
+and streams. There is no fallback: if the library is missing, loading fails
+with an error that says how to build it.
+
+Matrices cross the boundary column-major. A torch tensor of shape (M, N) is
+passed as is when its storage is already column-major (``A.stride(0) == 1``);
+otherwise a column-major copy is made.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+FLAT, BINARY, GREEDY, FIBONACCI = 0, 1, 2, 3
+TREES = {"flat": FLAT, "binary": BINARY, "greedy": GREEDY, "fibonacci": FIBONACCI}
+TS, TT = 0, 1
+FP64 = 0
+
+SUCCESS, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_CAPACITY, ERR_INVALID_LIST, ERR_SINGULAR, ERR_INTERNAL = range(8)
+
+ELIM_DTYPE = np.dtype([("k", np.int32), ("i", np.int32), ("killer", np.int32), ("kind", np.int32),
+                       ("level", np.int32), ("step", np.int32)])
+
+EXPORTS = ["hqr_elim_list", "hqr_validate_list", "hqr_geqrf", "hqr_refactor", "hqr_refactor_async",
+           "hqr_status", "hqr_get_r", "hqr_get_tiles", "hqr_get_t", "hqr_factors_info", "hqr_apply_q",
+           "hqr_gels", "hqr_debug_block_task", "hqr_factors_free", "hqr_set_timeout_ms", "hqr_strerror", "hqr_last_error",
+           "hqr_last_launches"]
+
+
+class HQRError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        text = _lib.hqr_strerror(status).decode() if _lib is not None else str(status)
+        if status == ERR_CUDA and _lib is not None:
+            text += ": " + _lib.hqr_last_error().decode()
+        super().__init__("%s failed with status %d (%s)" % (where, status, text))
+
+
+_lib = None
+
+
+def library_path():
+    return _build.OUT
+
+
+def load(build_if_missing=False):
+    """Load libhqr.so (building it first when asked). Raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise ImportError("libhqr.so is not built; run __graft_entry__.build() or "
+                              "python -m paper_1110_1553_gb300._build")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+    pf = ctypes.POINTER(vp)
+    lib.hqr_elim_list.argtypes = [i32, i32, i32, i32, i32, i32, vp, sz, ctypes.POINTER(sz)]
+    lib.hqr_validate_list.argtypes = [i32, i32, vp, sz]
+    lib.hqr_geqrf.argtypes = [vp, i32, i32, i32, i32, i32, i32, vp, sz, pf, vp]
+    lib.hqr_refactor.argtypes = [vp, vp, i32, vp]
+    lib.hqr_refactor_async.argtypes = [vp, vp, i32, vp]
+    lib.hqr_status.argtypes = [vp, vp]
+    lib.hqr_get_r.argtypes = [vp, vp, i32, vp]
+    lib.hqr_get_tiles.argtypes = [vp, vp, i32, vp]
+    lib.hqr_get_t.argtypes = [vp, vp, vp]
+    ip = ctypes.POINTER(i32)
+    lib.hqr_factors_info.argtypes = [vp, ip, ip, ip, ip, ip, ip, ctypes.POINTER(i64)]
+    lib.hqr_apply_q.argtypes = [vp, i32, vp, i32, i32, vp]
+    lib.hqr_gels.argtypes = [vp, i32, i32, i32, vp, i32, i32, vp, i32, i32, i32, i32, vp, sz, vp]
+    lib.hqr_debug_block_task.argtypes = [vp, i64, i32]
+    lib.hqr_factors_free.argtypes = [vp]
+    lib.hqr_factors_free.restype = None
+    lib.hqr_set_timeout_ms.argtypes = [i64]
+    lib.hqr_set_timeout_ms.restype = None
+    lib.hqr_strerror.argtypes = [i32]
+    lib.hqr_strerror.restype = ctypes.c_char_p
+    lib.hqr_last_error.restype = ctypes.c_char_p
+    lib.hqr_last_launches.restype = i64
+    _lib = lib
+    return lib
+
+
+def _check(status, where):
+    if status != 0:
+        raise HQRError(status, where)
+
+
+# ----------------------------------------------------------- host only --
+
+def elim_list(m, n, a, p, low, high):
+    """HQR elimination list as a structured numpy array (fields k, i,
+    killer, kind, level, step), sorted by (k, step, i)."""
+    lib = load()
+    low = TREES.get(low, low)
+    high = TREES.get(high, high)
+    cnt = ctypes.c_size_t(0)
+    st = lib.hqr_elim_list(m, n, a, p, low, high, None, 0, ctypes.byref(cnt))
+    if st not in (0, ERR_CAPACITY):
+        _check(st, "hqr_elim_list")
+    out = np.zeros(cnt.value, dtype=ELIM_DTYPE)
+    st = lib.hqr_elim_list(m, n, a, p, low, high, out.ctypes.data if cnt.value else None, cnt.value,
+                           ctypes.byref(cnt))
+    _check(st, "hqr_elim_list")
+    return out
+
+
+def as_records(lst):
+    """Structured elimination array -> list of (k, i, killer, kind, level, step)."""
+    return [tuple(int(x) for x in r) for r in lst]
+
+
+def to_array(records):
+    return np.array([tuple(r) for r in records], dtype=ELIM_DTYPE)
+
+
+def validate_list(m, n, records):
+    """Status of hqr_validate_list (0 = valid)."""
+    lib = load()
+    arr = records if isinstance(records, np.ndarray) else to_array(records)
+    arr = np.ascontiguousarray(arr, dtype=ELIM_DTYPE)
+    return lib.hqr_validate_list(m, n, arr.ctypes.data if len(arr) else None, len(arr))
+
+
+def set_timeout_ms(ms):
+    load().hqr_set_timeout_ms(int(ms))
+
+
+def last_launches():
+    return int(load().hqr_last_launches())
+
+
+# -------------------------------------------------------------- device --
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def colmajor(A):
+    """A column-major view or copy of a 2-D (or 1-D) float64 CUDA tensor.
+    Returns (tensor, ld)."""
+    torch = _torch()
+    if A.dim() == 1:
+        A = A.reshape(-1, 1)
+    if not A.is_cuda or A.dtype != torch.float64:
+        raise TypeError("expected a float64 CUDA tensor")
+    M = A.shape[0]
+    if A.stride(0) == 1 and (A.shape[1] == 1 or A.stride(1) >= max(M, 1)):
+        return A, max(A.stride(1) if A.shape[1] > 1 else M, 1)
+    C = A.t().contiguous().t()
+    return C, M
+
+
+def empty_colmajor(M, N, device="cuda"):
+    torch = _torch()
+    return torch.empty((N, M), dtype=torch.float64, device=device).t()
+
+
+class Factors:
+    """A factorization A = Q R made by ``geqrf`` (owns the library object)."""
+
+    def __init__(self, handle, M, N):
+        self._h = handle
+        self.M, self.N = M, N
+        lib = load()
+        vals = [ctypes.c_int(0) for _ in range(6)]
+        nt = ctypes.c_int64(0)
+        _check(lib.hqr_factors_info(self._h, *[ctypes.byref(v) for v in vals], ctypes.byref(nt)),
+               "hqr_factors_info")
+        self.Mp, self.Np, self.m, self.n, self.nb, self.ib = [v.value for v in vals]
+        self.ntasks = nt.value
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.hqr_factors_free(self._h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def refactor(self, A, stream=None):
+        A, lda = colmajor(A)
+        _check(load().hqr_refactor(self._h, ctypes.c_void_p(A.data_ptr()), lda, _stream_ptr(stream)),
+               "hqr_refactor")
+
+    def refactor_async(self, A, stream=None):
+        A, lda = colmajor(A)
+        _check(load().hqr_refactor_async(self._h, ctypes.c_void_p(A.data_ptr()), lda, _stream_ptr(stream)),
+               "hqr_refactor_async")
+
+    def debug_block_task(self, task, extra):
+        _check(load().hqr_debug_block_task(self._h, int(task), int(extra)), "hqr_debug_block_task")
+
+    def status(self, stream=None):
+        return load().hqr_status(self._h, _stream_ptr(stream))
+
+    def R(self, stream=None):
+        R = empty_colmajor(self.N, self.N)
+        _check(load().hqr_get_r(self._h, ctypes.c_void_p(R.data_ptr()), self.N, _stream_ptr(stream)),
+               "hqr_get_r")
+        return R
+
+    def tiles(self, stream=None):
+        X = empty_colmajor(self.Mp, self.Np)
+        _check(load().hqr_get_tiles(self._h, ctypes.c_void_p(X.data_ptr()), self.Mp, _stream_ptr(stream)),
+               "hqr_get_tiles")
+        return X
+
+    def T(self, stream=None):
+        """All T factors, shape (n, m, 2, nb, ib): [k, i, which] is the
+        ib x nb column-major array of tile (i, k) (which 0: GEQRT, 1: kill)."""
+        torch = _torch()
+        T = torch.empty((self.n, self.m, 2, self.nb, self.ib), dtype=torch.float64, device="cuda")
+        _check(load().hqr_get_t(self._h, ctypes.c_void_p(T.data_ptr()), _stream_ptr(stream)), "hqr_get_t")
+        return T
+
+    def apply_q(self, B, trans, stream=None):
+        """B <- Q^T B (trans=True) or Q B, in place when B is column-major;
+        returns the result."""
+        Bc, ldb = colmajor(B)
+        nrhs = Bc.shape[1] if Bc.dim() == 2 else 1
+        _check(load().hqr_apply_q(self._h, 1 if trans else 0, ctypes.c_void_p(Bc.data_ptr()), ldb, nrhs,
+                                  _stream_ptr(stream)), "hqr_apply_q")
+        if Bc.data_ptr() != B.data_ptr():
+            B.copy_(Bc.reshape(B.shape))
+        return B
+
+
+def _list_arg(records):
+    if records is None:
+        return None, 0, None
+    arr = records if isinstance(records, np.ndarray) else to_array(records)
+    arr = np.ascontiguousarray(arr, dtype=ELIM_DTYPE)
+    return ctypes.c_void_p(arr.ctypes.data), len(arr), arr
+
+
+def geqrf(A, nb, ib, records=None, stream=None):
+    """Tile QR of a float64 CUDA matrix with the given elimination list
+    (None = library default). Returns a Factors object."""
+    A, lda = colmajor(A)
+    M, N = A.shape
+    ptr, cnt, keep = _list_arg(records)
+    h = ctypes.c_void_p(0)
+    st = load().hqr_geqrf(ctypes.c_void_p(A.data_ptr()), M, N, lda, FP64, nb, ib, ptr, cnt, ctypes.byref(h),
+                          _stream_ptr(stream))
+    del keep
+    _check(st, "hqr_geqrf")
+    return Factors(h, M, N)
+
+
+def gels(A, b, nb, ib, records=None, stream=None):
+    """Least-squares solution x of min ||b - A x|| (b: M or M x nrhs)."""
+    A, lda = colmajor(A)
+    M, N = A.shape
+    vec = b.dim() == 1
+    bc, ldb = colmajor(b)
+    nrhs = bc.shape[1]
+    x = empty_colmajor(N, nrhs)
+    ptr, cnt, keep = _list_arg(records)
+    st = load().hqr_gels(ctypes.c_void_p(A.data_ptr()), M, N, lda, ctypes.c_void_p(bc.data_ptr()), ldb, nrhs,
+                         ctypes.c_void_p(x.data_ptr()), N, FP64, nb, ib, ptr, cnt, _stream_ptr(stream))
+    del keep
+    _check(st, "hqr_gels")
+    return x[:, 0] if vec else x
