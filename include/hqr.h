@@ -168,6 +168,11 @@ int hqr_get_tiles(const hqr_factors *F, void *dOut, int ld, void *stream);
  */
 int hqr_get_t(const hqr_factors *F, void *dT, void *stream);
 
+/* hqr_kernel_ms -- device time (CUDA events on the call's stream) of the
+ * persistent task kernel of the last factorization or apply-Q run on F.
+ * Waits for that kernel to finish. */
+int hqr_kernel_ms(hqr_factors *F, float *ms);
+
 /* hqr_factors_info -- sizes of a factorization: padded rows/cols, tiles,
  * tile size, inner block, number of tasks in the factorization graph. */
 int hqr_factors_info(const hqr_factors *F, int *Mp, int *Np, int *m, int *n,

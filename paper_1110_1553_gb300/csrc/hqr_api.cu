@@ -197,6 +197,8 @@ struct hqr_factors {
   DevGraph fg;
   std::map<std::pair<int, int>, DevGraph> ag;  // (trans, nslab) -> apply graph
   Ctl *last_ctl = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool timed = false;
   int64_t debug_task = -1;
   int debug_base = -1;
 };
@@ -253,8 +255,15 @@ int run_graph(hqr_factors *F, DevGraph &g, double *C, long long cstride, int w, 
   CK(cudaMemcpyAsync(g.slots, g.slots0, sizeof(int) * (size_t)kNumQueues * g.ntasks,
                      cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(g.ctl, g.ctl0, sizeof(Ctl), cudaMemcpyDeviceToDevice, s));
+  if (!F->ev0) {
+    CK(cudaEventCreate(&F->ev0));
+    CK(cudaEventCreate(&F->ev1));
+  }
+  CK(cudaEventRecord(F->ev0, s));
   hqr_sched_fp64<<<grid, NT, smem, s>>>(p);
   CK(cudaGetLastError());
+  CK(cudaEventRecord(F->ev1, s));
+  F->timed = true;
   g_launches += 1;
   F->last_ctl = g.ctl;
   F->grid = grid;
@@ -418,6 +427,15 @@ int hqr_get_t(const hqr_factors *F, void *dT, void *stream) {
   return HQR_SUCCESS;
 }
 
+int hqr_kernel_ms(hqr_factors *F, float *ms) {
+  if (!F) return -1;
+  if (!ms) return -2;
+  if (!F->timed) return HQR_ERR_INTERNAL;
+  CK(cudaEventSynchronize(F->ev1));
+  CK(cudaEventElapsedTime(ms, F->ev0, F->ev1));
+  return HQR_SUCCESS;
+}
+
 int hqr_factors_info(const hqr_factors *F, int *Mp, int *Np, int *m, int *n, int *nb, int *ib,
                      int64_t *ntasks) {
   if (!F) return -1;
@@ -566,6 +584,8 @@ void hqr_factors_free(hqr_factors *F) {
   cudaFree(F->dA);
   cudaFree(F->dT);
   cudaFree(F->dBw);
+  if (F->ev0) cudaEventDestroy(F->ev0);
+  if (F->ev1) cudaEventDestroy(F->ev1);
   delete F;
 }
 

@@ -27,7 +27,7 @@ ELIM_DTYPE = np.dtype([("k", np.int32), ("i", np.int32), ("killer", np.int32), (
                        ("level", np.int32), ("step", np.int32)])
 
 EXPORTS = ["hqr_elim_list", "hqr_validate_list", "hqr_geqrf", "hqr_refactor", "hqr_refactor_async",
-           "hqr_status", "hqr_get_r", "hqr_get_tiles", "hqr_get_t", "hqr_factors_info", "hqr_apply_q",
+           "hqr_status", "hqr_get_r", "hqr_get_tiles", "hqr_get_t", "hqr_factors_info", "hqr_kernel_ms", "hqr_apply_q",
            "hqr_gels", "hqr_debug_block_task", "hqr_factors_free", "hqr_set_timeout_ms", "hqr_strerror", "hqr_last_error",
            "hqr_last_launches"]
 
@@ -74,6 +74,7 @@ def load(build_if_missing=False):
     lib.hqr_get_t.argtypes = [vp, vp, vp]
     ip = ctypes.POINTER(i32)
     lib.hqr_factors_info.argtypes = [vp, ip, ip, ip, ip, ip, ip, ctypes.POINTER(i64)]
+    lib.hqr_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     lib.hqr_apply_q.argtypes = [vp, i32, vp, i32, i32, vp]
     lib.hqr_gels.argtypes = [vp, i32, i32, i32, vp, i32, i32, vp, i32, i32, i32, i32, vp, sz, vp]
     lib.hqr_debug_block_task.argtypes = [vp, i64, i32]
@@ -206,6 +207,12 @@ class Factors:
 
     def debug_block_task(self, task, extra):
         _check(load().hqr_debug_block_task(self._h, int(task), int(extra)), "hqr_debug_block_task")
+
+    def kernel_ms(self):
+        """Device time of the last persistent task-kernel run (CUDA events)."""
+        ms = ctypes.c_float(0)
+        _check(load().hqr_kernel_ms(self._h, ctypes.byref(ms)), "hqr_kernel_ms")
+        return ms.value
 
     def status(self, stream=None):
         return load().hqr_status(self._h, _stream_ptr(stream))
