@@ -185,6 +185,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rows", type=int, default=WORKLOAD["M"],
+                    help="rows M of the tall-skinny matrix (default: the full workload; smaller values "
+                         "only for profiling captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -207,7 +210,7 @@ def main():
         _build.build()
     barrier()
     hqr.load()
-    wl = WORKLOAD
+    wl = dict(WORKLOAD, M=args.rows)
     M, N, nb, ib = wl["M"], wl["N"], wl["nb"], wl["ib"]
     recs = hqr.elim_list(M // nb, N // nb, wl["a"], wl["p"], wl["low"], wl["high"])
     A = inputs.gaussian_torch(M, N, seed=1 + rank, device=dev)  # column-major, 2.1 GB
@@ -291,7 +294,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, **wl, "tasks": F.ntasks,
+        "config": {"workload": WORKLOAD_NAME if M == WORKLOAD["M"] else "profiling_%dx%d" % (M, N),
+                   **wl, "tasks": F.ntasks,
                    "l2": "inputs larger than L2 (A is %.2f GB)" % (M * N * 8 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": M * N * 8,
