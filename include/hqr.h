@@ -70,7 +70,8 @@ enum {
   HQR_ERR_CAPACITY = 4,  /* output array too small; *count holds the size needed */
   HQR_ERR_INVALID_LIST = 5, /* elimination list breaks a rule of Sec. 2 */
   HQR_ERR_SINGULAR = 6,  /* exact zero on the diagonal of R (hqr_gels) */
-  HQR_ERR_INTERNAL = 7   /* internal consistency check failed */
+  HQR_ERR_INTERNAL = 7,  /* internal consistency check failed */
+  HQR_ERR_TOO_LARGE = 8  /* problem exceeds the fixed limits of hqr_geqrf_r_noalloc */
 };
 
 /* Opaque factorization: owns the tile workspace (V and R), the T factors,
@@ -207,6 +208,34 @@ int hqr_gels(const void *dA, int M, int N, int lda, const void *db, int ldb, int
  * (after hqr_set_timeout_ms) instead of hanging. extra = 0 restores it.
  */
 int hqr_debug_block_task(hqr_factors *F, int64_t task, int extra);
+
+/*
+ * hqr_geqrf_r_noalloc -- the R factor of A with no memory allocation at all.
+ * The paper has no counterpart: this is an operational variant of hqr_geqrf
+ * for callers that may not allocate device memory (the device memory belongs
+ * to another allocator's pool, or cudaMalloc's implicit synchronization is
+ * not acceptable at that point) or may not grow the host heap.
+ *   dA, M, N, lda  device input, as in hqr_geqrf (read only).
+ *   nb, ib         as in hqr_geqrf, with nb <= 64.
+ *   list, count    elimination list for ceil(M/nb) x ceil(N/nb) tiles
+ *                  (required; e.g. from hqr_elim_list called beforehand).
+ *   dR, ldr        device output: the N x N upper triangular R (strict
+ *                  lower part set to zero), ldr >= N.
+ * Limits: at most 64 x 16 tile rows x columns and 256 tiles, at most 16384
+ * tasks, and everything (tiles, T factors, task graph) within one 16 MiB
+ * scratch array that is a static device variable of the library: it is
+ * reserved on every GPU that loads the library until the process exits.
+ * Larger problems return HQR_ERR_TOO_LARGE before any device work.
+ * No cudaMalloc, cudaFree or other allocating call is made. The first call
+ * on each device looks up that device's scratch address (a one-time set-up);
+ * make that first call before any stream capture. All calls share the one
+ * scratch array and the library's static host staging, so calls that
+ * overlap (on the GPU, or from several host threads) race; the array keeps
+ * the last call's contents and every call rewrites all it reads. The call
+ * synchronizes `stream` and returns the device status.
+ */
+int hqr_geqrf_r_noalloc(const void *dA, int M, int N, int lda, int nb, int ib,
+                        const hqr_elim_t *list, size_t count, void *dR, int ldr, void *stream);
 
 /* hqr_factors_free -- release a factorization (NULL is allowed). */
 void hqr_factors_free(hqr_factors *F);

@@ -308,6 +308,7 @@ const char *hqr_strerror(int status) {
     case HQR_ERR_INVALID_LIST: return "invalid elimination list";
     case HQR_ERR_SINGULAR: return "R has an exact zero on its diagonal";
     case HQR_ERR_INTERNAL: return "internal error";
+    case HQR_ERR_TOO_LARGE: return "problem exceeds the limits of the allocation-free entry point";
     default: return status < 0 ? "invalid argument" : "unknown status";
   }
 }
@@ -590,3 +591,341 @@ void hqr_factors_free(hqr_factors *F) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free factorization (hqr_geqrf_r_noalloc).
+//
+// Some callers cannot allocate: code running where the device memory is
+// owned by someone else's pool (a framework's caching allocator, a
+// pre-reserved arena in a latency-critical service), where cudaMalloc would
+// synchronize the device at the wrong moment, or where the process must not
+// grow its heap after start-up. This entry point factors small problems
+// using only the caller's buffers plus one fixed scratch array below, which
+// is part of the library image: every GPU that loads the library holds it
+// until the process exits. The task graph is built in static host storage,
+// so the call does not allocate on the host either.
+namespace {
+
+constexpr size_t kNaScratchBytes = (size_t)16 << 20;  // 16 MiB device scratch
+constexpr int kNaMaxM = 64, kNaMaxN = 16, kNaMaxTiles = 256;
+constexpr int kNaMaxSlabs = 4;  // nb <= 64 with 16-column slabs
+constexpr int kNaMaxTasks = 16384, kNaMaxEdges = 131072, kNaMaxReaders = 64;
+constexpr int kNaMaxRes = kNaMaxTiles * (kNaMaxSlabs + 2);
+constexpr int kNaMaxOps = 2 * kNaMaxTiles + kNaMaxN;
+constexpr int kNaMaxDevices = 64;
+
+// The device scratch. Host code must not pass `g_na_scratch` to a kernel
+// (in host code it names a host-side stand-in); it uses the device address
+// obtained with cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_na_scratch[kNaScratchBytes];
+
+struct NaHost {
+  Task tasks[kNaMaxTasks];
+  int indeg[kNaMaxTasks];
+  int slots[kNumQueues * kNaMaxTasks];
+  int succ[kNaMaxEdges];
+  int efrom[kNaMaxEdges], eto[kNaMaxEdges];
+  int cnt[kNaMaxTasks + 1];
+  int writer[kNaMaxRes];
+  int nread[kNaMaxRes];
+  int readers[kNaMaxRes][kNaMaxReaders];
+  int deps[4 * kNaMaxReaders * (kNaMaxSlabs + 4)];
+  long long pos[kNaMaxTiles];
+  int state[kNaMaxM], tri[kNaMaxM];
+  PanelOp ops[kNaMaxOps];
+  Ctl ctl;
+  int ntasks, nedges, ndeps, overflow;
+  size_t pend_w[2 * kNaMaxSlabs + 8], pend_r[8];
+  int npw, npr;
+};
+static NaHost g_na;
+static void *g_na_dev_ptr[kNaMaxDevices];
+static bool g_na_ready[kNaMaxDevices];
+
+constexpr int kNaMaxDeps = (int)(sizeof(NaHost::deps) / sizeof(int));
+constexpr int kNaMaxPendW = (int)(sizeof(NaHost::pend_w) / sizeof(size_t));
+constexpr int kNaMaxPendR = (int)(sizeof(NaHost::pend_r) / sizeof(size_t));
+
+void na_read(size_t res) {
+  if (g_na.ndeps + 1 > kNaMaxDeps || g_na.npr >= kNaMaxPendR) {
+    g_na.overflow = 1;
+    return;
+  }
+  if (g_na.writer[res] >= 0) g_na.deps[g_na.ndeps++] = g_na.writer[res];
+  g_na.pend_r[g_na.npr++] = res;
+}
+void na_write(size_t res) {
+  if (g_na.ndeps + 1 + g_na.nread[res] > kNaMaxDeps || g_na.npw >= kNaMaxPendW) {
+    g_na.overflow = 1;
+    return;
+  }
+  if (g_na.writer[res] >= 0) g_na.deps[g_na.ndeps++] = g_na.writer[res];
+  for (int q = 0; q < g_na.nread[res]; ++q) g_na.deps[g_na.ndeps++] = g_na.readers[res][q];
+  g_na.pend_w[g_na.npw++] = res;
+}
+void na_add(const Task &t) {
+  if (g_na.overflow) return;
+  if (g_na.ntasks >= kNaMaxTasks) {
+    g_na.overflow = 1;
+    return;
+  }
+  const int id = g_na.ntasks++;
+  std::sort(g_na.deps, g_na.deps + g_na.ndeps);
+  const int nd = (int)(std::unique(g_na.deps, g_na.deps + g_na.ndeps) - g_na.deps);
+  if (g_na.nedges + nd > kNaMaxEdges) {
+    g_na.overflow = 1;
+    return;
+  }
+  for (int q = 0; q < nd; ++q) {
+    g_na.efrom[g_na.nedges] = g_na.deps[q];
+    g_na.eto[g_na.nedges++] = id;
+  }
+  g_na.indeg[id] = nd;
+  g_na.tasks[id] = t;
+  for (int q = 0; q < g_na.npw; ++q) {
+    g_na.writer[g_na.pend_w[q]] = id;
+    g_na.nread[g_na.pend_w[q]] = 0;
+  }
+  for (int q = 0; q < g_na.npr; ++q) {
+    const size_t res = g_na.pend_r[q];
+    if (g_na.nread[res] >= kNaMaxReaders) {
+      g_na.overflow = 1;
+      return;
+    }
+    g_na.readers[res][g_na.nread[res]++] = id;
+  }
+  g_na.ndeps = g_na.npw = g_na.npr = 0;
+}
+Task na_task(int op, int prio, int i, int r, int k, int j, int c0, int cw) {
+  Task t;
+  t.op = (int8_t)op;
+  t.prio = (int8_t)prio;
+  t.trans = 1;
+  t.pad = 0;
+  t.i = i;
+  t.r = r;
+  t.k = k;
+  t.j = j;
+  t.c0 = c0;
+  t.cw = cw;
+  t.succ_begin = t.succ_end = 0;
+  return t;
+}
+
+// Validity rules of Sec. 2 (as hqr_validate_list), in static storage.
+bool na_list_valid(int m, int n, const hqr_elim_t *list, size_t count) {
+  const int K = std::min(m, n);
+  for (int e = 0; e < m * K; ++e) g_na.pos[e] = -1;
+  for (size_t q = 0; q < count; ++q) {
+    const hqr_elim_t &r = list[q];
+    if (r.k < 0 || r.k >= K || r.i <= r.k || r.i >= m || r.killer < r.k || r.killer >= m || r.killer == r.i)
+      return false;
+    if (r.kind != HQR_KIND_TS && r.kind != HQR_KIND_TT) return false;
+    long long &p = g_na.pos[(size_t)r.k * m + r.i];
+    if (p >= 0) return false;
+    p = (long long)q;
+  }
+  for (int k = 0; k < K; ++k)
+    for (int i = k + 1; i < m; ++i)
+      if (g_na.pos[(size_t)k * m + i] < 0) return false;
+  for (size_t q = 0; q < count; ++q) {
+    const hqr_elim_t &r = list[q];
+    for (int kp = 0; kp < r.k; ++kp) {
+      if (r.i > kp && g_na.pos[(size_t)kp * m + r.i] > (long long)q) return false;
+      if (r.killer > kp && g_na.pos[(size_t)kp * m + r.killer] > (long long)q) return false;
+    }
+    if (r.killer > r.k && g_na.pos[(size_t)r.k * m + r.killer] < (long long)q) return false;
+  }
+  for (int k = 0; k < K; ++k) {
+    for (int i = 0; i < m; ++i) g_na.state[i] = 0;
+    for (size_t q = 0; q < count; ++q) {
+      const hqr_elim_t &r = list[q];
+      if (r.k != k) continue;
+      if (g_na.state[r.killer] == 2) return false;
+      if (r.kind == HQR_KIND_TS && g_na.state[r.i] != 0) return false;
+      g_na.state[r.killer] = 1;
+      g_na.state[r.i] = 2;
+    }
+  }
+  return true;
+}
+
+size_t na_align(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int hqr_geqrf_r_noalloc(const void *dA, int M, int N, int lda, int nb, int ib,
+                                   const hqr_elim_t *list, size_t count, void *dR, int ldr, void *stream) {
+  if (!dA) return -1;
+  if (M < 1) return -2;
+  if (N < 1 || N > M) return -3;
+  if (lda < M) return -4;
+  if (nb < 8 || nb % 8) return -5;
+  if (ib < 2 || ib % 2 || nb % ib || (ib > 16 && ib != 32)) return -6;
+  if (!list) return -7;
+  if (!dR) return -9;
+  if (ldr < N) return -10;
+  if (nb > 64) return HQR_ERR_TOO_LARGE;
+  const int m = (M + nb - 1) / nb, n = (N + nb - 1) / nb;
+  if (m > kNaMaxM || n > kNaMaxN || m * n > kNaMaxTiles) return HQR_ERR_TOO_LARGE;
+  if (!na_list_valid(m, n, list, count)) return -7;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HQR_ERR_CUDA;
+  if (dev < 0 || dev >= kNaMaxDevices) return HQR_ERR_TOO_LARGE;
+  if (!g_na_ready[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) return HQR_ERR_CUDA;
+    g_na_dev_ptr[dev] = p;
+    g_na_ready[dev] = true;
+  }
+  const int w = std::min(16, nb), wt = std::min(16, nb), vc = std::min(ib, 16);
+  const int S = (nb + w - 1) / w;
+  // operation sequence of Alg. 1 / Alg. 2 (as expand_ops)
+  int nops = 0;
+  for (int i = 0; i < m; ++i) g_na.tri[i] = -1;
+  const int K = std::min(m, n);
+  for (int k = 0; k < K; ++k) {
+    bool any = false;
+    for (size_t q = 0; q < count; ++q) {
+      const hqr_elim_t &e = list[q];
+      if (e.k != k) continue;
+      any = true;
+      if (g_na.tri[e.killer] != k) {
+        g_na.ops[nops++] = {0, k, e.killer, e.killer};
+        g_na.tri[e.killer] = k;
+      }
+      if (e.kind == HQR_KIND_TT && g_na.tri[e.i] != k) {
+        g_na.ops[nops++] = {0, k, e.i, e.i};
+        g_na.tri[e.i] = k;
+      }
+      g_na.ops[nops++] = {(int8_t)(e.kind == HQR_KIND_TS ? 1 : 2), k, e.i, e.killer};
+    }
+    if (!any) g_na.ops[nops++] = {0, k, k, k};
+  }
+  // task graph (same storage pieces and edges as build_factor_graph)
+  const size_t per_tile = (size_t)S + 2;
+  const size_t nres = (size_t)m * n * per_tile;
+  for (size_t r = 0; r < nres; ++r) {
+    g_na.writer[r] = -1;
+    g_na.nread[r] = 0;
+  }
+  g_na.ntasks = g_na.nedges = g_na.ndeps = g_na.npw = g_na.npr = g_na.overflow = 0;
+  auto slab = [&](int i, int j, int sl) { return ((size_t)j * m + i) * per_tile + (size_t)sl; };
+  auto up = [&](int i, int j) { return ((size_t)j * m + i) * per_tile + (size_t)S; };
+  auto lo = [&](int i, int j) { return ((size_t)j * m + i) * per_tile + (size_t)S + 1; };
+  for (int q = 0; q < nops && !g_na.overflow; ++q) {
+    const PanelOp &o = g_na.ops[q];
+    const int k = o.k;
+    const int pop = o.kind == 0 ? OP_GEQRT : (o.kind == 1 ? OP_TSQRT : OP_TTQRT);
+    const int uop = o.kind == 0 ? OP_UNMQR : (o.kind == 1 ? OP_TSMQR : OP_TTMQR);
+    if (o.kind == 0) {
+      for (int sl = 0; sl < S; ++sl) na_write(slab(o.i, k, sl));
+      na_write(up(o.i, k));
+      na_write(lo(o.i, k));
+    } else if (o.kind == 1) {
+      na_write(up(o.r, k));
+      for (int sl = 0; sl < S; ++sl) na_write(slab(o.i, k, sl));
+      na_write(up(o.i, k));
+      na_write(lo(o.i, k));
+    } else {
+      na_write(up(o.r, k));
+      na_write(up(o.i, k));
+    }
+    na_add(na_task(pop, 0, o.i, o.kind == 0 ? o.i : o.r, k, k, 0, nb));
+    for (int j = k + 1; j < n; ++j)
+      for (int sl = 0; sl < S; ++sl) {
+        if (o.kind == 0) {
+          na_read(lo(o.i, k));
+          na_write(slab(o.i, j, sl));
+        } else {
+          na_read(up(o.i, k));
+          if (o.kind == 1) na_read(lo(o.i, k));
+          na_write(slab(o.r, j, sl));
+          na_write(slab(o.i, j, sl));
+        }
+        na_add(na_task(uop, j == k + 1 ? 1 : 2, o.i, o.kind == 0 ? o.i : o.r, k, j, sl * w,
+                       std::min(w, nb - sl * w)));
+      }
+  }
+  if (g_na.overflow) return HQR_ERR_TOO_LARGE;
+  const int nt = g_na.ntasks;
+  for (int t = 0; t <= nt; ++t) g_na.cnt[t] = 0;
+  for (int e = 0; e < g_na.nedges; ++e) g_na.cnt[g_na.efrom[e] + 1]++;
+  for (int t = 0; t < nt; ++t) g_na.cnt[t + 1] += g_na.cnt[t];
+  for (int t = 0; t < nt; ++t) {
+    g_na.tasks[t].succ_begin = g_na.cnt[t];
+    g_na.tasks[t].succ_end = g_na.cnt[t + 1];
+  }
+  for (int e = 0; e < g_na.nedges; ++e) g_na.succ[g_na.cnt[g_na.efrom[e]]++] = g_na.eto[e];
+  std::memset(&g_na.ctl, 0, sizeof(Ctl));
+  for (int q = 0; q < kNumQueues * nt; ++q) g_na.slots[q] = 0;
+  for (int t = 0; t < nt; ++t)
+    if (g_na.indeg[t] == 0) {
+      const int q = g_na.tasks[t].prio;
+      g_na.slots[(size_t)q * nt + g_na.ctl.tail[q]++] = t + 1;
+    }
+  // scratch layout
+  const size_t a_bytes = na_align(sizeof(double) * (size_t)m * nb * n * nb);
+  const size_t t_bytes = na_align(sizeof(double) * (size_t)m * n * 2 * ib * nb);
+  const size_t k_bytes = na_align(sizeof(Task) * nt);
+  const size_t s_bytes = na_align(sizeof(int) * std::max(g_na.nedges, 1));
+  const size_t d_bytes = na_align(sizeof(int) * nt);
+  const size_t q_bytes = na_align(sizeof(int) * kNumQueues * nt);
+  const size_t c_bytes = na_align(sizeof(Ctl));
+  if (a_bytes + t_bytes + k_bytes + s_bytes + d_bytes + q_bytes + c_bytes > kNaScratchBytes)
+    return HQR_ERR_TOO_LARGE;
+  unsigned char *base = (unsigned char *)g_na_dev_ptr[dev];
+  double *dws = (double *)base;
+  double *dT = (double *)(base + a_bytes);
+  Task *dtasks = (Task *)(base + a_bytes + t_bytes);
+  int *dsucc = (int *)(base + a_bytes + t_bytes + k_bytes);
+  int *dindeg = (int *)(base + a_bytes + t_bytes + k_bytes + s_bytes);
+  int *dslots = (int *)(base + a_bytes + t_bytes + k_bytes + s_bytes + d_bytes);
+  Ctl *dctl = (Ctl *)(base + a_bytes + t_bytes + k_bytes + s_bytes + d_bytes + q_bytes);
+  if (cudaMemcpyAsync(dtasks, g_na.tasks, sizeof(Task) * nt, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      (g_na.nedges > 0 &&
+       cudaMemcpyAsync(dsucc, g_na.succ, sizeof(int) * g_na.nedges, cudaMemcpyHostToDevice, s) != cudaSuccess) ||
+      cudaMemcpyAsync(dindeg, g_na.indeg, sizeof(int) * nt, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(dslots, g_na.slots, sizeof(int) * kNumQueues * nt, cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(dctl, &g_na.ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return HQR_ERR_CUDA;
+  const long long total = (long long)m * nb * n * nb;
+  pack_tiles<<<grid_for((int)total), 256, 0, s>>>((const double *)dA, lda, M, N, dws, m, nb, total);
+  EngineParams p;
+  p.A = dws;
+  p.T = dT;
+  p.C = dws;
+  p.cstride = (long long)nb * nb;
+  p.m = m;
+  p.n = n;
+  p.nb = nb;
+  p.ib = ib;
+  p.w = w;
+  p.wt = wt;
+  p.vc = vc;
+  p.lds = nb + 2;
+  p.tasks = dtasks;
+  p.ntasks = nt;
+  p.succ = dsucc;
+  p.indeg = dindeg;
+  p.slots = dslots;
+  p.ctl = dctl;
+  p.timeout_ns = g_timeout_ns;
+  const size_t smem = engine_smem_bytes(nb, ib, w, wt, vc);
+  int sms = 0, per_sm = 0;
+  if (cudaFuncSetAttribute(hqr_sched_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hqr_sched_fp64, NT, smem) != cudaSuccess ||
+      per_sm < 1)
+    return HQR_ERR_CUDA;
+  hqr_sched_fp64<<<std::max(1, std::min(sms * per_sm, nt)), NT, smem, s>>>(p);
+  unpack_tiles<<<grid_for(N * N), 256, 0, s>>>(dws, m, nb, (double *)dR, ldr, N, N, 1);
+  if (cudaGetLastError() != cudaSuccess) return HQR_ERR_CUDA;
+  if (cudaMemcpyAsync(&g_na.ctl, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return HQR_ERR_CUDA;
+  return g_na.ctl.status;
+}

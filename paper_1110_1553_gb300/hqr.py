@@ -21,14 +21,15 @@ TREES = {"flat": FLAT, "binary": BINARY, "greedy": GREEDY, "fibonacci": FIBONACC
 TS, TT = 0, 1
 FP64 = 0
 
-SUCCESS, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_CAPACITY, ERR_INVALID_LIST, ERR_SINGULAR, ERR_INTERNAL = range(8)
+(SUCCESS, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_CAPACITY, ERR_INVALID_LIST, ERR_SINGULAR, ERR_INTERNAL,
+ ERR_TOO_LARGE) = range(9)
 
 ELIM_DTYPE = np.dtype([("k", np.int32), ("i", np.int32), ("killer", np.int32), ("kind", np.int32),
                        ("level", np.int32), ("step", np.int32)])
 
 EXPORTS = ["hqr_elim_list", "hqr_validate_list", "hqr_geqrf", "hqr_refactor", "hqr_refactor_async",
            "hqr_status", "hqr_get_r", "hqr_get_tiles", "hqr_get_t", "hqr_factors_info", "hqr_kernel_ms", "hqr_apply_q",
-           "hqr_gels", "hqr_debug_block_task", "hqr_factors_free", "hqr_set_timeout_ms", "hqr_strerror", "hqr_last_error",
+           "hqr_gels", "hqr_geqrf_r_noalloc", "hqr_debug_block_task", "hqr_factors_free", "hqr_set_timeout_ms", "hqr_strerror", "hqr_last_error",
            "hqr_last_launches"]
 
 
@@ -77,6 +78,7 @@ def load(build_if_missing=False):
     lib.hqr_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     lib.hqr_apply_q.argtypes = [vp, i32, vp, i32, i32, vp]
     lib.hqr_gels.argtypes = [vp, i32, i32, i32, vp, i32, i32, vp, i32, i32, i32, i32, vp, sz, vp]
+    lib.hqr_geqrf_r_noalloc.argtypes = [vp, i32, i32, i32, i32, i32, vp, sz, vp, i32, vp]
     lib.hqr_debug_block_task.argtypes = [vp, i64, i32]
     lib.hqr_factors_free.argtypes = [vp]
     lib.hqr_factors_free.restype = None
@@ -285,3 +287,18 @@ def gels(A, b, nb, ib, records=None, stream=None):
     del keep
     _check(st, "hqr_gels")
     return x[:, 0] if vec else x
+
+
+def geqrf_r_noalloc(A, nb, ib, records, R, stream=None):
+    """R factor of A into the caller's column-major N x N tensor R through
+    hqr_geqrf_r_noalloc, which allocates no memory (limits in include/hqr.h).
+    Returns the library status (0 on success)."""
+    A, lda = colmajor(A)
+    M, N = A.shape
+    if R.stride(0) != 1 or R.shape != (N, N):
+        raise ValueError("R must be a column-major N x N float64 CUDA tensor")
+    ptr, cnt, keep = _list_arg(records)
+    st = load().hqr_geqrf_r_noalloc(ctypes.c_void_p(A.data_ptr()), M, N, lda, nb, ib, ptr, cnt,
+                                    ctypes.c_void_p(R.data_ptr()), R.stride(1), _stream_ptr(stream))
+    del keep
+    return st

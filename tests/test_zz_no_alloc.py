@@ -1,0 +1,58 @@
+"""The allocation-free entry point hqr_geqrf_r_noalloc, called through the C
+ABI, against the regular hqr_geqrf on two calls in a row.
+
+It exists for callers that may not allocate memory during the call: their
+device memory belongs to another allocator's pool, or cudaMalloc's implicit
+device synchronization is not acceptable where they run. Its scratch is one
+static device array shared by all calls, so the second call here also checks
+that nothing left over from the first call leaks into its result.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+from paper_1110_1553_gb300 import hqr, inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+R_TOL = 1e-11  # max|dR| / ||A||_F, as the other parity tests
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1110_1553_gb300 import _build
+    _build.build()
+    hqr.load()
+
+
+def test_noalloc_matches_geqrf_on_two_calls():
+    nb, ib = 64, 16
+    for call, (M, N, seed, a, p) in enumerate([(512, 256, 31, 2, 2), (300, 200, 32, 1, 3)]):
+        m, n = -(-M // nb), -(-N // nb)
+        recs = hqr.elim_list(m, n, a, p, "greedy", "fibonacci")
+        A = torch.from_numpy(inputs.gaussian(M, N, seed=seed)).cuda()
+        R = hqr.empty_colmajor(N, N)
+        R.fill_(np.nan)
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
+        st = hqr.geqrf_r_noalloc(A, nb, ib, recs, R)
+        free_after = torch.cuda.mem_get_info()[0]
+        assert st == 0, st
+        if call == 1:
+            # after the one-time set-up of the first call, no device memory moves
+            assert free_after == free_before
+        Rref = hqr.geqrf(A, nb, ib, recs).R()
+        err = ((R - Rref).abs().max() / torch.linalg.norm(A)).item()
+        assert err <= R_TOL, (call, err)
+
+
+def test_noalloc_rejects_oversized_problems():
+    nb, ib = 64, 16
+    M, N = 65 * nb, nb  # 65 tile rows: over the 64-row limit
+    recs = hqr.elim_list(65, 1, 1, 1, "flat", "flat")
+    A = torch.zeros((M, N), dtype=torch.float64, device="cuda")
+    R = hqr.empty_colmajor(N, N)
+    assert hqr.geqrf_r_noalloc(A, nb, ib, recs, R) == hqr.ERR_TOO_LARGE
+    recs = hqr.elim_list(2, 1, 1, 1, "flat", "flat")
+    A = torch.zeros((256, 128), dtype=torch.float64, device="cuda")
+    R = hqr.empty_colmajor(128, 128)
+    assert hqr.geqrf_r_noalloc(A, 128, 16, recs, R) == hqr.ERR_TOO_LARGE  # nb > 64
