@@ -28,7 +28,7 @@ WORKLOAD = dict(M=131072, N=2048, nb=256, ib=32, a=4, p=16, low="greedy", high="
 WORKLOAD_NAME = "hqr_fp64_tall_skinny_131072x2048_nb256_ib32_a4_p16_greedy_fibonacci"
 SAMPLE_M = 4096  # oracle sample: the first 16 tile rows, all 2048 columns
 PROFILE = os.path.join(ROOT, "profiles", "hqr_sched_fp64_tall_skinny.md")
-ENGINE_SRC = os.path.join(ROOT, "paper_1110_1553_gb300", "csrc", "engine_fp64.cuh")
+ENGINE_SRC = os.path.join(ROOT, "paper_1110_1553_gb300", "csrc", "engine.cuh")
 
 
 def qr_flops(M, N):

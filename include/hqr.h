@@ -59,8 +59,10 @@ typedef struct {
 } hqr_elim_t;
 
 /* Arithmetic of the factorization. HQR_FP64: FP64 storage and arithmetic
- * everywhere (the paper's setting, Sec. 5.1). */
-typedef enum { HQR_FP64 = 0 } hqr_prec_t;
+ * everywhere (the paper's setting, Sec. 5.1). HQR_FP32: FP32 storage and
+ * FP32 arithmetic (panel norms with a scaled second pass on under- or
+ * overflow); device buffers passed with it hold float. */
+typedef enum { HQR_FP64 = 0, HQR_FP32 = 1 } hqr_prec_t;
 
 enum {
   HQR_SUCCESS = 0,
@@ -118,7 +120,8 @@ int hqr_validate_list(int m, int n, const hqr_elim_t *list, size_t count);
  *   M, N    matrix size, M >= N >= 1. Padded with zeros to whole tiles.
  *   prec    hqr_prec_t.
  *   nb      tile size b: multiple of 8, 8 <= nb <= 256.
- *   ib      inner block of the compact-WY T factors: even, divides nb.
+ *   ib      inner block of the compact-WY T factors: divides nb, at most 16
+ *           or exactly 32, a multiple of 2 (FP64) or 4 (FP32).
  *   list    host array of `count` records for m = ceil(M/nb), n = ceil(N/nb)
  *           tiles, or NULL for the default list (flat TS domains of a = 4,
  *           p = 1, greedy low tree).
@@ -173,6 +176,15 @@ int hqr_get_t(const hqr_factors *F, void *dT, void *stream);
  * persistent task kernel of the last factorization or apply-Q run on F.
  * Waits for that kernel to finish. */
 int hqr_kernel_ms(hqr_factors *F, float *ms);
+
+/*
+ * hqr_trace -- per-task timing of the persistent kernel (for analysis).
+ * enable = 1: record from the next run on (allocates a device buffer of
+ * 3 x 8 bytes per task); 0: stop and free it; -1: copy the last run's
+ * records to `host` (cap >= 3 * *count entries): per task its start and end
+ * (%globaltimer, ns) and (CTA index << 32 | SM id). *count = tasks traced.
+ */
+int hqr_trace(hqr_factors *F, int enable, uint64_t *host, size_t cap, size_t *count);
 
 /* hqr_factors_info -- sizes of a factorization: padded rows/cols, tiles,
  * tile size, inner block, number of tasks in the factorization graph. */

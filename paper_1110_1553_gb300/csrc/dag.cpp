@@ -107,12 +107,13 @@ class Builder {
   Graph g_;
 };
 
-Task make_task(int op, int prio, int i, int r, int k, int j, int c0, int cw, int trans) {
+Task make_task(int op, int prio, int i, int r, int k, int j, int c0, int cw, int trans, int tgt, int pid) {
   Task t;
   t.op = (int8_t)op;
   t.prio = (int8_t)prio;
   t.trans = (int8_t)trans;
-  t.pad = 0;
+  t.tgt = (int8_t)tgt;
+  t.pid = pid;
   t.i = i;
   t.r = r;
   t.k = k;
@@ -125,7 +126,7 @@ Task make_task(int op, int prio, int i, int r, int k, int j, int c0, int cw, int
 
 }  // namespace
 
-Graph build_factor_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int w) {
+Graph build_factor_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int w, int pid) {
   const int S = (nb + w - 1) / w;  // column slabs per tile
   const size_t per_tile = (size_t)S + 2;
   // storage pieces of tile (i, j): S column slabs, then U (upper triangle
@@ -142,20 +143,20 @@ Graph build_factor_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, 
       for (int s = 0; s < S; ++s) tr.write(slab(o.i, k, s), d);
       tr.write(upart(o.i, k), d);
       tr.write(lpart(o.i, k), d);
-      b.add(make_task(OP_GEQRT, 0, o.i, o.i, k, k, 0, nb, 1));
+      b.add(make_task(OP_GEQRT, 0, o.i, o.i, k, k, 0, nb, 1, 0, pid));
       for (int j = k + 1; j < n; ++j)
         for (int s = 0; s < S; ++s) {
           tr.read(lpart(o.i, k), d);
           tr.write(slab(o.i, j, s), d);
           b.add(make_task(OP_UNMQR, j == k + 1 ? 1 : 2, o.i, o.i, k, j, s * w,
-                          std::min(w, nb - s * w), 1));
+                          std::min(w, nb - s * w), 1, 0, pid));
         }
     } else if (o.kind == 1) {  // TSQRT(i, r, k), TSMQR(i, r, k, j)
       tr.write(upart(o.r, k), d);
       for (int s = 0; s < S; ++s) tr.write(slab(o.i, k, s), d);
       tr.write(upart(o.i, k), d);
       tr.write(lpart(o.i, k), d);
-      b.add(make_task(OP_TSQRT, 0, o.i, o.r, k, k, 0, nb, 1));
+      b.add(make_task(OP_TSQRT, 0, o.i, o.r, k, k, 0, nb, 1, 0, pid));
       for (int j = k + 1; j < n; ++j)
         for (int s = 0; s < S; ++s) {
           tr.read(upart(o.i, k), d);
@@ -163,26 +164,26 @@ Graph build_factor_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, 
           tr.write(slab(o.r, j, s), d);
           tr.write(slab(o.i, j, s), d);
           b.add(make_task(OP_TSMQR, j == k + 1 ? 1 : 2, o.i, o.r, k, j, s * w,
-                          std::min(w, nb - s * w), 1));
+                          std::min(w, nb - s * w), 1, 0, pid));
         }
     } else {  // TTQRT(i, r, k), TTMQR(i, r, k, j)
       tr.write(upart(o.r, k), d);
       tr.write(upart(o.i, k), d);
-      b.add(make_task(OP_TTQRT, 0, o.i, o.r, k, k, 0, nb, 1));
+      b.add(make_task(OP_TTQRT, 0, o.i, o.r, k, k, 0, nb, 1, 0, pid));
       for (int j = k + 1; j < n; ++j)
         for (int s = 0; s < S; ++s) {
           tr.read(upart(o.i, k), d);
           tr.write(slab(o.r, j, s), d);
           tr.write(slab(o.i, j, s), d);
           b.add(make_task(OP_TTMQR, j == k + 1 ? 1 : 2, o.i, o.r, k, j, s * w,
-                          std::min(w, nb - s * w), 1));
+                          std::min(w, nb - s * w), 1, 0, pid));
         }
     }
   }
   return b.finish();
 }
 
-Graph build_apply_graph(const std::vector<PanelOp> &ops, int m, int nslab, int w, int trans) {
+Graph build_apply_graph(const std::vector<PanelOp> &ops, int m, int nslab, int w, int trans, int pid) {
   // storage pieces: (row tile, column slab) of the right-hand side
   auto piece = [&](int r, int s) { return (size_t)r * nslab + (size_t)s; };
   Builder b((size_t)m * nslab);
@@ -194,15 +195,28 @@ Graph build_apply_graph(const std::vector<PanelOp> &ops, int m, int nslab, int w
     for (int s = 0; s < nslab; ++s) {
       if (o.kind == 0) {
         tr.write(piece(o.i, s), d);
-        b.add(make_task(OP_UNMQR, 1, o.i, o.i, o.k, s, 0, w, trans));
+        b.add(make_task(OP_UNMQR, 1, o.i, o.i, o.k, s, 0, w, trans, 1, pid));
       } else {
         tr.write(piece(o.r, s), d);
         tr.write(piece(o.i, s), d);
-        b.add(make_task(o.kind == 1 ? OP_TSMQR : OP_TTMQR, 1, o.i, o.r, o.k, s, 0, w, trans));
+        b.add(make_task(o.kind == 1 ? OP_TSMQR : OP_TTMQR, 1, o.i, o.r, o.k, s, 0, w, trans, 1, pid));
       }
     }
   }
   return b.finish();
+}
+
+void append_graph(Graph &into, const Graph &g) {
+  const int32_t toff = (int32_t)into.tasks.size();
+  const int32_t eoff = (int32_t)into.succ.size();
+  for (Task t : g.tasks) {
+    t.succ_begin += eoff;
+    t.succ_end += eoff;
+    into.tasks.push_back(t);
+  }
+  for (int32_t s : g.succ) into.succ.push_back(s + toff);
+  into.indeg.insert(into.indeg.end(), g.indeg.begin(), g.indeg.end());
+  into.nedges += g.nedges;
 }
 
 }  // namespace hqr

@@ -1,5 +1,5 @@
-// FP64 tile kernels of tile Householder QR and the persistent task
-// scheduler that runs them (sm_103a).
+// Tile kernels of tile Householder QR and the persistent task scheduler that
+// runs them (sm_103a), for FP64 and FP32 storage and arithmetic.
 //
 // Every task of the graph (GEQRT, TSQRT, TTQRT and the UNMQR, TSMQR, TTMQR
 // updates of Alg. 2) is executed by one CTA of a persistent kernel. A CTA
@@ -8,7 +8,9 @@
 // column, completion counted on an mbarrier), computes, writes the tiles back
 // and releases its successors: each successor whose count of missing inputs
 // drops to zero is pushed to a queue (Sec. 4.2, "Execution scheme": each
-// kernel fires as soon as its dependencies are satisfied).
+// kernel fires as soon as its dependencies are satisfied). Tasks of several
+// independent problems can share one graph and one launch (each task names
+// its problem).
 //
 // Arithmetic (compact-WY Householder, reflectors grouped ib at a time):
 //   column j of (alpha, x2): s = ||x2|| (sum of squares; a max-scaled second
@@ -30,8 +32,22 @@ namespace hqr {
 
 constexpr int NT = 256;         // threads per CTA
 constexpr int NWARP = NT / 32;  // warps per CTA
-constexpr int VCMAX = 16;       // V columns staged per chunk in the updates
 constexpr int IBMAX = 32;       // largest inner block
+
+template <typename Real>
+struct RealTraits;
+template <>
+struct RealTraits<double> {
+  static constexpr double tiny = 1e-280, huge = 1e280;  // sum-of-squares range kept unscaled
+};
+template <>
+struct RealTraits<float> {
+  static constexpr float tiny = 1e-30f, huge = 1e30f;
+};
+// shared-memory column padding (elements): keeps every staged column on a
+// 16-byte boundary and spreads columns over banks
+template <typename Real>
+__host__ __device__ constexpr int smem_pad() { return 16 / (int)sizeof(Real); }
 
 // Device control words of one graph run.
 struct Ctl {
@@ -43,16 +59,20 @@ struct Ctl {
   int pad[3];
 };
 
-struct EngineParams {
-  double *A;           // tile workspace: tile (i, j) at ((j*m + i)*nb*nb), column-major
-  double *T;           // T factors: ((k*m + i)*2 + which)*ib*nb, ib x nb column-major
-  double *C;           // update targets: A for the factorization, RHS blocks for apply-Q
-  long long cstride;   // elements between target blocks of consecutive rows
+// One problem of a (possibly batched) task graph.
+struct Problem {
+  void *A;            // tile workspace: tile (i, j) at ((j*m + i)*nb*nb), column-major
+  void *T;            // T factors: ((k*m + i)*2 + which)*ib*nb, ib x nb column-major
+  void *B;            // right-hand-side blocks: block (r, s) at ((s*m + r)*nb*wb)
   int m, n, nb, ib;
-  int w;               // width of an update task's column slab (max)
-  int wt;              // slab width of the trailing update inside panel tasks
-  int vc;              // V columns staged per chunk in update tasks (divides ib)
-  int lds;             // shared-memory column stride (nb + 2)
+  int w;              // width of an update task's column slab (max)
+  int wt;             // slab width of the trailing update inside panel tasks
+  int vc;             // V columns staged per chunk in update tasks (divides ib)
+  int wb;             // right-hand-side block width
+};
+
+struct EngineParams {
+  const Problem *probs;
   const Task *tasks;
   int ntasks;
   const int *succ;
@@ -60,48 +80,63 @@ struct EngineParams {
   int *slots;          // kNumQueues x ntasks ready slots (task id + 1, 0 = empty)
   Ctl *ctl;
   long long timeout_ns;
+  unsigned long long *trace;  // optional: per task start, end (globaltimer), SM id
 };
 
+template <typename Real>
 struct Shared {
   uint64_t bar;
   int task;
   int abort;
-  double red[2 * NWARP];
-  double tau[IBMAX];
-  double wv[IBMAX];
-  double bc[4];
+  Real red[2 * NWARP];
+  Real tau[IBMAX];
+  Real wv[IBMAX];
+  Real bc[4];
 };
 
 // ---------------------------------------------------------------- helpers --
 
-__device__ __forceinline__ double *tile_ptr(const EngineParams &p, int i, int j) {
-  return p.A + ((size_t)j * p.m + i) * (size_t)p.nb * p.nb;
-}
-__device__ __forceinline__ double *t_ptr(const EngineParams &p, int which, int i, int k) {
-  return p.T + (((size_t)k * p.m + i) * 2 + which) * (size_t)p.ib * p.nb;
-}
-__device__ __forceinline__ double *target_ptr(const EngineParams &p, const Task &t, int row) {
-  return p.C + ((size_t)t.j * p.m + row) * (size_t)p.cstride + (size_t)t.c0 * p.nb;
-}
+// Geometry of one task's problem, read once per task from global memory.
+template <typename Real>
+struct Geo {
+  Real *A, *T, *B;
+  int m, n, nb, ib, w, wt, vc, wb, lds, ldt;
+  __device__ explicit Geo(const Problem &P)
+      : A((Real *)P.A), T((Real *)P.T), B((Real *)P.B), m(P.m), n(P.n), nb(P.nb), ib(P.ib), w(P.w),
+        wt(P.wt), vc(P.vc), wb(P.wb), lds(P.nb + smem_pad<Real>()), ldt(P.ib + smem_pad<Real>()) {}
+  __device__ Real *tile(int i, int j) const { return A + ((size_t)j * m + i) * (size_t)nb * nb; }
+  __device__ Real *tfac(int which, int i, int k) const {
+    return T + (((size_t)k * m + i) * 2 + which) * (size_t)ib * nb;
+  }
+  // columns [t.c0, t.c0 + t.cw) of the target block of row `row`
+  __device__ Real *target(const Task &t, int row) const {
+    if (t.tgt == 0) return A + ((size_t)t.j * m + row) * (size_t)nb * nb + (size_t)t.c0 * nb;
+    return B + ((size_t)t.j * m + row) * (size_t)nb * wb + (size_t)t.c0 * nb;
+  }
+};
 
 __device__ __forceinline__ void set_error(const EngineParams &p, int code, int task) {
   if (atomicCAS(&p.ctl->status, 0, code) == 0) p.ctl->err_task = task;
 }
 
+template <typename Real>
 struct Copy {
-  double *dst;
+  Real *dst;
   int ldd;
-  const double *src;
+  const Real *src;
   long long lds;
   int nrows, ncols;
 };
 
 // Stage up to 3 column-blocks global -> shared with bulk copies, one copy per
 // column, and wait for them (bounded). Callers sync before (dst free).
-__device__ void stage(const EngineParams &p, Shared &sh, const Copy *cp, int ncp, uint32_t &phase) {
+template <typename Real>
+__device__ void stage(const EngineParams &p, Shared<Real> &sh, const Copy<Real> *cp, int ncp,
+                      uint32_t &phase) {
   uint32_t total = 0;
   for (int q = 0; q < ncp; ++q)
-    if (cp[q].nrows > 0 && cp[q].ncols > 0) total += (uint32_t)cp[q].nrows * 8u * (uint32_t)cp[q].ncols;
+    if (cp[q].nrows > 0 && cp[q].ncols > 0)
+      total += (uint32_t)cp[q].nrows * (uint32_t)sizeof(Real) * (uint32_t)cp[q].ncols;
   if (total == 0) return;
   if (threadIdx.x < 32) {
     ptx::fence_proxy_async();
@@ -109,7 +144,7 @@ __device__ void stage(const EngineParams &p, Shared &sh, const Copy *cp, int ncp
     __syncwarp();
     for (int q = 0; q < ncp; ++q) {
       if (cp[q].nrows <= 0) continue;
-      const uint32_t bytes = (uint32_t)cp[q].nrows * 8u;
+      const uint32_t bytes = (uint32_t)cp[q].nrows * (uint32_t)sizeof(Real);
       for (int c = threadIdx.x; c < cp[q].ncols; c += 32)
         ptx::bulk_g2s(cp[q].dst + (size_t)c * cp[q].ldd, cp[q].src + (long long)c * cp[q].lds, bytes,
                       &sh.bar);
@@ -131,8 +166,9 @@ __device__ void stage(const EngineParams &p, Shared &sh, const Copy *cp, int ncp
 
 // Write an nrows x ncols block from shared to global (coalesced along rows).
 // mode 0: all; 1: only rows <= roff + col (upper part incl. diagonal).
-__device__ void store_cols(double *g, long long ldg, const double *s, int ldsm, int nrows, int ncols,
-                           int mode, int roff) {
+template <typename Real>
+__device__ void store_cols(Real *g, long long ldg, const Real *s, int ldsm, int nrows, int ncols, int mode,
+                           int roff) {
   const int total = nrows * ncols;
   for (int e = threadIdx.x; e < total; e += NT) {
     const int c = e / nrows, r = e - c * nrows;
@@ -141,30 +177,33 @@ __device__ void store_cols(double *g, long long ldg, const double *s, int ldsm, 
   }
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename Real>
+__device__ __forceinline__ Real warp_sum(Real v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
 // Sum over the CTA; every thread gets the same value (fixed order).
-__device__ double block_sum(double v, Shared &sh) {
+template <typename Real>
+__device__ Real block_sum(Real v, Shared<Real> &sh) {
   v = warp_sum(v);
   if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5] = v;
   __syncthreads();
-  double t = 0.0;
+  Real t = 0;
 #pragma unroll
   for (int q = 0; q < NWARP; ++q) t += sh.red[q];
   __syncthreads();
   return t;
 }
 
-__device__ double block_max(double v, Shared &sh) {
+template <typename Real>
+__device__ Real block_max(Real v, Shared<Real> &sh) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5] = v;
   __syncthreads();
-  double t = 0.0;
+  Real t = 0;
 #pragma unroll
   for (int q = 0; q < NWARP; ++q) t = fmax(t, sh.red[q]);
   __syncthreads();
@@ -173,25 +212,26 @@ __device__ double block_max(double v, Shared &sh) {
 
 // W(i,j) = [Cinit(i,j)] + sum_{k<K} V(k,i) C(k,j), i < Mi, j < Nj.
 // Short output sets split K among thread groups; partial sums are combined
-// in a fixed order through `scr` (>= NT doubles).
-__device__ void gemm_tn(double *W, int ldw, const double *V, int ldv, const double *Cm, int ldc, int K,
-                        int Mi, int Nj, const double *Cinit, int ldi, double *scr) {
+// in a fixed order through `scr` (>= NT elements).
+template <typename Real>
+__device__ void gemm_tn(Real *W, int ldw, const Real *V, int ldv, const Real *Cm, int ldc, int K, int Mi,
+                        int Nj, const Real *Cinit, int ldi, Real *scr) {
   const int O = Mi * Nj;
   if (O <= 0) return;
   const int tid = threadIdx.x;
   if (O >= NT / 2 || K < 64) {
     for (int o = tid; o < O; o += NT) {
       const int i = o % Mi, j = o / Mi;
-      const double *v = V + (size_t)i * ldv;
-      const double *c = Cm + (size_t)j * ldc;
-      double s0 = 0.0, s1 = 0.0;
+      const Real *v = V + (size_t)i * ldv;
+      const Real *c = Cm + (size_t)j * ldc;
+      Real s0 = 0, s1 = 0;
       int k = 0;
       for (; k + 1 < K; k += 2) {
         s0 = fma(v[k], c[k], s0);
         s1 = fma(v[k + 1], c[k + 1], s1);
       }
       if (k < K) s0 = fma(v[k], c[k], s0);
-      const double base = Cinit ? Cinit[i + (size_t)j * ldi] : 0.0;
+      const Real base = Cinit ? Cinit[i + (size_t)j * ldi] : Real(0);
       W[i + (size_t)j * ldw] = base + (s0 + s1);
     }
     __syncthreads();
@@ -203,38 +243,39 @@ __device__ void gemm_tn(double *W, int ldw, const double *V, int ldv, const doub
   const int o = tid % O, g = tid / O;
   if (g < G) {
     const int i = o % Mi, j = o / Mi;
-    const double *v = V + (size_t)i * ldv;
-    const double *c = Cm + (size_t)j * ldc;
+    const Real *v = V + (size_t)i * ldv;
+    const Real *c = Cm + (size_t)j * ldc;
     const int k0 = g * Kc, k1 = min(K, k0 + Kc);
-    double s = 0.0;
+    Real s = 0;
     for (int k = k0; k < k1; ++k) s = fma(v[k], c[k], s);
     scr[g * O + o] = s;
   }
   __syncthreads();
   if (tid < O) {
     const int i = tid % Mi, j = tid / Mi;
-    double s = 0.0;
+    Real s = 0;
     for (int q = 0; q < G; ++q) s += scr[q * O + tid];
-    const double base = Cinit ? Cinit[i + (size_t)j * ldi] : 0.0;
+    const Real base = Cinit ? Cinit[i + (size_t)j * ldi] : Real(0);
     W[i + (size_t)j * ldw] = base + s;
   }
   __syncthreads();
 }
 
 // C(k,j) -= sum_{i<Mi} V(k,i) W(i,j), k < K, j < Nj. Threads run along k.
-__device__ void gemm_nn_sub(double *Cm, int ldc, const double *V, int ldv, const double *W, int ldw, int K,
-                            int Mi, int Nj) {
+template <typename Real>
+__device__ void gemm_nn_sub(Real *Cm, int ldc, const Real *V, int ldv, const Real *W, int ldw, int K, int Mi,
+                            int Nj) {
   const int nchunk = (Nj + 7) / 8;
   const int total = K * nchunk;
   for (int it = threadIdx.x; it < total; it += NT) {
     const int k = it % K, jc = it / K;
     const int j0 = jc * 8, jn = min(8, Nj - j0);
-    double acc[8];
+    Real acc[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    for (int q = 0; q < 8; ++q) acc[q] = 0;
     for (int i = 0; i < Mi; ++i) {
-      const double v = V[k + (size_t)i * ldv];
-      const double *w = W + i + (size_t)j0 * ldw;
+      const Real v = V[k + (size_t)i * ldv];
+      const Real *w = W + i + (size_t)j0 * ldw;
 #pragma unroll
       for (int q = 0; q < 8; ++q)
         if (q < jn) acc[q] = fma(v, w[(size_t)q * ldw], acc[q]);
@@ -247,12 +288,13 @@ __device__ void gemm_nn_sub(double *Cm, int ldc, const double *V, int ldv, const
 }
 
 // W <- T^T W (trans) or T W, T an ib x ib upper triangle (ld ib).
-__device__ void trmm_tw(double *W, int ldw, const double *Tq, int ib, int Nj, int trans, double *tmp) {
+template <typename Real>
+__device__ void trmm_tw(Real *W, int ldw, const Real *Tq, int ib, int Nj, int trans, Real *tmp) {
   const int O = ib * Nj;
   for (int o = threadIdx.x; o < O; o += NT) {
     const int i = o % ib, j = o / ib;
-    const double *w = W + (size_t)j * ldw;
-    double s = 0.0;
+    const Real *w = W + (size_t)j * ldw;
+    Real s = 0;
     if (trans) {
       for (int l = 0; l <= i; ++l) s = fma(Tq[l + (size_t)i * ib], w[l], s);
     } else {
@@ -269,7 +311,8 @@ __device__ void trmm_tw(double *W, int ldw, const double *Tq, int ib, int Nj, in
 }
 
 // Ct(i,j) -= W(i,j): the identity top block of TS/TT reflectors.
-__device__ void sub_top(double *Ct, int ldt, const double *W, int ldw, int Mi, int Nj) {
+template <typename Real>
+__device__ void sub_top(Real *Ct, int ldt, const Real *W, int ldw, int Mi, int Nj) {
   for (int o = threadIdx.x; o < Mi * Nj; o += NT) {
     const int i = o % Mi, j = o / Mi;
     Ct[i + (size_t)j * ldt] -= W[i + (size_t)j * ldw];
@@ -285,45 +328,46 @@ enum { PANEL_GE = 0, PANEL_TS = 1, PANEL_TT = 2 };
 //  TT: alpha = Rt(jj,jj), x2 = P(0:q0+jj+1, jj) (upper-triangular tile).
 // On return P holds the reflectors' lower parts (GE: R above) and sh.tau the
 // scalars; Rt's upper triangle holds the updated R rows of the block.
-__device__ void factor_block(int mode, double *P, int ld, int L, int ib, double *Rt, int ldt, int q0,
-                             Shared &sh) {
+template <typename Real>
+__device__ void factor_block(int mode, Real *P, int ld, int L, int ib, Real *Rt, int ldt, int q0,
+                             Shared<Real> &sh) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int jj = 0; jj < ib; ++jj) {
     const int r0 = (mode == PANEL_GE) ? jj + 1 : 0;
     const int r1 = (mode == PANEL_TT) ? min(L, q0 + jj + 1) : L;
-    double *col = P + (size_t)jj * ld;
-    double ss = 0.0;
+    Real *col = P + (size_t)jj * ld;
+    Real ss = 0;
     for (int k = r0 + tid; k < r1; k += NT) ss = fma(col[k], col[k], ss);
     ss = block_sum(ss, sh);
-    double snorm;
-    if (ss > 1e-280 && ss < 1e280) {
+    Real snorm;
+    if (ss > RealTraits<Real>::tiny && ss < RealTraits<Real>::huge) {
       snorm = sqrt(ss);
     } else {
-      double am = 0.0;
+      Real am = 0;
       for (int k = r0 + tid; k < r1; k += NT) am = fmax(am, fabs(col[k]));
       am = block_max(am, sh);
-      if (am == 0.0) {
-        snorm = 0.0;
+      if (am == Real(0)) {
+        snorm = 0;
       } else {
-        const double inv = 1.0 / am;
-        double s2 = 0.0;
+        const Real inv = Real(1) / am;
+        Real s2 = 0;
         for (int k = r0 + tid; k < r1; k += NT) {
-          const double x = col[k] * inv;
+          const Real x = col[k] * inv;
           s2 = fma(x, x, s2);
         }
         s2 = block_sum(s2, sh);
         snorm = am * sqrt(s2);
       }
     }
-    double *diag = (mode == PANEL_GE) ? &col[jj] : &Rt[jj + (size_t)jj * ldt];
+    Real *diag = (mode == PANEL_GE) ? &col[jj] : &Rt[jj + (size_t)jj * ldt];
     if (tid == 0) {
-      const double alpha = *diag;
-      double beta = alpha, t = 0.0, scale = 0.0;
-      if (snorm != 0.0) {
-        const double h = hypot(alpha, snorm);
-        beta = (alpha >= 0.0) ? -h : h;
+      const Real alpha = *diag;
+      Real beta = alpha, t = 0, scale = 0;
+      if (snorm != Real(0)) {
+        const Real h = hypot(alpha, snorm);
+        beta = (alpha >= Real(0)) ? -h : h;
         t = (beta - alpha) / beta;
-        scale = 1.0 / (alpha - beta);
+        scale = Real(1) / (alpha - beta);
       }
       *diag = beta;
       sh.tau[jj] = t;
@@ -331,18 +375,18 @@ __device__ void factor_block(int mode, double *P, int ld, int L, int ib, double 
       sh.bc[1] = scale;
     }
     __syncthreads();
-    const double t = sh.bc[0], scale = sh.bc[1];
+    const Real t = sh.bc[0], scale = sh.bc[1];
     for (int k = r0 + tid; k < r1; k += NT) col[k] *= scale;
     __syncthreads();
-    if (t == 0.0) continue;  // identity reflector: nothing to apply
+    if (t == Real(0)) continue;  // identity reflector: nothing to apply
     // w_c = top(jj,c) + v^T P(:,c) for the block's later columns
     for (int c = jj + 1 + warp; c < ib; c += NWARP) {
-      const double *pc = P + (size_t)c * ld;
-      double s = 0.0;
+      const Real *pc = P + (size_t)c * ld;
+      Real s = 0;
       for (int k = r0 + lane; k < r1; k += 32) s = fma(col[k], pc[k], s);
       s = warp_sum(s);
       if (lane == 0) {
-        const double top = (mode == PANEL_GE) ? pc[jj] : Rt[jj + (size_t)c * ldt];
+        const Real top = (mode == PANEL_GE) ? pc[jj] : Rt[jj + (size_t)c * ldt];
         sh.wv[c] = t * (top + s);
       }
     }
@@ -350,7 +394,7 @@ __device__ void factor_block(int mode, double *P, int ld, int L, int ib, double 
     const int nr = r1 - r0, ncl = ib - jj - 1;
     for (int e = tid; e < nr * ncl; e += NT) {
       const int c = jj + 1 + e / nr, k = r0 + e % nr;
-      double *pc = P + (size_t)c * ld;
+      Real *pc = P + (size_t)c * ld;
       pc[k] = fma(-col[k], sh.wv[c], pc[k]);
     }
     if (tid > jj && tid < ib) {
@@ -364,13 +408,14 @@ __device__ void factor_block(int mode, double *P, int ld, int L, int ib, double 
 }
 
 // T of a block from the Gram matrix G = V^T V (only G(l, j), l < j, used).
-__device__ void build_t(double *Tq, const double *G, int ib, const Shared &sh) {
-  for (int e = threadIdx.x; e < ib * ib; e += NT) Tq[e] = 0.0;
+template <typename Real>
+__device__ void build_t(Real *Tq, const Real *G, int ib, const Shared<Real> &sh) {
+  for (int e = threadIdx.x; e < ib * ib; e += NT) Tq[e] = 0;
   __syncthreads();
   for (int jj = 0; jj < ib; ++jj) {
     const int tid = threadIdx.x;
     if (tid < jj) {
-      double y = 0.0;
+      Real y = 0;
       for (int l = tid; l < jj; ++l) y = fma(Tq[tid + (size_t)l * ib], G[l + (size_t)jj * ib], y);
       Tq[tid + (size_t)jj * ib] = -sh.tau[jj] * y;
     } else if (tid == jj) {
@@ -384,17 +429,18 @@ __device__ void build_t(double *Tq, const double *G, int ib, const Shared &sh) {
 //  GE: unit lower; chunk column cc is global block column coff + cc, local
 //      row kl is block row kl: zero above, one on the diagonal.
 //  TT: upper triangular: zero below row roff + coff + cc.
-__device__ void shape_v(double *V, int ld, int L, int ncols, int mode, int coff, int roff) {
+template <typename Real>
+__device__ void shape_v(Real *V, int ld, int L, int ncols, int mode, int coff, int roff) {
   for (int e = threadIdx.x; e < L * ncols; e += NT) {
     const int c = e / L, k = e - c * L;
-    double *x = V + (size_t)c * ld + k;
+    Real *x = V + (size_t)c * ld + k;
     if (mode == PANEL_GE) {
       if (k < coff + c)
-        *x = 0.0;
+        *x = 0;
       else if (k == coff + c)
-        *x = 1.0;
+        *x = 1;
     } else if (mode == PANEL_TT) {
-      if (k > roff + coff + c) *x = 0.0;
+      if (k > roff + coff + c) *x = 0;
     }
   }
   __syncthreads();
@@ -404,26 +450,28 @@ __device__ void shape_v(double *V, int ld, int L, int ncols, int mode, int coff,
 
 // Updates UNMQR / TSMQR / TTMQR of one column slab (also used for Q and Q^T
 // applied to right-hand-side blocks).
-__device__ void task_update(const EngineParams &p, const Task &t, Shared &sh, double *dyn,
-                            uint32_t &phase) {
-  const int nb = p.nb, ib = p.ib, lds = p.lds, cw = t.cw;
-  const int VC = p.vc;
+template <typename Real>
+__device__ void task_update(const EngineParams &p, const Geo<Real> &g, const Task &t, Shared<Real> &sh,
+                            Real *dyn, uint32_t &phase) {
+  const int nb = g.nb, ib = g.ib, lds = g.lds, cw = t.cw;
+  const int wmax = t.tgt == 0 ? g.w : g.wb;
+  const int VC = g.vc;
   const int nchunk = ib / VC;
-  double *C1 = dyn;
-  double *C2 = C1 + (size_t)lds * p.w;
-  double *Vc = C2 + (size_t)lds * p.w;
-  double *Tq = Vc + (size_t)lds * VC;
-  double *W = Tq + (size_t)ib * ib;
-  double *scr = W + (size_t)ib * p.w;
+  Real *C1 = dyn;
+  Real *C2 = C1 + (size_t)lds * wmax;
+  Real *Vc = C2 + (size_t)lds * wmax;
+  Real *Tq = Vc + (size_t)lds * VC;
+  Real *W = Tq + (size_t)ib * ib;
+  Real *scr = W + (size_t)ib * wmax;
   const int op = t.op;
   const bool pair = op != OP_UNMQR;
   const int mode = op == OP_UNMQR ? PANEL_GE : (op == OP_TSMQR ? PANEL_TS : PANEL_TT);
-  double *g1 = target_ptr(p, t, pair ? t.r : t.i);
-  double *g2 = pair ? target_ptr(p, t, t.i) : nullptr;
-  const double *Vt = tile_ptr(p, t.i, t.k);
-  const double *Tt = t_ptr(p, pair ? 1 : 0, t.i, t.k);
+  Real *g1 = g.target(t, pair ? t.r : t.i);
+  Real *g2 = pair ? g.target(t, t.i) : nullptr;
+  const Real *Vt = g.tile(t.i, t.k);
+  const Real *Tt = g.tfac(pair ? 1 : 0, t.i, t.k);
   {
-    Copy cp[2] = {{C1, lds, g1, nb, nb, cw}, {C2, lds, g2, nb, pair ? nb : 0, cw}};
+    Copy<Real> cp[2] = {{C1, lds, g1, nb, nb, cw}, {C2, lds, g2, nb, pair ? nb : 0, cw}};
     stage(p, sh, cp, 2, phase);
   }
   const int nq = nb / ib;
@@ -432,12 +480,12 @@ __device__ void task_update(const EngineParams &p, const Task &t, Shared &sh, do
     const int q0 = q * ib;
     const int vr0 = (mode == PANEL_GE) ? q0 : 0;
     const int L = (mode == PANEL_GE) ? nb - q0 : (mode == PANEL_TS ? nb : q0 + ib);
-    double *Cb = (mode == PANEL_GE) ? C1 + q0 : C2;
-    double *Ct = C1 + q0;
+    Real *Cb = (mode == PANEL_GE) ? C1 + q0 : C2;
+    Real *Ct = C1 + q0;
     for (int c = 0; c < nchunk; ++c) {
       __syncthreads();
-      Copy cp[2] = {{Vc, lds, Vt + (size_t)(q0 + c * VC) * nb + vr0, nb, L, VC},
-                    {Tq, ib, Tt + (size_t)q * ib * ib, ib, c == 0 ? ib : 0, ib}};
+      Copy<Real> cp[2] = {{Vc, lds, Vt + (size_t)(q0 + c * VC) * nb + vr0, nb, L, VC},
+                          {Tq, ib, Tt + (size_t)q * ib * ib, ib, c == 0 ? ib : 0, ib}};
       stage(p, sh, cp, 2, phase);
       shape_v(Vc, lds, L, VC, mode, c * VC, q0);
       gemm_tn(W + c * VC, ib, Vc, lds, Cb, lds, L, VC, cw, pair ? Ct + c * VC : nullptr, lds, scr);
@@ -447,7 +495,7 @@ __device__ void task_update(const EngineParams &p, const Task &t, Shared &sh, do
     for (int c = 0; c < nchunk; ++c) {
       if (nchunk > 1) {
         __syncthreads();
-        Copy cp[1] = {{Vc, lds, Vt + (size_t)(q0 + c * VC) * nb + vr0, nb, L, VC}};
+        Copy<Real> cp[1] = {{Vc, lds, Vt + (size_t)(q0 + c * VC) * nb + vr0, nb, L, VC}};
         stage(p, sh, cp, 1, phase);
         shape_v(Vc, lds, L, VC, mode, c * VC, q0);
       }
@@ -459,22 +507,22 @@ __device__ void task_update(const EngineParams &p, const Task &t, Shared &sh, do
 }
 
 // GEQRT (mode GE), TSQRT (TS) and TTQRT (TT) of one tile (pair).
-__device__ void task_panel(const EngineParams &p, const Task &t, Shared &sh, double *dyn,
-                           uint32_t &phase) {
-  const int nb = p.nb, ib = p.ib, lds = p.lds, wt = p.wt;
-  const int ldt = ib + 2;
+template <typename Real>
+__device__ void task_panel(const EngineParams &p, const Geo<Real> &g, const Task &t, Shared<Real> &sh,
+                           Real *dyn, uint32_t &phase) {
+  const int nb = g.nb, ib = g.ib, lds = g.lds, wt = g.wt, ldt = g.ldt;
   const int mode = t.op == OP_GEQRT ? PANEL_GE : (t.op == OP_TSQRT ? PANEL_TS : PANEL_TT);
-  double *P = dyn;
-  double *Rt = P + (size_t)lds * ib;
-  double *Tq = Rt + (size_t)ldt * ib;
-  double *Ct = Tq + (size_t)ib * ib;
-  double *Cb = Ct + (size_t)ldt * wt;
-  double *G = Cb;  // the Gram matrix is dead before the trailing slabs use Cb
-  double *W = Cb + (size_t)(lds * wt > ib * ib ? lds * wt : ib * ib);
-  double *scr = W + (size_t)ib * wt;
-  double *XR = tile_ptr(p, t.r, t.k);  // GE: the tile itself (r == i)
-  double *XB = tile_ptr(p, t.i, t.k);
-  double *Tg = t_ptr(p, mode == PANEL_GE ? 0 : 1, t.i, t.k);
+  Real *P = dyn;
+  Real *Rt = P + (size_t)lds * ib;
+  Real *Tq = Rt + (size_t)ldt * ib;
+  Real *Ct = Tq + (size_t)ib * ib;
+  Real *Cb = Ct + (size_t)ldt * wt;
+  Real *G = Cb;  // the Gram matrix is dead before the trailing slabs use Cb
+  Real *W = Cb + (size_t)(lds * wt > ib * ib ? lds * wt : ib * ib);
+  Real *scr = W + (size_t)ib * wt;
+  Real *XR = g.tile(t.r, t.k);  // GE: the tile itself (r == i)
+  Real *XB = g.tile(t.i, t.k);
+  Real *Tg = g.tfac(mode == PANEL_GE ? 0 : 1, t.i, t.k);
   const int nq = nb / ib;
   for (int q = 0; q < nq; ++q) {
     const int q0 = q * ib;
@@ -482,14 +530,14 @@ __device__ void task_panel(const EngineParams &p, const Task &t, Shared &sh, dou
     const int br0 = (mode == PANEL_GE) ? q0 : 0;  // first tile row held in P
     __syncthreads();
     {
-      Copy cp[2] = {{P, lds, XB + (size_t)q0 * nb + br0, nb, L, ib},
-                    {Rt, ldt, XR + (size_t)q0 * nb + q0, nb, mode == PANEL_GE ? 0 : ib, ib}};
+      Copy<Real> cp[2] = {{P, lds, XB + (size_t)q0 * nb + br0, nb, L, ib},
+                          {Rt, ldt, XR + (size_t)q0 * nb + q0, nb, mode == PANEL_GE ? 0 : ib, ib}};
       stage(p, sh, cp, 2, phase);
     }
     if (mode == PANEL_TT) {  // the strict lower part of R2's tile is GEQRT's V, not data
       for (int e = threadIdx.x; e < L * ib; e += NT) {
         const int c = e / L, k = e - c * L;
-        if (k > q0 + c) P[(size_t)c * lds + k] = 0.0;
+        if (k > q0 + c) P[(size_t)c * lds + k] = 0;
       }
       __syncthreads();
     }
@@ -503,7 +551,7 @@ __device__ void task_panel(const EngineParams &p, const Task &t, Shared &sh, dou
     }
     __syncthreads();
     if (mode == PANEL_GE) shape_v(P, lds, L, ib, PANEL_GE, 0, 0);
-    gemm_tn(G, ib, P, lds, P, lds, L, ib, ib, nullptr, 0, scr);
+    gemm_tn(G, ib, P, lds, P, lds, L, ib, ib, (const Real *)nullptr, 0, scr);
     build_t(Tq, G, ib, sh);
     store_cols(Tg + (size_t)q * ib * ib, ib, Tq, ib, ib, ib, 0, 0);
     // trailing columns of the tile(s): block reflector applied with Q^T
@@ -511,17 +559,17 @@ __device__ void task_panel(const EngineParams &p, const Task &t, Shared &sh, dou
       const int wc = min(wt, nb - c0);
       __syncthreads();
       if (mode == PANEL_GE) {
-        Copy cp[1] = {{Cb, lds, XB + (size_t)c0 * nb + q0, nb, L, wc}};
+        Copy<Real> cp[1] = {{Cb, lds, XB + (size_t)c0 * nb + q0, nb, L, wc}};
         stage(p, sh, cp, 1, phase);
-        gemm_tn(W, ib, P, lds, Cb, lds, L, ib, wc, nullptr, 0, scr);
+        gemm_tn(W, ib, P, lds, Cb, lds, L, ib, wc, (const Real *)nullptr, 0, scr);
         trmm_tw(W, ib, Tq, ib, wc, 1, scr);
         gemm_nn_sub(Cb, lds, P, lds, W, ib, L, ib, wc);
         store_cols(XB + (size_t)c0 * nb + q0, nb, Cb, lds, L, wc, 0, 0);
       } else {
-        Copy cp[2] = {{Ct, ldt, XR + (size_t)c0 * nb + q0, nb, ib, wc},
-                      {Cb, lds, XB + (size_t)c0 * nb, nb, L, wc}};
+        Copy<Real> cp[2] = {{Ct, ldt, XR + (size_t)c0 * nb + q0, nb, ib, wc},
+                            {Cb, lds, XB + (size_t)c0 * nb, nb, L, wc}};
         stage(p, sh, cp, 2, phase);
-        gemm_tn(W, ib, P, lds, Cb, lds, L, ib, wc, Ct, ldt, scr);
+        gemm_tn(W, ib, P, lds, Cb, lds, L, ib, wc, (const Real *)Ct, ldt, scr);
         trmm_tw(W, ib, Tq, ib, wc, 1, scr);
         sub_top(Ct, ldt, W, ib, ib, wc);
         gemm_nn_sub(Cb, lds, P, lds, W, ib, L, ib, wc);
@@ -578,9 +626,17 @@ __device__ int pop_ready(const EngineParams &p) {
   }
 }
 
-__global__ void __launch_bounds__(NT, 2) hqr_sched_fp64(EngineParams p) {
-  extern __shared__ __align__(16) double dyn[];
-  __shared__ Shared sh;
+__device__ __forceinline__ unsigned smid() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+  return r;
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(NT, 2) hqr_sched(EngineParams p) {
+  extern __shared__ __align__(16) unsigned char dyn_raw[];
+  Real *dyn = reinterpret_cast<Real *>(dyn_raw);
+  __shared__ Shared<Real> sh;
   if (threadIdx.x == 0) {
     ptx::mbar_init(&sh.bar, 1);
     sh.abort = 0;
@@ -593,12 +649,19 @@ __global__ void __launch_bounds__(NT, 2) hqr_sched_fp64(EngineParams p) {
     const int tid = sh.task;
     if (tid < 0) break;
     const Task t = p.tasks[tid];
+    const Geo<Real> g(p.probs[t.pid]);
+    const uint64_t t_start = (p.trace && threadIdx.x == 0) ? ptx::globaltimer() : 0;
     if (t.op == OP_GEQRT || t.op == OP_TSQRT || t.op == OP_TTQRT)
-      task_panel(p, t, sh, dyn, phase);
+      task_panel(p, g, t, sh, dyn, phase);
     else
-      task_update(p, t, sh, dyn, phase);
+      task_update(p, g, t, sh, dyn, phase);
     __syncthreads();
     if (threadIdx.x == 0) {
+      if (p.trace) {
+        p.trace[3 * (size_t)tid + 0] = t_start;
+        p.trace[3 * (size_t)tid + 1] = ptx::globaltimer();
+        p.trace[3 * (size_t)tid + 2] = ((unsigned long long)blockIdx.x << 32) | smid();
+      }
       ptx::fence_proxy_async();
       __threadfence();
       for (int e = t.succ_begin; e < t.succ_end; ++e) {
@@ -618,16 +681,17 @@ __global__ void __launch_bounds__(NT, 2) hqr_sched_fp64(EngineParams p) {
   }
 }
 
-// Shared memory (bytes) of the scheduler kernel for a configuration.
+// Shared memory (bytes) of the scheduler kernel for a problem configuration.
+template <typename Real>
 inline size_t engine_smem_bytes(int nb, int ib, int w, int wt, int vc) {
-  const int lds = nb + 2, ldt = ib + 2;
+  const int lds = nb + smem_pad<Real>(), ldt = ib + smem_pad<Real>();
   const size_t scr_u = (size_t)(ib * w > NT ? ib * w : NT);
   const size_t scr_p = (size_t)(ib * wt > NT ? ib * wt : NT);
   const size_t upd = (size_t)lds * (2 * w + vc) + (size_t)ib * ib + (size_t)ib * w + scr_u;
   const size_t cbg = (size_t)(lds * wt > ib * ib ? lds * wt : ib * ib);
   const size_t pan = (size_t)lds * ib + (size_t)ldt * (ib + wt) + (size_t)ib * ib + cbg +
                      (size_t)ib * wt + scr_p;
-  return 8 * (upd > pan ? upd : pan);
+  return sizeof(Real) * (upd > pan ? upd : pan);
 }
 
 }  // namespace hqr

@@ -10,7 +10,7 @@
 #include <vector>
 
 #include "../../include/hqr.h"
-#include "engine_fp64.cuh"
+#include "engine.cuh"
 #include "hqr_internal.h"
 
 using namespace hqr;
@@ -26,8 +26,8 @@ bool cuda_ok(cudaError_t e, const char *what) {
   g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
   return false;
 }
-#define CK(call)                                  \
-  do {                                            \
+#define CK(call)                                      \
+  do {                                                \
     if (!cuda_ok((call), #call)) return HQR_ERR_CUDA; \
   } while (0)
 
@@ -85,8 +85,9 @@ int upload_graph(const Graph &g, DevGraph &d) {
 }
 
 // Tile-major packing of a column-major matrix, zero padded to whole tiles.
-__global__ void pack_tiles(const double *__restrict__ A, long long lda, int M, int N, double *__restrict__ ws,
-                           int m, int nb, long long total) {
+template <typename Real>
+__global__ void pack_tiles(const Real *__restrict__ A, long long lda, int M, int N, Real *__restrict__ ws, int m,
+                           int nb, long long total) {
   const long long nb2 = (long long)nb * nb;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -95,29 +96,31 @@ __global__ void pack_tiles(const double *__restrict__ A, long long lda, int M, i
     const int cc = w / nb, rr = w - cc * nb;
     const int ti = (int)(tile % m), tj = (int)(tile / m);
     const int row = ti * nb + rr, col = tj * nb + cc;
-    ws[e] = (row < M && col < N) ? A[(long long)col * lda + row] : 0.0;
+    ws[e] = (row < M && col < N) ? A[(long long)col * lda + row] : Real(0);
   }
 }
 
-// Inverse of pack_tiles for the padded Mp x Np matrix; `upper_only` keeps
-// rows <= col and zeroes the rest (R), limited to rows, cols < lim.
-__global__ void unpack_tiles(const double *__restrict__ ws, int m, int nb, double *__restrict__ out,
-                             long long ld, int rows, int cols, int upper_only) {
+// Inverse of pack_tiles for the leading rows x cols of the padded matrix;
+// `upper_only` keeps rows <= col and zeroes the rest (R).
+template <typename Real>
+__global__ void unpack_tiles(const Real *__restrict__ ws, int m, int nb, Real *__restrict__ out, long long ld,
+                             int rows, int cols, int upper_only) {
   const long long total = (long long)rows * cols;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const int col = (int)(e / rows), row = (int)(e - (long long)col * rows);
     const int ti = row / nb, tj = col / nb;
-    double v = ws[((size_t)tj * m + ti) * nb * nb + (size_t)(col - tj * nb) * nb + (row - ti * nb)];
-    if (upper_only && row > col) v = 0.0;
+    Real v = ws[((size_t)tj * m + ti) * nb * nb + (size_t)(col - tj * nb) * nb + (row - ti * nb)];
+    if (upper_only && row > col) v = 0;
     out[(long long)col * ld + row] = v;
   }
 }
 
 // Right-hand side (M x nrhs) into blocks of nb rows x wa columns: block
 // (r, s) at ((s*m + r)*nb*wa), column-major inside.
-__global__ void pack_rhs(const double *__restrict__ B, long long ldb, int M, int nrhs, double *__restrict__ Bw,
-                         int m, int nb, int wa, long long total) {
+template <typename Real>
+__global__ void pack_rhs(const Real *__restrict__ B, long long ldb, int M, int nrhs, Real *__restrict__ Bw, int m,
+                         int nb, int wa, long long total) {
   const long long bs = (long long)nb * wa;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -126,12 +129,13 @@ __global__ void pack_rhs(const double *__restrict__ B, long long ldb, int M, int
     const int cc = w / nb, rr = w - cc * nb;
     const int r = (int)(blk % m), s = (int)(blk / m);
     const int row = r * nb + rr, col = s * wa + cc;
-    Bw[e] = (row < M && col < nrhs) ? B[(long long)col * ldb + row] : 0.0;
+    Bw[e] = (row < M && col < nrhs) ? B[(long long)col * ldb + row] : Real(0);
   }
 }
 
-__global__ void unpack_rhs(const double *__restrict__ Bw, double *__restrict__ B, long long ldb, int M, int nrhs,
-                           int m, int nb, int wa) {
+template <typename Real>
+__global__ void unpack_rhs(const Real *__restrict__ Bw, Real *__restrict__ B, long long ldb, int M, int nrhs, int m,
+                           int nb, int wa) {
   const long long total = (long long)M * nrhs;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -143,25 +147,26 @@ __global__ void unpack_rhs(const double *__restrict__ Bw, double *__restrict__ B
 
 // Back substitution with the diagonal tile i (nbi x nbi leading part), one
 // CTA per right-hand side; x holds c on entry.
-__global__ void trsv_diag(const double *__restrict__ ws, int m, int nb, int i, int nbi, double *X, long long ldx,
+template <typename Real>
+__global__ void trsv_diag(const Real *__restrict__ ws, int m, int nb, int i, int nbi, Real *X, long long ldx,
                           int *singular) {
-  __shared__ double xs[256];
-  double *x = X + (long long)blockIdx.x * ldx + (long long)i * nb;
-  const double *Rt = ws + ((size_t)i * m + i) * nb * nb;
+  __shared__ Real xs[256];
+  Real *x = X + (long long)blockIdx.x * ldx + (long long)i * nb;
+  const Real *Rt = ws + ((size_t)i * m + i) * nb * nb;
   for (int r = threadIdx.x; r < nbi; r += blockDim.x) xs[r] = x[r];
   __syncthreads();
   for (int r = nbi - 1; r >= 0; --r) {
     if (threadIdx.x == 0) {
-      const double d = Rt[(size_t)r * nb + r];
-      if (d == 0.0) {
+      const Real d = Rt[(size_t)r * nb + r];
+      if (d == Real(0)) {
         atomicExch(singular, 1);
-        xs[r] = 0.0;
+        xs[r] = 0;
       } else {
         xs[r] = xs[r] / d;
       }
     }
     __syncthreads();
-    const double xr = xs[r];
+    const Real xr = xs[r];
     for (int l = threadIdx.x; l < r; l += blockDim.x) xs[l] = fma(-Rt[(size_t)r * nb + l], xr, xs[l]);
     __syncthreads();
   }
@@ -169,77 +174,113 @@ __global__ void trsv_diag(const double *__restrict__ ws, int m, int nb, int i, i
 }
 
 // c[0 : i*nb) -= R[0 : i*nb, columns of tile i] x_i.
-__global__ void trsv_update(const double *__restrict__ ws, int m, int nb, int i, int nbi, double *X,
-                            long long ldx) {
+template <typename Real>
+__global__ void trsv_update(const Real *__restrict__ ws, int m, int nb, int i, int nbi, Real *X, long long ldx) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= i * nb) return;
   const int ti = row / nb, rr = row - ti * nb;
-  const double *Rt = ws + ((size_t)i * m + ti) * nb * nb;
-  const double *x = X + (long long)blockIdx.y * ldx + (long long)i * nb;
-  double s = 0.0;
+  const Real *Rt = ws + ((size_t)i * m + ti) * nb * nb;
+  const Real *x = X + (long long)blockIdx.y * ldx + (long long)i * nb;
+  Real s = 0;
   for (int c = 0; c < nbi; ++c) s = fma(Rt[(size_t)c * nb + rr], x[c], s);
   X[(long long)blockIdx.y * ldx + row] -= s;
 }
 
-int grid_for(int n) { return std::max(1, std::min(4096, (n + 255) / 256)); }
+int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>(4096, (n + 255) / 256)); }
+
+size_t elem_size(int prec) { return prec == HQR_FP64 ? sizeof(double) : sizeof(float); }
+
+// The persistent scheduler instantiation for a storage precision.
+const void *sched_kernel(int prec) {
+  return prec == HQR_FP64 ? (const void *)hqr_sched<double> : (const void *)hqr_sched<float>;
+}
+
+size_t smem_for(int prec, const Problem &P) {
+  const int wmax = std::max(P.w, P.wb);
+  return prec == HQR_FP64 ? engine_smem_bytes<double>(P.nb, P.ib, wmax, P.wt, P.vc)
+                          : engine_smem_bytes<float>(P.nb, P.ib, wmax, P.wt, P.vc);
+}
+
+// CTAs for a launch: every SM filled to the occupancy the kernel allows.
+int ctas_for(int prec, size_t smem, int ntasks, int *grid) {
+  static size_t attr[2] = {0, 0};
+  const void *k = sched_kernel(prec);
+  const int slot = prec == HQR_FP64 ? 0 : 1;
+  if (attr[slot] < smem) {
+    CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr[slot] = smem;
+  }
+  int dev = 0, sms = 0, per_sm = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem));
+  if (per_sm < 1) {
+    g_last_error = "scheduler kernel does not fit on an SM";
+    return HQR_ERR_CUDA;
+  }
+  *grid = std::max(1, std::min(sms * per_sm, ntasks));
+  return HQR_SUCCESS;
+}
+
+int launch_sched(int prec, const EngineParams &p, size_t smem, cudaStream_t s) {
+  int grid = 0;
+  int st = ctas_for(prec, smem, p.ntasks, &grid);
+  if (st) return st;
+  if (prec == HQR_FP64)
+    hqr_sched<double><<<grid, NT, smem, s>>>(p);
+  else
+    hqr_sched<float><<<grid, NT, smem, s>>>(p);
+  CK(cudaGetLastError());
+  g_launches += 1;
+  return HQR_SUCCESS;
+}
+
+// Tuning of the column-slab widths for a tile size and precision.
+void choose_widths(int prec, int nb, int ib, Problem &P) {
+  P.w = std::min(16, nb);
+  P.wb = std::min(16, nb);
+  if (prec == HQR_FP64) {
+    P.wt = nb > 128 ? 8 : std::min(16, nb);
+    P.vc = nb > 128 ? std::min(ib, 8) : std::min(ib, 16);
+  } else {
+    P.wt = std::min(16, nb);
+    P.vc = std::min(ib, 16);
+  }
+}
+
+bool valid_tile_sizes(int prec, int nb, int ib) {
+  if (nb < 8 || nb > 256 || nb % 8) return false;
+  const int align = prec == HQR_FP64 ? 2 : 4;  // rows per 16 bytes
+  if (ib < align || ib % align || nb % ib || (ib > 16 && ib != 32)) return false;
+  return true;
+}
 
 }  // namespace
 
 struct hqr_factors {
   int M = 0, N = 0, Mp = 0, Np = 0, m = 0, n = 0, nb = 0, ib = 0, prec = 0;
-  int w = 0, wt = 0, vc = 0, wa = 0;
-  size_t smem = 0;
-  int grid = 0;
   std::vector<hqr_elim_t> list;
   std::vector<PanelOp> ops;
-  double *dA = nullptr, *dT = nullptr, *dBw = nullptr;
+  Problem prob{};        // host copy of the device descriptor
+  Problem *dprob = nullptr;
+  void *dA = nullptr, *dT = nullptr, *dBw = nullptr;
   size_t bw_cap = 0;
   DevGraph fg;
   std::map<std::pair<int, int>, DevGraph> ag;  // (trans, nslab) -> apply graph
   Ctl *last_ctl = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool timed = false;
+  unsigned long long *dtrace = nullptr;
+  size_t trace_cap = 0;
   int64_t debug_task = -1;
   int debug_base = -1;
 };
 
 namespace {
 
-int ctas_for(const hqr_factors *F, size_t smem, int ntasks, int *grid) {
-  static bool attr_set = false;
-  static size_t attr_smem = 0;
-  if (!attr_set || attr_smem < smem) {
-    CK(cudaFuncSetAttribute(hqr_sched_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_set = true;
-    attr_smem = smem;
-  }
-  int dev = 0, sms = 0, per_sm = 0;
-  CK(cudaGetDevice(&dev));
-  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hqr_sched_fp64, NT, smem));
-  if (per_sm < 1) {
-    g_last_error = "scheduler kernel does not fit on an SM";
-    return HQR_ERR_CUDA;
-  }
-  (void)F;
-  *grid = std::max(1, std::min(sms * per_sm, ntasks));
-  return HQR_SUCCESS;
-}
-
-int run_graph(hqr_factors *F, DevGraph &g, double *C, long long cstride, int w, cudaStream_t s) {
+int run_graph(hqr_factors *F, DevGraph &g, cudaStream_t s) {
   EngineParams p;
-  p.A = F->dA;
-  p.T = F->dT;
-  p.C = C;
-  p.cstride = cstride;
-  p.m = F->m;
-  p.n = F->n;
-  p.nb = F->nb;
-  p.ib = F->ib;
-  p.w = w;
-  p.wt = F->wt;
-  p.vc = F->vc;
-  p.lds = F->nb + 2;
+  p.probs = F->dprob;
   p.tasks = g.tasks;
   p.ntasks = g.ntasks;
   p.succ = g.succ;
@@ -247,26 +288,22 @@ int run_graph(hqr_factors *F, DevGraph &g, double *C, long long cstride, int w, 
   p.slots = g.slots;
   p.ctl = g.ctl;
   p.timeout_ns = g_timeout_ns;
-  const size_t smem = engine_smem_bytes(F->nb, F->ib, w, F->wt, F->vc);
-  int grid = 0;
-  int st = ctas_for(F, smem, g.ntasks, &grid);
-  if (st) return st;
+  p.trace = (F->dtrace && F->trace_cap >= (size_t)g.ntasks) ? F->dtrace : nullptr;
+  const size_t smem = smem_for(F->prec, F->prob);
   CK(cudaMemcpyAsync(g.indeg, g.indeg0, sizeof(int) * g.ntasks, cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpyAsync(g.slots, g.slots0, sizeof(int) * (size_t)kNumQueues * g.ntasks,
-                     cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(g.slots, g.slots0, sizeof(int) * (size_t)kNumQueues * g.ntasks, cudaMemcpyDeviceToDevice,
+                     s));
   CK(cudaMemcpyAsync(g.ctl, g.ctl0, sizeof(Ctl), cudaMemcpyDeviceToDevice, s));
   if (!F->ev0) {
     CK(cudaEventCreate(&F->ev0));
     CK(cudaEventCreate(&F->ev1));
   }
   CK(cudaEventRecord(F->ev0, s));
-  hqr_sched_fp64<<<grid, NT, smem, s>>>(p);
-  CK(cudaGetLastError());
+  int st = launch_sched(F->prec, p, smem, s);
+  if (st) return st;
   CK(cudaEventRecord(F->ev1, s));
   F->timed = true;
-  g_launches += 1;
   F->last_ctl = g.ctl;
-  F->grid = grid;
   return HQR_SUCCESS;
 }
 
@@ -279,12 +316,25 @@ int read_status(hqr_factors *F, cudaStream_t s) {
   return HQR_SUCCESS;
 }
 
-int pack_a(hqr_factors *F, const double *dA, int lda, cudaStream_t s) {
+int pack_a(hqr_factors *F, const void *dA, int lda, cudaStream_t s) {
   const long long total = (long long)F->Mp * F->Np;
-  pack_tiles<<<grid_for((int)std::min<long long>(total, 1 << 30)), 256, 0, s>>>(dA, lda, F->M, F->N, F->dA,
-                                                                                 F->m, F->nb, total);
+  if (F->prec == HQR_FP64)
+    pack_tiles<double><<<grid_for(total), 256, 0, s>>>((const double *)dA, lda, F->M, F->N, (double *)F->dA,
+                                                       F->m, F->nb, total);
+  else
+    pack_tiles<float><<<grid_for(total), 256, 0, s>>>((const float *)dA, lda, F->M, F->N, (float *)F->dA, F->m,
+                                                      F->nb, total);
   CK(cudaGetLastError());
   g_launches += 1;
+  return HQR_SUCCESS;
+}
+
+int push_problem(hqr_factors *F) {
+  F->prob.A = F->dA;
+  F->prob.T = F->dT;
+  F->prob.B = F->dBw;
+  if (!F->dprob) CK(cudaMalloc(&F->dprob, sizeof(Problem)));
+  CK(cudaMemcpy(F->dprob, &F->prob, sizeof(Problem), cudaMemcpyHostToDevice));
   return HQR_SUCCESS;
 }
 
@@ -320,12 +370,11 @@ int hqr_geqrf(const void *dA, int M, int N, int lda, int prec, int nb, int ib, c
   if (M < 1) return -2;
   if (N < 1 || N > M) return -3;
   if (lda < M) return -4;
-  if (prec != HQR_FP64) return -5;
+  if (prec != HQR_FP64 && prec != HQR_FP32) return -5;
   if (nb < 8 || nb > 256 || nb % 8) return -6;
-  if (ib < 2 || ib % 2 || nb % ib || (ib > 16 && ib != 32)) return -7;
+  if (!valid_tile_sizes(prec, nb, ib)) return -7;
   if (!out) return -10;
   *out = nullptr;
-  cudaStream_t s = (cudaStream_t)stream;
   hqr_factors *F = new (std::nothrow) hqr_factors();
   if (!F) return HQR_ERR_NOMEM;
   F->M = M;
@@ -337,11 +386,11 @@ int hqr_geqrf(const void *dA, int M, int N, int lda, int prec, int nb, int ib, c
   F->n = (N + nb - 1) / nb;
   F->Mp = F->m * nb;
   F->Np = F->n * nb;
-  F->w = std::min(16, nb);
-  F->wt = nb > 128 ? 8 : std::min(16, nb);
-  F->vc = nb > 128 ? std::min(ib, 8) : std::min(ib, 16);
-  F->wa = std::min(16, nb);
-  // elimination list
+  F->prob.m = F->m;
+  F->prob.n = F->n;
+  F->prob.nb = nb;
+  F->prob.ib = ib;
+  choose_widths(prec, nb, ib, F->prob);
   if (list) {
     if (hqr_validate_list(F->m, F->n, list, count) != HQR_SUCCESS) {
       delete F;
@@ -352,22 +401,23 @@ int hqr_geqrf(const void *dA, int M, int N, int lda, int prec, int nb, int ib, c
     size_t cnt = 0;
     hqr_elim_list(F->m, F->n, 4, 1, HQR_GREEDY, HQR_GREEDY, nullptr, 0, &cnt);
     F->list.resize(cnt);
-    int st = hqr_elim_list(F->m, F->n, 4, 1, HQR_GREEDY, HQR_GREEDY, F->list.data(), cnt, &cnt);
-    if (st) {
+    if (hqr_elim_list(F->m, F->n, 4, 1, HQR_GREEDY, HQR_GREEDY, F->list.data(), cnt, &cnt)) {
       delete F;
       return HQR_ERR_INTERNAL;
     }
   }
   F->ops = expand_ops(F->list.data(), F->list.size(), F->m, F->n);
-  Graph g = build_factor_graph(F->ops, F->m, F->n, nb, F->w);
+  Graph g = build_factor_graph(F->ops, F->m, F->n, nb, F->prob.w);
   int st = upload_graph(g, F->fg);
+  const size_t es = elem_size(prec);
   if (!st) {
     const size_t tsz = (size_t)F->m * F->n * 2 * ib * nb;
-    if (!cuda_ok(cudaMalloc(&F->dA, sizeof(double) * (size_t)F->Mp * F->Np), "cudaMalloc(A)") ||
-        !cuda_ok(cudaMalloc(&F->dT, sizeof(double) * tsz), "cudaMalloc(T)") ||
-        !cuda_ok(cudaMemsetAsync(F->dT, 0, sizeof(double) * tsz, s), "memset(T)"))
+    if (!cuda_ok(cudaMalloc(&F->dA, es * (size_t)F->Mp * F->Np), "cudaMalloc(A)") ||
+        !cuda_ok(cudaMalloc(&F->dT, es * tsz), "cudaMalloc(T)") ||
+        !cuda_ok(cudaMemset(F->dT, 0, es * tsz), "memset(T)"))
       st = HQR_ERR_NOMEM;
   }
+  if (!st) st = push_problem(F);
   if (!st) st = hqr_refactor(F, dA, lda, stream);
   if (st) {
     hqr_factors_free(F);
@@ -383,9 +433,9 @@ int hqr_refactor_async(hqr_factors *F, const void *dA, int lda, void *stream) {
   if (lda < F->M) return -3;
   g_launches = 0;
   cudaStream_t s = (cudaStream_t)stream;
-  int st = pack_a(F, (const double *)dA, lda, s);
+  int st = pack_a(F, dA, lda, s);
   if (st) return st;
-  return run_graph(F, F->fg, F->dA, (long long)F->nb * F->nb, F->w, s);
+  return run_graph(F, F->fg, s);
 }
 
 int hqr_refactor(hqr_factors *F, const void *dA, int lda, void *stream) {
@@ -404,7 +454,13 @@ int hqr_get_r(const hqr_factors *F, void *dR, int ldr, void *stream) {
   if (!dR) return -2;
   if (ldr < F->N) return -3;
   cudaStream_t s = (cudaStream_t)stream;
-  unpack_tiles<<<grid_for(F->N * F->N), 256, 0, s>>>(F->dA, F->m, F->nb, (double *)dR, ldr, F->N, F->N, 1);
+  const long long total = (long long)F->N * F->N;
+  if (F->prec == HQR_FP64)
+    unpack_tiles<double><<<grid_for(total), 256, 0, s>>>((const double *)F->dA, F->m, F->nb, (double *)dR, ldr,
+                                                         F->N, F->N, 1);
+  else
+    unpack_tiles<float><<<grid_for(total), 256, 0, s>>>((const float *)F->dA, F->m, F->nb, (float *)dR, ldr, F->N,
+                                                        F->N, 1);
   CK(cudaGetLastError());
   return HQR_SUCCESS;
 }
@@ -414,8 +470,13 @@ int hqr_get_tiles(const hqr_factors *F, void *dOut, int ld, void *stream) {
   if (!dOut) return -2;
   if (ld < F->Mp) return -3;
   cudaStream_t s = (cudaStream_t)stream;
-  unpack_tiles<<<grid_for(F->Mp * F->Np), 256, 0, s>>>(F->dA, F->m, F->nb, (double *)dOut, ld, F->Mp, F->Np,
-                                                       0);
+  const long long total = (long long)F->Mp * F->Np;
+  if (F->prec == HQR_FP64)
+    unpack_tiles<double><<<grid_for(total), 256, 0, s>>>((const double *)F->dA, F->m, F->nb, (double *)dOut, ld,
+                                                         F->Mp, F->Np, 0);
+  else
+    unpack_tiles<float><<<grid_for(total), 256, 0, s>>>((const float *)F->dA, F->m, F->nb, (float *)dOut, ld,
+                                                        F->Mp, F->Np, 0);
   CK(cudaGetLastError());
   return HQR_SUCCESS;
 }
@@ -424,7 +485,7 @@ int hqr_get_t(const hqr_factors *F, void *dT, void *stream) {
   if (!F) return -1;
   if (!dT) return -2;
   const size_t tsz = (size_t)F->m * F->n * 2 * F->ib * F->nb;
-  CK(cudaMemcpyAsync(dT, F->dT, sizeof(double) * tsz, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  CK(cudaMemcpyAsync(dT, F->dT, elem_size(F->prec) * tsz, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
   return HQR_SUCCESS;
 }
 
@@ -434,6 +495,34 @@ int hqr_kernel_ms(hqr_factors *F, float *ms) {
   if (!F->timed) return HQR_ERR_INTERNAL;
   CK(cudaEventSynchronize(F->ev1));
   CK(cudaEventElapsedTime(ms, F->ev0, F->ev1));
+  return HQR_SUCCESS;
+}
+
+int hqr_trace(hqr_factors *F, int enable, uint64_t *host, size_t cap, size_t *count) {
+  if (!F) return -1;
+  if (enable == 1) {
+    const size_t need = (size_t)F->fg.ntasks;
+    if (F->trace_cap < need) {
+      cudaFree(F->dtrace);
+      F->dtrace = nullptr;
+      F->trace_cap = 0;
+      if (!cuda_ok(cudaMalloc(&F->dtrace, 3 * sizeof(unsigned long long) * need), "cudaMalloc(trace)"))
+        return HQR_ERR_NOMEM;
+      F->trace_cap = need;
+    }
+    return HQR_SUCCESS;
+  }
+  if (enable == 0) {
+    cudaFree(F->dtrace);
+    F->dtrace = nullptr;
+    F->trace_cap = 0;
+    return HQR_SUCCESS;
+  }
+  if (!count) return -5;
+  *count = F->trace_cap;
+  if (!F->dtrace) return HQR_SUCCESS;
+  if (!host || cap < 3 * F->trace_cap) return HQR_ERR_CAPACITY;
+  CK(cudaMemcpy(host, F->dtrace, 3 * sizeof(unsigned long long) * F->trace_cap, cudaMemcpyDeviceToHost));
   return HQR_SUCCESS;
 }
 
@@ -459,15 +548,19 @@ int hqr_apply_q(hqr_factors *F, int trans, void *dB, int ldb, int nrhs, void *st
   if (nrhs == 0) return HQR_SUCCESS;
   g_launches = 0;
   cudaStream_t s = (cudaStream_t)stream;
-  const int wa = F->wa;
+  const int wa = F->prob.wb;
   const int nslab = (nrhs + wa - 1) / wa;
   const size_t need = (size_t)F->Mp * nslab * wa;
+  const size_t es = elem_size(F->prec);
   if (need > F->bw_cap) {
+    CK(cudaStreamSynchronize(s));
     cudaFree(F->dBw);
     F->dBw = nullptr;
     F->bw_cap = 0;
-    if (!cuda_ok(cudaMalloc(&F->dBw, sizeof(double) * need), "cudaMalloc(B)")) return HQR_ERR_NOMEM;
+    if (!cuda_ok(cudaMalloc(&F->dBw, es * need), "cudaMalloc(B)")) return HQR_ERR_NOMEM;
     F->bw_cap = need;
+    int st = push_problem(F);
+    if (st) return st;
   }
   auto key = std::make_pair(trans, nslab);
   auto it = F->ag.find(key);
@@ -482,14 +575,23 @@ int hqr_apply_q(hqr_factors *F, int trans, void *dB, int ldb, int nrhs, void *st
     it = F->ag.emplace(key, d).first;
   }
   const long long total = (long long)need;
-  pack_rhs<<<grid_for((int)std::min<long long>(total, 1 << 30)), 256, 0, s>>>(
-      (const double *)dB, ldb, F->M, nrhs, F->dBw, F->m, F->nb, wa, total);
+  if (F->prec == HQR_FP64)
+    pack_rhs<double><<<grid_for(total), 256, 0, s>>>((const double *)dB, ldb, F->M, nrhs, (double *)F->dBw, F->m,
+                                                     F->nb, wa, total);
+  else
+    pack_rhs<float><<<grid_for(total), 256, 0, s>>>((const float *)dB, ldb, F->M, nrhs, (float *)F->dBw, F->m,
+                                                    F->nb, wa, total);
   CK(cudaGetLastError());
   g_launches += 1;
-  int st = run_graph(F, it->second, F->dBw, (long long)F->nb * wa, wa, s);
+  int st = run_graph(F, it->second, s);
   if (st) return st;
-  unpack_rhs<<<grid_for((int)std::min<long long>((long long)F->M * nrhs, 1 << 30)), 256, 0, s>>>(
-      F->dBw, (double *)dB, ldb, F->M, nrhs, F->m, F->nb, wa);
+  const long long tot2 = (long long)F->M * nrhs;
+  if (F->prec == HQR_FP64)
+    unpack_rhs<double><<<grid_for(tot2), 256, 0, s>>>((const double *)F->dBw, (double *)dB, ldb, F->M, nrhs, F->m,
+                                                      F->nb, wa);
+  else
+    unpack_rhs<float><<<grid_for(tot2), 256, 0, s>>>((const float *)F->dBw, (float *)dB, ldb, F->M, nrhs, F->m,
+                                                     F->nb, wa);
   CK(cudaGetLastError());
   g_launches += 1;
   return read_status(F, s);
@@ -506,17 +608,17 @@ int hqr_gels(const void *dA, int M, int N, int lda, const void *db, int ldb, int
   hqr_factors *F = nullptr;
   int st = hqr_geqrf(dA, M, N, lda, prec, nb, ib, list, count, &F, stream);
   if (st) return st > 0 ? st : (st <= -5 ? st - 5 : st);
-  double *c = nullptr;
+  const size_t es = elem_size(prec);
+  void *c = nullptr;
   int *dsing = nullptr;
   int64_t launches = g_launches;
   do {
-    if (!cuda_ok(cudaMalloc(&c, sizeof(double) * (size_t)M * nrhs), "cudaMalloc(c)") ||
+    if (!cuda_ok(cudaMalloc(&c, es * (size_t)M * nrhs), "cudaMalloc(c)") ||
         !cuda_ok(cudaMalloc(&dsing, sizeof(int)), "cudaMalloc(flag)")) {
       st = HQR_ERR_NOMEM;
       break;
     }
-    if (!cuda_ok(cudaMemcpy2DAsync(c, sizeof(double) * M, db, sizeof(double) * ldb, sizeof(double) * M, nrhs,
-                                   cudaMemcpyDeviceToDevice, s),
+    if (!cuda_ok(cudaMemcpy2DAsync(c, es * M, db, es * ldb, es * M, nrhs, cudaMemcpyDeviceToDevice, s),
                  "copy b") ||
         !cuda_ok(cudaMemsetAsync(dsing, 0, sizeof(int), s), "memset")) {
       st = HQR_ERR_CUDA;
@@ -527,17 +629,18 @@ int hqr_gels(const void *dA, int M, int N, int lda, const void *db, int ldb, int
     if (st) break;
     for (int i = F->n - 1; i >= 0; --i) {
       const int nbi = std::min(F->nb, N - i * F->nb);
-      trsv_diag<<<nrhs, 256, 0, s>>>(F->dA, F->m, F->nb, i, nbi, c, M, dsing);
-      launches += 1;
-      if (i > 0) {
-        dim3 gr((i * F->nb + 255) / 256, nrhs);
-        trsv_update<<<gr, 256, 0, s>>>(F->dA, F->m, F->nb, i, nbi, c, M);
-        launches += 1;
+      dim3 gr((i * F->nb + 255) / 256, nrhs);
+      if (prec == HQR_FP64) {
+        trsv_diag<double><<<nrhs, 256, 0, s>>>((const double *)F->dA, F->m, F->nb, i, nbi, (double *)c, M, dsing);
+        if (i > 0) trsv_update<double><<<gr, 256, 0, s>>>((const double *)F->dA, F->m, F->nb, i, nbi, (double *)c, M);
+      } else {
+        trsv_diag<float><<<nrhs, 256, 0, s>>>((const float *)F->dA, F->m, F->nb, i, nbi, (float *)c, M, dsing);
+        if (i > 0) trsv_update<float><<<gr, 256, 0, s>>>((const float *)F->dA, F->m, F->nb, i, nbi, (float *)c, M);
       }
+      launches += i > 0 ? 2 : 1;
     }
     if (!cuda_ok(cudaGetLastError(), "trsv") ||
-        !cuda_ok(cudaMemcpy2DAsync(dx, sizeof(double) * ldx, c, sizeof(double) * M, sizeof(double) * N, nrhs,
-                                   cudaMemcpyDeviceToDevice, s),
+        !cuda_ok(cudaMemcpy2DAsync(dx, es * ldx, c, es * M, es * N, nrhs, cudaMemcpyDeviceToDevice, s),
                  "copy x")) {
       st = HQR_ERR_CUDA;
       break;
@@ -561,13 +664,11 @@ int hqr_debug_block_task(hqr_factors *F, int64_t task, int extra) {
   if (!F) return -1;
   if (task < 0 || task >= F->fg.ntasks) return -2;
   if (extra < 0) return -3;
-  int base = 0;
-  // the pristine in-degree lives on the device; keep the original on the host
-  if (F->debug_task != task || F->debug_base < 0) {
-    CK(cudaMemcpy(&base, F->fg.indeg0 + task, sizeof(int), cudaMemcpyDeviceToHost));
-    if (F->debug_task >= 0 && F->debug_task != task) return HQR_ERR_INTERNAL;
+  if (F->debug_task >= 0 && F->debug_task != task) return HQR_ERR_INTERNAL;
+  if (F->debug_task < 0) {
+    // keep the task's true in-degree on the host to restore it later
+    CK(cudaMemcpy(&F->debug_base, F->fg.indeg0 + task, sizeof(int), cudaMemcpyDeviceToHost));
     F->debug_task = task;
-    F->debug_base = base;
   }
   const int v = F->debug_base + extra;
   CK(cudaMemcpy(F->fg.indeg0 + task, &v, sizeof(int), cudaMemcpyHostToDevice));
@@ -585,6 +686,8 @@ void hqr_factors_free(hqr_factors *F) {
   cudaFree(F->dA);
   cudaFree(F->dT);
   cudaFree(F->dBw);
+  cudaFree(F->dprob);
+  cudaFree(F->dtrace);
   if (F->ev0) cudaEventDestroy(F->ev0);
   if (F->ev1) cudaEventDestroy(F->ev1);
   delete F;
@@ -634,6 +737,7 @@ struct NaHost {
   int state[kNaMaxM], tri[kNaMaxM];
   PanelOp ops[kNaMaxOps];
   Ctl ctl;
+  Problem prob;
   int ntasks, nedges, ndeps, overflow;
   size_t pend_w[2 * kNaMaxSlabs + 8], pend_r[8];
   int npw, npr;
@@ -701,7 +805,8 @@ Task na_task(int op, int prio, int i, int r, int k, int j, int c0, int cw) {
   t.op = (int8_t)op;
   t.prio = (int8_t)prio;
   t.trans = 1;
-  t.pad = 0;
+  t.tgt = 0;
+  t.pid = 0;
   t.i = i;
   t.r = r;
   t.k = k;
@@ -873,7 +978,8 @@ extern "C" int hqr_geqrf_r_noalloc(const void *dA, int M, int N, int lda, int nb
   const size_t d_bytes = na_align(sizeof(int) * nt);
   const size_t q_bytes = na_align(sizeof(int) * kNumQueues * nt);
   const size_t c_bytes = na_align(sizeof(Ctl));
-  if (a_bytes + t_bytes + k_bytes + s_bytes + d_bytes + q_bytes + c_bytes > kNaScratchBytes)
+  const size_t p_bytes = na_align(sizeof(Problem));
+  if (a_bytes + t_bytes + k_bytes + s_bytes + d_bytes + q_bytes + c_bytes + p_bytes > kNaScratchBytes)
     return HQR_ERR_TOO_LARGE;
   unsigned char *base = (unsigned char *)g_na_dev_ptr[dev];
   double *dws = (double *)base;
@@ -883,29 +989,32 @@ extern "C" int hqr_geqrf_r_noalloc(const void *dA, int M, int N, int lda, int nb
   int *dindeg = (int *)(base + a_bytes + t_bytes + k_bytes + s_bytes);
   int *dslots = (int *)(base + a_bytes + t_bytes + k_bytes + s_bytes + d_bytes);
   Ctl *dctl = (Ctl *)(base + a_bytes + t_bytes + k_bytes + s_bytes + d_bytes + q_bytes);
+  Problem *dprob = (Problem *)(base + a_bytes + t_bytes + k_bytes + s_bytes + d_bytes + q_bytes + c_bytes);
+  g_na.prob.A = dws;
+  g_na.prob.T = dT;
+  g_na.prob.B = nullptr;
+  g_na.prob.m = m;
+  g_na.prob.n = n;
+  g_na.prob.nb = nb;
+  g_na.prob.ib = ib;
+  g_na.prob.w = w;
+  g_na.prob.wt = wt;
+  g_na.prob.vc = vc;
+  g_na.prob.wb = w;
   if (cudaMemcpyAsync(dtasks, g_na.tasks, sizeof(Task) * nt, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       (g_na.nedges > 0 &&
        cudaMemcpyAsync(dsucc, g_na.succ, sizeof(int) * g_na.nedges, cudaMemcpyHostToDevice, s) != cudaSuccess) ||
       cudaMemcpyAsync(dindeg, g_na.indeg, sizeof(int) * nt, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(dslots, g_na.slots, sizeof(int) * kNumQueues * nt, cudaMemcpyHostToDevice, s) !=
           cudaSuccess ||
-      cudaMemcpyAsync(dctl, &g_na.ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      cudaMemcpyAsync(dctl, &g_na.ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(dprob, &g_na.prob, sizeof(Problem), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return HQR_ERR_CUDA;
   const long long total = (long long)m * nb * n * nb;
-  pack_tiles<<<grid_for((int)total), 256, 0, s>>>((const double *)dA, lda, M, N, dws, m, nb, total);
+  pack_tiles<double><<<grid_for(total), 256, 0, s>>>((const double *)dA, lda, M, N, (double *)dws, m, nb, total);
   EngineParams p;
-  p.A = dws;
-  p.T = dT;
-  p.C = dws;
-  p.cstride = (long long)nb * nb;
-  p.m = m;
-  p.n = n;
-  p.nb = nb;
-  p.ib = ib;
-  p.w = w;
-  p.wt = wt;
-  p.vc = vc;
-  p.lds = nb + 2;
+  p.probs = dprob;
+  p.trace = nullptr;
   p.tasks = dtasks;
   p.ntasks = nt;
   p.succ = dsucc;
@@ -913,16 +1022,17 @@ extern "C" int hqr_geqrf_r_noalloc(const void *dA, int M, int N, int lda, int nb
   p.slots = dslots;
   p.ctl = dctl;
   p.timeout_ns = g_timeout_ns;
-  const size_t smem = engine_smem_bytes(nb, ib, w, wt, vc);
+  const size_t smem = engine_smem_bytes<double>(nb, ib, w, wt, vc);
   int sms = 0, per_sm = 0;
-  if (cudaFuncSetAttribute(hqr_sched_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+  if (cudaFuncSetAttribute(hqr_sched<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
           cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hqr_sched_fp64, NT, smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hqr_sched<double>, NT, smem) != cudaSuccess ||
       per_sm < 1)
     return HQR_ERR_CUDA;
-  hqr_sched_fp64<<<std::max(1, std::min(sms * per_sm, nt)), NT, smem, s>>>(p);
-  unpack_tiles<<<grid_for(N * N), 256, 0, s>>>(dws, m, nb, (double *)dR, ldr, N, N, 1);
+  hqr_sched<double><<<std::max(1, std::min(sms * per_sm, nt)), NT, smem, s>>>(p);
+  unpack_tiles<double><<<grid_for((long long)N * N), 256, 0, s>>>((const double *)dws, m, nb, (double *)dR, ldr, N,
+                                                                 N, 1);
   if (cudaGetLastError() != cudaSuccess) return HQR_ERR_CUDA;
   if (cudaMemcpyAsync(&g_na.ctl, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)

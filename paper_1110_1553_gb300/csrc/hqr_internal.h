@@ -30,16 +30,17 @@ struct Task {
   int8_t op;
   int8_t prio;
   int8_t trans;   // apply Q^T (1) or Q (0); factorization tasks use 1
-  int8_t pad;
+  int8_t tgt;     // update target: 0 = tiles of the matrix, 1 = right-hand-side blocks
   int32_t i;      // killed row (TS/TT), or the row of GEQRT/UNMQR
   int32_t r;      // killer row (TS/TT); equals i for GEQRT/UNMQR
   int32_t k;      // panel
   int32_t j;      // target tile column (updates) or right-hand-side block
-  int32_t c0;     // first column of the slab inside the target tile
+  int32_t c0;     // first column of the slab inside the target block
   int32_t cw;     // slab width
+  int32_t pid;    // problem index (several problems can share one graph)
   int32_t succ_begin, succ_end;  // successor range in the CSR array
 };
-static_assert(sizeof(Task) == 36, "Task layout");
+static_assert(sizeof(Task) == 40, "Task layout");
 
 // A task graph ready for upload: tasks in a topological order, successor
 // lists (CSR), in-degrees and per-queue initial ready lists.
@@ -63,11 +64,15 @@ std::vector<PanelOp> expand_ops(const hqr_elim_t *list, size_t count, int m, int
 
 // Factorization graph: every op expanded into its panel task and its update
 // tasks over the tile columns j > k, each split into column slabs of width w.
-Graph build_factor_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int w);
+Graph build_factor_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int w, int pid = 0);
 
 // Q^T (trans = 1) or Q (trans = 0) applied to a right-hand side split into
 // row tiles and `nslab` column slabs of width w: the update kernels replayed
 // forward or backwards.
-Graph build_apply_graph(const std::vector<PanelOp> &ops, int m, int nslab, int w, int trans);
+Graph build_apply_graph(const std::vector<PanelOp> &ops, int m, int nslab, int w, int trans, int pid = 0);
+
+// Append graph g to `into` (its task ids and successor lists renumbered);
+// the two graphs stay independent.
+void append_graph(Graph &into, const Graph &g);
 
 }  // namespace hqr

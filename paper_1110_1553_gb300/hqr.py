@@ -19,7 +19,7 @@ from . import _build
 FLAT, BINARY, GREEDY, FIBONACCI = 0, 1, 2, 3
 TREES = {"flat": FLAT, "binary": BINARY, "greedy": GREEDY, "fibonacci": FIBONACCI}
 TS, TT = 0, 1
-FP64 = 0
+FP64, FP32 = 0, 1
 
 (SUCCESS, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_CAPACITY, ERR_INVALID_LIST, ERR_SINGULAR, ERR_INTERNAL,
  ERR_TOO_LARGE) = range(9)
@@ -28,7 +28,7 @@ ELIM_DTYPE = np.dtype([("k", np.int32), ("i", np.int32), ("killer", np.int32), (
                        ("level", np.int32), ("step", np.int32)])
 
 EXPORTS = ["hqr_elim_list", "hqr_validate_list", "hqr_geqrf", "hqr_refactor", "hqr_refactor_async",
-           "hqr_status", "hqr_get_r", "hqr_get_tiles", "hqr_get_t", "hqr_factors_info", "hqr_kernel_ms", "hqr_apply_q",
+           "hqr_status", "hqr_get_r", "hqr_get_tiles", "hqr_get_t", "hqr_factors_info", "hqr_kernel_ms", "hqr_trace", "hqr_apply_q",
            "hqr_gels", "hqr_geqrf_r_noalloc", "hqr_debug_block_task", "hqr_factors_free", "hqr_set_timeout_ms", "hqr_strerror", "hqr_last_error",
            "hqr_last_launches"]
 
@@ -76,6 +76,7 @@ def load(build_if_missing=False):
     ip = ctypes.POINTER(i32)
     lib.hqr_factors_info.argtypes = [vp, ip, ip, ip, ip, ip, ip, ctypes.POINTER(i64)]
     lib.hqr_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    lib.hqr_trace.argtypes = [vp, i32, vp, sz, ctypes.POINTER(sz)]
     lib.hqr_apply_q.argtypes = [vp, i32, vp, i32, i32, vp]
     lib.hqr_gels.argtypes = [vp, i32, i32, i32, vp, i32, i32, vp, i32, i32, i32, i32, vp, sz, vp]
     lib.hqr_geqrf_r_noalloc.argtypes = [vp, i32, i32, i32, i32, i32, vp, sz, vp, i32, vp]
@@ -154,14 +155,23 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def colmajor(A):
-    """A column-major view or copy of a 2-D (or 1-D) float64 CUDA tensor.
-    Returns (tensor, ld)."""
+def prec_of(A):
     torch = _torch()
+    if A.dtype == torch.float64:
+        return FP64
+    if A.dtype == torch.float32:
+        return FP32
+    raise TypeError("expected a float64 or float32 CUDA tensor")
+
+
+def colmajor(A):
+    """A column-major view or copy of a 2-D (or 1-D) float64/float32 CUDA
+    tensor. Returns (tensor, ld)."""
     if A.dim() == 1:
         A = A.reshape(-1, 1)
-    if not A.is_cuda or A.dtype != torch.float64:
-        raise TypeError("expected a float64 CUDA tensor")
+    prec_of(A)
+    if not A.is_cuda:
+        raise TypeError("expected a CUDA tensor")
     M = A.shape[0]
     if A.stride(0) == 1 and (A.shape[1] == 1 or A.stride(1) >= max(M, 1)):
         return A, max(A.stride(1) if A.shape[1] > 1 else M, 1)
@@ -169,17 +179,18 @@ def colmajor(A):
     return C, M
 
 
-def empty_colmajor(M, N, device="cuda"):
+def empty_colmajor(M, N, device="cuda", dtype=None):
     torch = _torch()
-    return torch.empty((N, M), dtype=torch.float64, device=device).t()
+    return torch.empty((N, M), dtype=dtype or torch.float64, device=device).t()
 
 
 class Factors:
     """A factorization A = Q R made by ``geqrf`` (owns the library object)."""
 
-    def __init__(self, handle, M, N):
+    def __init__(self, handle, M, N, dtype):
         self._h = handle
         self.M, self.N = M, N
+        self.dtype = dtype
         lib = load()
         vals = [ctypes.c_int(0) for _ in range(6)]
         nt = ctypes.c_int64(0)
@@ -216,17 +227,34 @@ class Factors:
         _check(load().hqr_kernel_ms(self._h, ctypes.byref(ms)), "hqr_kernel_ms")
         return ms.value
 
+    def trace(self, enable=None):
+        """enable=True/False switches per-task tracing; with no argument,
+        returns the last run's records as an (ntasks, 3) uint64 array
+        (start ns, end ns, CTA << 32 | SM)."""
+        lib = load()
+        cnt = ctypes.c_size_t(0)
+        if enable is not None:
+            _check(lib.hqr_trace(self._h, 1 if enable else 0, None, 0, ctypes.byref(cnt)), "hqr_trace")
+            return None
+        st = lib.hqr_trace(self._h, -1, None, 0, ctypes.byref(cnt))
+        if st not in (0, ERR_CAPACITY):
+            _check(st, "hqr_trace")
+        out = np.zeros((cnt.value, 3), dtype=np.uint64)
+        if cnt.value:
+            _check(lib.hqr_trace(self._h, -1, out.ctypes.data, out.size, ctypes.byref(cnt)), "hqr_trace")
+        return out
+
     def status(self, stream=None):
         return load().hqr_status(self._h, _stream_ptr(stream))
 
     def R(self, stream=None):
-        R = empty_colmajor(self.N, self.N)
+        R = empty_colmajor(self.N, self.N, dtype=self.dtype)
         _check(load().hqr_get_r(self._h, ctypes.c_void_p(R.data_ptr()), self.N, _stream_ptr(stream)),
                "hqr_get_r")
         return R
 
     def tiles(self, stream=None):
-        X = empty_colmajor(self.Mp, self.Np)
+        X = empty_colmajor(self.Mp, self.Np, dtype=self.dtype)
         _check(load().hqr_get_tiles(self._h, ctypes.c_void_p(X.data_ptr()), self.Mp, _stream_ptr(stream)),
                "hqr_get_tiles")
         return X
@@ -235,7 +263,7 @@ class Factors:
         """All T factors, shape (n, m, 2, nb, ib): [k, i, which] is the
         ib x nb column-major array of tile (i, k) (which 0: GEQRT, 1: kill)."""
         torch = _torch()
-        T = torch.empty((self.n, self.m, 2, self.nb, self.ib), dtype=torch.float64, device="cuda")
+        T = torch.empty((self.n, self.m, 2, self.nb, self.ib), dtype=self.dtype, device="cuda")
         _check(load().hqr_get_t(self._h, ctypes.c_void_p(T.data_ptr()), _stream_ptr(stream)), "hqr_get_t")
         return T
 
@@ -266,11 +294,11 @@ def geqrf(A, nb, ib, records=None, stream=None):
     M, N = A.shape
     ptr, cnt, keep = _list_arg(records)
     h = ctypes.c_void_p(0)
-    st = load().hqr_geqrf(ctypes.c_void_p(A.data_ptr()), M, N, lda, FP64, nb, ib, ptr, cnt, ctypes.byref(h),
-                          _stream_ptr(stream))
+    st = load().hqr_geqrf(ctypes.c_void_p(A.data_ptr()), M, N, lda, prec_of(A), nb, ib, ptr, cnt,
+                          ctypes.byref(h), _stream_ptr(stream))
     del keep
     _check(st, "hqr_geqrf")
-    return Factors(h, M, N)
+    return Factors(h, M, N, A.dtype)
 
 
 def gels(A, b, nb, ib, records=None, stream=None):
@@ -280,10 +308,10 @@ def gels(A, b, nb, ib, records=None, stream=None):
     vec = b.dim() == 1
     bc, ldb = colmajor(b)
     nrhs = bc.shape[1]
-    x = empty_colmajor(N, nrhs)
+    x = empty_colmajor(N, nrhs, dtype=A.dtype)
     ptr, cnt, keep = _list_arg(records)
     st = load().hqr_gels(ctypes.c_void_p(A.data_ptr()), M, N, lda, ctypes.c_void_p(bc.data_ptr()), ldb, nrhs,
-                         ctypes.c_void_p(x.data_ptr()), N, FP64, nb, ib, ptr, cnt, _stream_ptr(stream))
+                         ctypes.c_void_p(x.data_ptr()), N, prec_of(A), nb, ib, ptr, cnt, _stream_ptr(stream))
     del keep
     _check(st, "hqr_gels")
     return x[:, 0] if vec else x

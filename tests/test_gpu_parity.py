@@ -203,3 +203,39 @@ def test_device_wait_times_out_instead_of_hanging():
         hqr.set_timeout_ms(20000)
     Fg.refactor(A)
     assert torch.equal(Fg.tiles(), good)
+
+
+# ---------------------------------------------------------------- FP32 --
+# FP32 storage and arithmetic against the FP64 oracle run on the same
+# (float-rounded) input: R within 5e-6 ||A||_F, Q^T B within 5e-6 ||B||.
+
+@pytest.mark.parametrize("nb,ib", [(16, 4), (64, 16), (256, 32)])
+@pytest.mark.parametrize("shape,a,p", [((1, 1), 1, 1), ((2, 1), 2, 1), ((2, 1), 1, 1), ((2, 2), 2, 1),
+                                       ((2, 2), 1, 1), ((3, 2), 1, 2)])
+def test_each_kernel_fp32(nb, ib, shape, a, p):
+    m, n = shape
+    A = inputs.gaussian(m * nb, n * nb, seed=300 + nb + 7 * m + n + a).astype(np.float32)
+    recs = hqr_elim_list(m, n, a, p, FLAT, FLAT)
+    Fo = tile_qr(A.astype(np.float64), nb, ib, recs)
+    Fg = hqr.geqrf(torch.from_numpy(np.ascontiguousarray(A)).cuda(), nb, ib, recs)
+    Rg = Fg.R().cpu().numpy().astype(np.float64)
+    nrm = np.linalg.norm(A.astype(np.float64))
+    assert np.max(np.abs(Rg - Fo.R())) <= 5e-6 * nrm
+    tiles = Fg.tiles().cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(tiles - Fo.A)) <= 5e-5 * max(1.0, nrm)
+
+
+@pytest.mark.parametrize("low,high", [(FLAT, FLAT), (GREEDY, FIBONACCI), (BINARY, GREEDY), (FIBONACCI, BINARY)])
+def test_tree_pairs_fp32_and_apply_q(low, high):
+    nb, ib, m, n = 32, 8, 9, 4
+    A = inputs.gaussian(m * nb, n * nb, seed=41).astype(np.float32)
+    recs = hqr_elim_list(m, n, 2, 3, low, high)
+    Fo = tile_qr(A.astype(np.float64), nb, ib, recs)
+    Fg = hqr.geqrf(torch.from_numpy(A).cuda(), nb, ib, recs)
+    nrm = np.linalg.norm(A.astype(np.float64))
+    assert np.max(np.abs(Fg.R().cpu().numpy() - Fo.R())) <= 5e-6 * nrm
+    B = inputs.gaussian(m * nb, 5, seed=42).astype(np.float32)
+    for trans in (True, False):
+        out = Fg.apply_q(torch.from_numpy(B.copy()).cuda(), trans=trans).cpu().numpy()
+        ref = o_apply_q(Fo, B.astype(np.float64), trans=trans)
+        assert np.max(np.abs(out - ref)) <= 5e-6 * np.linalg.norm(B.astype(np.float64))
