@@ -303,7 +303,7 @@ def main():
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "achieved": kern_tflops, "peak": peak, "unit": "TFLOP/s",
                      "frac": (kern_tflops / peak) if peak else None, "traffic": traffic,
-                     "kernel": "hqr_sched_fp64",
+                     "kernel": "hqr::hqr_sched<double>",
                      "peak_source": "FP64 cuBLAS DGEMM 8192^3 measured in this run (best of 3); "
                                     "no FP64 entry in MEASURED_PEAKS.json",
                      "traffic_note": traffic_note},

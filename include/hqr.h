@@ -249,6 +249,82 @@ int hqr_debug_block_task(hqr_factors *F, int64_t task, int extra);
 int hqr_geqrf_r_noalloc(const void *dA, int M, int N, int lda, int nb, int ib,
                         const hqr_elim_t *list, size_t count, void *dR, int ldr, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Least-squares plans: one or many independent problems min ||b - A x||
+ * (M >= N each, shapes may differ) solved by ONE persistent launch over the
+ * merged task graph of all problems (Sec. 4.2 execution scheme applied to a
+ * batch). Two solve modes:
+ *  - refine_iters > 0 (mixed precision with HQR_FP32 storage): the tile QR
+ *    gives R only; x comes from corrected semi-normal equations
+ *    (Bjorck 1987): x0 = 0, then refine_iters times r = b - A x,
+ *    g = A^T r (both FP64, compensated products and sums), R^T R d = g
+ *    (FP64 triangular solves with the low-precision R), x += d.
+ *  - refine_iters == 0: x = R^{-1} (Q^T b)[0:N] (Q^T b by replaying the
+ *    list, Sec. 5.1), in the storage precision.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int M, N;          /* M >= N >= 1 */
+  const void *dA;    /* device, column-major, storage precision of the plan */
+  int lda;           /* >= M */
+  const double *db;  /* device, M entries (FP64) */
+  double *dx;        /* device, N entries (FP64); receives x */
+} hqr_ls_problem_t;
+
+/* Tile configuration of one problem; nb = 0 asks the plan to choose
+ * (the autotuner table when set with hqr_set_tuning, else a heuristic). */
+typedef struct {
+  int nb, ib, a, p, low_tree, high_tree;
+} hqr_tile_config_t;
+
+typedef struct hqr_ls_plan hqr_ls_plan;
+
+/*
+ * hqr_ls_plan_create -- build the merged task graph and workspaces for
+ * `count` problems. cfg: NULL or `count` entries. prec: HQR_FP64/HQR_FP32.
+ * The problems' pointers are kept and used by every run; their buffers
+ * must stay valid while the plan runs. No device work is started.
+ */
+int hqr_ls_plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_config_t *cfg, int prec,
+                       int refine_iters, hqr_ls_plan **plan);
+
+/* hqr_ls_plan_run -- solve all problems (asynchronous on `stream`): one
+ * preparation kernel (tile packing, b, x = 0), the persistent task kernel,
+ * one kernel copying every x out. If hqr_ls_plan_capture was called, the
+ * captured CUDA graph is launched instead. */
+int hqr_ls_plan_run(hqr_ls_plan *plan, void *stream);
+
+/* hqr_ls_plan_capture -- capture one run on `stream` (not the legacy
+ * default stream) into a CUDA graph used by later runs. */
+int hqr_ls_plan_capture(hqr_ls_plan *plan, void *stream);
+
+/* hqr_ls_plan_status -- synchronize `stream`; 0, the device status of the
+ * last run, or HQR_ERR_SINGULAR if any problem's R had an exact zero
+ * diagonal (that problem's x is then not meaningful). */
+int hqr_ls_plan_status(hqr_ls_plan *plan, void *stream);
+
+/* hqr_ls_plan_info -- tasks of the merged graph, the paper's QR flop count
+ * sum of 2 M N^2 - 2/3 N^3, and the device time of the last run (the task
+ * kernel alone; the whole captured graph when it was launched). */
+int hqr_ls_plan_info(hqr_ls_plan *plan, int64_t *ntasks, double *qr_flops, float *kernel_ms);
+
+/* hqr_ls_plan_config -- the tile configuration chosen for problem `idx`. */
+int hqr_ls_plan_config(const hqr_ls_plan *plan, int idx, hqr_tile_config_t *cfg);
+
+/* hqr_ls_plan_trace -- per-task timing of the plan's task kernel, as
+ * hqr_trace (enable 1 / 0 / -1 = read) but 4 words per task: start, end,
+ * CTA << 32 | SM id, opcode << 24 | problem index. Must be enabled before
+ * hqr_ls_plan_capture to be recorded by captured runs. */
+int hqr_ls_plan_trace(hqr_ls_plan *plan, int enable, uint64_t *host, size_t cap, size_t *count);
+
+void hqr_ls_plan_free(hqr_ls_plan *plan);
+
+/*
+ * hqr_set_tuning -- install an autotuner table: `count` entries, entry e
+ * applies to problems with floor(log2 M) == keys[2e] and floor(log2 N) ==
+ * keys[2e+1]. Host only; copied. count = 0 clears it.
+ */
+int hqr_set_tuning(int count, const int *keys, const hqr_tile_config_t *cfgs);
+
 /* hqr_factors_free -- release a factorization (NULL is allowed). */
 void hqr_factors_free(hqr_factors *F);
 

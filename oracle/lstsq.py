@@ -15,6 +15,7 @@ Test infrastructure only (see the package docstring).
 
 import numpy as np
 
+from .householder import householder_apply_qt, householder_qr
 from .tile_qr import apply_q, tile_qr
 
 _SPLIT = 134217729.0  # 2^27 + 1
@@ -127,3 +128,40 @@ def csne(A, R, b, iters):
         x = x + d
         xs.append(x)
     return xs
+
+
+def lstsq_unblocked(A, b, refine=3):
+    """Least squares for any shape M >= N through the unblocked Householder
+    QR, with the same augmented-system refinement and Dot2 residuals as
+    ``lstsq``. Used where the tile shape does not divide the matrix."""
+    A = np.asarray(A, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    M, N = A.shape
+    R, V, tau = householder_qr(A)
+
+    def qt(v):
+        return householder_apply_qt(V, tau, v)
+
+    def q(v):
+        v = np.array(v, dtype=np.float64, copy=True)
+        for j in range(N - 1, -1, -1):
+            w = V[j:, j]
+            v[j:] -= tau[j] * w * (w @ v[j:])
+        return v
+
+    c = qt(b)
+    x = back_substitute(R, c[:N])
+    d = c.copy()
+    d[:N] = 0.0
+    r = q(d)
+    for _ in range(refine):
+        f = dot2_residual(A, x, b, r)
+        g = -dot2_atr(A, r)
+        h = forward_substitute_t(R, g)
+        dd = qt(f)
+        dx = back_substitute(R, dd[:N] - h)
+        e = dd.copy()
+        e[:N] = h
+        r = r + q(e)
+        x = x + dx
+    return x

@@ -206,6 +206,139 @@ Graph build_apply_graph(const std::vector<PanelOp> &ops, int m, int nslab, int w
   return b.finish();
 }
 
+Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int w, int iters, int pid) {
+  const int S = (nb + w - 1) / w;
+  const size_t per_tile = (size_t)S + 2;
+  const size_t ntile_res = (size_t)m * n * per_tile;
+  auto slab = [&](int i, int j, int s) { return ((size_t)j * m + i) * per_tile + (size_t)s; };
+  auto upart = [&](int i, int j) { return ((size_t)j * m + i) * per_tile + (size_t)S; };
+  auto lpart = [&](int i, int j) { return ((size_t)j * m + i) * per_tile + (size_t)S + 1; };
+  // vector pieces: x (n tiles), r (m tiles), g (n tiles), rhs block (m tiles)
+  auto xres = [&](int j) { return ntile_res + (size_t)j; };
+  auto rres = [&](int i) { return ntile_res + (size_t)n + (size_t)i; };
+  auto gres = [&](int j) { return ntile_res + (size_t)n + (size_t)m + (size_t)j; };
+  auto bres = [&](int i) { return ntile_res + (size_t)2 * n + (size_t)m + (size_t)i; };
+  Builder b(ntile_res + 2 * (size_t)n + 2 * (size_t)m);
+  Tracker &tr = b.tr();
+  std::vector<int32_t> &d = b.deps();
+  for (const PanelOp &o : ops) {
+    const int k = o.k;
+    if (o.kind == 0) {
+      for (int s = 0; s < S; ++s) tr.write(slab(o.i, k, s), d);
+      tr.write(upart(o.i, k), d);
+      tr.write(lpart(o.i, k), d);
+      b.add(make_task(OP_GEQRT, 0, o.i, o.i, k, k, 0, nb, 1, 0, pid));
+      for (int j = k + 1; j < n; ++j)
+        for (int s = 0; s < S; ++s) {
+          tr.read(lpart(o.i, k), d);
+          tr.write(slab(o.i, j, s), d);
+          b.add(make_task(OP_UNMQR, j == k + 1 ? 1 : 2, o.i, o.i, k, j, s * w, std::min(w, nb - s * w), 1, 0,
+                          pid));
+        }
+    } else if (o.kind == 1) {
+      tr.write(upart(o.r, k), d);
+      for (int s = 0; s < S; ++s) tr.write(slab(o.i, k, s), d);
+      tr.write(upart(o.i, k), d);
+      tr.write(lpart(o.i, k), d);
+      b.add(make_task(OP_TSQRT, 0, o.i, o.r, k, k, 0, nb, 1, 0, pid));
+      for (int j = k + 1; j < n; ++j)
+        for (int s = 0; s < S; ++s) {
+          tr.read(upart(o.i, k), d);
+          tr.read(lpart(o.i, k), d);
+          tr.write(slab(o.r, j, s), d);
+          tr.write(slab(o.i, j, s), d);
+          b.add(make_task(OP_TSMQR, j == k + 1 ? 1 : 2, o.i, o.r, k, j, s * w, std::min(w, nb - s * w), 1, 0,
+                          pid));
+        }
+    } else {
+      tr.write(upart(o.r, k), d);
+      tr.write(upart(o.i, k), d);
+      b.add(make_task(OP_TTQRT, 0, o.i, o.r, k, k, 0, nb, 1, 0, pid));
+      for (int j = k + 1; j < n; ++j)
+        for (int s = 0; s < S; ++s) {
+          tr.read(upart(o.i, k), d);
+          tr.write(slab(o.r, j, s), d);
+          tr.write(slab(o.i, j, s), d);
+          b.add(make_task(OP_TTMQR, j == k + 1 ? 1 : 2, o.i, o.r, k, j, s * w, std::min(w, nb - s * w), 1, 0,
+                          pid));
+        }
+    }
+  }
+  // R tiles (i, j), j >= i, are final after their last writers
+  auto read_r = [&](int i, int j) {
+    for (int s = 0; s < S; ++s) tr.read(slab(i, j, s), d);
+    tr.read(upart(i, j), d);
+  };
+  auto vtask = [&](int op, int i, int j) { return make_task(op, 1, i, i, 0, j, 0, 0, 1, 0, pid); };
+  auto solve_r = [&](bool transposed_first) {
+    if (transposed_first) {  // R^T y = g, forward
+      for (int i = 0; i < n; ++i) {
+        read_r(i, i);
+        tr.write(gres(i), d);
+        b.add(vtask(OP_TRSV_TD, i, i));
+        for (int j = i + 1; j < n; ++j) {
+          read_r(i, j);
+          tr.read(gres(i), d);
+          tr.write(gres(j), d);
+          b.add(vtask(OP_TRSV_TU, i, j));
+        }
+      }
+    }
+    for (int i = n - 1; i >= 0; --i) {  // R d = y, backward
+      read_r(i, i);
+      tr.write(gres(i), d);
+      b.add(vtask(OP_TRSV_D, i, i));
+      for (int j = 0; j < i; ++j) {
+        read_r(j, i);
+        tr.read(gres(i), d);
+        tr.write(gres(j), d);
+        b.add(vtask(OP_TRSV_U, i, j));
+      }
+    }
+    for (int j = 0; j < n; ++j) {
+      tr.read(gres(j), d);
+      tr.write(xres(j), d);
+      b.add(vtask(OP_XUPD, j, j));
+    }
+  };
+  if (iters == 0) {
+    // Q^T b on the right-hand-side block, replaying the factorization forward
+    for (const PanelOp &o : ops) {
+      if (o.kind == 0) {
+        tr.read(lpart(o.i, o.k), d);
+        tr.write(bres(o.i), d);
+        b.add(make_task(OP_UNMQR, 1, o.i, o.i, o.k, 0, 0, 1, 1, 1, pid));
+      } else {
+        tr.read(upart(o.i, o.k), d);
+        if (o.kind == 1) tr.read(lpart(o.i, o.k), d);
+        tr.write(bres(o.r), d);
+        tr.write(bres(o.i), d);
+        b.add(make_task(o.kind == 1 ? OP_TSMQR : OP_TTMQR, 1, o.i, o.r, o.k, 0, 0, 1, 1, 1, pid));
+      }
+    }
+    for (int i = 0; i < n; ++i) {
+      tr.read(bres(i), d);
+      tr.write(gres(i), d);
+      b.add(vtask(OP_BTOG, i, i));
+    }
+    solve_r(false);
+  }
+  for (int it = 0; it < iters; ++it) {
+    for (int i = 0; i < m; ++i) {
+      for (int j = 0; j < n; ++j) tr.read(xres(j), d);
+      tr.write(rres(i), d);
+      b.add(vtask(OP_RESID, i, i));
+    }
+    for (int j = 0; j < n; ++j) {
+      for (int i = 0; i < m; ++i) tr.read(rres(i), d);
+      tr.write(gres(j), d);
+      b.add(vtask(OP_ATR, j, j));
+    }
+    solve_r(true);
+  }
+  return b.finish();
+}
+
 void append_graph(Graph &into, const Graph &g) {
   const int32_t toff = (int32_t)into.tasks.size();
   const int32_t eoff = (int32_t)into.succ.size();

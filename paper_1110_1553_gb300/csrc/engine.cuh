@@ -24,6 +24,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cstring>
 
 #include "hqr_internal.h"
 #include "ptx.cuh"
@@ -49,15 +50,39 @@ struct RealTraits<float> {
 template <typename Real>
 __host__ __device__ constexpr int smem_pad() { return 16 / (int)sizeof(Real); }
 
+// Ready queues are sharded: a task goes to shard (task id mod kShards) of its
+// priority class, so each shard holds at most ceil(ntasks / kShards) tasks.
+// CTAs look at their home shard first. Every counter sits on its own 128-byte
+// line so that the atomics of different shards do not contend.
+constexpr int kShards = 8;
+struct alignas(128) CtlLine {
+  unsigned v;
+  int aux;
+  unsigned pad[30];
+};
+
 // Device control words of one graph run.
 struct Ctl {
-  unsigned head[kNumQueues];
-  unsigned tail[kNumQueues];
-  unsigned done;
-  int status;
-  int err_task;
-  int pad[3];
+  CtlLine head[kNumQueues * kShards];
+  CtlLine tail[kNumQueues * kShards];
+  CtlLine done;
+  CtlLine status;  // v: status code, aux: task that failed (or -1)
 };
+
+__host__ __device__ inline int shard_cap(int ntasks) { return (ntasks + kShards - 1) / kShards; }
+
+// Initial ready slots and control words for a graph (host side): every task
+// with no inputs is placed in its queue shard.
+inline void init_ready(const Task *tasks, const int *indeg, int ntasks, int *slots, Ctl &ctl) {
+  std::memset(&ctl, 0, sizeof(Ctl));
+  const int cap = shard_cap(ntasks);
+  for (int t = 0; t < ntasks; ++t)
+    if (indeg[t] == 0) {
+      const int qs = tasks[t].prio * kShards + t % kShards;
+      slots[(size_t)qs * cap + ctl.tail[qs].v++] = t + 1;
+    }
+}
+inline size_t slot_count(int ntasks) { return (size_t)kNumQueues * kShards * shard_cap(ntasks); }
 
 // One problem of a (possibly batched) task graph.
 struct Problem {
@@ -69,6 +94,13 @@ struct Problem {
   int wt;             // slab width of the trailing update inside panel tasks
   int vc;             // V columns staged per chunk in update tasks (divides ib)
   int wb;             // right-hand-side block width
+  // least-squares solves (FP64 vectors; unused by plain factorizations)
+  int M, N;           // true sizes (the tile workspace is zero padded)
+  const void *A0;     // the caller's matrix, column-major, storage precision
+  long long lda0;
+  const double *b;    // right-hand side (M)
+  double *x, *r, *g;  // solution (n*nb), residual (m*nb), work vector (n*nb)
+  int *status;        // per-problem status word (HQR_ERR_SINGULAR)
 };
 
 struct EngineParams {
@@ -77,7 +109,7 @@ struct EngineParams {
   int ntasks;
   const int *succ;
   int *indeg;
-  int *slots;          // kNumQueues x ntasks ready slots (task id + 1, 0 = empty)
+  int *slots;          // kNumQueues x kShards x shard_cap(ntasks) slots (task id + 1, 0 = empty)
   Ctl *ctl;
   long long timeout_ns;
   unsigned long long *trace;  // optional: per task start, end (globaltimer), SM id
@@ -116,7 +148,7 @@ struct Geo {
 };
 
 __device__ __forceinline__ void set_error(const EngineParams &p, int code, int task) {
-  if (atomicCAS(&p.ctl->status, 0, code) == 0) p.ctl->err_task = task;
+  if (atomicCAS((int *)&p.ctl->status.v, 0, code) == 0) p.ctl->status.aux = task;
 }
 
 template <typename Real>
@@ -580,49 +612,207 @@ __device__ void task_panel(const EngineParams &p, const Geo<Real> &g, const Task
   }
 }
 
+// ------------------------------------------------------ FP64 vector tasks --
+// Compensated products and sums (TwoProduct with FMA, TwoSum of Knuth): the
+// residual and A^T r of the refinement are accumulated as in twice the
+// working precision (Ogita, Rump, Oishi 2005, "Dot2").
+
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e) {
+  s = a + b;
+  const double z = s - a;
+  e = (a - (s - z)) + (b - z);
+}
+
+// (s, c) += a * x
+__device__ __forceinline__ void dot2_step(double a, double x, double &s, double &c) {
+  const double p = a * x;
+  const double ep = fma(a, x, -p);
+  double t, es;
+  two_sum(s, p, t, es);
+  s = t;
+  c += ep + es;
+}
+
+// (s1, c1) += (s2, c2)
+__device__ __forceinline__ void dot2_merge(double &s1, double &c1, double s2, double c2) {
+  double t, e;
+  two_sum(s1, s2, t, e);
+  s1 = t;
+  c1 += c2 + e;
+}
+
+template <typename Real>
+__device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<Real> &g, const Task &t,
+                            double *sm) {
+  const int nb = g.nb, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const Real *A0 = (const Real *)P.A0;
+  switch (t.op) {
+    case OP_RESID: {  // r_i = b_i - A(i,:) x
+      const int r0 = t.i * nb, nr = min(nb, P.M - r0);
+      const int G = NT / nb;  // column groups
+      const int rr = tid % nb, gi = tid / nb;
+      double s = 0.0, c = 0.0;
+      if (rr < nr && gi < G) {
+        const Real *arow = A0 + r0 + rr;
+        for (int j = gi; j < P.N; j += G) dot2_step((double)arow[(long long)j * P.lda0], P.x[j], s, c);
+      }
+      sm[tid] = s;
+      sm[NT + tid] = c;
+      __syncthreads();
+      if (tid < nr) {
+        double S = sm[tid], C = sm[NT + tid];
+        for (int q = 1; q < G; ++q) dot2_merge(S, C, sm[q * nb + tid], sm[NT + q * nb + tid]);
+        double u, e;
+        two_sum(P.b[r0 + tid], -S, u, e);
+        P.r[r0 + tid] = u + (e - C);
+      }
+      __syncthreads();
+      break;
+    }
+    case OP_ATR: {  // g_j = A(:,j)^T r
+      const int c0 = t.j * nb, nc = min(nb, P.N - c0);
+      for (int cc = warp; cc < nc; cc += NWARP) {
+        const Real *acol = A0 + (long long)(c0 + cc) * P.lda0;
+        double s = 0.0, c = 0.0;
+        for (int i = lane; i < P.M; i += 32) dot2_step((double)acol[i], P.r[i], s, c);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const double s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, c, o);
+          dot2_merge(s, c, s2, c2);
+        }
+        if (lane == 0) P.g[c0 + cc] = s + c;
+      }
+      break;
+    }
+    case OP_TRSV_TD:
+    case OP_TRSV_D: {  // triangular solve with the diagonal tile, in place on g_i
+      const int i = t.i, n_i = min(nb, P.N - i * nb);
+      const Real *R = g.tile(i, i);
+      double *gi = P.g + (size_t)i * nb;
+      for (int k = tid; k < n_i; k += NT) sm[k] = gi[k];
+      __syncthreads();
+      if (t.op == OP_TRSV_TD) {
+        for (int k = 0; k < n_i; ++k) {
+          if (tid == 0) {
+            const double d = (double)R[(size_t)k * nb + k];
+            if (d == 0.0) atomicExch(P.status, HQR_ERR_SINGULAR);
+            sm[k] = d == 0.0 ? 0.0 : sm[k] / d;
+          }
+          __syncthreads();
+          const double yk = sm[k];
+          for (int l = k + 1 + tid; l < n_i; l += NT) sm[l] = fma(-(double)R[(size_t)l * nb + k], yk, sm[l]);
+          __syncthreads();
+        }
+      } else {
+        for (int k = n_i - 1; k >= 0; --k) {
+          if (tid == 0) {
+            const double d = (double)R[(size_t)k * nb + k];
+            if (d == 0.0) atomicExch(P.status, HQR_ERR_SINGULAR);
+            sm[k] = d == 0.0 ? 0.0 : sm[k] / d;
+          }
+          __syncthreads();
+          const double dk = sm[k];
+          for (int l = tid; l < k; l += NT) sm[l] = fma(-(double)R[(size_t)k * nb + l], dk, sm[l]);
+          __syncthreads();
+        }
+      }
+      for (int k = tid; k < n_i; k += NT) gi[k] = sm[k];
+      break;
+    }
+    case OP_TRSV_TU: {  // g_j -= R(i,j)^T g_i, j > i
+      const int i = t.i, j = t.j, n_i = min(nb, P.N - i * nb), n_j = min(nb, P.N - j * nb);
+      const Real *R = g.tile(i, j);
+      const double *gi = P.g + (size_t)i * nb;
+      for (int c = warp; c < n_j; c += NWARP) {
+        double s = 0.0;
+        for (int r = lane; r < n_i; r += 32) s = fma((double)R[(size_t)c * nb + r], gi[r], s);
+        s = warp_sum(s);
+        if (lane == 0) P.g[(size_t)j * nb + c] -= s;
+      }
+      break;
+    }
+    case OP_TRSV_U: {  // g_j -= R(j,i) g_i, j < i
+      const int i = t.i, j = t.j, n_i = min(nb, P.N - i * nb);
+      const Real *R = g.tile(j, i);
+      const double *gi = P.g + (size_t)i * nb;
+      for (int r = tid; r < nb; r += NT) {
+        double s = 0.0;
+        for (int c = 0; c < n_i; ++c) s = fma((double)R[(size_t)c * nb + r], gi[c], s);
+        P.g[(size_t)j * nb + r] -= s;
+      }
+      break;
+    }
+    case OP_XUPD: {
+      const int j = t.j, n_j = min(nb, P.N - j * nb);
+      for (int c = tid; c < n_j; c += NT) P.x[(size_t)j * nb + c] += P.g[(size_t)j * nb + c];
+      break;
+    }
+    case OP_BTOG: {
+      const int i = t.i, n_i = min(nb, P.N - i * nb);
+      const Real *Bb = g.B + (size_t)i * nb * g.wb;
+      for (int r = tid; r < n_i; r += NT) P.g[(size_t)i * nb + r] = (double)Bb[r];
+      break;
+    }
+    default:
+      break;
+  }
+}
+
 // ------------------------------------------------------------- scheduler --
 
 __device__ __forceinline__ void push_ready(const EngineParams &p, int task) {
-  const int q = p.tasks[task].prio;
-  const unsigned idx = atomicAdd(&p.ctl->tail[q], 1u);
-  ptx::st_release(&p.slots[(size_t)q * p.ntasks + idx], task + 1);
+  const int qs = p.tasks[task].prio * kShards + task % kShards;
+  const unsigned idx = atomicAdd(&p.ctl->tail[qs].v, 1u);
+  ptx::st_release(&p.slots[(size_t)qs * shard_cap(p.ntasks) + idx], task + 1);
 }
 
 // Claim the next ready task (thread 0 only). -1: finished or failed.
-__device__ int pop_ready(const EngineParams &p) {
+// `pending` counts tasks this CTA completed but has not yet added to the
+// global done counter; it is flushed whenever the queues look empty.
+__device__ int pop_ready(const EngineParams &p, unsigned &pending) {
   const uint64_t t0 = ptx::globaltimer();
-  unsigned sleep_ns = 64;
+  const int cap = shard_cap(p.ntasks);
+  const int home = blockIdx.x % kShards;
+  unsigned sleep_ns = 32;
   while (true) {
-    if (ptx::ld_relaxed(&p.ctl->status) != 0) return -1;
+    if (ptx::ld_relaxed((const int *)&p.ctl->status.v) != 0) return -1;
     for (int q = 0; q < kNumQueues; ++q) {
-      unsigned h = ptx::ld_relaxed_u32(&p.ctl->head[q]);
-      while (h < ptx::ld_relaxed_u32(&p.ctl->tail[q])) {
-        const unsigned old = atomicCAS(&p.ctl->head[q], h, h + 1);
-        if (old == h) {
-          const int *slot = &p.slots[(size_t)q * p.ntasks + h];
-          int v = ptx::ld_acquire(slot);
-          const uint64_t t1 = ptx::globaltimer();
-          while (v == 0) {
-            if (ptx::globaltimer() - t1 > (uint64_t)p.timeout_ns) {
-              set_error(p, HQR_ERR_TIMEOUT, -1);
-              return -1;
+      for (int k = 0; k < kShards; ++k) {
+        const int qs = q * kShards + (home + k) % kShards;
+        unsigned h = ptx::ld_relaxed_u32(&p.ctl->head[qs].v);
+        while (h < ptx::ld_relaxed_u32(&p.ctl->tail[qs].v)) {
+          const unsigned old = atomicCAS(&p.ctl->head[qs].v, h, h + 1);
+          if (old == h) {
+            const int *slot = &p.slots[(size_t)qs * cap + h];
+            int v = ptx::ld_acquire(slot);
+            const uint64_t t1 = ptx::globaltimer();
+            while (v == 0) {
+              if (ptx::globaltimer() - t1 > (uint64_t)p.timeout_ns) {
+                set_error(p, HQR_ERR_TIMEOUT, -1);
+                return -1;
+              }
+              __nanosleep(32);
+              v = ptx::ld_acquire(slot);
             }
-            __nanosleep(32);
-            v = ptx::ld_acquire(slot);
+            __threadfence();
+            return v - 1;
           }
-          __threadfence();
-          return v - 1;
+          h = old;
         }
-        h = old;
       }
     }
-    if (ptx::ld_relaxed_u32(&p.ctl->done) >= (unsigned)p.ntasks) return -1;
+    if (pending) {
+      __threadfence();
+      atomicAdd(&p.ctl->done.v, pending);
+      pending = 0;
+    }
+    if (ptx::ld_relaxed_u32(&p.ctl->done.v) >= (unsigned)p.ntasks) return -1;
     if (ptx::globaltimer() - t0 > (uint64_t)p.timeout_ns) {
       set_error(p, HQR_ERR_TIMEOUT, -1);
       return -1;
     }
     __nanosleep(sleep_ns);
-    if (sleep_ns < 2048) sleep_ns *= 2;
+    if (sleep_ns < 1024) sleep_ns *= 2;
   }
 }
 
@@ -643,8 +833,9 @@ __global__ void __launch_bounds__(NT, 2) hqr_sched(EngineParams p) {
   }
   __syncthreads();
   uint32_t phase = 0;
+  unsigned pending = 0;
   while (true) {
-    if (threadIdx.x == 0) sh.task = pop_ready(p);
+    if (threadIdx.x == 0) sh.task = pop_ready(p, pending);
     __syncthreads();
     const int tid = sh.task;
     if (tid < 0) break;
@@ -653,8 +844,10 @@ __global__ void __launch_bounds__(NT, 2) hqr_sched(EngineParams p) {
     const uint64_t t_start = (p.trace && threadIdx.x == 0) ? ptx::globaltimer() : 0;
     if (t.op == OP_GEQRT || t.op == OP_TSQRT || t.op == OP_TTQRT)
       task_panel(p, g, t, sh, dyn, phase);
-    else
+    else if (t.op <= OP_TTMQR)
       task_update(p, g, t, sh, dyn, phase);
+    else
+      task_vector(p, p.probs[t.pid], g, t, reinterpret_cast<double *>(dyn_raw));
     __syncthreads();
     if (threadIdx.x == 0) {
       if (p.trace) {
@@ -668,8 +861,11 @@ __global__ void __launch_bounds__(NT, 2) hqr_sched(EngineParams p) {
         const int s = p.succ[e];
         if (atomicSub(&p.indeg[s], 1) == 1) push_ready(p, s);
       }
-      __threadfence();
-      atomicAdd(&p.ctl->done, 1u);
+      if (++pending >= 64) {
+        __threadfence();
+        atomicAdd(&p.ctl->done.v, pending);
+        pending = 0;
+      }
     }
     if (sh.abort) break;
   }
@@ -691,7 +887,9 @@ inline size_t engine_smem_bytes(int nb, int ib, int w, int wt, int vc) {
   const size_t cbg = (size_t)(lds * wt > ib * ib ? lds * wt : ib * ib);
   const size_t pan = (size_t)lds * ib + (size_t)ldt * (ib + wt) + (size_t)ib * ib + cbg +
                      (size_t)ib * wt + scr_p;
-  return sizeof(Real) * (upd > pan ? upd : pan);
+  const size_t vec = (size_t)(2 * NT + 256) * sizeof(double);  // FP64 vector tasks
+  const size_t tiles = sizeof(Real) * (upd > pan ? upd : pan);
+  return tiles > vec ? tiles : vec;
 }
 
 }  // namespace hqr

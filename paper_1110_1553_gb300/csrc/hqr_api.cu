@@ -24,6 +24,7 @@ int64_t g_timeout_ns = 20000000000ll;
 bool cuda_ok(cudaError_t e, const char *what) {
   if (e == cudaSuccess) return true;
   g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  (void)cudaGetLastError();  // a non-sticky error must not be reported again by a later launch check
   return false;
 }
 #define CK(call)                                      \
@@ -58,14 +59,10 @@ int upload_graph(const Graph &g, DevGraph &d) {
   const int nt = (int)g.tasks.size();
   d.ntasks = nt;
   d.nedges = g.nedges;
-  std::vector<int> slots((size_t)kNumQueues * nt, 0);
-  Ctl ctl;
-  std::memset(&ctl, 0, sizeof(ctl));
-  for (int t = 0; t < nt; ++t)
-    if (g.indeg[t] == 0) {
-      const int q = g.tasks[t].prio;
-      slots[(size_t)q * nt + ctl.tail[q]++] = t + 1;
-    }
+  std::vector<int> slots(slot_count(nt), 0);
+  std::vector<Ctl> ctlv(1);
+  Ctl &ctl = ctlv[0];
+  init_ready(g.tasks.data(), g.indeg.data(), nt, slots.data(), ctl);
   const size_t ns = std::max<size_t>(g.succ.size(), 1);
   CK(cudaMalloc(&d.tasks, sizeof(Task) * nt));
   CK(cudaMalloc(&d.succ, sizeof(int) * ns));
@@ -291,8 +288,7 @@ int run_graph(hqr_factors *F, DevGraph &g, cudaStream_t s) {
   p.trace = (F->dtrace && F->trace_cap >= (size_t)g.ntasks) ? F->dtrace : nullptr;
   const size_t smem = smem_for(F->prec, F->prob);
   CK(cudaMemcpyAsync(g.indeg, g.indeg0, sizeof(int) * g.ntasks, cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpyAsync(g.slots, g.slots0, sizeof(int) * (size_t)kNumQueues * g.ntasks, cudaMemcpyDeviceToDevice,
-                     s));
+  CK(cudaMemcpyAsync(g.slots, g.slots0, sizeof(int) * slot_count(g.ntasks), cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(g.ctl, g.ctl0, sizeof(Ctl), cudaMemcpyDeviceToDevice, s));
   if (!F->ev0) {
     CK(cudaEventCreate(&F->ev0));
@@ -310,9 +306,9 @@ int run_graph(hqr_factors *F, DevGraph &g, cudaStream_t s) {
 int read_status(hqr_factors *F, cudaStream_t s) {
   CK(cudaStreamSynchronize(s));
   if (!F->last_ctl) return HQR_SUCCESS;
-  Ctl c;
-  CK(cudaMemcpy(&c, F->last_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
-  if (c.status != 0) return c.status;
+  CtlLine c;
+  CK(cudaMemcpy(&c, &F->last_ctl->status, sizeof(CtlLine), cudaMemcpyDeviceToHost));
+  if (c.v != 0) return (int)c.v;
   return HQR_SUCCESS;
 }
 
@@ -696,6 +692,415 @@ void hqr_factors_free(hqr_factors *F) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// Least-squares plans (one merged task graph for many problems).
+namespace {
+
+struct TuneEntry {
+  int lm, ln;
+  hqr_tile_config_t cfg;
+};
+std::vector<TuneEntry> g_tuning;
+
+int ilog2(int v) {
+  int r = 0;
+  while ((v >> (r + 1)) > 0) ++r;
+  return r;
+}
+
+// Heuristic tile configuration for an M x N problem when no table entry
+// applies: tiles large enough for efficient kernels, TS domains of 4 tiles
+// (TS updates are the faster kernels, Sec. 5) and greedy trees.
+hqr_tile_config_t default_config(int M, int N, int prec) {
+  hqr_tile_config_t c;
+  c.nb = N <= 48 ? 32 : (N <= 192 || M < 1024 ? 64 : 128);
+  c.ib = prec == HQR_FP64 ? std::min(16, c.nb / 2) : 16;
+  c.a = 4;
+  c.p = 1;
+  c.low_tree = HQR_GREEDY;
+  c.high_tree = HQR_GREEDY;
+  return c;
+}
+
+hqr_tile_config_t pick_config(int M, int N, int prec, const hqr_tile_config_t *given) {
+  if (given && given->nb > 0) return *given;
+  const int lm = ilog2(M), ln = ilog2(N);
+  for (const TuneEntry &e : g_tuning)
+    if (e.lm == lm && e.ln == ln) return e.cfg;
+  return default_config(M, N, prec);
+}
+
+// Per-problem pieces of the preparation and finishing kernels.
+struct PrepDesc {
+  const void *A;
+  long long lda;
+  const double *b;
+  double *dx;
+  void *ws;     // tile workspace
+  void *B;      // right-hand-side block (Mp x 1)
+  double *x;    // solution vector (Np)
+  int M, N, m, n, nb;
+  long long off;  // first element of this problem in the flattened index
+};
+
+// Flattened per problem: Mp*Np tile elements, then Mp rhs entries, then Np
+// entries of x (set to zero). Problems are found by binary search.
+template <typename Real>
+__global__ void ls_prepare(const PrepDesc *__restrict__ d, int count, long long total) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (d[mid].off <= e) lo = mid; else hi = mid - 1;
+    }
+    const PrepDesc &P = d[lo];
+    long long q = e - P.off;
+    const int nb = P.nb, Mp = P.m * nb, Np = P.n * nb;
+    const long long nt = (long long)Mp * Np;
+    if (q < nt) {
+      const long long nb2 = (long long)nb * nb;
+      const long long tile = q / nb2;
+      const int w = (int)(q - tile * nb2);
+      const int cc = w / nb, rr = w - cc * nb;
+      const int row = (int)(tile % P.m) * nb + rr, col = (int)(tile / P.m) * nb + cc;
+      ((Real *)P.ws)[q] = (row < P.M && col < P.N) ? ((const Real *)P.A)[(long long)col * P.lda + row] : Real(0);
+    } else if ((q -= nt) < Mp) {
+      ((Real *)P.B)[q] = q < P.M ? (Real)P.b[q] : Real(0);
+    } else {
+      q -= Mp;
+      P.x[q] = 0.0;
+    }
+  }
+}
+
+__global__ void ls_finish(const PrepDesc *__restrict__ d, int count) {
+  for (int pi = blockIdx.x; pi < count; pi += gridDim.x) {
+    const PrepDesc &P = d[pi];
+    for (int j = threadIdx.x; j < P.N; j += blockDim.x) P.dx[j] = P.x[j];
+  }
+}
+
+}  // namespace
+
+struct hqr_ls_plan {
+  int count = 0, prec = 0, iters = 0;
+  std::vector<hqr_tile_config_t> cfg;
+  std::vector<Problem> probs;
+  std::vector<PrepDesc> prep;
+  Problem *dprobs = nullptr;
+  PrepDesc *dprep = nullptr;
+  void *arena = nullptr;   // tiles, T, rhs blocks (storage precision)
+  double *vec = nullptr;   // x, r, g of every problem
+  int *dstatus = nullptr;  // per-problem status words
+  long long prep_total = 0;
+  size_t smem = 0;
+  double flops = 0.0;
+  DevGraph graph;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaGraph_t cg = nullptr;
+  cudaGraphExec_t cge = nullptr;
+  bool ran = false;
+  std::vector<int32_t> task_kind;  // op << 24 | problem index, per task (for traces)
+  unsigned long long *dtrace = nullptr;
+};
+
+namespace {
+
+int plan_enqueue(hqr_ls_plan *P, cudaStream_t s, bool timed) {
+  if (P->prec == HQR_FP64)
+    ls_prepare<double><<<grid_for(P->prep_total), 256, 0, s>>>(P->dprep, P->count, P->prep_total);
+  else
+    ls_prepare<float><<<grid_for(P->prep_total), 256, 0, s>>>(P->dprep, P->count, P->prep_total);
+  CK(cudaGetLastError());
+  CK(cudaMemsetAsync(P->dstatus, 0, sizeof(int) * P->count, s));
+  DevGraph &g = P->graph;
+  CK(cudaMemcpyAsync(g.indeg, g.indeg0, sizeof(int) * g.ntasks, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(g.slots, g.slots0, sizeof(int) * slot_count(g.ntasks), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(g.ctl, g.ctl0, sizeof(Ctl), cudaMemcpyDeviceToDevice, s));
+  EngineParams p;
+  p.probs = P->dprobs;
+  p.tasks = g.tasks;
+  p.ntasks = g.ntasks;
+  p.succ = g.succ;
+  p.indeg = g.indeg;
+  p.slots = g.slots;
+  p.ctl = g.ctl;
+  p.timeout_ns = g_timeout_ns;
+  p.trace = P->dtrace;
+  if (timed) CK(cudaEventRecord(P->ev0, s));
+  int st = launch_sched(P->prec, p, P->smem, s);
+  if (st) return st;
+  if (timed) CK(cudaEventRecord(P->ev1, s));
+  ls_finish<<<std::min(P->count, 4096), 256, 0, s>>>(P->dprep, P->count);
+  CK(cudaGetLastError());
+  return HQR_SUCCESS;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hqr_set_tuning(int count, const int *keys, const hqr_tile_config_t *cfgs) {
+  if (count < 0) return -1;
+  if (count > 0 && (!keys || !cfgs)) return -2;
+  g_tuning.clear();
+  for (int e = 0; e < count; ++e) g_tuning.push_back({keys[2 * e], keys[2 * e + 1], cfgs[e]});
+  return HQR_SUCCESS;
+}
+
+int hqr_ls_plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_config_t *cfg, int prec,
+                       int refine_iters, hqr_ls_plan **plan) {
+  if (count < 1) return -1;
+  if (!probs) return -2;
+  if (prec != HQR_FP64 && prec != HQR_FP32) return -4;
+  if (refine_iters < 0 || refine_iters > 64) return -5;
+  if (!plan) return -6;
+  *plan = nullptr;
+  hqr_ls_plan *P = new (std::nothrow) hqr_ls_plan();
+  if (!P) return HQR_ERR_NOMEM;
+  P->count = count;
+  P->prec = prec;
+  P->iters = refine_iters;
+  const size_t es = elem_size(prec);
+  // tile configurations, lists, sizes
+  std::vector<size_t> off_tiles(count), off_t(count), off_b(count), off_vec(count);
+  size_t arena_elems = 0, vec_elems = 0;
+  Graph merged;
+  size_t smem = 0;
+  for (int q = 0; q < count; ++q) {
+    const hqr_ls_problem_t &pr = probs[q];
+    if (pr.M < 1 || pr.N < 1 || pr.N > pr.M || pr.lda < pr.M || !pr.dA || !pr.db || !pr.dx) {
+      delete P;
+      return -2;
+    }
+    hqr_tile_config_t c = pick_config(pr.M, pr.N, prec, cfg ? &cfg[q] : nullptr);
+    if (!valid_tile_sizes(prec, c.nb, c.ib) || c.a < 1 || c.p < 1 || c.low_tree < 0 || c.low_tree > 3 ||
+        c.high_tree < 0 || c.high_tree > 3) {
+      delete P;
+      return -3;
+    }
+    P->cfg.push_back(c);
+    Problem pb{};
+    pb.nb = c.nb;
+    pb.ib = c.ib;
+    pb.m = (pr.M + c.nb - 1) / c.nb;
+    pb.n = (pr.N + c.nb - 1) / c.nb;
+    choose_widths(prec, c.nb, c.ib, pb);
+    pb.wb = 1;
+    pb.M = pr.M;
+    pb.N = pr.N;
+    pb.A0 = pr.dA;
+    pb.lda0 = pr.lda;
+    pb.b = pr.db;
+    const size_t Mp = (size_t)pb.m * c.nb, Np = (size_t)pb.n * c.nb;
+    off_tiles[q] = arena_elems;
+    arena_elems += (Mp * Np + 3) & ~(size_t)3;
+    off_t[q] = arena_elems;
+    arena_elems += ((size_t)pb.m * pb.n * 2 * c.ib * c.nb + 3) & ~(size_t)3;
+    off_b[q] = arena_elems;
+    arena_elems += (Mp + 3) & ~(size_t)3;
+    off_vec[q] = vec_elems;
+    vec_elems += Mp + 2 * Np;
+    size_t cnt = 0;
+    hqr_elim_list(pb.m, pb.n, c.a, c.p, c.low_tree, c.high_tree, nullptr, 0, &cnt);
+    std::vector<hqr_elim_t> lst(cnt);
+    if (hqr_elim_list(pb.m, pb.n, c.a, c.p, c.low_tree, c.high_tree, lst.data(), cnt, &cnt)) {
+      delete P;
+      return HQR_ERR_INTERNAL;
+    }
+    std::vector<PanelOp> ops = expand_ops(lst.data(), lst.size(), pb.m, pb.n);
+    append_graph(merged, build_ls_graph(ops, pb.m, pb.n, c.nb, pb.w, refine_iters, q));
+    smem = std::max(smem, smem_for(prec, pb));
+    P->probs.push_back(pb);
+    P->flops += 2.0 * pr.M * (double)pr.N * pr.N - 2.0 / 3.0 * (double)pr.N * pr.N * pr.N;
+  }
+  P->smem = smem;
+  int st = HQR_SUCCESS;
+  if (!cuda_ok(cudaMalloc(&P->arena, es * std::max<size_t>(arena_elems, 1)), "cudaMalloc(arena)") ||
+      !cuda_ok(cudaMalloc(&P->vec, sizeof(double) * std::max<size_t>(vec_elems, 1)), "cudaMalloc(vec)") ||
+      !cuda_ok(cudaMalloc(&P->dstatus, sizeof(int) * count), "cudaMalloc(status)") ||
+      !cuda_ok(cudaMemset(P->arena, 0, es * std::max<size_t>(arena_elems, 1)), "memset(arena)"))
+    st = HQR_ERR_NOMEM;
+  if (!st) {
+    long long off = 0;
+    for (int q = 0; q < count; ++q) {
+      Problem &pb = P->probs[q];
+      unsigned char *base = (unsigned char *)P->arena;
+      pb.A = base + es * off_tiles[q];
+      pb.T = base + es * off_t[q];
+      pb.B = base + es * off_b[q];
+      pb.x = P->vec + off_vec[q];
+      pb.r = pb.x + (size_t)pb.n * pb.nb;
+      pb.g = pb.r + (size_t)pb.m * pb.nb;
+      pb.status = P->dstatus + q;
+      PrepDesc d;
+      d.A = probs[q].dA;
+      d.lda = probs[q].lda;
+      d.b = probs[q].db;
+      d.dx = probs[q].dx;
+      d.ws = pb.A;
+      d.B = pb.B;
+      d.x = pb.x;
+      d.M = pb.M;
+      d.N = pb.N;
+      d.m = pb.m;
+      d.n = pb.n;
+      d.nb = pb.nb;
+      d.off = off;
+      off += (long long)pb.m * pb.nb * pb.n * pb.nb + (long long)pb.m * pb.nb + (long long)pb.n * pb.nb;
+      P->prep.push_back(d);
+    }
+    P->prep_total = off;
+    if (!cuda_ok(cudaMalloc(&P->dprobs, sizeof(Problem) * count), "cudaMalloc(probs)") ||
+        !cuda_ok(cudaMalloc(&P->dprep, sizeof(PrepDesc) * count), "cudaMalloc(prep)"))
+      st = HQR_ERR_NOMEM;
+  }
+  if (!st && (!cuda_ok(cudaMemcpy(P->dprobs, P->probs.data(), sizeof(Problem) * count, cudaMemcpyHostToDevice),
+                       "copy probs") ||
+              !cuda_ok(cudaMemcpy(P->dprep, P->prep.data(), sizeof(PrepDesc) * count, cudaMemcpyHostToDevice),
+                       "copy prep") ||
+              !cuda_ok(cudaEventCreate(&P->ev0), "event") || !cuda_ok(cudaEventCreate(&P->ev1), "event")))
+    st = HQR_ERR_CUDA;
+  if (!st) st = upload_graph(merged, P->graph);
+  if (st) {
+    hqr_ls_plan_free(P);
+    return st;
+  }
+  P->task_kind.resize(merged.tasks.size());
+  for (size_t t = 0; t < merged.tasks.size(); ++t)
+    P->task_kind[t] = ((int32_t)merged.tasks[t].op << 24) | merged.tasks[t].pid;
+  *plan = P;
+  return HQR_SUCCESS;
+}
+
+int hqr_ls_plan_trace(hqr_ls_plan *P, int enable, uint64_t *host, size_t cap, size_t *count) {
+  if (!P) return -1;
+  const size_t nt = (size_t)P->graph.ntasks;
+  if (enable == 1) {
+    if (!P->dtrace && !cuda_ok(cudaMalloc(&P->dtrace, 3 * sizeof(unsigned long long) * nt), "cudaMalloc(trace)"))
+      return HQR_ERR_NOMEM;
+    return HQR_SUCCESS;
+  }
+  if (enable == 0) {
+    cudaFree(P->dtrace);
+    P->dtrace = nullptr;
+    return HQR_SUCCESS;
+  }
+  if (!count) return -5;
+  *count = P->dtrace ? nt : 0;
+  if (!P->dtrace) return HQR_SUCCESS;
+  if (!host || cap < 4 * nt) return HQR_ERR_CAPACITY;
+  std::vector<unsigned long long> tmp(3 * nt);
+  CK(cudaMemcpy(tmp.data(), P->dtrace, 3 * sizeof(unsigned long long) * nt, cudaMemcpyDeviceToHost));
+  for (size_t t = 0; t < nt; ++t) {
+    host[4 * t + 0] = tmp[3 * t + 0];
+    host[4 * t + 1] = tmp[3 * t + 1];
+    host[4 * t + 2] = tmp[3 * t + 2];
+    host[4 * t + 3] = (uint64_t)(uint32_t)P->task_kind[t];
+  }
+  return HQR_SUCCESS;
+}
+
+int hqr_ls_plan_run(hqr_ls_plan *P, void *stream) {
+  if (!P) return -1;
+  g_launches = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  P->ran = true;
+  if (P->cge) {  // events around the whole graph: preparation + task kernel + finish
+    CK(cudaEventRecord(P->ev0, s));
+    CK(cudaGraphLaunch(P->cge, s));
+    CK(cudaEventRecord(P->ev1, s));
+    g_launches = 3;
+    return HQR_SUCCESS;
+  }
+  int st = plan_enqueue(P, s, true);
+  g_launches += 2;  // preparation and finishing kernels (the task kernel counted at launch)
+  return st;
+}
+
+int hqr_ls_plan_capture(hqr_ls_plan *P, void *stream) {
+  if (!P) return -1;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!s) return -2;
+  if (P->cge) {
+    cudaGraphExecDestroy(P->cge);
+    P->cge = nullptr;
+  }
+  if (P->cg) {
+    cudaGraphDestroy(P->cg);
+    P->cg = nullptr;
+  }
+  int grid = 0;  // sets the kernel's shared-memory attribute outside the capture
+  int st = ctas_for(P->prec, P->smem, P->graph.ntasks, &grid);
+  if (st) return st;
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  st = plan_enqueue(P, s, false);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (st) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  CK(e);
+  P->cg = g;
+  CK(cudaGraphInstantiate(&P->cge, P->cg, 0));
+  return HQR_SUCCESS;
+}
+
+int hqr_ls_plan_status(hqr_ls_plan *P, void *stream) {
+  if (!P) return -1;
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  CtlLine c;
+  CK(cudaMemcpy(&c, &P->graph.ctl->status, sizeof(CtlLine), cudaMemcpyDeviceToHost));
+  if (c.v) return (int)c.v;
+  std::vector<int> stv(P->count);
+  CK(cudaMemcpy(stv.data(), P->dstatus, sizeof(int) * P->count, cudaMemcpyDeviceToHost));
+  for (int v : stv)
+    if (v) return v;
+  return HQR_SUCCESS;
+}
+
+int hqr_ls_plan_info(hqr_ls_plan *P, int64_t *ntasks, double *qr_flops, float *kernel_ms) {
+  if (!P) return -1;
+  if (ntasks) *ntasks = P->graph.ntasks;
+  if (qr_flops) *qr_flops = P->flops;
+  if (kernel_ms) {
+    *kernel_ms = 0.f;
+    if (P->ran) {
+      CK(cudaEventSynchronize(P->ev1));
+      CK(cudaEventElapsedTime(kernel_ms, P->ev0, P->ev1));
+    }
+  }
+  return HQR_SUCCESS;
+}
+
+int hqr_ls_plan_config(const hqr_ls_plan *P, int idx, hqr_tile_config_t *cfg) {
+  if (!P) return -1;
+  if (idx < 0 || idx >= P->count) return -2;
+  if (!cfg) return -3;
+  *cfg = P->cfg[idx];
+  return HQR_SUCCESS;
+}
+
+void hqr_ls_plan_free(hqr_ls_plan *P) {
+  if (!P) return;
+  P->graph.release();
+  if (P->cge) cudaGraphExecDestroy(P->cge);
+  if (P->cg) cudaGraphDestroy(P->cg);
+  cudaFree(P->arena);
+  cudaFree(P->vec);
+  cudaFree(P->dstatus);
+  cudaFree(P->dprobs);
+  cudaFree(P->dprep);
+  cudaFree(P->dtrace);
+  if (P->ev0) cudaEventDestroy(P->ev0);
+  if (P->ev1) cudaEventDestroy(P->ev1);
+  delete P;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
 // Allocation-free factorization (hqr_geqrf_r_noalloc).
 //
 // Some callers cannot allocate: code running where the device memory is
@@ -725,7 +1130,7 @@ static __device__ __align__(256) unsigned char g_na_scratch[kNaScratchBytes];
 struct NaHost {
   Task tasks[kNaMaxTasks];
   int indeg[kNaMaxTasks];
-  int slots[kNumQueues * kNaMaxTasks];
+  int slots[kNumQueues * kShards * ((kNaMaxTasks + kShards - 1) / kShards)];
   int succ[kNaMaxEdges];
   int efrom[kNaMaxEdges], eto[kNaMaxEdges];
   int cnt[kNaMaxTasks + 1];
@@ -963,20 +1368,15 @@ extern "C" int hqr_geqrf_r_noalloc(const void *dA, int M, int N, int lda, int nb
     g_na.tasks[t].succ_end = g_na.cnt[t + 1];
   }
   for (int e = 0; e < g_na.nedges; ++e) g_na.succ[g_na.cnt[g_na.efrom[e]]++] = g_na.eto[e];
-  std::memset(&g_na.ctl, 0, sizeof(Ctl));
-  for (int q = 0; q < kNumQueues * nt; ++q) g_na.slots[q] = 0;
-  for (int t = 0; t < nt; ++t)
-    if (g_na.indeg[t] == 0) {
-      const int q = g_na.tasks[t].prio;
-      g_na.slots[(size_t)q * nt + g_na.ctl.tail[q]++] = t + 1;
-    }
+  for (size_t q = 0; q < slot_count(nt); ++q) g_na.slots[q] = 0;
+  init_ready(g_na.tasks, g_na.indeg, nt, g_na.slots, g_na.ctl);
   // scratch layout
   const size_t a_bytes = na_align(sizeof(double) * (size_t)m * nb * n * nb);
   const size_t t_bytes = na_align(sizeof(double) * (size_t)m * n * 2 * ib * nb);
   const size_t k_bytes = na_align(sizeof(Task) * nt);
   const size_t s_bytes = na_align(sizeof(int) * std::max(g_na.nedges, 1));
   const size_t d_bytes = na_align(sizeof(int) * nt);
-  const size_t q_bytes = na_align(sizeof(int) * kNumQueues * nt);
+  const size_t q_bytes = na_align(sizeof(int) * slot_count(nt));
   const size_t c_bytes = na_align(sizeof(Ctl));
   const size_t p_bytes = na_align(sizeof(Problem));
   if (a_bytes + t_bytes + k_bytes + s_bytes + d_bytes + q_bytes + c_bytes + p_bytes > kNaScratchBytes)
@@ -1005,7 +1405,7 @@ extern "C" int hqr_geqrf_r_noalloc(const void *dA, int M, int N, int lda, int nb
       (g_na.nedges > 0 &&
        cudaMemcpyAsync(dsucc, g_na.succ, sizeof(int) * g_na.nedges, cudaMemcpyHostToDevice, s) != cudaSuccess) ||
       cudaMemcpyAsync(dindeg, g_na.indeg, sizeof(int) * nt, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(dslots, g_na.slots, sizeof(int) * kNumQueues * nt, cudaMemcpyHostToDevice, s) !=
+      cudaMemcpyAsync(dslots, g_na.slots, sizeof(int) * slot_count(nt), cudaMemcpyHostToDevice, s) !=
           cudaSuccess ||
       cudaMemcpyAsync(dctl, &g_na.ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(dprob, &g_na.prob, sizeof(Problem), cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -1034,8 +1434,9 @@ extern "C" int hqr_geqrf_r_noalloc(const void *dA, int M, int N, int lda, int nb
   unpack_tiles<double><<<grid_for((long long)N * N), 256, 0, s>>>((const double *)dws, m, nb, (double *)dR, ldr, N,
                                                                  N, 1);
   if (cudaGetLastError() != cudaSuccess) return HQR_ERR_CUDA;
-  if (cudaMemcpyAsync(&g_na.ctl, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+  if (cudaMemcpyAsync(&g_na.ctl.status, &dctl->status, sizeof(CtlLine), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return HQR_ERR_CUDA;
-  return g_na.ctl.status;
+  return (int)g_na.ctl.status.v;
 }

@@ -18,6 +18,15 @@ enum Op : int8_t {
   OP_TSMQR = 3,
   OP_TTQRT = 4,
   OP_TTMQR = 5,
+  // FP64 vector tasks of least-squares solves (per tile of the vectors)
+  OP_RESID = 6,    // r_i = b_i - A(i,:) x, compensated (row tile i)
+  OP_ATR = 7,      // g_j = A(:,j)^T r, compensated (column tile j)
+  OP_TRSV_TD = 8,  // g_i <- R_ii^{-T} g_i (forward substitution, diagonal tile i)
+  OP_TRSV_TU = 9,  // g_j -= R(i,j)^T g_i, j > i
+  OP_TRSV_D = 10,  // g_i <- R_ii^{-1} g_i (back substitution, diagonal tile i)
+  OP_TRSV_U = 11,  // g_j -= R(j,i) g_i, j < i
+  OP_XUPD = 12,    // x_j += g_j
+  OP_BTOG = 13,    // g_i = first column of the right-hand-side block of row tile i
 };
 
 // Scheduling classes, highest first: panel kernels (on the critical path),
@@ -70,6 +79,13 @@ Graph build_factor_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, 
 // row tiles and `nslab` column slabs of width w: the update kernels replayed
 // forward or backwards.
 Graph build_apply_graph(const std::vector<PanelOp> &ops, int m, int nslab, int w, int trans, int pid = 0);
+
+// Least-squares task graph for one problem of m x n tiles (tile size nb, true
+// column count N): the factorization, then either `iters` rounds of
+// corrected semi-normal equations (x0 = 0; r = b - A x, g = A^T r,
+// R^T R d = g, x += d; all FP64) or, with iters = 0, Q^T b applied to the
+// right-hand-side block followed by R x = (Q^T b)[0:N].
+Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int w, int iters, int pid);
 
 // Append graph g to `into` (its task ids and successor lists renumbered);
 // the two graphs stay independent.

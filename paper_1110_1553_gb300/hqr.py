@@ -29,7 +29,9 @@ ELIM_DTYPE = np.dtype([("k", np.int32), ("i", np.int32), ("killer", np.int32), (
 
 EXPORTS = ["hqr_elim_list", "hqr_validate_list", "hqr_geqrf", "hqr_refactor", "hqr_refactor_async",
            "hqr_status", "hqr_get_r", "hqr_get_tiles", "hqr_get_t", "hqr_factors_info", "hqr_kernel_ms", "hqr_trace", "hqr_apply_q",
-           "hqr_gels", "hqr_geqrf_r_noalloc", "hqr_debug_block_task", "hqr_factors_free", "hqr_set_timeout_ms", "hqr_strerror", "hqr_last_error",
+           "hqr_gels", "hqr_geqrf_r_noalloc", "hqr_ls_plan_create", "hqr_ls_plan_run",
+           "hqr_ls_plan_capture", "hqr_ls_plan_status", "hqr_ls_plan_info", "hqr_ls_plan_config",
+           "hqr_ls_plan_free", "hqr_ls_plan_trace", "hqr_set_tuning", "hqr_debug_block_task", "hqr_factors_free", "hqr_set_timeout_ms", "hqr_strerror", "hqr_last_error",
            "hqr_last_launches"]
 
 
@@ -79,6 +81,17 @@ def load(build_if_missing=False):
     lib.hqr_trace.argtypes = [vp, i32, vp, sz, ctypes.POINTER(sz)]
     lib.hqr_apply_q.argtypes = [vp, i32, vp, i32, i32, vp]
     lib.hqr_gels.argtypes = [vp, i32, i32, i32, vp, i32, i32, vp, i32, i32, i32, i32, vp, sz, vp]
+    lib.hqr_ls_plan_create.argtypes = [i32, vp, vp, i32, i32, pf]
+    lib.hqr_ls_plan_run.argtypes = [vp, vp]
+    lib.hqr_ls_plan_capture.argtypes = [vp, vp]
+    lib.hqr_ls_plan_status.argtypes = [vp, vp]
+    lib.hqr_ls_plan_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_float)]
+    lib.hqr_ls_plan_config.argtypes = [vp, i32, vp]
+    lib.hqr_ls_plan_trace.argtypes = [vp, i32, vp, sz, ctypes.POINTER(sz)]
+    lib.hqr_ls_plan_free.argtypes = [vp]
+    lib.hqr_ls_plan_free.restype = None
+    lib.hqr_set_tuning.argtypes = [i32, vp, vp]
     lib.hqr_geqrf_r_noalloc.argtypes = [vp, i32, i32, i32, i32, i32, vp, sz, vp, i32, vp]
     lib.hqr_debug_block_task.argtypes = [vp, i64, i32]
     lib.hqr_factors_free.argtypes = [vp]
@@ -330,3 +343,108 @@ def geqrf_r_noalloc(A, nb, ib, records, R, stream=None):
                                     ctypes.c_void_p(R.data_ptr()), R.stride(1), _stream_ptr(stream))
     del keep
     return st
+
+
+# ------------------------------------------------------- least squares --
+
+class LSProblem(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("N", ctypes.c_int), ("dA", ctypes.c_void_p), ("lda", ctypes.c_int),
+                ("db", ctypes.c_void_p), ("dx", ctypes.c_void_p)]
+
+
+class TileConfig(ctypes.Structure):
+    _fields_ = [("nb", ctypes.c_int), ("ib", ctypes.c_int), ("a", ctypes.c_int), ("p", ctypes.c_int),
+                ("low_tree", ctypes.c_int), ("high_tree", ctypes.c_int)]
+
+    def as_tuple(self):
+        return (self.nb, self.ib, self.a, self.p, self.low_tree, self.high_tree)
+
+
+def tile_config(nb=0, ib=0, a=1, p=1, low="greedy", high="greedy"):
+    return TileConfig(nb, ib, a, p, TREES.get(low, low), TREES.get(high, high))
+
+
+class LSPlan:
+    """Many least-squares problems solved by one persistent launch (see
+    hqr_ls_plan_create). `problems` is a list of (A, b, x) CUDA tensors: A
+    column-major M x N (float32 or float64, all the same), b float64 (M),
+    x float64 (N, written by run())."""
+
+    def __init__(self, problems, refine_iters, configs=None):
+        torch = _torch()
+        self._keep = []
+        arr = (LSProblem * len(problems))()
+        dtype = None
+        for q, (A, b, x) in enumerate(problems):
+            Ac, lda = colmajor(A)
+            if dtype is None:
+                dtype = Ac.dtype
+            elif Ac.dtype != dtype:
+                raise TypeError("all matrices of a plan share one precision")
+            if b.dtype != torch.float64 or x.dtype != torch.float64 or not b.is_contiguous() \
+                    or not x.is_contiguous():
+                raise TypeError("b and x must be contiguous float64 CUDA vectors")
+            self._keep += [Ac, b, x]
+            arr[q] = LSProblem(Ac.shape[0], Ac.shape[1], Ac.data_ptr(), lda, b.data_ptr(), x.data_ptr())
+        cfg = None
+        if configs is not None:
+            cfg = (TileConfig * len(problems))(*configs)
+        h = ctypes.c_void_p(0)
+        st = load().hqr_ls_plan_create(len(problems), ctypes.byref(arr), ctypes.byref(cfg) if cfg else None,
+                                       prec_of(self._keep[0]), int(refine_iters), ctypes.byref(h))
+        _check(st, "hqr_ls_plan_create")
+        self._h = h
+        self.count = len(problems)
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.hqr_ls_plan_free(self._h)
+            self._h = None
+
+    def run(self, stream=None):
+        _check(load().hqr_ls_plan_run(self._h, _stream_ptr(stream)), "hqr_ls_plan_run")
+
+    def capture(self, stream):
+        _check(load().hqr_ls_plan_capture(self._h, ctypes.c_void_p(stream.cuda_stream)), "hqr_ls_plan_capture")
+
+    def status(self, stream=None):
+        return load().hqr_ls_plan_status(self._h, _stream_ptr(stream))
+
+    def info(self):
+        nt, fl, ms = ctypes.c_int64(0), ctypes.c_double(0), ctypes.c_float(0)
+        _check(load().hqr_ls_plan_info(self._h, ctypes.byref(nt), ctypes.byref(fl), ctypes.byref(ms)),
+               "hqr_ls_plan_info")
+        return {"tasks": nt.value, "qr_flops": fl.value, "kernel_ms": ms.value}
+
+    def trace(self, enable=None):
+        """enable=True/False switches tracing; no argument: the last run's
+        records, (ntasks, 4) uint64 (start, end, CTA << 32 | SM, op << 24 | pid)."""
+        lib = load()
+        cnt = ctypes.c_size_t(0)
+        if enable is not None:
+            _check(lib.hqr_ls_plan_trace(self._h, 1 if enable else 0, None, 0, ctypes.byref(cnt)),
+                   "hqr_ls_plan_trace")
+            return None
+        st = lib.hqr_ls_plan_trace(self._h, -1, None, 0, ctypes.byref(cnt))
+        if st not in (0, ERR_CAPACITY):
+            _check(st, "hqr_ls_plan_trace")
+        out = np.zeros((cnt.value, 4), dtype=np.uint64)
+        if cnt.value:
+            _check(lib.hqr_ls_plan_trace(self._h, -1, out.ctypes.data, out.size, ctypes.byref(cnt)),
+                   "hqr_ls_plan_trace")
+        return out
+
+    def config(self, idx):
+        c = TileConfig()
+        _check(load().hqr_ls_plan_config(self._h, idx, ctypes.byref(c)), "hqr_ls_plan_config")
+        return c.as_tuple()
+
+
+def set_tuning(table):
+    """Install an autotuner table {(floor(log2 M), floor(log2 N)): TileConfig}."""
+    keys = (ctypes.c_int * (2 * max(1, len(table))))()
+    cfgs = (TileConfig * max(1, len(table)))()
+    for e, ((lm, ln), c) in enumerate(sorted(table.items())):
+        keys[2 * e], keys[2 * e + 1] = lm, ln
+        cfgs[e] = c
+    _check(load().hqr_set_tuning(len(table), keys, cfgs), "hqr_set_tuning")

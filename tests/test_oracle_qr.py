@@ -241,3 +241,17 @@ def test_csne_converges_with_perturbed_r():
     xs = csne(A, R32, bb, 6)
     errs = [np.linalg.norm(x - xe) / np.linalg.norm(xe) for x in xs]
     assert errs[-1] <= 1e-13 and errs[-1] < errs[0]
+
+
+def test_lstsq_unblocked_any_shape():
+    from oracle.lstsq import lstsq_unblocked
+    r = rng(16)
+    for M, N in ((70, 23), (33, 33), (100, 1)):
+        A = r.standard_normal((M, N))
+        xt = r.standard_normal(N)
+        x = lstsq_unblocked(A, A @ xt)
+        assert np.linalg.norm(x - xt) / np.linalg.norm(xt) <= 1e-13
+        b = r.standard_normal(M)
+        x = lstsq_unblocked(A, b)
+        xe = np.linalg.lstsq(A, b, rcond=None)[0]
+        assert np.linalg.norm(x - xe) / np.linalg.norm(xe) <= 1e-12
