@@ -20,6 +20,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -56,6 +58,29 @@ def oracle_rate(M, N, wl, repeats=1):
         tile_qr(A, wl["nb"], wl["ib"], L)
         times.append(time.perf_counter() - t0)
     return qr_flops(M, N) / 1e12 / statistics.median(times), statistics.median(times)
+
+
+def oracle_batched(b, sample=8):
+    """CPU oracle on the first `sample` batched problems: its solves/s and the
+    relative error of both GPU paths' x against it."""
+    import numpy as np
+
+    from oracle.lstsq import lstsq_unblocked
+    shapes, data = b["_data"]
+    errs = {"mixed": [], "fp64": []}
+    t0 = time.perf_counter()
+    for q in range(sample):
+        A = data[q][0].double().cpu().numpy()
+        bb = data[q][1].cpu().numpy()
+        xo = lstsq_unblocked(A, bb)
+        for label in errs:
+            x = b["_x_" + label][q].cpu().numpy()
+            errs[label].append(float(np.linalg.norm(x - xo) / np.linalg.norm(xo)))
+    secs = time.perf_counter() - t0
+    return {"kind": "oracle", "unit": "solves/s", "value": sample / secs, "cores": host_threads(),
+            "sample": "oracle least squares (unblocked Householder QR + Dot2 refinement) of the first %d "
+                      "batched problems" % sample,
+            "max_rel_err_vs_oracle": {k: max(v) for k, v in errs.items()}}
 
 
 def host_threads():
@@ -152,6 +177,170 @@ def ncu_traffic():
     return float(m_b.group(1)), None
 
 
+def latency_square(torch, hqr, inputs, dev, reps=100):
+    """512 x 512 FP64 (nb 64, ib 16, flat TS a = 8): QR plus Q applied to I,
+    device time per call, p50 / p99 over `reps` calls."""
+    A = inputs.gaussian_torch(512, 512, seed=11, device=dev)
+    recs = hqr.elim_list(8, 8, 8, 1, "flat", "flat")
+    F = hqr.geqrf(A, 64, 16, recs)
+    I = torch.eye(512, dtype=torch.float64, device=dev)
+    Q = I.clone().t().contiguous().t()
+    times = []
+    for q in range(reps + 5):
+        Q.copy_(I)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        F.refactor_async(A)
+        F.apply_q(Q, trans=False)
+        e1.record()
+        e1.synchronize()
+        if q >= 5:
+            times.append(e0.elapsed_time(e1) * 1e3)
+    times.sort()
+    fl = 2 * 512 ** 3 - 2 / 3 * 512 ** 3
+    return {"workload": "fp64_square_512_nb64_ib16_flat_ts", "p50_us": times[len(times) // 2],
+            "p99_us": times[min(len(times) - 1, int(0.99 * len(times)))], "qr_flops": fl,
+            "includes": "tile QR + Q applied to I (apply-Q graph), per call"}
+
+
+def batched(torch, hqr, dev, count=1024, refine=4, tune=True):
+    """1024 uneven least-squares problems in one persistent launch: mixed
+    (FP32 QR + FP64 CSNE) and plain FP64 (QR + Q^T b + back substitution)."""
+    from paper_1110_1553_gb300 import workloads
+    shapes = workloads.uneven_shapes(count)
+    out = {"workload": "batched_uneven_%d_fp32_ls" % count, "problems": count}
+    g = torch.Generator(device=dev)
+    g.manual_seed(1234)
+    data = [(torch.randn((n, m), dtype=torch.float32, device=dev, generator=g).t(),
+             torch.randn(m, dtype=torch.float64, device=dev, generator=g)) for (m, n) in shapes]
+    for label, dtype, iters in (("mixed", torch.float32, refine), ("fp64", torch.float64, 0)):
+        if tune:
+            t0 = time.perf_counter()
+            table = hqr.autotune(shapes, dtype, iters, reps=24)
+            out[label + "_autotune_s"] = time.perf_counter() - t0
+            out[label + "_autotune_classes"] = len(table)
+        probs = [(A if dtype == torch.float32 else A.double().t().contiguous().t(), b,
+                  torch.zeros(n, dtype=torch.float64, device=dev)) for (A, b), (m, n) in zip(data, shapes)]
+        plan = hqr.LSPlan(probs, refine_iters=iters)
+        s = torch.cuda.Stream(dev)
+        plan.capture(s)
+        for _ in range(2):
+            plan.run(s)
+        s.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record(s)
+        for _ in range(reps):
+            plan.run(s)
+        e1.record(s)
+        e1.synchronize()
+        st = plan.status(s)
+        ms = e0.elapsed_time(e1) / reps
+        info = plan.info()
+        out[label] = {"solves_per_s": count / (ms * 1e-3), "ms_per_batch": ms,
+                      "qr_tflops": info["qr_flops"] / (ms * 1e-3) / 1e12, "tasks": info["tasks"],
+                      "refine_iters": iters, "status": st, "launches_per_batch": 3, "cuda_graph": True}
+        out["_x_" + label] = [p[2] for p in probs[:8]]
+        hqr.set_tuning({})
+    out["mixed_over_fp64"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    out["_data"] = (shapes, data)
+    return out
+
+
+def serving(torch, hqr, dev, rate=2000.0, seconds=5.0, refine=5):
+    """Poisson request stream at `rate` req/s for `seconds`: 90 % uneven
+    batched-like shapes, 10 % 32768 x 1024 FP32 with kappa = 1e4. Mixed server
+    vs plain FP64 server on the same arrivals."""
+    from collections import deque
+
+    from paper_1110_1553_gb300 import inputs, workloads
+    rng = inputs.rng(5, 0)
+    small_shapes = workloads.uneven_shapes(256, seed=6)
+    g = torch.Generator(device=dev)
+    g.manual_seed(99)
+    small = [(torch.randn((n, m), dtype=torch.float32, device=dev, generator=g).t(),
+              torch.randn(m, dtype=torch.float64, device=dev, generator=g)) for (m, n) in small_shapes]
+    large = [(workloads.conditioned(torch, 32768, 1024, 1e4, seed=40 + q, device=dev),
+              torch.randn(32768, dtype=torch.float64, device=dev, generator=g)) for q in range(4)]
+    n_req = int(rate * seconds)
+    gaps = rng.exponential(1.0 / rate, n_req)
+    arrivals = np.cumsum(gaps)
+    kinds = rng.uniform(size=n_req) < 0.1
+    idx = rng.integers(0, 1 << 30, size=n_req)
+    out = {"workload": "serving_poisson_%d_per_s_%gs_90pct_uneven_10pct_32768x1024_kappa1e4" % (rate, seconds),
+           "offered_per_s": rate, "requests": n_req}
+    for label, dtype, iters in (("mixed", torch.float32, refine), ("fp64", torch.float64, 0)):
+        pool_s = small if dtype == torch.float32 else [(A.double().t().contiguous().t(), b) for A, b in small]
+        pool_l = large if dtype == torch.float32 else [(A.double().t().contiguous().t(), b) for A, b in large]
+        srv = hqr.Server(dtype, refine_iters=iters, max_live=2048, hbm_budget=120 << 30,
+                         task_pool=16 << 20, edge_pool=64 << 20)
+        srv.start()
+        lat, inflight, queue = [], {}, deque()
+        t0 = time.perf_counter()
+        i = 0
+        try:
+            while i < n_req or queue or inflight:
+                now = time.perf_counter() - t0
+                while i < n_req and arrivals[i] <= now:
+                    queue.append(i)
+                    i += 1
+                while queue:
+                    q = queue[0]
+                    A, b = pool_l[idx[q] % 4] if kinds[q] else pool_s[idx[q] % 256]
+                    x = torch.zeros(A.shape[1], dtype=torch.float64, device=dev)
+                    t = srv.submit(A, b, x)
+                    if t is None:
+                        break
+                    inflight[t] = arrivals[q]
+                    queue.popleft()
+                done = srv.poll()
+                now = time.perf_counter() - t0
+                for t in done:
+                    lat.append(now - inflight.pop(t))
+                if now > seconds * 4:  # a saturated server: stop at 4x the arrival window
+                    break
+            wall = time.perf_counter() - t0
+        finally:
+            srv.stop()
+        lat.sort()
+        out[label] = {"completed": len(lat), "not_completed": n_req - len(lat),
+                      "solves_per_s": len(lat) / wall, "wall_s": wall,
+                      "p50_ms": 1e3 * lat[len(lat) // 2] if lat else None,
+                      "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None,
+                      "refine_iters": iters}
+        del srv
+    return out
+
+
+def square_mixed(torch, hqr, dev, n=16384, refine=12):
+    """16384^2 FP32 least squares, A = U diag(s) V^T, s geometric 1 .. 1e-6,
+    b = A x_true + 1e-8 N(0,1): FP32 tile QR + FP64 CSNE."""
+    from paper_1110_1553_gb300 import workloads
+    A = workloads.conditioned(torch, n, n, 1e6, seed=30, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(31)
+    xt = torch.randn(n, dtype=torch.float64, device=dev, generator=g)
+    b = A.double() @ xt + 1e-8 * torch.randn(n, dtype=torch.float64, device=dev, generator=g)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    cfg = [hqr.tile_config(128, 16, 4, 1, "greedy", "greedy")]
+    plan = hqr.LSPlan([(A, b, x)], refine_iters=refine, configs=cfg)
+    plan.run()
+    plan.status()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    plan.run()
+    e1.record()
+    e1.synchronize()
+    st = plan.status()
+    ms = e0.elapsed_time(e1)
+    info = plan.info()
+    r = b - A.double() @ x
+    atr = (A.double().t() @ r).norm().item() / (torch.linalg.norm(A.double()).item() * r.norm().item())
+    return {"workload": "square_mixed_ls_16384_kappa1e6", "ms": ms, "solves_per_s": 1e3 / ms,
+            "qr_tflops": info["qr_flops"] / (ms * 1e-3) / 1e12, "refine_iters": refine, "status": st,
+            "normal_eq_residual": atr, "tasks": info["tasks"], "_x": x, "_A": A, "_b": b}
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
@@ -185,6 +374,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the latency, batched, serving and square mixed-precision measurements")
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--rows", type=int, default=WORKLOAD["M"],
                     help="rows M of the tall-skinny matrix (default: the full workload; smaller values "
                          "only for profiling captures)")
@@ -281,6 +473,16 @@ def main():
 
     peak = measured_dgemm_tflops(torch, dev) if rank == 0 else None
     traffic, traffic_note = ncu_traffic()
+    ntasks = F.ntasks
+    del F
+    torch.cuda.empty_cache()
+
+    extras = {}
+    if not args.no_extras and M == WORKLOAD["M"]:
+        extras["latency_square"] = latency_square(torch, hqr, inputs, dev)
+        extras["batched"] = batched(torch, hqr, dev)
+        extras["square_mixed"] = square_mixed(torch, hqr, dev)
+        extras["serving"] = serving(torch, hqr, dev, seconds=args.serve_seconds)
 
     if rank != 0:
         return 0
@@ -290,12 +492,17 @@ def main():
         cpu = {"value": rate, "unit": "TFLOP/s", "cores": host_threads(), "kind": "oracle",
                "sample": "oracle tile QR (NumPy FP64) of the first %d x %d rows/cols of the workload, "
                          "%.1f s" % (SAMPLE_M, N, secs)}
+        if "batched" in extras:
+            cpu["batched"] = oracle_batched(extras["batched"])
+    for key in list(extras):
+        if isinstance(extras[key], dict):
+            extras[key] = {k: v for k, v in extras[key].items() if not k.startswith("_")}
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME if M == WORKLOAD["M"] else "profiling_%dx%d" % (M, N),
-                   **wl, "tasks": F.ntasks,
+                   **wl, "tasks": ntasks,
                    "l2": "inputs larger than L2 (A is %.2f GB)" % (M * N * 8 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": M * N * 8,
@@ -310,9 +517,10 @@ def main():
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
         "accuracy": {"max_rel_colnorm_err_R_vs_A": cn_err},
+        "extras": extras,
         "setup_s": t_setup,
     }
-    print(json.dumps(line))
+    print(json.dumps(line, default=lambda o: None))
     if dist is not None:
         dist.destroy_process_group()
     return 0

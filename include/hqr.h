@@ -73,7 +73,9 @@ enum {
   HQR_ERR_INVALID_LIST = 5, /* elimination list breaks a rule of Sec. 2 */
   HQR_ERR_SINGULAR = 6,  /* exact zero on the diagonal of R (hqr_gels) */
   HQR_ERR_INTERNAL = 7,  /* internal consistency check failed */
-  HQR_ERR_TOO_LARGE = 8  /* problem exceeds the fixed limits of hqr_geqrf_r_noalloc */
+  HQR_ERR_TOO_LARGE = 8, /* problem exceeds the fixed limits of hqr_geqrf_r_noalloc */
+  HQR_ERR_BUSY = 9,      /* server: no slot, memory or pool space free right now; retry later */
+  HQR_ERR_BUDGET = 10    /* server: the request can never fit the server's budget */
 };
 
 /* Opaque factorization: owns the tile workspace (V and R), the T factors,
@@ -324,6 +326,83 @@ void hqr_ls_plan_free(hqr_ls_plan *plan);
  * keys[2e+1]. Host only; copied. count = 0 clears it.
  */
 int hqr_set_tuning(int count, const int *keys, const hqr_tile_config_t *cfgs);
+
+/*
+ * hqr_autotune -- measured autotuner for least-squares plans. For every
+ * shape class (floor(log2 M), floor(log2 N)) among the `count` shapes
+ * (Ms[q] x Ns[q]), times candidate tile configurations (nb in {32, 64, 128},
+ * TS domains a in {1, 4, 16} with greedy trees, or one flat TS domain) on
+ * `reps` random problems of the class's geometric-mean shape solved in one
+ * plan (prec, refine_iters as in hqr_ls_plan_create), and installs the
+ * fastest per class with hqr_set_tuning. The chosen table is also copied to
+ * keys_out (2 ints per class) / cfg_out when cap is large enough;
+ * *nout = number of classes. Synchronizes `stream`; allocates and frees its
+ * own random test matrices.
+ */
+int hqr_autotune(int count, const int *Ms, const int *Ns, int prec, int refine_iters, int reps,
+                 int *keys_out, hqr_tile_config_t *cfg_out, int cap, int *nout, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Least-squares server (continuous batching). One resident persistent task
+ * kernel serves requests for its whole lifetime: a request submitted while
+ * others are running is admitted as soon as a slot, workspace memory within
+ * the HBM budget and task-pool space are free, its task graph (packing,
+ * tile QR, solve as in hqr_ls_plan_create) is copied into the device pools
+ * and announced through an inbox that the kernel polls, and its tasks then
+ * run interleaved with those of every other live request. Each request's
+ * tiles, T factors and vectors stay resident in its own workspace until it
+ * completes. Completion is published in host-mapped memory.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int prec;            /* HQR_FP32 (mixed precision) or HQR_FP64 */
+  int refine_iters;    /* as in hqr_ls_plan_create */
+  int max_live;        /* requests in flight at most */
+  size_t hbm_budget;   /* bytes of request workspace (tiles, T, vectors) */
+  int64_t task_pool;   /* task records in the device pool */
+  int64_t edge_pool;   /* successor entries in the device pool */
+} hqr_server_opts;
+
+typedef struct hqr_server hqr_server;
+
+/* hqr_server_create -- allocate the pools and the workspace arena
+ * (hbm_budget bytes); nothing runs yet. */
+int hqr_server_create(const hqr_server_opts *opts, hqr_server **server);
+
+/* hqr_server_start -- launch the resident task kernel on the server's own
+ * stream; returns at once. The kernel leaves by itself after about one
+ * second without work (so an idle or forgotten server does not hold the
+ * GPU); submit, poll and stop relaunch it whenever work is owed. */
+int hqr_server_start(hqr_server *server);
+
+/* hqr_server_submit -- admit one request (pointers as in hqr_ls_problem_t;
+ * the caller keeps A, b and x valid until the request completes). Returns 0
+ * and a ticket, HQR_ERR_BUSY when it does not fit right now (poll, then
+ * retry), or HQR_ERR_BUDGET when it can never fit. The tile configuration
+ * comes from the tuning table (hqr_set_tuning / hqr_autotune) or the
+ * heuristic, with nb <= 128. */
+int hqr_server_submit(hqr_server *server, const hqr_ls_problem_t *problem, int64_t *ticket);
+
+/* hqr_server_poll -- collect requests completed since the last poll
+ * (their tickets into done[0 .. min(cap, *count)) ) and free their
+ * resources. Returns the kernel's status (0 while healthy). */
+int hqr_server_poll(hqr_server *server, int64_t *done, int cap, int *count);
+
+/* hqr_server_stats -- requests submitted / completed, live requests, bytes
+ * of the budget in use. */
+int hqr_server_stats(const hqr_server *server, int64_t *submitted, int64_t *completed, int *live,
+                     size_t *bytes_in_use);
+
+/* hqr_server_counters -- device-side counters for monitoring: out[0] inbox
+ * entries claimed, out[1] inbox entries posted, out[2] stop flag, out[3]
+ * tasks outstanding (approximate while running), out[4] 1 if the resident
+ * kernel is running. cap >= 5. */
+int hqr_server_counters(const hqr_server *server, uint32_t *out, int cap);
+
+/* hqr_server_stop -- let the kernel finish all admitted work and exit;
+ * returns its status. */
+int hqr_server_stop(hqr_server *server);
+
+void hqr_server_free(hqr_server *server);
 
 /* hqr_factors_free -- release a factorization (NULL is allowed). */
 void hqr_factors_free(hqr_factors *F);

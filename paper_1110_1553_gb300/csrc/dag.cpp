@@ -206,7 +206,8 @@ Graph build_apply_graph(const std::vector<PanelOp> &ops, int m, int nslab, int w
   return b.finish();
 }
 
-Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int w, int iters, int pid) {
+Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int w, int iters, int pid,
+                     bool pack) {
   const int S = (nb + w - 1) / w;
   const size_t per_tile = (size_t)S + 2;
   const size_t ntile_res = (size_t)m * n * per_tile;
@@ -218,9 +219,25 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
   auto rres = [&](int i) { return ntile_res + (size_t)n + (size_t)i; };
   auto gres = [&](int j) { return ntile_res + (size_t)n + (size_t)m + (size_t)j; };
   auto bres = [&](int i) { return ntile_res + (size_t)2 * n + (size_t)m + (size_t)i; };
-  Builder b(ntile_res + 2 * (size_t)n + 2 * (size_t)m);
+  const int nch = atr_chunks(m);
+  auto pres = [&](int c, int j) { return ntile_res + (size_t)2 * n + 2 * (size_t)m + (size_t)c * n + (size_t)j; };
+  Builder b(ntile_res + 2 * (size_t)n + 2 * (size_t)m + (size_t)nch * n);
   Tracker &tr = b.tr();
   std::vector<int32_t> &d = b.deps();
+  if (pack) {
+    for (int j = 0; j < n; ++j) {
+      for (int i = 0; i < m; ++i) {
+        for (int s = 0; s < S; ++s) tr.write(slab(i, j, s), d);
+        tr.write(upart(i, j), d);
+        tr.write(lpart(i, j), d);
+      }
+      if (j == 0) {
+        for (int i = 0; i < m; ++i) tr.write(bres(i), d);
+        for (int jj = 0; jj < n; ++jj) tr.write(xres(jj), d);
+      }
+      b.add(make_task(OP_PACK, 0, 0, 0, 0, j, 0, 0, 1, 0, pid));
+    }
+  }
   for (const PanelOp &o : ops) {
     const int k = o.k;
     if (o.kind == 0) {
@@ -330,9 +347,14 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
       b.add(vtask(OP_RESID, i, i));
     }
     for (int j = 0; j < n; ++j) {
-      for (int i = 0; i < m; ++i) tr.read(rres(i), d);
+      for (int c = 0; c < nch; ++c) {
+        for (int i = c * kAtrChunk; i < std::min(m, (c + 1) * kAtrChunk); ++i) tr.read(rres(i), d);
+        tr.write(pres(c, j), d);
+        b.add(vtask(OP_ATR, c, j));
+      }
+      for (int c = 0; c < nch; ++c) tr.read(pres(c, j), d);
       tr.write(gres(j), d);
-      b.add(vtask(OP_ATR, j, j));
+      b.add(vtask(OP_ATRR, j, j));
     }
     solve_r(true);
   }

@@ -85,7 +85,7 @@ inline void init_ready(const Task *tasks, const int *indeg, int ntasks, int *slo
 inline size_t slot_count(int ntasks) { return (size_t)kNumQueues * kShards * shard_cap(ntasks); }
 
 // One problem of a (possibly batched) task graph.
-struct Problem {
+struct alignas(16) Problem {
   void *A;            // tile workspace: tile (i, j) at ((j*m + i)*nb*nb), column-major
   void *T;            // T factors: ((k*m + i)*2 + which)*ib*nb, ib x nb column-major
   void *B;            // right-hand-side blocks: block (r, s) at ((s*m + r)*nb*wb)
@@ -99,9 +99,11 @@ struct Problem {
   const void *A0;     // the caller's matrix, column-major, storage precision
   long long lda0;
   const double *b;    // right-hand side (M)
-  double *x, *r, *g;  // solution (n*nb), residual (m*nb), work vector (n*nb)
+  double *x, *r, *g;  // solution (N), residual (m*nb), work vector (n*nb)
+  double *gp;         // partial sums of A^T r: (row chunk, column) pairs (sum, compensation)
   int *status;        // per-problem status word (HQR_ERR_SINGULAR)
 };
+static_assert(sizeof(Problem) % 16 == 0, "Problem is read in 16-byte pieces");
 
 struct EngineParams {
   const Problem *probs;
@@ -669,18 +671,35 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
       __syncthreads();
       break;
     }
-    case OP_ATR: {  // g_j = A(:,j)^T r
+    case OP_ATR: {  // partial sums of A(rows of chunk t.i, tile j)^T r
       const int c0 = t.j * nb, nc = min(nb, P.N - c0);
+      const int rlo = t.i * kAtrChunk * nb, rhi = min(P.M, rlo + kAtrChunk * nb);
+      const size_t np = (size_t)g.n * nb;
       for (int cc = warp; cc < nc; cc += NWARP) {
         const Real *acol = A0 + (long long)(c0 + cc) * P.lda0;
         double s = 0.0, c = 0.0;
-        for (int i = lane; i < P.M; i += 32) dot2_step((double)acol[i], P.r[i], s, c);
+        for (int i = rlo + lane; i < rhi; i += 32) dot2_step((double)acol[i], P.r[i], s, c);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           const double s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, c, o);
           dot2_merge(s, c, s2, c2);
         }
-        if (lane == 0) P.g[c0 + cc] = s + c;
+        if (lane == 0) {
+          P.gp[2 * ((size_t)t.i * np + c0 + cc)] = s;
+          P.gp[2 * ((size_t)t.i * np + c0 + cc) + 1] = c;
+        }
+      }
+      break;
+    }
+    case OP_ATRR: {  // g_j = sum of the chunk partials, in chunk order
+      const int c0 = t.j * nb, nc = min(nb, P.N - c0);
+      const int nch = (g.m + kAtrChunk - 1) / kAtrChunk;
+      const size_t np = (size_t)g.n * nb;
+      for (int cc = tid; cc < nc; cc += NT) {
+        double s = P.gp[2 * (size_t)(c0 + cc)], c = P.gp[2 * (size_t)(c0 + cc) + 1];
+        for (int q = 1; q < nch; ++q)
+          dot2_merge(s, c, P.gp[2 * ((size_t)q * np + c0 + cc)], P.gp[2 * ((size_t)q * np + c0 + cc) + 1]);
+        P.g[c0 + cc] = s + c;
       }
       break;
     }
@@ -751,6 +770,23 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
       const int i = t.i, n_i = min(nb, P.N - i * nb);
       const Real *Bb = g.B + (size_t)i * nb * g.wb;
       for (int r = tid; r < n_i; r += NT) P.g[(size_t)i * nb + r] = (double)Bb[r];
+      break;
+    }
+    case OP_PACK: {  // tile column j of the workspace, zero padded; column 0 also b and x = 0
+      const int j = t.j, m = g.m;
+      const long long per_col = (long long)m * nb * nb;
+      Real *ws = g.A + (size_t)j * per_col;
+      for (long long e = tid; e < per_col; e += NT) {
+        const long long tile = e / ((long long)nb * nb);
+        const int w = (int)(e - tile * nb * nb);
+        const int cc = w / nb, rr = w - cc * nb;
+        const int row = (int)tile * nb + rr, col = j * nb + cc;
+        ws[e] = (row < P.M && col < P.N) ? A0[(long long)col * P.lda0 + row] : Real(0);
+      }
+      if (j == 0) {
+        for (int r = tid; r < m * nb; r += NT) g.B[r] = r < P.M ? (Real)P.b[r] : Real(0);
+        for (int c = tid; c < P.N; c += NT) P.x[c] = 0.0;
+      }
       break;
     }
     default:
@@ -870,6 +906,201 @@ __global__ void __launch_bounds__(NT, 2) hqr_sched(EngineParams p) {
     if (sh.abort) break;
   }
   // a bulk copy that outlived its wait must land before the CTA exits
+  if (sh.abort && threadIdx.x == 0) {
+    const uint64_t t0 = ptx::globaltimer();
+    while (!ptx::mbar_try_wait(&sh.bar, phase) && ptx::globaltimer() - t0 < 1000000000ull) {
+    }
+  }
+}
+
+
+// ------------------------------------------------------------ server mode --
+// A resident variant of the scheduler for continuous batching: requests
+// (each a least-squares task graph in a pool range, with its own problem
+// slot) arrive through an inbox written by the host while the kernel runs.
+// A CTA with nothing to do claims the next inbox entry and releases the
+// request's initial tasks; when a request's last task completes, its
+// sequence number is written to host-mapped memory. Ready queues are rings
+// (slots cleared after use). The kernel exits once the host has set `stop`
+// and no task is outstanding.
+
+struct ServeCtl {
+  CtlLine inbox_head, inbox_tail, stop, outstanding;
+};
+
+struct InboxEntry {
+  int slot, task_base, ninit, ntasks;
+};
+
+struct ServeParams {
+  EngineParams e;                 // probs (per slot), task / successor / in-degree pools, rings, status
+  ServeCtl *sc;
+  const InboxEntry *inbox;
+  int inbox_cap;                  // power of two
+  const int *initlist;            // initial ready tasks of a request at [task_base, task_base + ninit)
+  int *req_done;                  // per slot: tasks completed
+  const int *req_total;           // per slot: tasks of the request
+  const long long *req_seq;       // per slot: sequence number of the request
+  volatile long long *comp;       // host-mapped, per slot: last completed sequence number
+  int ring_cap;                   // power of two, per queue shard
+};
+
+__device__ __forceinline__ long long ld_acquire_sys_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.sys.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// A pool task, read around L1 (pool entries are rewritten for every request).
+__device__ __forceinline__ Task load_task_cg(const Task *tp) {
+  static_assert(sizeof(Task) == 40, "Task is read in 8-byte pieces");
+  Task t;
+  const int2 *src = reinterpret_cast<const int2 *>(tp);
+  int2 *dst = reinterpret_cast<int2 *>(&t);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) dst[q] = __ldcg(src + q);
+  return t;
+}
+
+__device__ __forceinline__ void serve_push(const ServeParams &sp, int task) {
+  const int2 head = __ldcg(reinterpret_cast<const int2 *>(sp.e.tasks + task));
+  const int prio = (int)(signed char)((head.x >> 8) & 0xff);  // byte 1 of the task record
+  const int qs = prio * kShards + task % kShards;
+  const unsigned idx = atomicAdd(&sp.e.ctl->tail[qs].v, 1u);
+  ptx::st_release(&sp.e.slots[(size_t)qs * sp.ring_cap + (idx & (unsigned)(sp.ring_cap - 1))], task + 1);
+}
+
+// Besides -1 (stop, error) a CTA also leaves after kIdleExitNs without any
+// work, so that an unused server never holds the GPU; the host relaunches
+// the kernel when new work arrives.
+constexpr uint64_t kIdleExitNs = 1000000000ull;
+
+__device__ int serve_pop(const ServeParams &sp, unsigned &pending) {
+  const EngineParams &p = sp.e;
+  const int home = blockIdx.x % kShards;
+  unsigned sleep_ns = 64;
+  const uint64_t idle_since = ptx::globaltimer();
+  unsigned seen_out = 0xffffffffu;  // watchdog: outstanding count last seen and since when
+  uint64_t seen_at = idle_since;
+  while (true) {
+    if (ptx::ld_relaxed((const int *)&p.ctl->status.v) != 0) return -1;
+    for (int q = 0; q < kNumQueues; ++q) {
+      for (int k = 0; k < kShards; ++k) {
+        const int qs = q * kShards + (home + k) % kShards;
+        unsigned h = ptx::ld_relaxed_u32(&p.ctl->head[qs].v);
+        while (h < ptx::ld_relaxed_u32(&p.ctl->tail[qs].v)) {
+          const unsigned old = atomicCAS(&p.ctl->head[qs].v, h, h + 1);
+          if (old == h) {
+            int *slot = &p.slots[(size_t)qs * sp.ring_cap + (h & (unsigned)(sp.ring_cap - 1))];
+            int v = ptx::ld_acquire(slot);
+            const uint64_t t1 = ptx::globaltimer();
+            while (v == 0) {
+              if (ptx::globaltimer() - t1 > (uint64_t)p.timeout_ns) {
+                set_error(p, HQR_ERR_TIMEOUT, -1);
+                return -1;
+              }
+              __nanosleep(32);
+              v = ptx::ld_acquire(slot);
+            }
+            *slot = 0;  // the ring slot can be reused
+            __threadfence();
+            return v - 1;
+          }
+          h = old;
+        }
+      }
+    }
+    // new request?
+    unsigned ih = ptx::ld_relaxed_u32(&sp.sc->inbox_head.v);
+    if (ih < (unsigned)ld_acquire_sys_u32(&sp.sc->inbox_tail.v)) {
+      if (atomicCAS(&sp.sc->inbox_head.v, ih, ih + 1) == ih) {
+        const InboxEntry *en = sp.inbox + (ih & (unsigned)(sp.inbox_cap - 1));
+        const int base = __ldcg(&en->task_base), ninit = __ldcg(&en->ninit), nt = __ldcg(&en->ntasks);
+        atomicAdd(&sp.sc->outstanding.v, (unsigned)nt);
+        for (int k = 0; k < ninit; ++k) serve_push(sp, __ldcg(sp.initlist + base + k));
+      }
+      continue;
+    }
+    if (pending) {
+      __threadfence();
+      atomicSub(&sp.sc->outstanding.v, pending);
+      pending = 0;
+    }
+    const unsigned outst = ptx::ld_relaxed_u32(&sp.sc->outstanding.v);
+    const uint64_t now = ptx::globaltimer();
+    if (outst != seen_out) {
+      seen_out = outst;
+      seen_at = now;
+    }
+    if (outst == 0 && ld_acquire_sys_u32(&sp.sc->stop.v) != 0 &&
+        ptx::ld_relaxed_u32(&sp.sc->inbox_head.v) == (unsigned)ld_acquire_sys_u32(&sp.sc->inbox_tail.v))
+      return -1;
+    if (outst != 0) {  // work outstanding but no task finished for the whole limit: a lost dependency
+      if (now - seen_at > (uint64_t)p.timeout_ns) {
+        set_error(p, HQR_ERR_TIMEOUT, -1);
+        return -1;
+      }
+    } else if (now - idle_since > kIdleExitNs) {
+      return -1;  // idle: leave; the host relaunches on new work
+    }
+    __nanosleep(sleep_ns);
+    if (sleep_ns < 4096) sleep_ns *= 2;
+  }
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(NT, 2) hqr_serve(ServeParams sp) {
+  extern __shared__ __align__(16) unsigned char dyn_raw[];
+  Real *dyn = reinterpret_cast<Real *>(dyn_raw);
+  __shared__ Shared<Real> sh;
+  const EngineParams &p = sp.e;
+  if (threadIdx.x == 0) {
+    ptx::mbar_init(&sh.bar, 1);
+    sh.abort = 0;
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  unsigned pending = 0;
+  while (true) {
+    if (threadIdx.x == 0) sh.task = serve_pop(sp, pending);
+    __syncthreads();
+    const int tid = sh.task;
+    if (tid < 0) break;
+    const Task t = load_task_cg(p.tasks + tid);
+    Problem P;
+    {
+      const int4 *src = reinterpret_cast<const int4 *>(p.probs + t.pid);
+      int4 *dst = reinterpret_cast<int4 *>(&P);
+      for (int q = 0; q < (int)(sizeof(Problem) / 16); ++q) dst[q] = __ldcg(src + q);
+    }
+    const Geo<Real> g(P);
+    if (t.op == OP_GEQRT || t.op == OP_TSQRT || t.op == OP_TTQRT)
+      task_panel(p, g, t, sh, dyn, phase);
+    else if (t.op <= OP_TTMQR)
+      task_update(p, g, t, sh, dyn, phase);
+    else
+      task_vector(p, P, g, t, reinterpret_cast<double *>(dyn_raw));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      ptx::fence_proxy_async();
+      __threadfence();
+      for (int e = t.succ_begin; e < t.succ_end; ++e) {
+        const int s = __ldcg(p.succ + e);
+        if (atomicSub(&p.indeg[s], 1) == 1) serve_push(sp, s);
+      }
+      if (atomicAdd(&sp.req_done[t.pid], 1) + 1 == __ldcg(sp.req_total + t.pid)) {
+        __threadfence_system();
+        sp.comp[t.pid] = __ldcg(sp.req_seq + t.pid);
+        __threadfence_system();
+      }
+      if (++pending >= 32) {  // keep the outstanding count current for the watchdogs
+        __threadfence();
+        atomicSub(&sp.sc->outstanding.v, pending);
+        pending = 0;
+      }
+    }
+    if (sh.abort) break;
+  }
   if (sh.abort && threadIdx.x == 0) {
     const uint64_t t0 = ptx::globaltimer();
     while (!ptx::mbar_try_wait(&sh.bar, phase) && ptx::globaltimer() - t0 < 1000000000ull) {

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -355,6 +356,8 @@ const char *hqr_strerror(int status) {
     case HQR_ERR_SINGULAR: return "R has an exact zero on its diagonal";
     case HQR_ERR_INTERNAL: return "internal error";
     case HQR_ERR_TOO_LARGE: return "problem exceeds the limits of the allocation-free entry point";
+    case HQR_ERR_BUSY: return "no room for the request right now";
+    case HQR_ERR_BUDGET: return "request exceeds the server's budget";
     default: return status < 0 ? "invalid argument" : "unknown status";
   }
 }
@@ -900,7 +903,7 @@ int hqr_ls_plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_
     off_b[q] = arena_elems;
     arena_elems += (Mp + 3) & ~(size_t)3;
     off_vec[q] = vec_elems;
-    vec_elems += Mp + 2 * Np;
+    vec_elems += Np + Mp + Np + 2 * (size_t)atr_chunks(pb.m) * Np;
     size_t cnt = 0;
     hqr_elim_list(pb.m, pb.n, c.a, c.p, c.low_tree, c.high_tree, nullptr, 0, &cnt);
     std::vector<hqr_elim_t> lst(cnt);
@@ -932,6 +935,7 @@ int hqr_ls_plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_
       pb.x = P->vec + off_vec[q];
       pb.r = pb.x + (size_t)pb.n * pb.nb;
       pb.g = pb.r + (size_t)pb.m * pb.nb;
+      pb.gp = pb.g + (size_t)pb.n * pb.nb;
       pb.status = P->dstatus + q;
       PrepDesc d;
       d.A = probs[q].dA;
@@ -1096,6 +1100,568 @@ void hqr_ls_plan_free(hqr_ls_plan *P) {
   if (P->ev0) cudaEventDestroy(P->ev0);
   if (P->ev1) cudaEventDestroy(P->ev1);
   delete P;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Measured autotuner for least-squares plans.
+namespace {
+
+// Uniform(-1, 1) entries from a counter-based hash (SplitMix64 finaliser);
+// only used to time candidate configurations.
+template <typename Real>
+__global__ void fill_uniform(Real *x, long long n, unsigned long long seed) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(e + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    x[e] = (Real)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+  }
+}
+
+}  // namespace
+
+extern "C" int hqr_autotune(int count, const int *Ms, const int *Ns, int prec, int refine_iters, int reps,
+                            int *keys_out, hqr_tile_config_t *cfg_out, int cap, int *nout, void *stream) {
+  if (count < 1) return -1;
+  if (!Ms) return -2;
+  if (!Ns) return -3;
+  if (prec != HQR_FP64 && prec != HQR_FP32) return -4;
+  if (reps < 1) return -6;
+  if (!nout) return -10;
+  cudaStream_t s = (cudaStream_t)stream;
+  // representative shape per class: geometric mean of its members
+  std::map<std::pair<int, int>, std::pair<double, double>> acc;
+  std::map<std::pair<int, int>, int> cnt;
+  for (int q = 0; q < count; ++q) {
+    if (Ms[q] < Ns[q] || Ns[q] < 1) return -2;
+    auto key = std::make_pair(ilog2(Ms[q]), ilog2(Ns[q]));
+    acc[key].first += std::log((double)Ms[q]);
+    acc[key].second += std::log((double)Ns[q]);
+    cnt[key] += 1;
+  }
+  const size_t es = elem_size(prec);
+  std::vector<int> keys;
+  std::vector<hqr_tile_config_t> best_cfgs;
+  for (auto &kv : acc) {
+    const int c = cnt[kv.first];
+    int M = (int)std::lround(std::exp(kv.second.first / c));
+    int N = (int)std::lround(std::exp(kv.second.second / c));
+    N = std::max(1, std::min(N, M));
+    // workspaces for `reps` copies of the class shape
+    void *A = nullptr;
+    double *bx = nullptr;
+    if (!cuda_ok(cudaMalloc(&A, es * (size_t)M * N * reps), "cudaMalloc(tune A)") ||
+        !cuda_ok(cudaMalloc(&bx, sizeof(double) * ((size_t)M + N) * reps), "cudaMalloc(tune b)")) {
+      cudaFree(A);
+      return HQR_ERR_NOMEM;
+    }
+    const long long na = (long long)M * N * reps;
+    if (prec == HQR_FP64)
+      fill_uniform<double><<<grid_for(na), 256, 0, s>>>((double *)A, na, 12345ull + M);
+    else
+      fill_uniform<float><<<grid_for(na), 256, 0, s>>>((float *)A, na, 12345ull + M);
+    fill_uniform<double><<<grid_for((long long)M * reps), 256, 0, s>>>(bx, (long long)M * reps, 777ull + N);
+    std::vector<hqr_ls_problem_t> probs(reps);
+    for (int r = 0; r < reps; ++r) {
+      probs[r].M = M;
+      probs[r].N = N;
+      probs[r].dA = (const unsigned char *)A + es * (size_t)M * N * r;
+      probs[r].lda = M;
+      probs[r].db = bx + (size_t)M * r;
+      probs[r].dx = bx + (size_t)M * reps + (size_t)N * r;
+    }
+    std::vector<hqr_tile_config_t> cands;
+    for (int nb : {32, 64, 128}) {
+      if (nb > 32 && nb / 2 >= N) continue;  // no tile much wider than the matrix
+      const int ib = 16;
+      const int mtiles = (M + nb - 1) / nb;
+      for (int a : {1, 4, 16}) {
+        if (a > 1 && a >= 2 * mtiles) continue;
+        cands.push_back({nb, ib, a, 1, HQR_GREEDY, HQR_GREEDY});
+      }
+      cands.push_back({nb, ib, mtiles, 1, HQR_FLAT, HQR_GREEDY});
+    }
+    float best = 1e30f;
+    hqr_tile_config_t best_cfg = default_config(M, N, prec);
+    for (const hqr_tile_config_t &cf : cands) {
+      if (!valid_tile_sizes(prec, cf.nb, cf.ib)) continue;
+      std::vector<hqr_tile_config_t> cfv(reps, cf);
+      hqr_ls_plan *P = nullptr;
+      int st = hqr_ls_plan_create(reps, probs.data(), cfv.data(), prec, refine_iters, &P);
+      if (st) continue;
+      float ms = 0.f, tot = 0.f;
+      bool ok = hqr_ls_plan_run(P, stream) == HQR_SUCCESS;  // warm-up
+      for (int it = 0; ok && it < 2; ++it) {
+        ok = hqr_ls_plan_run(P, stream) == HQR_SUCCESS && hqr_ls_plan_info(P, nullptr, nullptr, &ms) == 0;
+        tot += ms;
+      }
+      if (ok && hqr_ls_plan_status(P, stream) == HQR_SUCCESS && tot < best) {
+        best = tot;
+        best_cfg = cf;
+      }
+      hqr_ls_plan_free(P);
+    }
+    cudaFree(A);
+    cudaFree(bx);
+    keys.push_back(kv.first.first);
+    keys.push_back(kv.first.second);
+    best_cfgs.push_back(best_cfg);
+  }
+  *nout = (int)best_cfgs.size();
+  int st = hqr_set_tuning((int)best_cfgs.size(), keys.data(), best_cfgs.data());
+  if (st) return st;
+  if (keys_out && cfg_out && cap >= (int)best_cfgs.size()) {
+    std::memcpy(keys_out, keys.data(), sizeof(int) * keys.size());
+    std::memcpy(cfg_out, best_cfgs.data(), sizeof(hqr_tile_config_t) * best_cfgs.size());
+  }
+  return HQR_SUCCESS;
+}
+
+// ---------------------------------------------------------------------------
+// Least-squares server: continuous batching on a resident task kernel.
+namespace {
+
+// First-fit allocator over [0, cap) (units are the caller's).
+class RangeAlloc {
+ public:
+  void init(size_t cap) {
+    free_.clear();
+    if (cap) free_[0] = cap;
+    used_ = 0;
+  }
+  bool alloc(size_t n, size_t &off) {
+    if (n == 0) n = 1;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= n) {
+        off = it->first;
+        const size_t rest = it->second - n;
+        free_.erase(it);
+        if (rest) free_[off + n] = rest;
+        used_ += n;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t n) {
+    if (n == 0) n = 1;
+    used_ -= n;
+    auto it = free_.emplace(off, n).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  size_t used() const { return used_; }
+
+ private:
+  std::map<size_t, size_t> free_;
+  size_t used_ = 0;
+};
+
+struct CachedGraph {
+  Graph g;
+  std::vector<int> init;  // tasks with no inputs
+};
+
+size_t pow2_at_least(size_t v) {
+  size_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+}  // namespace
+
+struct hqr_server {
+  hqr_server_opts o{};
+  size_t es = 0;
+  Task *tasks = nullptr;
+  int *succ = nullptr, *indeg = nullptr, *initlist = nullptr, *slots = nullptr;
+  Ctl *ctl = nullptr;
+  ServeCtl *sc = nullptr;
+  InboxEntry *inbox = nullptr;
+  Problem *probs = nullptr;
+  int *req_done = nullptr, *req_total = nullptr, *dstatus = nullptr;
+  long long *req_seq = nullptr;
+  long long *comp_host = nullptr, *comp_dev = nullptr;
+  unsigned char *arena = nullptr;
+  int ring_cap = 0, inbox_cap = 0;
+  RangeAlloc arena_alloc, task_alloc, edge_alloc;
+  std::vector<int> free_slots;
+  struct Live {
+    long long seq = -1;
+    size_t a_off = 0, a_n = 0, t_off = 0, t_n = 0, e_off = 0, e_n = 0;
+    bool live = false;
+  };
+  std::vector<Live> live;
+  std::map<std::vector<int>, CachedGraph> cache;
+  unsigned inbox_tail = 0;
+  long long next_seq = 1;
+  cudaStream_t kstream = nullptr, cstream = nullptr;
+  bool running = false;
+  size_t smem = 0;
+  int64_t submitted = 0, completed = 0;
+};
+
+namespace {
+
+void server_release(hqr_server *S) {
+  cudaFree(S->tasks);
+  cudaFree(S->succ);
+  cudaFree(S->indeg);
+  cudaFree(S->initlist);
+  cudaFree(S->slots);
+  cudaFree(S->ctl);
+  cudaFree(S->sc);
+  cudaFree(S->inbox);
+  cudaFree(S->probs);
+  cudaFree(S->req_done);
+  cudaFree(S->req_total);
+  cudaFree(S->req_seq);
+  cudaFree(S->dstatus);
+  cudaFree(S->arena);
+  if (S->comp_host) cudaFreeHost(S->comp_host);
+  if (S->kstream) cudaStreamDestroy(S->kstream);
+  if (S->cstream) cudaStreamDestroy(S->cstream);
+}
+
+// Largest shared memory any request configuration of the server may need.
+size_t server_smem(int prec) {
+  size_t m = 0;
+  for (int nb : {32, 64, 128})
+    for (int ib : {8, 16, 32}) {
+      if (!valid_tile_sizes(prec, nb, ib)) continue;
+      Problem pb{};
+      pb.nb = nb;
+      pb.ib = ib;
+      choose_widths(prec, nb, ib, pb);
+      pb.wb = 1;
+      m = std::max(m, smem_for(prec, pb));
+    }
+  return m;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hqr_server_create(const hqr_server_opts *o, hqr_server **out) {
+  if (!o) return -1;
+  if (!out) return -2;
+  *out = nullptr;
+  if (o->prec != HQR_FP64 && o->prec != HQR_FP32) return -1;
+  if (o->refine_iters < 0 || o->max_live < 1 || o->task_pool < 1024 || o->edge_pool < 1024 || o->hbm_budget < 1)
+    return -1;
+  hqr_server *S = new (std::nothrow) hqr_server();
+  if (!S) return HQR_ERR_NOMEM;
+  S->o = *o;
+  S->es = elem_size(o->prec);
+  const size_t TP = (size_t)o->task_pool, EP = (size_t)o->edge_pool, L = (size_t)o->max_live;
+  S->ring_cap = (int)pow2_at_least(TP / kShards + L + 64);
+  S->inbox_cap = (int)pow2_at_least(2 * L);
+  const size_t nslots = (size_t)kNumQueues * kShards * S->ring_cap;
+  int st = HQR_SUCCESS;
+  if (!cuda_ok(cudaMalloc(&S->tasks, sizeof(Task) * TP), "server tasks") ||
+      !cuda_ok(cudaMalloc(&S->succ, sizeof(int) * EP), "server succ") ||
+      !cuda_ok(cudaMalloc(&S->indeg, sizeof(int) * TP), "server indeg") ||
+      !cuda_ok(cudaMalloc(&S->initlist, sizeof(int) * TP), "server init") ||
+      !cuda_ok(cudaMalloc(&S->slots, sizeof(int) * nslots), "server slots") ||
+      !cuda_ok(cudaMalloc(&S->ctl, sizeof(Ctl)), "server ctl") ||
+      !cuda_ok(cudaMalloc(&S->sc, sizeof(ServeCtl)), "server sc") ||
+      !cuda_ok(cudaMalloc(&S->inbox, sizeof(InboxEntry) * S->inbox_cap), "server inbox") ||
+      !cuda_ok(cudaMalloc(&S->probs, sizeof(Problem) * L), "server probs") ||
+      !cuda_ok(cudaMalloc(&S->req_done, sizeof(int) * L), "server done") ||
+      !cuda_ok(cudaMalloc(&S->req_total, sizeof(int) * L), "server total") ||
+      !cuda_ok(cudaMalloc(&S->req_seq, sizeof(long long) * L), "server seq") ||
+      !cuda_ok(cudaMalloc(&S->dstatus, sizeof(int) * L), "server status") ||
+      !cuda_ok(cudaMalloc(&S->arena, o->hbm_budget), "server arena") ||
+      !cuda_ok(cudaHostAlloc(&S->comp_host, sizeof(long long) * L, cudaHostAllocMapped), "server comp") ||
+      !cuda_ok(cudaHostGetDevicePointer(&S->comp_dev, S->comp_host, 0), "server comp ptr") ||
+      !cuda_ok(cudaMemset(S->slots, 0, sizeof(int) * nslots), "memset slots") ||
+      !cuda_ok(cudaMemset(S->ctl, 0, sizeof(Ctl)), "memset ctl") ||
+      !cuda_ok(cudaMemset(S->sc, 0, sizeof(ServeCtl)), "memset sc") ||
+      !cuda_ok(cudaMemset(S->req_done, 0, sizeof(int) * L), "memset done") ||
+      !cuda_ok(cudaStreamCreateWithFlags(&S->kstream, cudaStreamNonBlocking), "stream") ||
+      !cuda_ok(cudaStreamCreateWithFlags(&S->cstream, cudaStreamNonBlocking), "stream"))
+    st = HQR_ERR_NOMEM;
+  if (st) {
+    server_release(S);
+    delete S;
+    return st;
+  }
+  for (size_t q = 0; q < L; ++q) S->comp_host[q] = -1;
+  S->arena_alloc.init(o->hbm_budget / 256);
+  S->task_alloc.init(TP);
+  S->edge_alloc.init(EP);
+  S->live.resize(L);
+  for (int q = (int)L - 1; q >= 0; --q) S->free_slots.push_back(q);
+  S->smem = server_smem(o->prec);
+  *out = S;
+  return HQR_SUCCESS;
+}
+
+// Relaunch the resident kernel if it left (idle exit) while work is owed.
+int server_ensure_running(hqr_server *S);
+
+int hqr_server_start(hqr_server *S) {
+  if (!S) return -1;
+  if (S->running && cudaStreamQuery(S->kstream) == cudaErrorNotReady) return HQR_SUCCESS;
+  ServeParams sp;
+  sp.e.probs = S->probs;
+  sp.e.tasks = S->tasks;
+  sp.e.ntasks = (int)S->o.task_pool;
+  sp.e.succ = S->succ;
+  sp.e.indeg = S->indeg;
+  sp.e.slots = S->slots;
+  sp.e.ctl = S->ctl;
+  sp.e.timeout_ns = g_timeout_ns;
+  sp.e.trace = nullptr;
+  sp.sc = S->sc;
+  sp.inbox = S->inbox;
+  sp.inbox_cap = S->inbox_cap;
+  sp.initlist = S->initlist;
+  sp.req_done = S->req_done;
+  sp.req_total = S->req_total;
+  sp.req_seq = S->req_seq;
+  sp.comp = S->comp_dev;
+  sp.ring_cap = S->ring_cap;
+  const void *k = S->o.prec == HQR_FP64 ? (const void *)hqr_serve<double> : (const void *)hqr_serve<float>;
+  int dev = 0, sms = 0, per_sm = 0;
+  CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem));
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, S->smem));
+  if (per_sm < 1) return HQR_ERR_CUDA;
+  CK(cudaStreamSynchronize(S->cstream));
+  if (S->o.prec == HQR_FP64)
+    hqr_serve<double><<<sms * per_sm, NT, S->smem, S->kstream>>>(sp);
+  else
+    hqr_serve<float><<<sms * per_sm, NT, S->smem, S->kstream>>>(sp);
+  CK(cudaGetLastError());
+  S->running = true;
+  return HQR_SUCCESS;
+}
+
+int server_ensure_running(hqr_server *S) {
+  if (!S->running) return HQR_SUCCESS;
+  const cudaError_t q = cudaStreamQuery(S->kstream);
+  if (q == cudaErrorNotReady) return HQR_SUCCESS;
+  CK(q);
+  CtlLine stl;
+  CK(cudaMemcpy(&stl, &S->ctl->status, sizeof(CtlLine), cudaMemcpyDeviceToHost));
+  if (stl.v) return (int)stl.v;
+  S->running = false;
+  return hqr_server_start(S);
+}
+
+int hqr_server_submit(hqr_server *S, const hqr_ls_problem_t *pr, int64_t *ticket) {
+  if (!S) return -1;
+  if (!pr || pr->M < 1 || pr->N < 1 || pr->N > pr->M || pr->lda < pr->M || !pr->dA || !pr->db || !pr->dx)
+    return -2;
+  if (!ticket) return -3;
+  if (!S->running) return HQR_ERR_INTERNAL;
+  const int prec = S->o.prec;
+  hqr_tile_config_t c = pick_config(pr->M, pr->N, prec, nullptr);
+  if (c.nb > 128) c.nb = 128;
+  if (!valid_tile_sizes(prec, c.nb, c.ib)) c = default_config(pr->M, pr->N, prec);
+  Problem pb{};
+  pb.nb = c.nb;
+  pb.ib = c.ib;
+  pb.m = (pr->M + c.nb - 1) / c.nb;
+  pb.n = (pr->N + c.nb - 1) / c.nb;
+  choose_widths(prec, c.nb, c.ib, pb);
+  pb.wb = 1;
+  // graph of this shape and configuration (cached)
+  std::vector<int> key = {pr->M, pr->N, c.nb, c.ib, c.a, c.p, c.low_tree, c.high_tree};
+  auto it = S->cache.find(key);
+  if (it == S->cache.end()) {
+    size_t cnt = 0;
+    hqr_elim_list(pb.m, pb.n, c.a, c.p, c.low_tree, c.high_tree, nullptr, 0, &cnt);
+    std::vector<hqr_elim_t> lst(cnt);
+    if (hqr_elim_list(pb.m, pb.n, c.a, c.p, c.low_tree, c.high_tree, lst.data(), cnt, &cnt))
+      return HQR_ERR_INTERNAL;
+    CachedGraph cg;
+    cg.g = build_ls_graph(expand_ops(lst.data(), lst.size(), pb.m, pb.n), pb.m, pb.n, c.nb, pb.w,
+                          S->o.refine_iters, 0, true);
+    for (size_t t = 0; t < cg.g.tasks.size(); ++t)
+      if (cg.g.indeg[t] == 0) cg.init.push_back((int)t);
+    if (S->cache.size() > 4096) S->cache.clear();
+    it = S->cache.emplace(key, std::move(cg)).first;
+  }
+  const CachedGraph &cg = it->second;
+  const size_t nt = cg.g.tasks.size(), ne = std::max<size_t>(cg.g.succ.size(), 1);
+  const size_t Mp = (size_t)pb.m * c.nb, Np = (size_t)pb.n * c.nb, es = S->es;
+  auto r256 = [](size_t b) { return (b + 255) / 256; };
+  const size_t a_tiles = r256(es * Mp * Np), a_t = r256(es * (size_t)pb.m * pb.n * 2 * c.ib * c.nb),
+               a_b = r256(es * Mp), a_r = r256(8 * Mp), a_g = r256(8 * Np),
+               a_gp = r256(16 * (size_t)atr_chunks(pb.m) * Np);
+  const size_t a_units = a_tiles + a_t + a_b + a_r + a_g + a_gp;
+  if (a_units * 256 > S->o.hbm_budget || nt > (size_t)S->o.task_pool || ne > (size_t)S->o.edge_pool)
+    return HQR_ERR_BUDGET;
+  if (S->free_slots.empty()) return HQR_ERR_BUSY;
+  size_t a_off = 0, t_off = 0, e_off = 0;
+  if (!S->arena_alloc.alloc(a_units, a_off)) return HQR_ERR_BUSY;
+  if (!S->task_alloc.alloc(nt, t_off)) {
+    S->arena_alloc.release(a_off, a_units);
+    return HQR_ERR_BUSY;
+  }
+  if (!S->edge_alloc.alloc(ne, e_off)) {
+    S->arena_alloc.release(a_off, a_units);
+    S->task_alloc.release(t_off, nt);
+    return HQR_ERR_BUSY;
+  }
+  const int slot = S->free_slots.back();
+  S->free_slots.pop_back();
+  // patched copies: tasks name the slot, successors are global pool ids
+  std::vector<Task> tk(cg.g.tasks);
+  for (Task &t : tk) {
+    t.pid = slot;
+    t.succ_begin += (int32_t)e_off;
+    t.succ_end += (int32_t)e_off;
+  }
+  std::vector<int> sc(cg.g.succ);
+  for (int &v : sc) v += (int)t_off;
+  std::vector<int> init(cg.init);
+  for (int &v : init) v += (int)t_off;
+  unsigned char *base = S->arena + a_off * 256;
+  pb.A = base;
+  pb.T = base + a_tiles * 256;
+  pb.B = base + (a_tiles + a_t) * 256;
+  pb.r = (double *)(base + (a_tiles + a_t + a_b) * 256);
+  pb.g = (double *)(base + (a_tiles + a_t + a_b + a_r) * 256);
+  pb.gp = (double *)(base + (a_tiles + a_t + a_b + a_r + a_g) * 256);
+  pb.x = pr->dx;
+  pb.M = pr->M;
+  pb.N = pr->N;
+  pb.A0 = pr->dA;
+  pb.lda0 = pr->lda;
+  pb.b = pr->db;
+  pb.status = S->dstatus + slot;
+  const long long seq = S->next_seq++;
+  const int total = (int)nt, zero = 0;
+  S->comp_host[slot] = -1;
+  InboxEntry en{slot, (int)t_off, (int)init.size(), (int)nt};
+  cudaStream_t s = S->cstream;
+  const unsigned new_tail = S->inbox_tail + 1;
+  CK(cudaMemcpyAsync(S->tasks + t_off, tk.data(), sizeof(Task) * nt, cudaMemcpyHostToDevice, s));
+  if (!cg.g.succ.empty())
+    CK(cudaMemcpyAsync(S->succ + e_off, sc.data(), sizeof(int) * sc.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(S->indeg + t_off, cg.g.indeg.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(S->initlist + t_off, init.data(), sizeof(int) * init.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(S->probs + slot, &pb, sizeof(Problem), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(S->req_total + slot, &total, sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(S->req_done + slot, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(S->req_seq + slot, &seq, sizeof(long long), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(S->dstatus + slot, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(S->inbox + (S->inbox_tail & (unsigned)(S->inbox_cap - 1)), &en, sizeof(InboxEntry),
+                     cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(&S->sc->inbox_tail.v, &new_tail, sizeof(unsigned), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));  // the staged host copies above are stack / temporary buffers
+  S->inbox_tail = new_tail;
+  {
+    const int rs = server_ensure_running(S);
+    if (rs) return rs;
+  }
+  hqr_server::Live &lv = S->live[slot];
+  lv.seq = seq;
+  lv.a_off = a_off;
+  lv.a_n = a_units;
+  lv.t_off = t_off;
+  lv.t_n = nt;
+  lv.e_off = e_off;
+  lv.e_n = ne;
+  lv.live = true;
+  S->submitted += 1;
+  *ticket = seq;
+  return HQR_SUCCESS;
+}
+
+int hqr_server_poll(hqr_server *S, int64_t *done, int cap, int *count) {
+  if (!S) return -1;
+  if (!count) return -4;
+  int n = 0;
+  for (size_t slot = 0; slot < S->live.size(); ++slot) {
+    hqr_server::Live &lv = S->live[slot];
+    if (!lv.live) continue;
+    const long long c = *(volatile long long *)&S->comp_host[slot];
+    if (c != lv.seq) continue;
+    if (done && n < cap) done[n] = lv.seq;
+    ++n;
+    S->arena_alloc.release(lv.a_off, lv.a_n);
+    S->task_alloc.release(lv.t_off, lv.t_n);
+    S->edge_alloc.release(lv.e_off, lv.e_n);
+    lv.live = false;
+    S->free_slots.push_back((int)slot);
+    S->completed += 1;
+    if (done && n >= cap) break;
+  }
+  *count = n;
+  CtlLine stl;
+  CK(cudaMemcpyAsync(&stl, &S->ctl->status, sizeof(CtlLine), cudaMemcpyDeviceToHost, S->cstream));
+  CK(cudaStreamSynchronize(S->cstream));
+  if (stl.v) return (int)stl.v;
+  if (S->submitted > S->completed) return server_ensure_running(S);  // work owed: keep a kernel up
+  return HQR_SUCCESS;
+}
+
+int hqr_server_counters(const hqr_server *S, uint32_t *out, int cap) {
+  if (!S) return -1;
+  if (!out || cap < 5) return -2;
+  ServeCtl sc;
+  CK(cudaMemcpy(&sc, S->sc, sizeof(ServeCtl), cudaMemcpyDeviceToHost));
+  out[0] = sc.inbox_head.v;
+  out[1] = sc.inbox_tail.v;
+  out[2] = sc.stop.v;
+  out[3] = sc.outstanding.v;
+  out[4] = cudaStreamQuery(S->kstream) == cudaErrorNotReady ? 1u : 0u;
+  return HQR_SUCCESS;
+}
+
+int hqr_server_stats(const hqr_server *S, int64_t *submitted, int64_t *completed, int *live, size_t *bytes_in_use) {
+  if (!S) return -1;
+  if (submitted) *submitted = S->submitted;
+  if (completed) *completed = S->completed;
+  if (live) *live = (int)(S->live.size() - S->free_slots.size());
+  if (bytes_in_use) *bytes_in_use = S->arena_alloc.used() * 256;
+  return HQR_SUCCESS;
+}
+
+int hqr_server_stop(hqr_server *S) {
+  if (!S) return -1;
+  if (!S->running) return HQR_SUCCESS;
+  {
+    const int rs = server_ensure_running(S);  // admitted work must finish before the kernel leaves
+    if (rs) return rs;
+  }
+  const unsigned one = 1;
+  CK(cudaMemcpyAsync(&S->sc->stop.v, &one, sizeof(unsigned), cudaMemcpyHostToDevice, S->cstream));
+  CK(cudaStreamSynchronize(S->cstream));
+  CK(cudaStreamSynchronize(S->kstream));
+  S->running = false;
+  CtlLine stl;
+  CK(cudaMemcpy(&stl, &S->ctl->status, sizeof(CtlLine), cudaMemcpyDeviceToHost));
+  const unsigned zero = 0;  // a later start serves again
+  CK(cudaMemcpy(&S->sc->stop.v, &zero, sizeof(unsigned), cudaMemcpyHostToDevice));
+  return (int)stl.v;
+}
+
+void hqr_server_free(hqr_server *S) {
+  if (!S) return;
+  if (S->running) hqr_server_stop(S);
+  server_release(S);
+  delete S;
 }
 
 }  // extern "C"

@@ -20,14 +20,20 @@ enum Op : int8_t {
   OP_TTMQR = 5,
   // FP64 vector tasks of least-squares solves (per tile of the vectors)
   OP_RESID = 6,    // r_i = b_i - A(i,:) x, compensated (row tile i)
-  OP_ATR = 7,      // g_j = A(:,j)^T r, compensated (column tile j)
+  OP_ATR = 7,      // partial sums of A(rows of chunk i, j)^T r, compensated (column tile j, row chunk i)
   OP_TRSV_TD = 8,  // g_i <- R_ii^{-T} g_i (forward substitution, diagonal tile i)
   OP_TRSV_TU = 9,  // g_j -= R(i,j)^T g_i, j > i
   OP_TRSV_D = 10,  // g_i <- R_ii^{-1} g_i (back substitution, diagonal tile i)
   OP_TRSV_U = 11,  // g_j -= R(j,i) g_i, j < i
   OP_XUPD = 12,    // x_j += g_j
   OP_BTOG = 13,    // g_i = first column of the right-hand-side block of row tile i
+  OP_PACK = 14,    // tile column j of the workspace from the caller's matrix (j = 0 also b, x = 0)
+  OP_ATRR = 15,    // g_j = sum over row chunks of the OP_ATR partial sums
 };
+
+// Row tiles per chunk of the A^T r partial sums.
+constexpr int kAtrChunk = 8;
+inline int atr_chunks(int m) { return (m + kAtrChunk - 1) / kAtrChunk; }
 
 // Scheduling classes, highest first: panel kernels (on the critical path),
 // updates of the next panel's column (look-ahead), other updates.
@@ -85,7 +91,11 @@ Graph build_apply_graph(const std::vector<PanelOp> &ops, int m, int nslab, int w
 // corrected semi-normal equations (x0 = 0; r = b - A x, g = A^T r,
 // R^T R d = g, x += d; all FP64) or, with iters = 0, Q^T b applied to the
 // right-hand-side block followed by R x = (Q^T b)[0:N].
-Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int w, int iters, int pid);
+// With `pack`, the graph starts with one OP_PACK task per tile column that
+// copies the caller's matrix into the workspace (for runs where no separate
+// preparation kernel can be launched).
+Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int w, int iters, int pid,
+                     bool pack = false);
 
 // Append graph g to `into` (its task ids and successor lists renumbered);
 // the two graphs stay independent.

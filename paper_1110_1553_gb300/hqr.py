@@ -22,7 +22,7 @@ TS, TT = 0, 1
 FP64, FP32 = 0, 1
 
 (SUCCESS, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_CAPACITY, ERR_INVALID_LIST, ERR_SINGULAR, ERR_INTERNAL,
- ERR_TOO_LARGE) = range(9)
+ ERR_TOO_LARGE, ERR_BUSY, ERR_BUDGET) = range(11)
 
 ELIM_DTYPE = np.dtype([("k", np.int32), ("i", np.int32), ("killer", np.int32), ("kind", np.int32),
                        ("level", np.int32), ("step", np.int32)])
@@ -31,7 +31,8 @@ EXPORTS = ["hqr_elim_list", "hqr_validate_list", "hqr_geqrf", "hqr_refactor", "h
            "hqr_status", "hqr_get_r", "hqr_get_tiles", "hqr_get_t", "hqr_factors_info", "hqr_kernel_ms", "hqr_trace", "hqr_apply_q",
            "hqr_gels", "hqr_geqrf_r_noalloc", "hqr_ls_plan_create", "hqr_ls_plan_run",
            "hqr_ls_plan_capture", "hqr_ls_plan_status", "hqr_ls_plan_info", "hqr_ls_plan_config",
-           "hqr_ls_plan_free", "hqr_ls_plan_trace", "hqr_set_tuning", "hqr_debug_block_task", "hqr_factors_free", "hqr_set_timeout_ms", "hqr_strerror", "hqr_last_error",
+           "hqr_ls_plan_free", "hqr_ls_plan_trace", "hqr_set_tuning", "hqr_autotune", "hqr_server_create", "hqr_server_start",
+           "hqr_server_submit", "hqr_server_poll", "hqr_server_stats", "hqr_server_counters", "hqr_server_stop", "hqr_server_free", "hqr_debug_block_task", "hqr_factors_free", "hqr_set_timeout_ms", "hqr_strerror", "hqr_last_error",
            "hqr_last_launches"]
 
 
@@ -92,6 +93,17 @@ def load(build_if_missing=False):
     lib.hqr_ls_plan_free.argtypes = [vp]
     lib.hqr_ls_plan_free.restype = None
     lib.hqr_set_tuning.argtypes = [i32, vp, vp]
+    lib.hqr_server_create.argtypes = [vp, pf]
+    lib.hqr_server_start.argtypes = [vp]
+    lib.hqr_server_submit.argtypes = [vp, vp, ctypes.POINTER(i64)]
+    lib.hqr_server_poll.argtypes = [vp, vp, i32, ctypes.POINTER(i32)]
+    lib.hqr_server_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                     ctypes.POINTER(sz)]
+    lib.hqr_server_counters.argtypes = [vp, vp, i32]
+    lib.hqr_server_stop.argtypes = [vp]
+    lib.hqr_server_free.argtypes = [vp]
+    lib.hqr_server_free.restype = None
+    lib.hqr_autotune.argtypes = [i32, vp, vp, i32, i32, i32, vp, vp, i32, ctypes.POINTER(i32), vp]
     lib.hqr_geqrf_r_noalloc.argtypes = [vp, i32, i32, i32, i32, i32, vp, sz, vp, i32, vp]
     lib.hqr_debug_block_task.argtypes = [vp, i64, i32]
     lib.hqr_factors_free.argtypes = [vp]
@@ -448,3 +460,88 @@ def set_tuning(table):
         keys[2 * e], keys[2 * e + 1] = lm, ln
         cfgs[e] = c
     _check(load().hqr_set_tuning(len(table), keys, cfgs), "hqr_set_tuning")
+
+
+def autotune(shapes, dtype, refine_iters, reps=32, stream=None):
+    """Run the library's measured autotuner over the shape classes of
+    `shapes` [(M, N), ...]; installs and returns the table
+    {(log2 M, log2 N): (nb, ib, a, p, low, high)}."""
+    n = len(shapes)
+    Ms = (ctypes.c_int * n)(*[m for m, _ in shapes])
+    Ns = (ctypes.c_int * n)(*[k for _, k in shapes])
+    cap = 256
+    keys = (ctypes.c_int * (2 * cap))()
+    cfgs = (TileConfig * cap)()
+    nout = ctypes.c_int(0)
+    torch = _torch()
+    prec = FP64 if dtype == torch.float64 else FP32
+    _check(load().hqr_autotune(n, Ms, Ns, prec, int(refine_iters), int(reps), keys, cfgs, cap, ctypes.byref(nout),
+                               _stream_ptr(stream)), "hqr_autotune")
+    return {(keys[2 * e], keys[2 * e + 1]): cfgs[e].as_tuple() for e in range(nout.value)}
+
+
+# --------------------------------------------------------------- server --
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("refine_iters", ctypes.c_int), ("max_live", ctypes.c_int),
+                ("hbm_budget", ctypes.c_size_t), ("task_pool", ctypes.c_int64), ("edge_pool", ctypes.c_int64)]
+
+
+class Server:
+    """Continuous-batching least-squares server (hqr_server_*). submit()
+    returns a ticket, or None when the request does not fit right now."""
+
+    def __init__(self, dtype, refine_iters, max_live=1024, hbm_budget=8 << 30, task_pool=8 << 20,
+                 edge_pool=32 << 20):
+        torch = _torch()
+        prec = FP64 if dtype == torch.float64 else FP32
+        o = ServerOpts(prec, int(refine_iters), int(max_live), int(hbm_budget), int(task_pool), int(edge_pool))
+        h = ctypes.c_void_p(0)
+        _check(load().hqr_server_create(ctypes.byref(o), ctypes.byref(h)), "hqr_server_create")
+        self._h = h
+        self._keep = {}
+        self._done = (ctypes.c_int64 * 4096)()
+
+    def start(self):
+        _check(load().hqr_server_start(self._h), "hqr_server_start")
+
+    def submit(self, A, b, x):
+        Ac, lda = colmajor(A)
+        pr = LSProblem(Ac.shape[0], Ac.shape[1], Ac.data_ptr(), lda, b.data_ptr(), x.data_ptr())
+        t = ctypes.c_int64(0)
+        st = load().hqr_server_submit(self._h, ctypes.byref(pr), ctypes.byref(t))
+        if st == ERR_BUSY:
+            return None
+        _check(st, "hqr_server_submit")
+        self._keep[t.value] = (Ac, b, x)
+        return t.value
+
+    def poll(self):
+        """Tickets completed since the last poll."""
+        cnt = ctypes.c_int(0)
+        st = load().hqr_server_poll(self._h, self._done, len(self._done), ctypes.byref(cnt))
+        _check(st, "hqr_server_poll")
+        out = [self._done[q] for q in range(min(cnt.value, len(self._done)))]
+        for t in out:
+            self._keep.pop(t, None)
+        return out
+
+    def stats(self):
+        s, c, lv, by = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int(0), ctypes.c_size_t(0)
+        _check(load().hqr_server_stats(self._h, ctypes.byref(s), ctypes.byref(c), ctypes.byref(lv), ctypes.byref(by)),
+               "hqr_server_stats")
+        return {"submitted": s.value, "completed": c.value, "live": lv.value, "bytes_in_use": by.value}
+
+    def counters(self):
+        out = (ctypes.c_uint32 * 5)()
+        _check(load().hqr_server_counters(self._h, out, 5), "hqr_server_counters")
+        return {"inbox_claimed": out[0], "inbox_posted": out[1], "stop": out[2], "outstanding": out[3],
+                "running": bool(out[4])}
+
+    def stop(self):
+        _check(load().hqr_server_stop(self._h), "hqr_server_stop")
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.hqr_server_free(self._h)
+            self._h = None

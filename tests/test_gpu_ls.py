@@ -107,3 +107,23 @@ def test_singular_problem_reported():
     p = hqr.LSPlan([to_dev(A, b, 64)], refine_iters=2, configs=[hqr.tile_config(32, 8, 1, 1)])
     p.run()
     assert p.status() == hqr.ERR_SINGULAR
+
+
+@pytest.mark.parametrize("kappa,iters", [(1e4, 8), (1e6, 20)])
+def test_mixed_square_conditioned_matches_oracle(kappa, iters):
+    # the square mixed-precision recipe at n = 1024: A = U diag(s) V^T with s
+    # geometric from 1 to 1/kappa, b = A x_true + 1e-8 N(0,1)
+    from paper_1110_1553_gb300 import workloads
+    n = 1024
+    A = workloads.conditioned(torch, n, n, kappa, seed=30 + int(np.log10(kappa)))
+    g = torch.Generator(device="cuda")
+    g.manual_seed(31)
+    xt = torch.randn(n, dtype=torch.float64, device="cuda", generator=g)
+    b = A.double() @ xt + 1e-8 * torch.randn(n, dtype=torch.float64, device="cuda", generator=g)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    plan = hqr.LSPlan([(A, b, x)], refine_iters=iters, configs=[hqr.tile_config(128, 16, 4, 1)])
+    plan.run()
+    assert plan.status() == 0
+    xo = lstsq_unblocked(A.double().cpu().numpy(), b.cpu().numpy())
+    err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
+    assert err <= 1e-12, err
