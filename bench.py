@@ -312,7 +312,7 @@ def serving(torch, hqr, dev, rate=2000.0, seconds=5.0, refine=5):
     return out
 
 
-def square_mixed(torch, hqr, dev, n=16384, refine=12):
+def square_mixed(torch, hqr, dev, n=16384, refine=24):
     """16384^2 FP32 least squares, A = U diag(s) V^T, s geometric 1 .. 1e-6,
     b = A x_true + 1e-8 N(0,1): FP32 tile QR + FP64 CSNE."""
     from paper_1110_1553_gb300 import workloads
@@ -334,11 +334,12 @@ def square_mixed(torch, hqr, dev, n=16384, refine=12):
     st = plan.status()
     ms = e0.elapsed_time(e1)
     info = plan.info()
-    r = b - A.double() @ x
-    atr = (A.double().t() @ r).norm().item() / (torch.linalg.norm(A.double()).item() * r.norm().item())
+    # independent cross-check (a library FP64 QR solve, itself accurate to about kappa * u64)
+    ref = torch.linalg.lstsq(A.double(), b.unsqueeze(1), driver="gels").solution[:, 0]
+    cross = ((x - ref).norm() / ref.norm()).item()
     return {"workload": "square_mixed_ls_16384_kappa1e6", "ms": ms, "solves_per_s": 1e3 / ms,
             "qr_tflops": info["qr_flops"] / (ms * 1e-3) / 1e12, "refine_iters": refine, "status": st,
-            "normal_eq_residual": atr, "tasks": info["tasks"], "_x": x, "_A": A, "_b": b}
+            "rel_diff_vs_cusolver_fp64_qr": cross, "tasks": info["tasks"]}
 
 
 def run_reference(args):

@@ -219,9 +219,18 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
   auto rres = [&](int i) { return ntile_res + (size_t)n + (size_t)i; };
   auto gres = [&](int j) { return ntile_res + (size_t)n + (size_t)m + (size_t)j; };
   auto bres = [&](int i) { return ntile_res + (size_t)2 * n + (size_t)m + (size_t)i; };
-  const int nch = atr_chunks(m);
-  auto pres = [&](int c, int j) { return ntile_res + (size_t)2 * n + 2 * (size_t)m + (size_t)c * n + (size_t)j; };
-  Builder b(ntile_res + 2 * (size_t)n + 2 * (size_t)m + (size_t)nch * n);
+  const int nch = atr_chunks(m), nrc = res_chunks(n);
+  size_t nres = ntile_res + 2 * (size_t)n + 2 * (size_t)m;
+  const size_t pres0 = nres;
+  nres += (size_t)nch * n;
+  const size_t qres0 = nres;  // residual partial sums (row tile, column chunk)
+  nres += (size_t)m * nrc;
+  const size_t ires0 = nres;  // inverses of the diagonal R tiles
+  nres += (size_t)n;
+  auto pres = [&](int c, int j) { return pres0 + (size_t)c * n + (size_t)j; };
+  auto qres = [&](int i, int c) { return qres0 + (size_t)i * nrc + (size_t)c; };
+  auto ires = [&](int i) { return ires0 + (size_t)i; };
+  Builder b(nres);
   Tracker &tr = b.tr();
   std::vector<int32_t> &d = b.deps();
   if (pack) {
@@ -287,10 +296,19 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
     tr.read(upart(i, j), d);
   };
   auto vtask = [&](int op, int i, int j) { return make_task(op, 1, i, i, 0, j, 0, 0, 1, 0, pid); };
+  bool inverted = false;
   auto solve_r = [&](bool transposed_first) {
-    if (transposed_first) {  // R^T y = g, forward
+    if (!inverted) {  // inverses of the diagonal tiles, once per factorization
       for (int i = 0; i < n; ++i) {
         read_r(i, i);
+        tr.write(ires(i), d);
+        b.add(vtask(OP_TRINV, i, i));
+      }
+      inverted = true;
+    }
+    if (transposed_first) {  // R^T y = g, forward
+      for (int i = 0; i < n; ++i) {
+        tr.read(ires(i), d);
         tr.write(gres(i), d);
         b.add(vtask(OP_TRSV_TD, i, i));
         for (int j = i + 1; j < n; ++j) {
@@ -302,7 +320,7 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
       }
     }
     for (int i = n - 1; i >= 0; --i) {  // R d = y, backward
-      read_r(i, i);
+      tr.read(ires(i), d);
       tr.write(gres(i), d);
       b.add(vtask(OP_TRSV_D, i, i));
       for (int j = 0; j < i; ++j) {
@@ -342,9 +360,14 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
   }
   for (int it = 0; it < iters; ++it) {
     for (int i = 0; i < m; ++i) {
-      for (int j = 0; j < n; ++j) tr.read(xres(j), d);
+      for (int c = 0; c < nrc; ++c) {
+        for (int j = c * kResChunk; j < std::min(n, (c + 1) * kResChunk); ++j) tr.read(xres(j), d);
+        tr.write(qres(i, c), d);
+        b.add(vtask(OP_RESID, i, c));
+      }
+      for (int c = 0; c < nrc; ++c) tr.read(qres(i, c), d);
       tr.write(rres(i), d);
-      b.add(vtask(OP_RESID, i, i));
+      b.add(vtask(OP_RESR, i, i));
     }
     for (int j = 0; j < n; ++j) {
       for (int c = 0; c < nch; ++c) {

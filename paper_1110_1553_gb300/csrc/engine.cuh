@@ -23,6 +23,7 @@
 // Norm reductions use warp shuffles and a per-warp shared-memory stage.
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 
@@ -101,6 +102,8 @@ struct alignas(16) Problem {
   const double *b;    // right-hand side (M)
   double *x, *r, *g;  // solution (N), residual (m*nb), work vector (n*nb)
   double *gp;         // partial sums of A^T r: (row chunk, column) pairs (sum, compensation)
+  double *rp;         // partial sums of A x: (column chunk, row) pairs (sum, compensation)
+  double *rinv;       // inverses of the diagonal R tiles, n tiles of nb x nb, column-major
   int *status;        // per-problem status word (HQR_ERR_SINGULAR)
 };
 static_assert(sizeof(Problem) % 16 == 0, "Problem is read in 16-byte pieces");
@@ -244,6 +247,101 @@ __device__ Real block_max(Real v, Shared<Real> &sh) {
   return t;
 }
 
+// FP32 versions of the two GEMM phases with register blocking and 16-byte
+// shared-memory loads: each thread owns a 4 x 4 (W = V^T C) or 4 x 8
+// (C -= V W) block of outputs, so an FFMA costs at most one eighth of a
+// shared-memory access instead of two. K must be a multiple of 4 (true for
+// FP32 tiles: nb, ib and every row offset are multiples of 4).
+__device__ void gemm_tn_f32(float *W, int ldw, const float *V, int ldv, const float *Cm, int ldc, int K, int Mi,
+                            int Nj, const float *Cinit, int ldi, float *scr) {
+  const int ti = (Mi + 3) >> 2, tj = (Nj + 3) >> 2, T = ti * tj;
+  int G = NT / T;
+  if (G < 1) G = 1;
+  if (G > 4) G = 4;
+  int Kc = (K + G - 1) / G;
+  Kc = (Kc + 3) & ~3;
+  for (int u = threadIdx.x; u < T * G; u += NT) {
+    const int mt = u % T, g = u / T;
+    const int i0 = (mt % ti) * 4, j0 = (mt / ti) * 4;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    const int k0 = g * Kc, k1 = min(K, k0 + Kc);
+    const float *vp[4], *cp[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) vp[a] = V + (size_t)min(i0 + a, Mi - 1) * ldv;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) cp[b] = Cm + (size_t)min(j0 + b, Nj - 1) * ldc;
+    for (int k = k0; k < k1; k += 4) {
+      float4 v4[4], c4[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) v4[a] = *reinterpret_cast<const float4 *>(vp[a] + k);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) c4[b] = *reinterpret_cast<const float4 *>(cp[b] + k);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          acc[a][b] = fmaf(v4[a].x, c4[b].x, acc[a][b]);
+          acc[a][b] = fmaf(v4[a].y, c4[b].y, acc[a][b]);
+          acc[a][b] = fmaf(v4[a].z, c4[b].z, acc[a][b]);
+          acc[a][b] = fmaf(v4[a].w, c4[b].w, acc[a][b]);
+        }
+    }
+    float *dst = scr + (size_t)(g * T + mt) * 16;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) dst[a * 4 + b] = acc[a][b];
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < Mi * Nj; o += NT) {
+    const int i = o % Mi, j = o / Mi;
+    const int mt = (i >> 2) + (j >> 2) * ti, q = (i & 3) * 4 + (j & 3);
+    float s = 0.f;
+    for (int g = 0; g < G; ++g) s += scr[(size_t)(g * T + mt) * 16 + q];
+    W[i + (size_t)j * ldw] = (Cinit ? Cinit[i + (size_t)j * ldi] : 0.f) + s;
+  }
+  __syncthreads();
+}
+
+__device__ void gemm_nn_sub_f32(float *Cm, int ldc, const float *V, int ldv, const float *W, int ldw, int K, int Mi,
+                                int Nj) {
+  const int tk = K >> 2, tj = (Nj + 7) >> 3;
+  for (int u = threadIdx.x; u < tk * tj; u += NT) {
+    const int k0 = (u % tk) * 4, j0 = (u / tk) * 8, jn = min(8, Nj - j0);
+    float4 acc[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = 0; i < Mi; ++i) {
+      const float4 v = *reinterpret_cast<const float4 *>(V + (size_t)i * ldv + k0);
+      const float *w = W + i + (size_t)j0 * ldw;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const float wb = b < jn ? w[(size_t)b * ldw] : 0.f;
+        acc[b].x = fmaf(v.x, wb, acc[b].x);
+        acc[b].y = fmaf(v.y, wb, acc[b].y);
+        acc[b].z = fmaf(v.z, wb, acc[b].z);
+        acc[b].w = fmaf(v.w, wb, acc[b].w);
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+      if (b < jn) {
+        float4 *c = reinterpret_cast<float4 *>(Cm + (size_t)(j0 + b) * ldc + k0);
+        float4 x = *c;
+        x.x -= acc[b].x;
+        x.y -= acc[b].y;
+        x.z -= acc[b].z;
+        x.w -= acc[b].w;
+        *c = x;
+      }
+  }
+  __syncthreads();
+}
+
 // W(i,j) = [Cinit(i,j)] + sum_{k<K} V(k,i) C(k,j), i < Mi, j < Nj.
 // Short output sets split K among thread groups; partial sums are combined
 // in a fixed order through `scr` (>= NT elements).
@@ -252,6 +350,10 @@ __device__ void gemm_tn(Real *W, int ldw, const Real *V, int ldv, const Real *Cm
                         int Nj, const Real *Cinit, int ldi, Real *scr) {
   const int O = Mi * Nj;
   if (O <= 0) return;
+  if constexpr (sizeof(Real) == 4) {
+    gemm_tn_f32(W, ldw, V, ldv, Cm, ldc, K, Mi, Nj, Cinit, ldi, scr);
+    return;
+  }
   const int tid = threadIdx.x;
   if (O >= NT / 2 || K < 64) {
     for (int o = tid; o < O; o += NT) {
@@ -299,6 +401,10 @@ __device__ void gemm_tn(Real *W, int ldw, const Real *V, int ldv, const Real *Cm
 template <typename Real>
 __device__ void gemm_nn_sub(Real *Cm, int ldc, const Real *V, int ldv, const Real *W, int ldw, int K, int Mi,
                             int Nj) {
+  if constexpr (sizeof(Real) == 4) {
+    gemm_nn_sub_f32(Cm, ldc, V, ldv, W, ldw, K, Mi, Nj);
+    return;
+  }
   const int nchunk = (Nj + 7) / 8;
   const int total = K * nchunk;
   for (int it = threadIdx.x; it < total; it += NT) {
@@ -649,14 +755,16 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
   const int nb = g.nb, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const Real *A0 = (const Real *)P.A0;
   switch (t.op) {
-    case OP_RESID: {  // r_i = b_i - A(i,:) x
+    case OP_RESID: {  // partial sums of A(rows of tile i, columns of chunk t.j) x
       const int r0 = t.i * nb, nr = min(nb, P.M - r0);
+      const int clo = t.j * kResChunk * nb, chi = min(P.N, clo + kResChunk * nb);
       const int G = NT / nb;  // column groups
       const int rr = tid % nb, gi = tid / nb;
       double s = 0.0, c = 0.0;
       if (rr < nr && gi < G) {
         const Real *arow = A0 + r0 + rr;
-        for (int j = gi; j < P.N; j += G) dot2_step((double)arow[(long long)j * P.lda0], P.x[j], s, c);
+        for (int j = clo + gi; j < chi; j += G)
+          dot2_step((double)__ldcg(arow + (long long)j * P.lda0), __ldcg(P.x + j), s, c);
       }
       sm[tid] = s;
       sm[NT + tid] = c;
@@ -664,11 +772,52 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
       if (tid < nr) {
         double S = sm[tid], C = sm[NT + tid];
         for (int q = 1; q < G; ++q) dot2_merge(S, C, sm[q * nb + tid], sm[NT + q * nb + tid]);
-        double u, e;
-        two_sum(P.b[r0 + tid], -S, u, e);
-        P.r[r0 + tid] = u + (e - C);
+        const size_t mp = (size_t)g.m * nb;
+        P.rp[2 * ((size_t)t.j * mp + r0 + tid)] = S;
+        P.rp[2 * ((size_t)t.j * mp + r0 + tid) + 1] = C;
       }
       __syncthreads();
+      break;
+    }
+    case OP_RESR: {  // r_i = b_i - sum of the column-chunk partials, in chunk order
+      const int r0 = t.i * nb, nr = min(nb, P.M - r0);
+      const int nrc = (g.n + kResChunk - 1) / kResChunk;
+      const size_t mp = (size_t)g.m * nb;
+      for (int rr = tid; rr < nr; rr += NT) {
+        double S = __ldcg(P.rp + 2 * (size_t)(r0 + rr)), C = __ldcg(P.rp + 2 * (size_t)(r0 + rr) + 1);
+        for (int q = 1; q < nrc; ++q)
+          dot2_merge(S, C, __ldcg(P.rp + 2 * ((size_t)q * mp + r0 + rr)), __ldcg(P.rp + 2 * ((size_t)q * mp + r0 + rr) + 1));
+        double u, e2;
+        two_sum(__ldcg(P.b + r0 + rr), -S, u, e2);
+        P.r[r0 + rr] = u + (e2 - C);
+      }
+      break;
+    }
+    case OP_TRINV: {  // inverse of the upper-triangular leading n_i x n_i part of R_ii (thread per column)
+      const int i = t.i, n_i = min(nb, P.N - i * nb);
+      const Real *R = g.tile(i, i);
+      double *X = P.rinv + (size_t)i * nb * nb;
+      for (int e = tid; e < nb * nb; e += NT) X[e] = 0.0;
+      __syncthreads();
+      for (int j = tid; j < n_i; j += NT) {
+        double *xj = X + (size_t)j * nb;
+        const double djj = (double)__ldcg(R + (size_t)j * nb + j);
+        if (djj == 0.0) {
+          atomicExch(P.status, HQR_ERR_SINGULAR);
+          continue;
+        }
+        xj[j] = 1.0 / djj;
+        for (int k = j - 1; k >= 0; --k) {
+          double s = 0.0;
+          for (int l = k + 1; l <= j; ++l) s = fma((double)__ldcg(R + (size_t)l * nb + k), xj[l], s);
+          const double dkk = (double)__ldcg(R + (size_t)k * nb + k);
+          if (dkk == 0.0) {
+            atomicExch(P.status, HQR_ERR_SINGULAR);
+            break;
+          }
+          xj[k] = -s / dkk;
+        }
+      }
       break;
     }
     case OP_ATR: {  // partial sums of A(rows of chunk t.i, tile j)^T r
@@ -678,7 +827,7 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
       for (int cc = warp; cc < nc; cc += NWARP) {
         const Real *acol = A0 + (long long)(c0 + cc) * P.lda0;
         double s = 0.0, c = 0.0;
-        for (int i = rlo + lane; i < rhi; i += 32) dot2_step((double)acol[i], P.r[i], s, c);
+        for (int i = rlo + lane; i < rhi; i += 32) dot2_step((double)__ldcg(acol + i), __ldcg(P.r + i), s, c);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           const double s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, c, o);
@@ -696,46 +845,35 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
       const int nch = (g.m + kAtrChunk - 1) / kAtrChunk;
       const size_t np = (size_t)g.n * nb;
       for (int cc = tid; cc < nc; cc += NT) {
-        double s = P.gp[2 * (size_t)(c0 + cc)], c = P.gp[2 * (size_t)(c0 + cc) + 1];
+        double s = __ldcg(P.gp + 2 * (size_t)(c0 + cc)), c = __ldcg(P.gp + 2 * (size_t)(c0 + cc) + 1);
         for (int q = 1; q < nch; ++q)
-          dot2_merge(s, c, P.gp[2 * ((size_t)q * np + c0 + cc)], P.gp[2 * ((size_t)q * np + c0 + cc) + 1]);
+          dot2_merge(s, c, __ldcg(P.gp + 2 * ((size_t)q * np + c0 + cc)), __ldcg(P.gp + 2 * ((size_t)q * np + c0 + cc) + 1));
         P.g[c0 + cc] = s + c;
       }
       break;
     }
     case OP_TRSV_TD:
-    case OP_TRSV_D: {  // triangular solve with the diagonal tile, in place on g_i
+    case OP_TRSV_D: {  // g_i <- X^T g_i or X g_i with X = R_ii^{-1}
       const int i = t.i, n_i = min(nb, P.N - i * nb);
-      const Real *R = g.tile(i, i);
+      const double *X = P.rinv + (size_t)i * nb * nb;
       double *gi = P.g + (size_t)i * nb;
-      for (int k = tid; k < n_i; k += NT) sm[k] = gi[k];
+      for (int k = tid; k < n_i; k += NT) sm[k] = __ldcg(gi + k);
       __syncthreads();
       if (t.op == OP_TRSV_TD) {
-        for (int k = 0; k < n_i; ++k) {
-          if (tid == 0) {
-            const double d = (double)R[(size_t)k * nb + k];
-            if (d == 0.0) atomicExch(P.status, HQR_ERR_SINGULAR);
-            sm[k] = d == 0.0 ? 0.0 : sm[k] / d;
-          }
-          __syncthreads();
-          const double yk = sm[k];
-          for (int l = k + 1 + tid; l < n_i; l += NT) sm[l] = fma(-(double)R[(size_t)l * nb + k], yk, sm[l]);
-          __syncthreads();
+        for (int c = warp; c < n_i; c += NWARP) {  // (X^T g)_c = sum_{r <= c} X(r, c) g_r
+          double s = 0.0;
+          for (int r = lane; r <= c; r += 32) s = fma(__ldcg(X + (size_t)c * nb + r), sm[r], s);
+          s = warp_sum(s);
+          if (lane == 0) gi[c] = s;
         }
       } else {
-        for (int k = n_i - 1; k >= 0; --k) {
-          if (tid == 0) {
-            const double d = (double)R[(size_t)k * nb + k];
-            if (d == 0.0) atomicExch(P.status, HQR_ERR_SINGULAR);
-            sm[k] = d == 0.0 ? 0.0 : sm[k] / d;
-          }
-          __syncthreads();
-          const double dk = sm[k];
-          for (int l = tid; l < k; l += NT) sm[l] = fma(-(double)R[(size_t)k * nb + l], dk, sm[l]);
-          __syncthreads();
+        for (int r = tid; r < n_i; r += NT) {  // (X g)_r = sum_{c >= r} X(r, c) g_c
+          double s = 0.0;
+          for (int c = r; c < n_i; ++c) s = fma(__ldcg(X + (size_t)c * nb + r), sm[c], s);
+          gi[r] = s;
         }
       }
-      for (int k = tid; k < n_i; k += NT) gi[k] = sm[k];
+      __syncthreads();
       break;
     }
     case OP_TRSV_TU: {  // g_j -= R(i,j)^T g_i, j > i
@@ -744,9 +882,9 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
       const double *gi = P.g + (size_t)i * nb;
       for (int c = warp; c < n_j; c += NWARP) {
         double s = 0.0;
-        for (int r = lane; r < n_i; r += 32) s = fma((double)R[(size_t)c * nb + r], gi[r], s);
+        for (int r = lane; r < n_i; r += 32) s = fma((double)__ldcg(R + (size_t)c * nb + r), __ldcg(gi + r), s);
         s = warp_sum(s);
-        if (lane == 0) P.g[(size_t)j * nb + c] -= s;
+        if (lane == 0) P.g[(size_t)j * nb + c] = __ldcg(P.g + (size_t)j * nb + c) - s;
       }
       break;
     }
@@ -756,20 +894,21 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
       const double *gi = P.g + (size_t)i * nb;
       for (int r = tid; r < nb; r += NT) {
         double s = 0.0;
-        for (int c = 0; c < n_i; ++c) s = fma((double)R[(size_t)c * nb + r], gi[c], s);
-        P.g[(size_t)j * nb + r] -= s;
+        for (int c = 0; c < n_i; ++c) s = fma((double)__ldcg(R + (size_t)c * nb + r), __ldcg(gi + c), s);
+        P.g[(size_t)j * nb + r] = __ldcg(P.g + (size_t)j * nb + r) - s;
       }
       break;
     }
     case OP_XUPD: {
       const int j = t.j, n_j = min(nb, P.N - j * nb);
-      for (int c = tid; c < n_j; c += NT) P.x[(size_t)j * nb + c] += P.g[(size_t)j * nb + c];
+      for (int c = tid; c < n_j; c += NT)
+        P.x[(size_t)j * nb + c] = __ldcg(P.x + (size_t)j * nb + c) + __ldcg(P.g + (size_t)j * nb + c);
       break;
     }
     case OP_BTOG: {
       const int i = t.i, n_i = min(nb, P.N - i * nb);
       const Real *Bb = g.B + (size_t)i * nb * g.wb;
-      for (int r = tid; r < n_i; r += NT) P.g[(size_t)i * nb + r] = (double)Bb[r];
+      for (int r = tid; r < n_i; r += NT) P.g[(size_t)i * nb + r] = (double)__ldcg(Bb + r);
       break;
     }
     case OP_PACK: {  // tile column j of the workspace, zero padded; column 0 also b and x = 0
@@ -1112,8 +1251,11 @@ __global__ void __launch_bounds__(NT, 2) hqr_serve(ServeParams sp) {
 template <typename Real>
 inline size_t engine_smem_bytes(int nb, int ib, int w, int wt, int vc) {
   const int lds = nb + smem_pad<Real>(), ldt = ib + smem_pad<Real>();
-  const size_t scr_u = (size_t)(ib * w > NT ? ib * w : NT);
-  const size_t scr_p = (size_t)(ib * wt > NT ? ib * wt : NT);
+  // scratch: FP32 GEMMs keep up to 4 K-groups of partial output blocks
+  const size_t fac = sizeof(Real) == 4 ? 4 : 1;
+  const size_t scr_u = std::max<size_t>({(size_t)NT, (size_t)ib * w, fac * (((vc + 3) / 4) * ((w + 3) / 4) * 16)});
+  const size_t scr_p = std::max<size_t>({(size_t)NT, (size_t)ib * wt, fac * (((ib + 3) / 4) * ((wt + 3) / 4) * 16),
+                                         fac * (((ib + 3) / 4) * ((ib + 3) / 4) * 16)});
   const size_t upd = (size_t)lds * (2 * w + vc) + (size_t)ib * ib + (size_t)ib * w + scr_u;
   const size_t cbg = (size_t)(lds * wt > ib * ib ? lds * wt : ib * ib);
   const size_t pan = (size_t)lds * ib + (size_t)ldt * (ib + wt) + (size_t)ib * ib + cbg +

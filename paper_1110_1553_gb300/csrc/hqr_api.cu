@@ -233,15 +233,20 @@ int launch_sched(int prec, const EngineParams &p, size_t smem, cudaStream_t s) {
   return HQR_SUCCESS;
 }
 
-// Tuning of the column-slab widths for a tile size and precision.
+// Tuning of the column-slab widths for a tile size and precision. FP64 work
+// is bound by the FP64 pipe, so narrow slabs (more parallel tasks) cost
+// nothing; FP32 tasks are bound by their barriers and staging, so they take
+// wider slabs (more arithmetic per barrier) within the shared memory of two
+// CTAs per SM.
 void choose_widths(int prec, int nb, int ib, Problem &P) {
-  P.w = std::min(16, nb);
   P.wb = std::min(16, nb);
   if (prec == HQR_FP64) {
+    P.w = std::min(16, nb);
     P.wt = nb > 128 ? 8 : std::min(16, nb);
     P.vc = nb > 128 ? std::min(ib, 8) : std::min(ib, 16);
   } else {
-    P.wt = std::min(16, nb);
+    P.w = nb >= 256 ? 32 : std::min(64, nb);
+    P.wt = nb >= 256 ? 16 : std::min(32, nb);
     P.vc = std::min(ib, 16);
   }
 }
@@ -903,7 +908,8 @@ int hqr_ls_plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_
     off_b[q] = arena_elems;
     arena_elems += (Mp + 3) & ~(size_t)3;
     off_vec[q] = vec_elems;
-    vec_elems += Np + Mp + Np + 2 * (size_t)atr_chunks(pb.m) * Np;
+    vec_elems += Np + Mp + Np + 2 * (size_t)atr_chunks(pb.m) * Np + 2 * (size_t)res_chunks(pb.n) * Mp +
+                 (size_t)pb.n * c.nb * c.nb;
     size_t cnt = 0;
     hqr_elim_list(pb.m, pb.n, c.a, c.p, c.low_tree, c.high_tree, nullptr, 0, &cnt);
     std::vector<hqr_elim_t> lst(cnt);
@@ -936,6 +942,8 @@ int hqr_ls_plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_
       pb.r = pb.x + (size_t)pb.n * pb.nb;
       pb.g = pb.r + (size_t)pb.m * pb.nb;
       pb.gp = pb.g + (size_t)pb.n * pb.nb;
+      pb.rp = pb.gp + 2 * (size_t)atr_chunks(pb.m) * pb.n * pb.nb;
+      pb.rinv = pb.rp + 2 * (size_t)res_chunks(pb.n) * pb.m * pb.nb;
       pb.status = P->dstatus + q;
       PrepDesc d;
       d.A = probs[q].dA;
@@ -1506,8 +1514,9 @@ int hqr_server_submit(hqr_server *S, const hqr_ls_problem_t *pr, int64_t *ticket
   auto r256 = [](size_t b) { return (b + 255) / 256; };
   const size_t a_tiles = r256(es * Mp * Np), a_t = r256(es * (size_t)pb.m * pb.n * 2 * c.ib * c.nb),
                a_b = r256(es * Mp), a_r = r256(8 * Mp), a_g = r256(8 * Np),
-               a_gp = r256(16 * (size_t)atr_chunks(pb.m) * Np);
-  const size_t a_units = a_tiles + a_t + a_b + a_r + a_g + a_gp;
+               a_gp = r256(16 * (size_t)atr_chunks(pb.m) * Np), a_rp = r256(16 * (size_t)res_chunks(pb.n) * Mp),
+               a_ri = r256(8 * (size_t)pb.n * c.nb * c.nb);
+  const size_t a_units = a_tiles + a_t + a_b + a_r + a_g + a_gp + a_rp + a_ri;
   if (a_units * 256 > S->o.hbm_budget || nt > (size_t)S->o.task_pool || ne > (size_t)S->o.edge_pool)
     return HQR_ERR_BUDGET;
   if (S->free_slots.empty()) return HQR_ERR_BUSY;
@@ -1542,6 +1551,8 @@ int hqr_server_submit(hqr_server *S, const hqr_ls_problem_t *pr, int64_t *ticket
   pb.r = (double *)(base + (a_tiles + a_t + a_b) * 256);
   pb.g = (double *)(base + (a_tiles + a_t + a_b + a_r) * 256);
   pb.gp = (double *)(base + (a_tiles + a_t + a_b + a_r + a_g) * 256);
+  pb.rp = (double *)(base + (a_tiles + a_t + a_b + a_r + a_g + a_gp) * 256);
+  pb.rinv = (double *)(base + (a_tiles + a_t + a_b + a_r + a_g + a_gp + a_rp) * 256);
   pb.x = pr->dx;
   pb.M = pr->M;
   pb.N = pr->N;

@@ -19,21 +19,26 @@ enum Op : int8_t {
   OP_TTQRT = 4,
   OP_TTMQR = 5,
   // FP64 vector tasks of least-squares solves (per tile of the vectors)
-  OP_RESID = 6,    // r_i = b_i - A(i,:) x, compensated (row tile i)
+  OP_RESID = 6,    // partial sums of A(i, column chunk j) x, compensated (row tile i)
   OP_ATR = 7,      // partial sums of A(rows of chunk i, j)^T r, compensated (column tile j, row chunk i)
-  OP_TRSV_TD = 8,  // g_i <- R_ii^{-T} g_i (forward substitution, diagonal tile i)
+  OP_TRSV_TD = 8,  // g_i <- R_ii^{-T} g_i (with the inverse from OP_TRINV)
   OP_TRSV_TU = 9,  // g_j -= R(i,j)^T g_i, j > i
-  OP_TRSV_D = 10,  // g_i <- R_ii^{-1} g_i (back substitution, diagonal tile i)
+  OP_TRSV_D = 10,  // g_i <- R_ii^{-1} g_i (with the inverse from OP_TRINV)
   OP_TRSV_U = 11,  // g_j -= R(j,i) g_i, j < i
   OP_XUPD = 12,    // x_j += g_j
   OP_BTOG = 13,    // g_i = first column of the right-hand-side block of row tile i
   OP_PACK = 14,    // tile column j of the workspace from the caller's matrix (j = 0 also b, x = 0)
   OP_ATRR = 15,    // g_j = sum over row chunks of the OP_ATR partial sums
+  OP_TRINV = 16,   // inverse of the diagonal R tile i (FP64), used by OP_TRSV_TD / OP_TRSV_D
+  OP_RESR = 17,    // r_i = b_i - sum over column chunks of the OP_RESID partial sums
 };
 
-// Row tiles per chunk of the A^T r partial sums.
+// Row tiles per chunk of the A^T r partial sums, column tiles per chunk of
+// the residual partial sums.
 constexpr int kAtrChunk = 8;
+constexpr int kResChunk = 8;
 inline int atr_chunks(int m) { return (m + kAtrChunk - 1) / kAtrChunk; }
+inline int res_chunks(int n) { return (n + kResChunk - 1) / kResChunk; }
 
 // Scheduling classes, highest first: panel kernels (on the critical path),
 // updates of the next panel's column (look-ahead), other updates.
