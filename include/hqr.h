@@ -407,6 +407,21 @@ void hqr_server_free(hqr_server *server);
 /* hqr_factors_free -- release a factorization (NULL is allowed). */
 void hqr_factors_free(hqr_factors *F);
 
+/* hqr_set_slab_widths -- engine tuning for factorizations and plans created
+ * afterwards: column-slab width of an update task (w), of the trailing
+ * update inside a panel task (wt), and V columns staged per chunk (vc,
+ * must divide ib). 0 restores the built-in choice; values are even.
+ * Larger slabs mean fewer, longer tasks and more shared memory per CTA. */
+int hqr_set_slab_widths(int w, int wt, int vc);
+
+/* hqr_set_priority_policy -- ready-queue priorities of task graphs created
+ * afterwards (factorizations, plans, server requests): 1 (default) by the
+ * length of the longest chain of estimated task costs that still follows
+ * each task (critical path first); 0 panel kernels first, then updates of
+ * the next panel's column, then the rest (a look-ahead order; cf. the
+ * priority function of Sec. 4.3). */
+int hqr_set_priority_policy(int policy);
+
 /* hqr_set_timeout_ms -- time limit of every device-side wait (default 20000). */
 void hqr_set_timeout_ms(int64_t ms);
 

@@ -384,6 +384,39 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
   return b.finish();
 }
 
+void critical_path_priorities(Graph &g, int nb) {
+  const size_t nt = g.tasks.size();
+  if (nt == 0) return;
+  // estimated cost in units of b^3/3 (Sec. 2 weights), updates scaled by slab width
+  auto cost = [&](const Task &t) {
+    const double slab = t.cw > 0 ? (double)t.cw / nb : 1.0;
+    switch (t.op) {
+      case OP_GEQRT: return 4.0;
+      case OP_TSQRT: return 6.0;
+      case OP_TTQRT: return 2.0;
+      case OP_UNMQR: return 6.0 * slab;
+      case OP_TSMQR: return 12.0 * slab;
+      case OP_TTMQR: return 6.0 * slab;
+      default: return 0.5;
+    }
+  };
+  std::vector<double> bl(nt, 0.0);
+  for (size_t q = nt; q-- > 0;) {  // tasks are in a topological order
+    double best = 0.0;
+    for (int32_t e = g.tasks[q].succ_begin; e < g.tasks[q].succ_end; ++e) best = std::max(best, bl[g.succ[e]]);
+    bl[q] = cost(g.tasks[q]) + best;
+  }
+  std::vector<double> sorted(bl);
+  std::sort(sorted.begin(), sorted.end());
+  double cut[kNumQueues];
+  for (int c = 0; c < kNumQueues; ++c) cut[c] = sorted[(size_t)((double)(kNumQueues - 1 - c) / kNumQueues * (nt - 1))];
+  for (size_t q = 0; q < nt; ++q) {
+    int c = kNumQueues - 1;
+    while (c > 0 && bl[q] >= cut[c - 1]) --c;
+    g.tasks[q].prio = (int8_t)c;
+  }
+}
+
 void append_graph(Graph &into, const Graph &g) {
   const int32_t toff = (int32_t)into.tasks.size();
   const int32_t eoff = (int32_t)into.succ.size();

@@ -233,6 +233,11 @@ int launch_sched(int prec, const EngineParams &p, size_t smem, cudaStream_t s) {
   return HQR_SUCCESS;
 }
 
+// Explicit slab widths (0 = built-in choice), set by hqr_set_slab_widths.
+int g_w_override = 0, g_wt_override = 0, g_vc_override = 0;
+// Priority policy of task graphs (hqr_set_priority_policy).
+int g_priority_policy = 1;
+
 // Tuning of the column-slab widths for a tile size and precision. FP64 work
 // is bound by the FP64 pipe, so narrow slabs (more parallel tasks) cost
 // nothing; FP32 tasks are bound by their barriers and staging, so they take
@@ -249,6 +254,9 @@ void choose_widths(int prec, int nb, int ib, Problem &P) {
     P.wt = nb >= 256 ? 16 : std::min(32, nb);
     P.vc = std::min(ib, 16);
   }
+  if (g_w_override > 0) P.w = std::min(g_w_override, nb);
+  if (g_wt_override > 0) P.wt = std::min(g_wt_override, nb);
+  if (g_vc_override > 0 && ib % g_vc_override == 0) P.vc = std::min(g_vc_override, ib);
 }
 
 bool valid_tile_sizes(int prec, int nb, int ib) {
@@ -346,6 +354,22 @@ extern "C" {
 
 void hqr_set_timeout_ms(int64_t ms) { g_timeout_ns = (ms > 0 ? ms : 1) * 1000000ll; }
 
+int hqr_set_priority_policy(int policy) {
+  if (policy != 0 && policy != 1) return -1;
+  g_priority_policy = policy;
+  return HQR_SUCCESS;
+}
+
+int hqr_set_slab_widths(int w, int wt, int vc) {
+  if (w < 0 || w % 2) return -1;
+  if (wt < 0 || wt % 2) return -2;
+  if (vc < 0 || (vc && vc % 2)) return -3;
+  g_w_override = w;
+  g_wt_override = wt;
+  g_vc_override = vc;
+  return HQR_SUCCESS;
+}
+
 const char *hqr_last_error(void) { return g_last_error.c_str(); }
 
 int64_t hqr_last_launches(void) { return g_launches; }
@@ -412,6 +436,7 @@ int hqr_geqrf(const void *dA, int M, int N, int lda, int prec, int nb, int ib, c
   }
   F->ops = expand_ops(F->list.data(), F->list.size(), F->m, F->n);
   Graph g = build_factor_graph(F->ops, F->m, F->n, nb, F->prob.w);
+  if (g_priority_policy == 1) critical_path_priorities(g, nb);
   int st = upload_graph(g, F->fg);
   const size_t es = elem_size(prec);
   if (!st) {
@@ -973,7 +998,10 @@ int hqr_ls_plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_
                        "copy prep") ||
               !cuda_ok(cudaEventCreate(&P->ev0), "event") || !cuda_ok(cudaEventCreate(&P->ev1), "event")))
     st = HQR_ERR_CUDA;
-  if (!st) st = upload_graph(merged, P->graph);
+  if (!st) {
+    if (g_priority_policy == 1) critical_path_priorities(merged, 128);
+    st = upload_graph(merged, P->graph);
+  }
   if (st) {
     hqr_ls_plan_free(P);
     return st;
@@ -1503,6 +1531,7 @@ int hqr_server_submit(hqr_server *S, const hqr_ls_problem_t *pr, int64_t *ticket
     CachedGraph cg;
     cg.g = build_ls_graph(expand_ops(lst.data(), lst.size(), pb.m, pb.n), pb.m, pb.n, c.nb, pb.w,
                           S->o.refine_iters, 0, true);
+    if (g_priority_policy == 1) critical_path_priorities(cg.g, c.nb);
     for (size_t t = 0; t < cg.g.tasks.size(); ++t)
       if (cg.g.indeg[t] == 0) cg.init.push_back((int)t);
     if (S->cache.size() > 4096) S->cache.clear();

@@ -42,7 +42,7 @@ inline int res_chunks(int n) { return (n + kResChunk - 1) / kResChunk; }
 
 // Scheduling classes, highest first: panel kernels (on the critical path),
 // updates of the next panel's column (look-ahead), other updates.
-constexpr int kNumQueues = 3;
+constexpr int kNumQueues = 4;
 
 // One task of the device task graph. For update tasks, columns
 // [c0, c0 + cw) of the target tiles are updated (a column slab).
@@ -101,6 +101,12 @@ Graph build_apply_graph(const std::vector<PanelOp> &ops, int m, int nslab, int w
 // preparation kernel can be launched).
 Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int w, int iters, int pid,
                      bool pack = false);
+
+// Priorities from the critical path: every task gets its bottom level (its
+// own estimated cost plus the longest chain of estimated costs after it)
+// and the queue 0 (longest remaining chain) .. kNumQueues-1 of its quantile.
+// Replaces the default classes (panel kernels, next-column updates, rest).
+void critical_path_priorities(Graph &g, int nb);
 
 // Append graph g to `into` (its task ids and successor lists renumbered);
 // the two graphs stay independent.
