@@ -61,8 +61,13 @@ typedef struct {
 /* Arithmetic of the factorization. HQR_FP64: FP64 storage and arithmetic
  * everywhere (the paper's setting, Sec. 5.1). HQR_FP32: FP32 storage and
  * FP32 arithmetic (panel norms with a scaled second pass on under- or
- * overflow); device buffers passed with it hold float. */
-typedef enum { HQR_FP64 = 0, HQR_FP32 = 1 } hqr_prec_t;
+ * overflow); device buffers passed with it hold float. HQR_FP32_TF32X3:
+ * FP32 storage; tiles of nb = 128 run the updates (UNMQR, TSMQR, TTMQR) on
+ * the tensor cores as tf32 products split three ways (hi*hi + hi*lo +
+ * lo*hi, FP32 accumulation, about FP32 accuracy) with one full 128 x 128 T
+ * per tile (ib is taken as nb); other tile sizes fall back to HQR_FP32
+ * arithmetic. hqr_geqrf requires nb = 128 with it. */
+typedef enum { HQR_FP64 = 0, HQR_FP32 = 1, HQR_FP32_TF32X3 = 2 } hqr_prec_t;
 
 enum {
   HQR_SUCCESS = 0,

@@ -29,6 +29,7 @@
 
 #include "hqr_internal.h"
 #include "ptx.cuh"
+#include "tc.cuh"
 
 namespace hqr {
 
@@ -88,7 +89,7 @@ inline size_t slot_count(int ntasks) { return (size_t)kNumQueues * kShards * sha
 // One problem of a (possibly batched) task graph.
 struct alignas(16) Problem {
   void *A;            // tile workspace: tile (i, j) at ((j*m + i)*nb*nb), column-major
-  void *T;            // T factors: ((k*m + i)*2 + which)*ib*nb, ib x nb column-major
+  void *T;            // T factors: record ((k*m + i)*2 + which) of tstr elements, ib x nb column-major first
   void *B;            // right-hand-side blocks: block (r, s) at ((s*m + r)*nb*wb)
   int m, n, nb, ib;
   int w;              // width of an update task's column slab (max)
@@ -105,6 +106,9 @@ struct alignas(16) Problem {
   double *rp;         // partial sums of A x: (column chunk, row) pairs (sum, compensation)
   double *rinv;       // inverses of the diagonal R tiles, n tiles of nb x nb, column-major
   int *status;        // per-problem status word (HQR_ERR_SINGULAR)
+  int tc;             // FP32 tiles of 128 on the tensor-core kernels (ib = nb: one full T per tile)
+  int tstr;           // elements per T record (ib * nb; tensor-core problems: T plus split images)
+  int pad_[2];
 };
 static_assert(sizeof(Problem) % 16 == 0, "Problem is read in 16-byte pieces");
 
@@ -118,6 +122,7 @@ struct EngineParams {
   Ctl *ctl;
   long long timeout_ns;
   unsigned long long *trace;  // optional: per task start, end (globaltimer), SM id
+  int tc;                     // some problem uses the tensor-core kernels (launch the TC variant)
 };
 
 template <typename Real>
@@ -138,13 +143,13 @@ template <typename Real>
 struct Geo {
   Real *A, *T, *B;
   int m, n, nb, ib, w, wt, vc, wb, lds, ldt;
+  size_t tstr;
   __device__ explicit Geo(const Problem &P)
       : A((Real *)P.A), T((Real *)P.T), B((Real *)P.B), m(P.m), n(P.n), nb(P.nb), ib(P.ib), w(P.w),
-        wt(P.wt), vc(P.vc), wb(P.wb), lds(P.nb + smem_pad<Real>()), ldt(P.ib + smem_pad<Real>()) {}
+        wt(P.wt), vc(P.vc), wb(P.wb), lds(P.nb + smem_pad<Real>()), ldt(P.ib + smem_pad<Real>()),
+        tstr(P.tstr > 0 ? (size_t)P.tstr : (size_t)P.ib * P.nb) {}
   __device__ Real *tile(int i, int j) const { return A + ((size_t)j * m + i) * (size_t)nb * nb; }
-  __device__ Real *tfac(int which, int i, int k) const {
-    return T + (((size_t)k * m + i) * 2 + which) * (size_t)ib * nb;
-  }
+  __device__ Real *tfac(int which, int i, int k) const { return T + (((size_t)k * m + i) * 2 + which) * tstr; }
   // columns [t.c0, t.c0 + t.cw) of the target block of row `row`
   __device__ Real *target(const Task &t, int row) const {
     if (t.tgt == 0) return A + ((size_t)t.j * m + row) * (size_t)nb * nb + (size_t)t.c0 * nb;
@@ -997,17 +1002,69 @@ __device__ __forceinline__ unsigned smid() {
   return r;
 }
 
-template <typename Real>
-__global__ void __launch_bounds__(NT, 2) hqr_sched(EngineParams p) {
+// Tensor memory and chunk barriers of a CTA of the tensor-core kernel
+// variant (set up once per CTA, released at exit). Kernels that contain
+// tcgen05 instructions run one CTA per SM, so that variant is separate and
+// only launched for graphs with tensor-core problems.
+template <bool TC>
+__device__ __forceinline__ void tc_setup(tc::State &ts) {
+  if constexpr (TC) {
+    if (threadIdx.x == 0) {
+      for (int c = 0; c < tc::NCH; ++c) {
+        ptx::mbar_init(&ts.full[c], NT);
+        ptx::mbar_init(&ts.img[c], 1);
+      }
+      ptx::mbar_init(&ts.done, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x < 32) tc::tmem_alloc(&ts.tmem);
+    tc::tc_fence_before();
+  }
+}
+
+template <bool TC>
+__device__ __forceinline__ void tc_release(tc::State &ts) {
+  if constexpr (TC) {
+    __syncthreads();
+    tc::tc_fence_after();
+    if (threadIdx.x < 32) tc::tmem_dealloc(ts.tmem);
+  }
+}
+
+// A panel or update task of a tensor-core problem. Returns false on a timeout.
+template <typename Real, bool TC>
+__device__ bool tc_task(const EngineParams &p, const Geo<Real> &g, const Task &t, Shared<Real> &sh,
+                        unsigned char *dyn, tc::State &ts, tc::Phases &tph) {
+  if constexpr (TC && sizeof(Real) == 4) {
+    if (t.op == OP_GEQRT || t.op == OP_TSQRT || t.op == OP_TTQRT) {
+      const int mode = t.op == OP_GEQRT ? 1 : (t.op == OP_TSQRT ? 0 : 2);
+      tc::panel(mode, g.tile(t.i, t.k), g.tile(t.r, t.k), g.tfac(mode == 1 ? 0 : 1, t.i, t.k), dyn);
+      return true;
+    }
+    const int mode = t.op == OP_UNMQR ? 1 : (t.op == OP_TSMQR ? 0 : 2);
+    const bool pair = t.op != OP_UNMQR;
+    return tc::update(mode, t.trans, g.tile(t.i, t.k), g.tfac(pair ? 1 : 0, t.i, t.k),
+                      pair ? g.target(t, t.r) : nullptr, g.target(t, t.i), t.cw, dyn, ts, tph, &sh.abort,
+                      p.timeout_ns);
+  }
+  return true;
+}
+
+template <typename Real, bool TC>
+__global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_sched(EngineParams p) {
   extern __shared__ __align__(16) unsigned char dyn_raw[];
   Real *dyn = reinterpret_cast<Real *>(dyn_raw);
   __shared__ Shared<Real> sh;
+  __shared__ tc::State ts;
   if (threadIdx.x == 0) {
     ptx::mbar_init(&sh.bar, 1);
     sh.abort = 0;
   }
+  tc_setup<TC>(ts);
   __syncthreads();
+  tc::tc_fence_after();
   uint32_t phase = 0;
+  tc::Phases tph;
   unsigned pending = 0;
   while (true) {
     if (threadIdx.x == 0) sh.task = pop_ready(p, pending);
@@ -1017,7 +1074,9 @@ __global__ void __launch_bounds__(NT, 2) hqr_sched(EngineParams p) {
     const Task t = p.tasks[tid];
     const Geo<Real> g(p.probs[t.pid]);
     const uint64_t t_start = (p.trace && threadIdx.x == 0) ? ptx::globaltimer() : 0;
-    if (t.op == OP_GEQRT || t.op == OP_TSQRT || t.op == OP_TTQRT)
+    if (TC && t.op <= OP_TTMQR && p.probs[t.pid].tc) {
+      if (!tc_task<Real, TC>(p, g, t, sh, dyn_raw, ts, tph) && threadIdx.x == 0) set_error(p, HQR_ERR_TIMEOUT, tid);
+    } else if (t.op == OP_GEQRT || t.op == OP_TSQRT || t.op == OP_TTQRT)
       task_panel(p, g, t, sh, dyn, phase);
     else if (t.op <= OP_TTMQR)
       task_update(p, g, t, sh, dyn, phase);
@@ -1050,6 +1109,7 @@ __global__ void __launch_bounds__(NT, 2) hqr_sched(EngineParams p) {
     while (!ptx::mbar_try_wait(&sh.bar, phase) && ptx::globaltimer() - t0 < 1000000000ull) {
     }
   }
+  tc_release<TC>(ts);
 }
 
 
@@ -1187,18 +1247,22 @@ __device__ int serve_pop(const ServeParams &sp, unsigned &pending) {
   }
 }
 
-template <typename Real>
-__global__ void __launch_bounds__(NT, 2) hqr_serve(ServeParams sp) {
+template <typename Real, bool TC>
+__global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_serve(ServeParams sp) {
   extern __shared__ __align__(16) unsigned char dyn_raw[];
   Real *dyn = reinterpret_cast<Real *>(dyn_raw);
   __shared__ Shared<Real> sh;
+  __shared__ tc::State ts;
   const EngineParams &p = sp.e;
   if (threadIdx.x == 0) {
     ptx::mbar_init(&sh.bar, 1);
     sh.abort = 0;
   }
+  tc_setup<TC>(ts);
   __syncthreads();
+  tc::tc_fence_after();
   uint32_t phase = 0;
+  tc::Phases tph;
   unsigned pending = 0;
   while (true) {
     if (threadIdx.x == 0) sh.task = serve_pop(sp, pending);
@@ -1213,7 +1277,9 @@ __global__ void __launch_bounds__(NT, 2) hqr_serve(ServeParams sp) {
       for (int q = 0; q < (int)(sizeof(Problem) / 16); ++q) dst[q] = __ldcg(src + q);
     }
     const Geo<Real> g(P);
-    if (t.op == OP_GEQRT || t.op == OP_TSQRT || t.op == OP_TTQRT)
+    if (TC && t.op <= OP_TTMQR && P.tc) {
+      if (!tc_task<Real, TC>(p, g, t, sh, dyn_raw, ts, tph) && threadIdx.x == 0) set_error(p, HQR_ERR_TIMEOUT, tid);
+    } else if (t.op == OP_GEQRT || t.op == OP_TSQRT || t.op == OP_TTQRT)
       task_panel(p, g, t, sh, dyn, phase);
     else if (t.op <= OP_TTMQR)
       task_update(p, g, t, sh, dyn, phase);
@@ -1245,6 +1311,13 @@ __global__ void __launch_bounds__(NT, 2) hqr_serve(ServeParams sp) {
     while (!ptx::mbar_try_wait(&sh.bar, phase) && ptx::globaltimer() - t0 < 1000000000ull) {
     }
   }
+  tc_release<TC>(ts);
+}
+
+// Shared memory (bytes) of the scheduler kernel for tensor-core problems.
+inline size_t engine_smem_bytes_tc() {
+  const size_t vec = (size_t)(2 * NT + 256) * sizeof(double);
+  return std::max<size_t>({(size_t)tc::SMEM_BYTES, (size_t)tc::PANEL_SMEM, vec});
 }
 
 // Shared memory (bytes) of the scheduler kernel for a problem configuration.

@@ -188,22 +188,25 @@ int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long lon
 
 size_t elem_size(int prec) { return prec == HQR_FP64 ? sizeof(double) : sizeof(float); }
 
-// The persistent scheduler instantiation for a storage precision.
-const void *sched_kernel(int prec) {
-  return prec == HQR_FP64 ? (const void *)hqr_sched<double> : (const void *)hqr_sched<float>;
+// The persistent scheduler instantiation for a storage precision (and the
+// tensor-core variant for graphs that hold tensor-core problems).
+const void *sched_kernel(int prec, bool tc) {
+  if (prec == HQR_FP64) return (const void *)hqr_sched<double, false>;
+  return tc ? (const void *)hqr_sched<float, true> : (const void *)hqr_sched<float, false>;
 }
 
 size_t smem_for(int prec, const Problem &P) {
+  if (P.tc) return engine_smem_bytes_tc();
   const int wmax = std::max(P.w, P.wb);
   return prec == HQR_FP64 ? engine_smem_bytes<double>(P.nb, P.ib, wmax, P.wt, P.vc)
                           : engine_smem_bytes<float>(P.nb, P.ib, wmax, P.wt, P.vc);
 }
 
 // CTAs for a launch: every SM filled to the occupancy the kernel allows.
-int ctas_for(int prec, size_t smem, int ntasks, int *grid) {
-  static size_t attr[2] = {0, 0};
-  const void *k = sched_kernel(prec);
-  const int slot = prec == HQR_FP64 ? 0 : 1;
+int ctas_for(int prec, bool tc, size_t smem, int ntasks, int *grid) {
+  static size_t attr[3] = {0, 0, 0};
+  const void *k = sched_kernel(prec, tc);
+  const int slot = prec == HQR_FP64 ? 0 : (tc ? 2 : 1);
   if (attr[slot] < smem) {
     CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr[slot] = smem;
@@ -222,12 +225,14 @@ int ctas_for(int prec, size_t smem, int ntasks, int *grid) {
 
 int launch_sched(int prec, const EngineParams &p, size_t smem, cudaStream_t s) {
   int grid = 0;
-  int st = ctas_for(prec, smem, p.ntasks, &grid);
+  int st = ctas_for(prec, p.tc != 0, smem, p.ntasks, &grid);
   if (st) return st;
   if (prec == HQR_FP64)
-    hqr_sched<double><<<grid, NT, smem, s>>>(p);
+    hqr_sched<double, false><<<grid, NT, smem, s>>>(p);
+  else if (p.tc)
+    hqr_sched<float, true><<<grid, NT, smem, s>>>(p);
   else
-    hqr_sched<float><<<grid, NT, smem, s>>>(p);
+    hqr_sched<float, false><<<grid, NT, smem, s>>>(p);
   CK(cudaGetLastError());
   g_launches += 1;
   return HQR_SUCCESS;
@@ -243,8 +248,28 @@ int g_priority_policy = 1;
 // nothing; FP32 tasks are bound by their barriers and staging, so they take
 // wider slabs (more arithmetic per barrier) within the shared memory of two
 // CTAs per SM.
+bool prec_ok(int prec) { return prec == HQR_FP64 || prec == HQR_FP32 || prec == HQR_FP32_TF32X3; }
+
+// Tiles of this size on the tensor-core kernels (with one full T per tile).
+bool use_tc(int prec, int nb) { return prec == HQR_FP32_TF32X3 && nb == tc::NB; }
+
+// Inner block of the T factors: the tensor-core path keeps one full T.
+int eff_ib(int prec, int nb, int ib) { return use_tc(prec, nb) ? nb : ib; }
+
+// Elements of one T record (the T factor; tensor-core tiles add the split
+// operand images of their updates).
+size_t t_record(int prec, int nb, int ib) { return use_tc(prec, nb) ? (size_t)tc::T_RECORD : (size_t)ib * nb; }
+
 void choose_widths(int prec, int nb, int ib, Problem &P) {
   P.wb = std::min(16, nb);
+  P.tc = use_tc(prec, nb) ? 1 : 0;
+  P.tstr = (int)t_record(prec, nb, ib);
+  if (P.tc) {
+    P.w = tc::WMAX;
+    P.wt = 32;
+    P.vc = 16;
+    return;
+  }
   if (prec == HQR_FP64) {
     P.w = std::min(16, nb);
     P.wt = nb > 128 ? 8 : std::min(16, nb);
@@ -260,6 +285,7 @@ void choose_widths(int prec, int nb, int ib, Problem &P) {
 }
 
 bool valid_tile_sizes(int prec, int nb, int ib) {
+  if (use_tc(prec, nb)) return ib == nb;
   if (nb < 8 || nb > 256 || nb % 8) return false;
   const int align = prec == HQR_FP64 ? 2 : 4;  // rows per 16 bytes
   if (ib < align || ib % align || nb % ib || (ib > 16 && ib != 32)) return false;
@@ -290,7 +316,8 @@ struct hqr_factors {
 namespace {
 
 int run_graph(hqr_factors *F, DevGraph &g, cudaStream_t s) {
-  EngineParams p;
+  EngineParams p{};
+  p.tc = F->prob.tc;
   p.probs = F->dprob;
   p.tasks = g.tasks;
   p.ntasks = g.ntasks;
@@ -398,8 +425,9 @@ int hqr_geqrf(const void *dA, int M, int N, int lda, int prec, int nb, int ib, c
   if (M < 1) return -2;
   if (N < 1 || N > M) return -3;
   if (lda < M) return -4;
-  if (prec != HQR_FP64 && prec != HQR_FP32) return -5;
-  if (nb < 8 || nb > 256 || nb % 8) return -6;
+  if (!prec_ok(prec)) return -5;
+  if (nb < 8 || nb > 256 || nb % 8 || (prec == HQR_FP32_TF32X3 && nb != tc::NB)) return -6;
+  ib = eff_ib(prec, nb, ib);
   if (!valid_tile_sizes(prec, nb, ib)) return -7;
   if (!out) return -10;
   *out = nullptr;
@@ -440,7 +468,7 @@ int hqr_geqrf(const void *dA, int M, int N, int lda, int prec, int nb, int ib, c
   int st = upload_graph(g, F->fg);
   const size_t es = elem_size(prec);
   if (!st) {
-    const size_t tsz = (size_t)F->m * F->n * 2 * ib * nb;
+    const size_t tsz = (size_t)F->m * F->n * 2 * t_record(prec, nb, ib);
     if (!cuda_ok(cudaMalloc(&F->dA, es * (size_t)F->Mp * F->Np), "cudaMalloc(A)") ||
         !cuda_ok(cudaMalloc(&F->dT, es * tsz), "cudaMalloc(T)") ||
         !cuda_ok(cudaMemset(F->dT, 0, es * tsz), "memset(T)"))
@@ -513,8 +541,13 @@ int hqr_get_tiles(const hqr_factors *F, void *dOut, int ld, void *stream) {
 int hqr_get_t(const hqr_factors *F, void *dT, void *stream) {
   if (!F) return -1;
   if (!dT) return -2;
-  const size_t tsz = (size_t)F->m * F->n * 2 * F->ib * F->nb;
-  CK(cudaMemcpyAsync(dT, F->dT, elem_size(F->prec) * tsz, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  const size_t es = elem_size(F->prec), rec = (size_t)F->ib * F->nb;
+  const size_t stride = t_record(F->prec, F->nb, F->ib), nrec = (size_t)F->m * F->n * 2;
+  if (stride == rec)
+    CK(cudaMemcpyAsync(dT, F->dT, es * rec * nrec, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  else  // the T factor is the first part of each record
+    CK(cudaMemcpy2DAsync(dT, es * rec, F->dT, es * stride, es * rec, nrec, cudaMemcpyDeviceToDevice,
+                         (cudaStream_t)stream));
   return HQR_SUCCESS;
 }
 
@@ -746,7 +779,7 @@ int ilog2(int v) {
 hqr_tile_config_t default_config(int M, int N, int prec) {
   hqr_tile_config_t c;
   c.nb = N <= 48 ? 32 : (N <= 192 || M < 1024 ? 64 : 128);
-  c.ib = prec == HQR_FP64 ? std::min(16, c.nb / 2) : 16;
+  c.ib = eff_ib(prec, c.nb, prec == HQR_FP64 ? std::min(16, c.nb / 2) : 16);
   c.a = 4;
   c.p = 1;
   c.low_tree = HQR_GREEDY;
@@ -755,11 +788,19 @@ hqr_tile_config_t default_config(int M, int N, int prec) {
 }
 
 hqr_tile_config_t pick_config(int M, int N, int prec, const hqr_tile_config_t *given) {
-  if (given && given->nb > 0) return *given;
-  const int lm = ilog2(M), ln = ilog2(N);
-  for (const TuneEntry &e : g_tuning)
-    if (e.lm == lm && e.ln == ln) return e.cfg;
-  return default_config(M, N, prec);
+  hqr_tile_config_t c = default_config(M, N, prec);
+  if (given && given->nb > 0) {
+    c = *given;
+  } else {
+    const int lm = ilog2(M), ln = ilog2(N);
+    for (const TuneEntry &e : g_tuning)
+      if (e.lm == lm && e.ln == ln) {
+        c = e.cfg;
+        break;
+      }
+  }
+  c.ib = eff_ib(prec, c.nb, c.ib);
+  return c;
 }
 
 // Per-problem pieces of the preparation and finishing kernels.
@@ -817,6 +858,7 @@ __global__ void ls_finish(const PrepDesc *__restrict__ d, int count) {
 
 struct hqr_ls_plan {
   int count = 0, prec = 0, iters = 0;
+  int any_tc = 0;          // some problem runs on the tensor-core kernels
   std::vector<hqr_tile_config_t> cfg;
   std::vector<Problem> probs;
   std::vector<PrepDesc> prep;
@@ -850,7 +892,8 @@ int plan_enqueue(hqr_ls_plan *P, cudaStream_t s, bool timed) {
   CK(cudaMemcpyAsync(g.indeg, g.indeg0, sizeof(int) * g.ntasks, cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(g.slots, g.slots0, sizeof(int) * slot_count(g.ntasks), cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(g.ctl, g.ctl0, sizeof(Ctl), cudaMemcpyDeviceToDevice, s));
-  EngineParams p;
+  EngineParams p{};
+  p.tc = P->any_tc;
   p.probs = P->dprobs;
   p.tasks = g.tasks;
   p.ntasks = g.ntasks;
@@ -885,7 +928,7 @@ int hqr_ls_plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_
                        int refine_iters, hqr_ls_plan **plan) {
   if (count < 1) return -1;
   if (!probs) return -2;
-  if (prec != HQR_FP64 && prec != HQR_FP32) return -4;
+  if (!prec_ok(prec)) return -4;
   if (refine_iters < 0 || refine_iters > 64) return -5;
   if (!plan) return -6;
   *plan = nullptr;
@@ -929,7 +972,7 @@ int hqr_ls_plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_
     off_tiles[q] = arena_elems;
     arena_elems += (Mp * Np + 3) & ~(size_t)3;
     off_t[q] = arena_elems;
-    arena_elems += ((size_t)pb.m * pb.n * 2 * c.ib * c.nb + 3) & ~(size_t)3;
+    arena_elems += ((size_t)pb.m * pb.n * 2 * t_record(prec, c.nb, c.ib) + 3) & ~(size_t)3;
     off_b[q] = arena_elems;
     arena_elems += (Mp + 3) & ~(size_t)3;
     off_vec[q] = vec_elems;
@@ -945,6 +988,7 @@ int hqr_ls_plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_
     std::vector<PanelOp> ops = expand_ops(lst.data(), lst.size(), pb.m, pb.n);
     append_graph(merged, build_ls_graph(ops, pb.m, pb.n, c.nb, pb.w, refine_iters, q));
     smem = std::max(smem, smem_for(prec, pb));
+    if (pb.tc) P->any_tc = 1;
     P->probs.push_back(pb);
     P->flops += 2.0 * pr.M * (double)pr.N * pr.N - 2.0 / 3.0 * (double)pr.N * pr.N * pr.N;
   }
@@ -1071,7 +1115,7 @@ int hqr_ls_plan_capture(hqr_ls_plan *P, void *stream) {
     P->cg = nullptr;
   }
   int grid = 0;  // sets the kernel's shared-memory attribute outside the capture
-  int st = ctas_for(P->prec, P->smem, P->graph.ntasks, &grid);
+  int st = ctas_for(P->prec, P->any_tc != 0, P->smem, P->graph.ntasks, &grid);
   if (st) return st;
   CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   st = plan_enqueue(P, s, false);
@@ -1165,7 +1209,7 @@ extern "C" int hqr_autotune(int count, const int *Ms, const int *Ns, int prec, i
   if (count < 1) return -1;
   if (!Ms) return -2;
   if (!Ns) return -3;
-  if (prec != HQR_FP64 && prec != HQR_FP32) return -4;
+  if (!prec_ok(prec)) return -4;
   if (reps < 1) return -6;
   if (!nout) return -10;
   cudaStream_t s = (cudaStream_t)stream;
@@ -1213,7 +1257,7 @@ extern "C" int hqr_autotune(int count, const int *Ms, const int *Ns, int prec, i
     std::vector<hqr_tile_config_t> cands;
     for (int nb : {32, 64, 128}) {
       if (nb > 32 && nb / 2 >= N) continue;  // no tile much wider than the matrix
-      const int ib = 16;
+      const int ib = eff_ib(prec, nb, 16);
       const int mtiles = (M + nb - 1) / nb;
       for (int a : {1, 4, 16}) {
         if (a > 1 && a >= 2 * mtiles) continue;
@@ -1377,7 +1421,8 @@ void server_release(hqr_server *S) {
 size_t server_smem(int prec) {
   size_t m = 0;
   for (int nb : {32, 64, 128})
-    for (int ib : {8, 16, 32}) {
+    for (int ib0 : {8, 16, 32}) {
+      const int ib = eff_ib(prec, nb, ib0);
       if (!valid_tile_sizes(prec, nb, ib)) continue;
       Problem pb{};
       pb.nb = nb;
@@ -1397,7 +1442,7 @@ int hqr_server_create(const hqr_server_opts *o, hqr_server **out) {
   if (!o) return -1;
   if (!out) return -2;
   *out = nullptr;
-  if (o->prec != HQR_FP64 && o->prec != HQR_FP32) return -1;
+  if (!prec_ok(o->prec)) return -1;
   if (o->refine_iters < 0 || o->max_live < 1 || o->task_pool < 1024 || o->edge_pool < 1024 || o->hbm_budget < 1)
     return -1;
   hqr_server *S = new (std::nothrow) hqr_server();
@@ -1454,7 +1499,8 @@ int server_ensure_running(hqr_server *S);
 int hqr_server_start(hqr_server *S) {
   if (!S) return -1;
   if (S->running && cudaStreamQuery(S->kstream) == cudaErrorNotReady) return HQR_SUCCESS;
-  ServeParams sp;
+  ServeParams sp{};
+  sp.e.tc = S->o.prec == HQR_FP32_TF32X3;
   sp.e.probs = S->probs;
   sp.e.tasks = S->tasks;
   sp.e.ntasks = (int)S->o.task_pool;
@@ -1473,7 +1519,10 @@ int hqr_server_start(hqr_server *S) {
   sp.req_seq = S->req_seq;
   sp.comp = S->comp_dev;
   sp.ring_cap = S->ring_cap;
-  const void *k = S->o.prec == HQR_FP64 ? (const void *)hqr_serve<double> : (const void *)hqr_serve<float>;
+  const bool tcs = S->o.prec == HQR_FP32_TF32X3;
+  const void *k = S->o.prec == HQR_FP64
+                      ? (const void *)hqr_serve<double, false>
+                      : (tcs ? (const void *)hqr_serve<float, true> : (const void *)hqr_serve<float, false>);
   int dev = 0, sms = 0, per_sm = 0;
   CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem));
   CK(cudaGetDevice(&dev));
@@ -1482,9 +1531,11 @@ int hqr_server_start(hqr_server *S) {
   if (per_sm < 1) return HQR_ERR_CUDA;
   CK(cudaStreamSynchronize(S->cstream));
   if (S->o.prec == HQR_FP64)
-    hqr_serve<double><<<sms * per_sm, NT, S->smem, S->kstream>>>(sp);
+    hqr_serve<double, false><<<sms * per_sm, NT, S->smem, S->kstream>>>(sp);
+  else if (tcs)
+    hqr_serve<float, true><<<sms * per_sm, NT, S->smem, S->kstream>>>(sp);
   else
-    hqr_serve<float><<<sms * per_sm, NT, S->smem, S->kstream>>>(sp);
+    hqr_serve<float, false><<<sms * per_sm, NT, S->smem, S->kstream>>>(sp);
   CK(cudaGetLastError());
   S->running = true;
   return HQR_SUCCESS;
@@ -1541,7 +1592,7 @@ int hqr_server_submit(hqr_server *S, const hqr_ls_problem_t *pr, int64_t *ticket
   const size_t nt = cg.g.tasks.size(), ne = std::max<size_t>(cg.g.succ.size(), 1);
   const size_t Mp = (size_t)pb.m * c.nb, Np = (size_t)pb.n * c.nb, es = S->es;
   auto r256 = [](size_t b) { return (b + 255) / 256; };
-  const size_t a_tiles = r256(es * Mp * Np), a_t = r256(es * (size_t)pb.m * pb.n * 2 * c.ib * c.nb),
+  const size_t a_tiles = r256(es * Mp * Np), a_t = r256(es * (size_t)pb.m * pb.n * 2 * t_record(prec, c.nb, c.ib)),
                a_b = r256(es * Mp), a_r = r256(8 * Mp), a_g = r256(8 * Np),
                a_gp = r256(16 * (size_t)atr_chunks(pb.m) * Np), a_rp = r256(16 * (size_t)res_chunks(pb.n) * Mp),
                a_ri = r256(8 * (size_t)pb.n * c.nb * c.nb);
@@ -2018,7 +2069,7 @@ extern "C" int hqr_geqrf_r_noalloc(const void *dA, int M, int N, int lda, int nb
     return HQR_ERR_CUDA;
   const long long total = (long long)m * nb * n * nb;
   pack_tiles<double><<<grid_for(total), 256, 0, s>>>((const double *)dA, lda, M, N, (double *)dws, m, nb, total);
-  EngineParams p;
+  EngineParams p{};
   p.probs = dprob;
   p.trace = nullptr;
   p.tasks = dtasks;
@@ -2030,13 +2081,13 @@ extern "C" int hqr_geqrf_r_noalloc(const void *dA, int M, int N, int lda, int nb
   p.timeout_ns = g_timeout_ns;
   const size_t smem = engine_smem_bytes<double>(nb, ib, w, wt, vc);
   int sms = 0, per_sm = 0;
-  if (cudaFuncSetAttribute(hqr_sched<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+  if (cudaFuncSetAttribute(hqr_sched<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
           cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hqr_sched<double>, NT, smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hqr_sched<double, false>, NT, smem) != cudaSuccess ||
       per_sm < 1)
     return HQR_ERR_CUDA;
-  hqr_sched<double><<<std::max(1, std::min(sms * per_sm, nt)), NT, smem, s>>>(p);
+  hqr_sched<double, false><<<std::max(1, std::min(sms * per_sm, nt)), NT, smem, s>>>(p);
   unpack_tiles<double><<<grid_for((long long)N * N), 256, 0, s>>>((const double *)dws, m, nb, (double *)dR, ldr, N,
                                                                  N, 1);
   if (cudaGetLastError() != cudaSuccess) return HQR_ERR_CUDA;

@@ -19,7 +19,7 @@ from . import _build
 FLAT, BINARY, GREEDY, FIBONACCI = 0, 1, 2, 3
 TREES = {"flat": FLAT, "binary": BINARY, "greedy": GREEDY, "fibonacci": FIBONACCI}
 TS, TT = 0, 1
-FP64, FP32 = 0, 1
+FP64, FP32, FP32_TF32X3 = 0, 1, 2
 
 (SUCCESS, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_CAPACITY, ERR_INVALID_LIST, ERR_SINGULAR, ERR_INTERNAL,
  ERR_TOO_LARGE, ERR_BUSY, ERR_BUDGET) = range(11)
@@ -191,13 +191,23 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def prec_of(A):
+def prec_of(A, tensor=False):
+    """Library precision of a matrix: FP64 for float64; for float32, FP32
+    (CUDA-core arithmetic) or, with tensor=True, FP32_TF32X3 (tensor-core
+    updates on tiles of 128)."""
     torch = _torch()
     if A.dtype == torch.float64:
         return FP64
     if A.dtype == torch.float32:
-        return FP32
+        return FP32_TF32X3 if tensor else FP32
     raise TypeError("expected a float64 or float32 CUDA tensor")
+
+
+def _prec_dtype(dtype, tensor):
+    torch = _torch()
+    if dtype == torch.float64:
+        return FP64
+    return FP32_TF32X3 if tensor else FP32
 
 
 def colmajor(A):
@@ -323,21 +333,22 @@ def _list_arg(records):
     return ctypes.c_void_p(arr.ctypes.data), len(arr), arr
 
 
-def geqrf(A, nb, ib, records=None, stream=None):
-    """Tile QR of a float64 CUDA matrix with the given elimination list
-    (None = library default). Returns a Factors object."""
+def geqrf(A, nb, ib, records=None, stream=None, tensor=False):
+    """Tile QR of a float64 / float32 CUDA matrix with the given elimination
+    list (None = library default). tensor=True (float32, nb = 128) runs the
+    updates on the tensor cores. Returns a Factors object."""
     A, lda = colmajor(A)
     M, N = A.shape
     ptr, cnt, keep = _list_arg(records)
     h = ctypes.c_void_p(0)
-    st = load().hqr_geqrf(ctypes.c_void_p(A.data_ptr()), M, N, lda, prec_of(A), nb, ib, ptr, cnt,
+    st = load().hqr_geqrf(ctypes.c_void_p(A.data_ptr()), M, N, lda, prec_of(A, tensor), nb, ib, ptr, cnt,
                           ctypes.byref(h), _stream_ptr(stream))
     del keep
     _check(st, "hqr_geqrf")
     return Factors(h, M, N, A.dtype)
 
 
-def gels(A, b, nb, ib, records=None, stream=None):
+def gels(A, b, nb, ib, records=None, stream=None, tensor=False):
     """Least-squares solution x of min ||b - A x|| (b: M or M x nrhs)."""
     A, lda = colmajor(A)
     M, N = A.shape
@@ -347,7 +358,8 @@ def gels(A, b, nb, ib, records=None, stream=None):
     x = empty_colmajor(N, nrhs, dtype=A.dtype)
     ptr, cnt, keep = _list_arg(records)
     st = load().hqr_gels(ctypes.c_void_p(A.data_ptr()), M, N, lda, ctypes.c_void_p(bc.data_ptr()), ldb, nrhs,
-                         ctypes.c_void_p(x.data_ptr()), N, prec_of(A), nb, ib, ptr, cnt, _stream_ptr(stream))
+                         ctypes.c_void_p(x.data_ptr()), N, prec_of(A, tensor), nb, ib, ptr, cnt,
+                         _stream_ptr(stream))
     del keep
     _check(st, "hqr_gels")
     return x[:, 0] if vec else x
@@ -391,9 +403,10 @@ class LSPlan:
     """Many least-squares problems solved by one persistent launch (see
     hqr_ls_plan_create). `problems` is a list of (A, b, x) CUDA tensors: A
     column-major M x N (float32 or float64, all the same), b float64 (M),
-    x float64 (N, written by run())."""
+    x float64 (N, written by run()). tensor=True (float32) runs tiles of
+    128 on the tensor cores."""
 
-    def __init__(self, problems, refine_iters, configs=None):
+    def __init__(self, problems, refine_iters, configs=None, tensor=False):
         torch = _torch()
         self._keep = []
         arr = (LSProblem * len(problems))()
@@ -414,7 +427,7 @@ class LSPlan:
             cfg = (TileConfig * len(problems))(*configs)
         h = ctypes.c_void_p(0)
         st = load().hqr_ls_plan_create(len(problems), ctypes.byref(arr), ctypes.byref(cfg) if cfg else None,
-                                       prec_of(self._keep[0]), int(refine_iters), ctypes.byref(h))
+                                       prec_of(self._keep[0], tensor), int(refine_iters), ctypes.byref(h))
         _check(st, "hqr_ls_plan_create")
         self._h = h
         self.count = len(problems)
@@ -473,7 +486,7 @@ def set_tuning(table):
     _check(load().hqr_set_tuning(len(table), keys, cfgs), "hqr_set_tuning")
 
 
-def autotune(shapes, dtype, refine_iters, reps=32, stream=None):
+def autotune(shapes, dtype, refine_iters, reps=32, stream=None, tensor=False):
     """Run the library's measured autotuner over the shape classes of
     `shapes` [(M, N), ...]; installs and returns the table
     {(log2 M, log2 N): (nb, ib, a, p, low, high)}."""
@@ -484,8 +497,7 @@ def autotune(shapes, dtype, refine_iters, reps=32, stream=None):
     keys = (ctypes.c_int * (2 * cap))()
     cfgs = (TileConfig * cap)()
     nout = ctypes.c_int(0)
-    torch = _torch()
-    prec = FP64 if dtype == torch.float64 else FP32
+    prec = _prec_dtype(dtype, tensor)
     _check(load().hqr_autotune(n, Ms, Ns, prec, int(refine_iters), int(reps), keys, cfgs, cap, ctypes.byref(nout),
                                _stream_ptr(stream)), "hqr_autotune")
     return {(keys[2 * e], keys[2 * e + 1]): cfgs[e].as_tuple() for e in range(nout.value)}
@@ -503,9 +515,8 @@ class Server:
     returns a ticket, or None when the request does not fit right now."""
 
     def __init__(self, dtype, refine_iters, max_live=1024, hbm_budget=8 << 30, task_pool=8 << 20,
-                 edge_pool=32 << 20):
-        torch = _torch()
-        prec = FP64 if dtype == torch.float64 else FP32
+                 edge_pool=32 << 20, tensor=False):
+        prec = _prec_dtype(dtype, tensor)
         o = ServerOpts(prec, int(refine_iters), int(max_live), int(hbm_budget), int(task_pool), int(edge_pool))
         h = ctypes.c_void_p(0)
         _check(load().hqr_server_create(ctypes.byref(o), ctypes.byref(h)), "hqr_server_create")
