@@ -67,7 +67,7 @@ def oracle_batched(b, sample=8):
 
     from oracle.lstsq import lstsq_unblocked
     shapes, data = b["_data"]
-    errs = {"mixed": [], "fp64": []}
+    errs = {"mixed_tc": [], "mixed": [], "fp64": []}
     t0 = time.perf_counter()
     for q in range(sample):
         A = data[q][0].double().cpu().numpy()
@@ -213,15 +213,18 @@ def batched(torch, hqr, dev, count=1024, refine=4, tune=True):
     g.manual_seed(1234)
     data = [(torch.randn((n, m), dtype=torch.float32, device=dev, generator=g).t(),
              torch.randn(m, dtype=torch.float64, device=dev, generator=g)) for (m, n) in shapes]
-    for label, dtype, iters in (("mixed", torch.float32, refine), ("fp64", torch.float64, 0)):
+    variants = (("mixed_tc", torch.float32, refine, True), ("mixed", torch.float32, refine, False),
+                ("fp64", torch.float64, 0, False))
+    for label, dtype, iters, tensor in variants:
         if tune:
             t0 = time.perf_counter()
-            table = hqr.autotune(shapes, dtype, iters, reps=24)
+            table = hqr.autotune(shapes, dtype, iters, reps=24, tensor=tensor)
             out[label + "_autotune_s"] = time.perf_counter() - t0
             out[label + "_autotune_classes"] = len(table)
+            out[label + "_tiles_128"] = sum(1 for c in table.values() if c[0] == 128)
         probs = [(A if dtype == torch.float32 else A.double().t().contiguous().t(), b,
                   torch.zeros(n, dtype=torch.float64, device=dev)) for (A, b), (m, n) in zip(data, shapes)]
-        plan = hqr.LSPlan(probs, refine_iters=iters)
+        plan = hqr.LSPlan(probs, refine_iters=iters, tensor=tensor)
         s = torch.cuda.Stream(dev)
         plan.capture(s)
         for _ in range(2):
@@ -239,10 +242,12 @@ def batched(torch, hqr, dev, count=1024, refine=4, tune=True):
         info = plan.info()
         out[label] = {"solves_per_s": count / (ms * 1e-3), "ms_per_batch": ms,
                       "qr_tflops": info["qr_flops"] / (ms * 1e-3) / 1e12, "tasks": info["tasks"],
-                      "refine_iters": iters, "status": st, "launches_per_batch": 3, "cuda_graph": True}
+                      "refine_iters": iters, "status": st, "launches_per_batch": 3, "cuda_graph": True,
+                      "tensor_cores": tensor}
         out["_x_" + label] = [p[2] for p in probs[:8]]
         hqr.set_tuning({})
     out["mixed_over_fp64"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    out["mixed_tc_over_fp64"] = out["mixed_tc"]["solves_per_s"] / out["fp64"]["solves_per_s"]
     out["_data"] = (shapes, data)
     return out
 
@@ -269,11 +274,12 @@ def serving(torch, hqr, dev, rate=2000.0, seconds=5.0, refine=5):
     idx = rng.integers(0, 1 << 30, size=n_req)
     out = {"workload": "serving_poisson_%d_per_s_%gs_90pct_uneven_10pct_32768x1024_kappa1e4" % (rate, seconds),
            "offered_per_s": rate, "requests": n_req}
-    for label, dtype, iters in (("mixed", torch.float32, refine), ("fp64", torch.float64, 0)):
+    for label, dtype, iters, tensor in (("mixed_tc", torch.float32, refine, True),
+                                        ("fp64", torch.float64, 0, False)):
         pool_s = small if dtype == torch.float32 else [(A.double().t().contiguous().t(), b) for A, b in small]
         pool_l = large if dtype == torch.float32 else [(A.double().t().contiguous().t(), b) for A, b in large]
         srv = hqr.Server(dtype, refine_iters=iters, max_live=2048, hbm_budget=120 << 30,
-                         task_pool=16 << 20, edge_pool=64 << 20)
+                         task_pool=16 << 20, edge_pool=64 << 20, tensor=tensor)
         srv.start()
         lat, inflight, queue = [], {}, deque()
         t0 = time.perf_counter()
@@ -307,14 +313,15 @@ def serving(torch, hqr, dev, rate=2000.0, seconds=5.0, refine=5):
                       "solves_per_s": len(lat) / wall, "wall_s": wall,
                       "p50_ms": 1e3 * lat[len(lat) // 2] if lat else None,
                       "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None,
-                      "refine_iters": iters}
+                      "refine_iters": iters, "tensor_cores": tensor}
         del srv
     return out
 
 
 def square_mixed(torch, hqr, dev, n=16384, refine=24):
     """16384^2 FP32 least squares, A = U diag(s) V^T, s geometric 1 .. 1e-6,
-    b = A x_true + 1e-8 N(0,1): FP32 tile QR + FP64 CSNE."""
+    b = A x_true + 1e-8 N(0,1): FP32 tile QR with tensor-core updates
+    (BF16x3) + FP64 CSNE."""
     from paper_1110_1553_gb300 import workloads
     A = workloads.conditioned(torch, n, n, 1e6, seed=30, device=dev)
     g = torch.Generator(device=dev)
@@ -322,8 +329,8 @@ def square_mixed(torch, hqr, dev, n=16384, refine=24):
     xt = torch.randn(n, dtype=torch.float64, device=dev, generator=g)
     b = A.double() @ xt + 1e-8 * torch.randn(n, dtype=torch.float64, device=dev, generator=g)
     x = torch.zeros(n, dtype=torch.float64, device=dev)
-    cfg = [hqr.tile_config(128, 16, 4, 1, "greedy", "greedy")]
-    plan = hqr.LSPlan([(A, b, x)], refine_iters=refine, configs=cfg)
+    cfg = [hqr.tile_config(128, 128, 16, 1, "greedy", "greedy")]
+    plan = hqr.LSPlan([(A, b, x)], refine_iters=refine, configs=cfg, tensor=True)
     plan.run()
     plan.status()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

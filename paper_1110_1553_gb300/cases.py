@@ -1,0 +1,73 @@
+"""Named single runs of the library's workloads, for profilers and quick
+checks: each builds its seeded synthetic input, runs the operation once
+(after one untimed run unless --once), prints one line and exits 0.
+
+    python -m paper_1110_1553_gb300.cases fp64_tall_skinny --rows 16384
+    python -m paper_1110_1553_gb300.cases fp32_tc_square --n 6144
+    python -m paper_1110_1553_gb300.cases fp32_tc_ls --n 4096 --iters 16
+
+Cases:
+  fp64_tall_skinny  FP64 HQR of rows x 2048 (nb 256, ib 32, a 4, p 16,
+                    greedy / Fibonacci), the benchmark's configuration
+  fp32_tc_square    FP32 tile QR of n x n on the tensor-core kernels
+                    (nb 128, a 16, greedy / greedy)
+  fp32_cc_square    the same on the CUDA-core FP32 kernels (ib 16)
+  fp32_tc_ls        least squares n x n, kappa 1e6, tensor-core QR + FP64
+                    corrected semi-normal-equation refinement
+"""
+import argparse
+import time
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["fp64_tall_skinny", "fp32_tc_square", "fp32_cc_square", "fp32_tc_ls"])
+    ap.add_argument("--rows", type=int, default=131072)
+    ap.add_argument("--n", type=int, default=6144)
+    ap.add_argument("--iters", type=int, default=16)
+    ap.add_argument("--once", action="store_true", help="no untimed first run")
+    a = ap.parse_args(argv)
+    import torch
+
+    from paper_1110_1553_gb300 import _build, hqr, inputs, workloads
+    _build.build()
+    hqr.load()
+    dev = torch.device("cuda", 0)
+    runs = 1 if a.once else 2
+    t0 = time.perf_counter()
+    if a.case == "fp64_tall_skinny":
+        M, N, nb = a.rows, 2048, 256
+        A = inputs.gaussian_torch(M, N, seed=1, device=dev)
+        recs = hqr.elim_list(M // nb, N // nb, 4, 16, "greedy", "fibonacci")
+        F = hqr.geqrf(A, nb, 32, recs)
+        for _ in range(runs - 1):
+            F.refactor(A)
+        info = "kernel %.2f ms" % F.kernel_ms()
+    elif a.case in ("fp32_tc_square", "fp32_cc_square"):
+        n, tensor = a.n, a.case == "fp32_tc_square"
+        g = torch.Generator(device=dev)
+        g.manual_seed(3)
+        A = torch.randn((n, n), dtype=torch.float32, device=dev, generator=g).t()
+        recs = hqr.elim_list(n // 128, n // 128, 16, 1, "greedy", "greedy")
+        F = hqr.geqrf(A, 128, 128 if tensor else 16, recs, tensor=tensor)
+        for _ in range(runs - 1):
+            F.refactor(A)
+        info = "kernel %.2f ms" % F.kernel_ms()
+    else:
+        n = a.n
+        A = workloads.conditioned(torch, n, n, 1e6, seed=30, device=dev)
+        b = A.double() @ torch.ones(n, dtype=torch.float64, device=dev)
+        x = torch.zeros(n, dtype=torch.float64, device=dev)
+        plan = hqr.LSPlan([(A, b, x)], refine_iters=a.iters, configs=[hqr.tile_config(128, 128, 16, 1)],
+                          tensor=True)
+        for _ in range(runs):
+            plan.run()
+        st = plan.status()
+        info = "status %d, |x - 1|_max %.2e" % (st, (x - 1).abs().max().item())
+    torch.cuda.synchronize()
+    print("%s: %s (%.2f s)" % (a.case, info, time.perf_counter() - t0))
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())
