@@ -61,13 +61,14 @@ typedef struct {
 /* Arithmetic of the factorization. HQR_FP64: FP64 storage and arithmetic
  * everywhere (the paper's setting, Sec. 5.1). HQR_FP32: FP32 storage and
  * FP32 arithmetic (panel norms with a scaled second pass on under- or
- * overflow); device buffers passed with it hold float. HQR_FP32_TF32X3:
+ * overflow); device buffers passed with it hold float. HQR_FP32_BF16X3:
  * FP32 storage; tiles of nb = 128 run the updates (UNMQR, TSMQR, TTMQR) on
- * the tensor cores as tf32 products split three ways (hi*hi + hi*lo +
- * lo*hi, FP32 accumulation, about FP32 accuracy) with one full 128 x 128 T
- * per tile (ib is taken as nb); other tile sizes fall back to HQR_FP32
- * arithmetic. hqr_geqrf requires nb = 128 with it. */
-typedef enum { HQR_FP64 = 0, HQR_FP32 = 1, HQR_FP32_TF32X3 = 2 } hqr_prec_t;
+ * the tensor cores (tcgen05) with every FP32 operand split into three BF16
+ * pieces (six BF16 products per step, FP32 accumulation: about FP32
+ * accuracy) and one full 128 x 128 T per tile (ib is taken as nb); other
+ * tile sizes fall back to HQR_FP32 arithmetic. hqr_geqrf requires nb = 128
+ * with it. */
+typedef enum { HQR_FP64 = 0, HQR_FP32 = 1, HQR_FP32_BF16X3 = 2 } hqr_prec_t;
 
 enum {
   HQR_SUCCESS = 0,
@@ -359,7 +360,7 @@ int hqr_autotune(int count, const int *Ms, const int *Ns, int prec, int refine_i
  * completes. Completion is published in host-mapped memory.
  * ------------------------------------------------------------------------ */
 typedef struct {
-  int prec;            /* HQR_FP32 (mixed precision) or HQR_FP64 */
+  int prec;            /* HQR_FP32 or HQR_FP32_BF16X3 (mixed precision), or HQR_FP64 */
   int refine_iters;    /* as in hqr_ls_plan_create */
   int max_live;        /* requests in flight at most */
   size_t hbm_budget;   /* bytes of request workspace (tiles, T, vectors) */

@@ -248,10 +248,10 @@ int g_priority_policy = 1;
 // nothing; FP32 tasks are bound by their barriers and staging, so they take
 // wider slabs (more arithmetic per barrier) within the shared memory of two
 // CTAs per SM.
-bool prec_ok(int prec) { return prec == HQR_FP64 || prec == HQR_FP32 || prec == HQR_FP32_TF32X3; }
+bool prec_ok(int prec) { return prec == HQR_FP64 || prec == HQR_FP32 || prec == HQR_FP32_BF16X3; }
 
 // Tiles of this size on the tensor-core kernels (with one full T per tile).
-bool use_tc(int prec, int nb) { return prec == HQR_FP32_TF32X3 && nb == tc::NB; }
+bool use_tc(int prec, int nb) { return prec == HQR_FP32_BF16X3 && nb == tc::NB; }
 
 // Inner block of the T factors: the tensor-core path keeps one full T.
 int eff_ib(int prec, int nb, int ib) { return use_tc(prec, nb) ? nb : ib; }
@@ -426,7 +426,7 @@ int hqr_geqrf(const void *dA, int M, int N, int lda, int prec, int nb, int ib, c
   if (N < 1 || N > M) return -3;
   if (lda < M) return -4;
   if (!prec_ok(prec)) return -5;
-  if (nb < 8 || nb > 256 || nb % 8 || (prec == HQR_FP32_TF32X3 && nb != tc::NB)) return -6;
+  if (nb < 8 || nb > 256 || nb % 8 || (prec == HQR_FP32_BF16X3 && nb != tc::NB)) return -6;
   ib = eff_ib(prec, nb, ib);
   if (!valid_tile_sizes(prec, nb, ib)) return -7;
   if (!out) return -10;
@@ -1500,7 +1500,7 @@ int hqr_server_start(hqr_server *S) {
   if (!S) return -1;
   if (S->running && cudaStreamQuery(S->kstream) == cudaErrorNotReady) return HQR_SUCCESS;
   ServeParams sp{};
-  sp.e.tc = S->o.prec == HQR_FP32_TF32X3;
+  sp.e.tc = S->o.prec == HQR_FP32_BF16X3;
   sp.e.probs = S->probs;
   sp.e.tasks = S->tasks;
   sp.e.ntasks = (int)S->o.task_pool;
@@ -1519,7 +1519,7 @@ int hqr_server_start(hqr_server *S) {
   sp.req_seq = S->req_seq;
   sp.comp = S->comp_dev;
   sp.ring_cap = S->ring_cap;
-  const bool tcs = S->o.prec == HQR_FP32_TF32X3;
+  const bool tcs = S->o.prec == HQR_FP32_BF16X3;
   const void *k = S->o.prec == HQR_FP64
                       ? (const void *)hqr_serve<double, false>
                       : (tcs ? (const void *)hqr_serve<float, true> : (const void *)hqr_serve<float, false>);

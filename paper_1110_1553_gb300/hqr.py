@@ -19,7 +19,7 @@ from . import _build
 FLAT, BINARY, GREEDY, FIBONACCI = 0, 1, 2, 3
 TREES = {"flat": FLAT, "binary": BINARY, "greedy": GREEDY, "fibonacci": FIBONACCI}
 TS, TT = 0, 1
-FP64, FP32, FP32_TF32X3 = 0, 1, 2
+FP64, FP32, FP32_BF16X3 = 0, 1, 2
 
 (SUCCESS, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_CAPACITY, ERR_INVALID_LIST, ERR_SINGULAR, ERR_INTERNAL,
  ERR_TOO_LARGE, ERR_BUSY, ERR_BUDGET) = range(11)
@@ -193,13 +193,13 @@ def _stream_ptr(stream):
 
 def prec_of(A, tensor=False):
     """Library precision of a matrix: FP64 for float64; for float32, FP32
-    (CUDA-core arithmetic) or, with tensor=True, FP32_TF32X3 (tensor-core
+    (CUDA-core arithmetic) or, with tensor=True, FP32_BF16X3 (tensor-core
     updates on tiles of 128)."""
     torch = _torch()
     if A.dtype == torch.float64:
         return FP64
     if A.dtype == torch.float32:
-        return FP32_TF32X3 if tensor else FP32
+        return FP32_BF16X3 if tensor else FP32
     raise TypeError("expected a float64 or float32 CUDA tensor")
 
 
@@ -207,7 +207,7 @@ def _prec_dtype(dtype, tensor):
     torch = _torch()
     if dtype == torch.float64:
         return FP64
-    return FP32_TF32X3 if tensor else FP32
+    return FP32_BF16X3 if tensor else FP32
 
 
 def colmajor(A):

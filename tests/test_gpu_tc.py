@@ -1,4 +1,4 @@
-"""GPU parity of the tensor-core FP32 path (HQR_FP32_TF32X3: tiles of 128,
+"""GPU parity of the tensor-core FP32 path (HQR_FP32_BF16X3: tiles of 128,
 register-resident unblocked panels with one full T per tile, tcgen05
 updates on BF16x3-split operands) against the FP64 oracle run on the same
 float-rounded input, with the same elimination list.
