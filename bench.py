@@ -318,7 +318,7 @@ def serving(torch, hqr, dev, rate=2000.0, seconds=5.0, refine=5):
     return out
 
 
-def square_mixed(torch, hqr, dev, n=16384, refine=24):
+def square_mixed(torch, hqr, dev, n=16384, refine=20):
     """16384^2 FP32 least squares, A = U diag(s) V^T, s geometric 1 .. 1e-6,
     b = A x_true + 1e-8 N(0,1): FP32 tile QR with tensor-core updates
     (BF16x3) + FP64 CSNE."""

@@ -358,12 +358,18 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
     }
     solve_r(false);
   }
+  // Residuals and A^T r of the last rounds are compensated (Dot2); the earlier rounds, whose
+  // corrections are still far above the FP64 rounding level, use plain FP64 sums (1 FMA per
+  // element instead of ~10 FP64 operations). Vector tasks carry the choice in `tgt`.
+  const int ncomp = std::min(iters, std::max(4, (2 * iters + 4) / 5));
   for (int it = 0; it < iters; ++it) {
+    const int comp = it >= iters - ncomp ? 1 : 0;
+    auto rtask = [&](int op, int i, int j) { return make_task(op, 1, i, i, 0, j, 0, 0, 1, comp, pid); };
     for (int i = 0; i < m; ++i) {
       for (int c = 0; c < nrc; ++c) {
         for (int j = c * kResChunk; j < std::min(n, (c + 1) * kResChunk); ++j) tr.read(xres(j), d);
         tr.write(qres(i, c), d);
-        b.add(vtask(OP_RESID, i, c));
+        b.add(rtask(OP_RESID, i, c));
       }
       for (int c = 0; c < nrc; ++c) tr.read(qres(i, c), d);
       tr.write(rres(i), d);
@@ -373,7 +379,7 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
       for (int c = 0; c < nch; ++c) {
         for (int i = c * kAtrChunk; i < std::min(m, (c + 1) * kAtrChunk); ++i) tr.read(rres(i), d);
         tr.write(pres(c, j), d);
-        b.add(vtask(OP_ATR, c, j));
+        b.add(rtask(OP_ATR, c, j));
       }
       for (int c = 0; c < nch; ++c) tr.read(pres(c, j), d);
       tr.write(gres(j), d);
@@ -387,7 +393,10 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
 void critical_path_priorities(Graph &g, int nb) {
   const size_t nt = g.tasks.size();
   if (nt == 0) return;
-  // estimated cost in units of b^3/3 (Sec. 2 weights), updates scaled by slab width
+  // estimated cost in units of b^3/3 (Sec. 2 weights), updates scaled by slab width; the FP64
+  // vector tasks of least-squares graphs by their relative durations (a compensated residual or
+  // A^T r chunk costs about a GEQRT, a plain one a fifth of it, a triangular-solve step a few
+  // percent), so that the solve chains keep their place ahead of the next round's residuals
   auto cost = [&](const Task &t) {
     const double slab = t.cw > 0 ? (double)t.cw / nb : 1.0;
     switch (t.op) {
@@ -397,7 +406,14 @@ void critical_path_priorities(Graph &g, int nb) {
       case OP_UNMQR: return 6.0 * slab;
       case OP_TSMQR: return 12.0 * slab;
       case OP_TTMQR: return 6.0 * slab;
-      default: return 0.5;
+      case OP_RESID:
+      case OP_ATR: return t.tgt ? 3.5 : 0.7;
+      case OP_TRINV: return 12.0;
+      case OP_TRSV_TD:
+      case OP_TRSV_TU:
+      case OP_TRSV_D:
+      case OP_TRSV_U: return 0.2;
+      default: return 0.1;
     }
   };
   std::vector<double> bl(nt, 0.0);
@@ -405,6 +421,12 @@ void critical_path_priorities(Graph &g, int nb) {
     double best = 0.0;
     for (int32_t e = g.tasks[q].succ_begin; e < g.tasks[q].succ_end; ++e) best = std::max(best, bl[g.succ[e]]);
     bl[q] = cost(g.tasks[q]) + best;
+  }
+  // successors in decreasing bottom level: the most critical ones are released first
+  for (size_t q = 0; q < nt; ++q) {
+    const Task &t = g.tasks[q];
+    std::stable_sort(g.succ.begin() + t.succ_begin, g.succ.begin() + t.succ_end,
+                     [&](int32_t a, int32_t b) { return bl[a] > bl[b]; });
   }
   std::vector<double> sorted(bl);
   std::sort(sorted.begin(), sorted.end());

@@ -754,6 +754,28 @@ __device__ __forceinline__ void dot2_merge(double &s1, double &c1, double s2, do
   c1 += c2 + e;
 }
 
+// sum over q = q0, q0 + step, ... < q1 of M(q, o) g_q (transposed) or M(o, q) g_q, M column-major
+// with leading dimension ld, in FP64 with four independent chains. M is final for the whole launch
+// (R tiles after their factorization, the inverses after their TRINV task), so its loads may use L1.
+template <typename M>
+__device__ __forceinline__ double tile_dot(const M *__restrict__ m, int ld, bool transposed, int o, int q0, int q1,
+                                           int step, const double *g) {
+  const M *base = transposed ? m + (size_t)o * ld : m + o;
+  const size_t qs = transposed ? 1 : (size_t)ld;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int q = q0;
+  for (; q + 3 * step < q1; q += 4 * step) {
+    const double m0 = (double)base[q * qs], m1 = (double)base[(q + step) * qs];
+    const double m2 = (double)base[(q + 2 * step) * qs], m3 = (double)base[(q + 3 * step) * qs];
+    a0 = fma(m0, g[q], a0);
+    a1 = fma(m1, g[q + step], a1);
+    a2 = fma(m2, g[q + 2 * step], a2);
+    a3 = fma(m3, g[q + 3 * step], a3);
+  }
+  for (; q < q1; q += step) a0 = fma((double)base[q * qs], g[q], a0);
+  return (a0 + a1) + (a2 + a3);
+}
+
 template <typename Real>
 __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<Real> &g, const Task &t,
                             double *sm) {
@@ -766,10 +788,37 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
       const int G = NT / nb;  // column groups
       const int rr = tid % nb, gi = tid / nb;
       double s = 0.0, c = 0.0;
-      if (rr < nr && gi < G) {
+      if (rr < nr && gi < G && !t.tgt) {  // plain FP64 round: four independent FMA chains
         const Real *arow = A0 + r0 + rr;
-        for (int j = clo + gi; j < chi; j += G)
-          dot2_step((double)__ldcg(arow + (long long)j * P.lda0), __ldcg(P.x + j), s, c);
+        double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int j = clo + gi;
+        for (; j + 3 * G < chi; j += 4 * G) {
+          s = fma((double)__ldcg(arow + (long long)j * P.lda0), __ldcg(P.x + j), s);
+          s1 = fma((double)__ldcg(arow + (long long)(j + G) * P.lda0), __ldcg(P.x + j + G), s1);
+          s2 = fma((double)__ldcg(arow + (long long)(j + 2 * G) * P.lda0), __ldcg(P.x + j + 2 * G), s2);
+          s3 = fma((double)__ldcg(arow + (long long)(j + 3 * G) * P.lda0), __ldcg(P.x + j + 3 * G), s3);
+        }
+        for (; j < chi; j += G) s = fma((double)__ldcg(arow + (long long)j * P.lda0), __ldcg(P.x + j), s);
+        s = (s + s1) + (s2 + s3);
+      } else if (rr < nr && gi < G) {
+        // four independent compensated sums (more FP64 work in flight), merged in a fixed order
+        const Real *arow = A0 + r0 + rr;
+        double s1 = 0.0, c1 = 0.0, s2 = 0.0, c2 = 0.0, s3 = 0.0, c3 = 0.0;
+        int j = clo + gi;
+        for (; j + 3 * G < chi; j += 4 * G) {
+          const double a0 = (double)__ldcg(arow + (long long)j * P.lda0);
+          const double a1 = (double)__ldcg(arow + (long long)(j + G) * P.lda0);
+          const double a2 = (double)__ldcg(arow + (long long)(j + 2 * G) * P.lda0);
+          const double a3 = (double)__ldcg(arow + (long long)(j + 3 * G) * P.lda0);
+          dot2_step(a0, __ldcg(P.x + j), s, c);
+          dot2_step(a1, __ldcg(P.x + j + G), s1, c1);
+          dot2_step(a2, __ldcg(P.x + j + 2 * G), s2, c2);
+          dot2_step(a3, __ldcg(P.x + j + 3 * G), s3, c3);
+        }
+        for (; j < chi; j += G) dot2_step((double)__ldcg(arow + (long long)j * P.lda0), __ldcg(P.x + j), s, c);
+        dot2_merge(s, c, s1, c1);
+        dot2_merge(s2, c2, s3, c3);
+        dot2_merge(s, c, s2, c2);
       }
       sm[tid] = s;
       sm[NT + tid] = c;
@@ -831,8 +880,35 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
       const size_t np = (size_t)g.n * nb;
       for (int cc = warp; cc < nc; cc += NWARP) {
         const Real *acol = A0 + (long long)(c0 + cc) * P.lda0;
-        double s = 0.0, c = 0.0;
-        for (int i = rlo + lane; i < rhi; i += 32) dot2_step((double)__ldcg(acol + i), __ldcg(P.r + i), s, c);
+        double s = 0.0, c = 0.0, s1 = 0.0, c1 = 0.0, s2 = 0.0, c2 = 0.0, s3 = 0.0, c3 = 0.0;
+        int i = rlo + lane;
+        if (!t.tgt) {  // plain FP64 round: FMA chains, then a plain warp sum
+          for (; i + 96 < rhi; i += 128) {
+            s = fma((double)__ldcg(acol + i), __ldcg(P.r + i), s);
+            s1 = fma((double)__ldcg(acol + i + 32), __ldcg(P.r + i + 32), s1);
+            s2 = fma((double)__ldcg(acol + i + 64), __ldcg(P.r + i + 64), s2);
+            s3 = fma((double)__ldcg(acol + i + 96), __ldcg(P.r + i + 96), s3);
+          }
+          for (; i < rhi; i += 32) s = fma((double)__ldcg(acol + i), __ldcg(P.r + i), s);
+          s = warp_sum((s + s1) + (s2 + s3));
+          if (lane == 0) {
+            P.gp[2 * ((size_t)t.i * np + c0 + cc)] = s;
+            P.gp[2 * ((size_t)t.i * np + c0 + cc) + 1] = 0.0;
+          }
+          continue;
+        }
+        for (; i + 96 < rhi; i += 128) {  // four independent compensated sums, merged in a fixed order
+          const double a0 = (double)__ldcg(acol + i), a1 = (double)__ldcg(acol + i + 32);
+          const double a2 = (double)__ldcg(acol + i + 64), a3 = (double)__ldcg(acol + i + 96);
+          dot2_step(a0, __ldcg(P.r + i), s, c);
+          dot2_step(a1, __ldcg(P.r + i + 32), s1, c1);
+          dot2_step(a2, __ldcg(P.r + i + 64), s2, c2);
+          dot2_step(a3, __ldcg(P.r + i + 96), s3, c3);
+        }
+        for (; i < rhi; i += 32) dot2_step((double)__ldcg(acol + i), __ldcg(P.r + i), s, c);
+        dot2_merge(s, c, s1, c1);
+        dot2_merge(s2, c2, s3, c3);
+        dot2_merge(s, c, s2, c2);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           const double s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, c, o);
@@ -858,50 +934,44 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
       break;
     }
     case OP_TRSV_TD:
-    case OP_TRSV_D: {  // g_i <- X^T g_i or X g_i with X = R_ii^{-1}
+    case OP_TRSV_D:
+    case OP_TRSV_TU:
+    case OP_TRSV_U: {
+      // Triangular-solve steps with one tile: TD g_i <- X^T g_i, D g_i <- X g_i (X = R_ii^{-1}, FP64),
+      // TU g_j -= R(i,j)^T g_i (j > i), U g_j -= R(j,i) g_i (j < i). g_i is staged once; every thread
+      // owns one output (and half of its sum) and keeps four independent FP64 chains, with no FP64
+      // cross-lane reductions (a warp-wide FP64 operation takes 16 cycles of the FP64 pipe).
       const int i = t.i, n_i = min(nb, P.N - i * nb);
-      const double *X = P.rinv + (size_t)i * nb * nb;
+      const bool diag = t.op == OP_TRSV_TD || t.op == OP_TRSV_D;
+      const bool transposed = t.op == OP_TRSV_TD || t.op == OP_TRSV_TU;
+      const int j = diag ? i : t.j;
+      const int n_out = min(nb, P.N - j * nb);
       double *gi = P.g + (size_t)i * nb;
-      for (int k = tid; k < n_i; k += NT) sm[k] = __ldcg(gi + k);
+      double *go = P.g + (size_t)j * nb;
+      double *gs = sm;         // g_i
+      double *part = sm + nb;  // partial sums, (NT / nb) x nb
+      for (int k = tid; k < nb; k += NT) gs[k] = k < n_i ? __ldcg(gi + k) : 0.0;
       __syncthreads();
-      if (t.op == OP_TRSV_TD) {
-        for (int c = warp; c < n_i; c += NWARP) {  // (X^T g)_c = sum_{r <= c} X(r, c) g_r
-          double s = 0.0;
-          for (int r = lane; r <= c; r += 32) s = fma(__ldcg(X + (size_t)c * nb + r), sm[r], s);
-          s = warp_sum(s);
-          if (lane == 0) gi[c] = s;
-        }
-      } else {
-        for (int r = tid; r < n_i; r += NT) {  // (X g)_r = sum_{c >= r} X(r, c) g_c
-          double s = 0.0;
-          for (int c = r; c < n_i; ++c) s = fma(__ldcg(X + (size_t)c * nb + r), sm[c], s);
-          gi[r] = s;
-        }
+      const int o = tid % nb, h = tid / nb, H = NT / nb;  // output index, part of the sum
+      double acc = 0.0;
+      if (o < n_out && h < H) {
+        // out_o = sum_q M(row(q), col(q)) g_q: transposed M(q, o) (a column of M, o's own), else
+        // M(o, q) (a row; consecutive threads read consecutive addresses). X is upper triangular.
+        const int qlo = (diag && !transposed) ? o : 0;
+        const int qhi = (diag && transposed) ? o + 1 : n_i;
+        if (diag)
+          acc = tile_dot(P.rinv + (size_t)i * nb * nb, nb, transposed, o, qlo + h, qhi, H, gs);
+        else
+          acc = tile_dot(transposed ? g.tile(i, j) : g.tile(j, i), nb, transposed, o, qlo + h, qhi, H, gs);
+      }
+      if (h < H) part[h * nb + o] = acc;
+      __syncthreads();
+      if (tid < n_out) {
+        double v = 0.0;
+        for (int q = 0; q < H; ++q) v += part[q * nb + tid];
+        go[tid] = diag ? v : __ldcg(go + tid) - v;
       }
       __syncthreads();
-      break;
-    }
-    case OP_TRSV_TU: {  // g_j -= R(i,j)^T g_i, j > i
-      const int i = t.i, j = t.j, n_i = min(nb, P.N - i * nb), n_j = min(nb, P.N - j * nb);
-      const Real *R = g.tile(i, j);
-      const double *gi = P.g + (size_t)i * nb;
-      for (int c = warp; c < n_j; c += NWARP) {
-        double s = 0.0;
-        for (int r = lane; r < n_i; r += 32) s = fma((double)__ldcg(R + (size_t)c * nb + r), __ldcg(gi + r), s);
-        s = warp_sum(s);
-        if (lane == 0) P.g[(size_t)j * nb + c] = __ldcg(P.g + (size_t)j * nb + c) - s;
-      }
-      break;
-    }
-    case OP_TRSV_U: {  // g_j -= R(j,i) g_i, j < i
-      const int i = t.i, j = t.j, n_i = min(nb, P.N - i * nb);
-      const Real *R = g.tile(j, i);
-      const double *gi = P.g + (size_t)i * nb;
-      for (int r = tid; r < nb; r += NT) {
-        double s = 0.0;
-        for (int c = 0; c < n_i; ++c) s = fma((double)__ldcg(R + (size_t)c * nb + r), __ldcg(gi + c), s);
-        P.g[(size_t)j * nb + r] = __ldcg(P.g + (size_t)j * nb + r) - s;
-      }
       break;
     }
     case OP_XUPD: {
@@ -1083,19 +1153,19 @@ __global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_sched(EngineParams p) {
     else
       task_vector(p, p.probs[t.pid], g, t, reinterpret_cast<double *>(dyn_raw));
     __syncthreads();
-    if (threadIdx.x == 0) {
-      if (p.trace) {
+    if (threadIdx.x < 32) {  // warp 0 releases the successors, 32 at a time (most critical first)
+      if (threadIdx.x == 0 && p.trace) {
         p.trace[3 * (size_t)tid + 0] = t_start;
         p.trace[3 * (size_t)tid + 1] = ptx::globaltimer();
         p.trace[3 * (size_t)tid + 2] = ((unsigned long long)blockIdx.x << 32) | smid();
       }
       ptx::fence_proxy_async();
       __threadfence();
-      for (int e = t.succ_begin; e < t.succ_end; ++e) {
+      for (int e = t.succ_begin + (int)threadIdx.x; e < t.succ_end; e += 32) {
         const int s = p.succ[e];
         if (atomicSub(&p.indeg[s], 1) == 1) push_ready(p, s);
       }
-      if (++pending >= 64) {
+      if (threadIdx.x == 0 && ++pending >= 64) {
         __threadfence();
         atomicAdd(&p.ctl->done.v, pending);
         pending = 0;
@@ -1286,13 +1356,15 @@ __global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_serve(ServeParams sp) {
     else
       task_vector(p, P, g, t, reinterpret_cast<double *>(dyn_raw));
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {  // warp 0 releases the successors, 32 at a time
       ptx::fence_proxy_async();
       __threadfence();
-      for (int e = t.succ_begin; e < t.succ_end; ++e) {
+      for (int e = t.succ_begin + (int)threadIdx.x; e < t.succ_end; e += 32) {
         const int s = __ldcg(p.succ + e);
         if (atomicSub(&p.indeg[s], 1) == 1) serve_push(sp, s);
       }
+    }
+    if (threadIdx.x == 0) {
       if (atomicAdd(&sp.req_done[t.pid], 1) + 1 == __ldcg(sp.req_total + t.pid)) {
         __threadfence_system();
         sp.comp[t.pid] = __ldcg(sp.req_seq + t.pid);
