@@ -1085,6 +1085,7 @@ __device__ __forceinline__ void tc_setup(tc::State &ts) {
         ptx::mbar_init(&ts.img[c], 1);
       }
       ptx::mbar_init(&ts.done, 1);
+      ptx::mbar_init(&ts.slab, 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (threadIdx.x < 32) tc::tmem_alloc(&ts.tmem);

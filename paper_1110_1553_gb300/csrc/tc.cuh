@@ -28,9 +28,9 @@
 // bytes so that its transposed writes from tensor memory are free of bank
 // conflicts. Hand-off uses mbarriers: every thread arrives on a chunk's
 // barrier after writing it, one thread issues that chunk's MMAs, and one
-// commit signals the end of a product. The slab values that the epilogues
-// update are read into registers while the products run. Every wait is
-// bounded by the global timer.
+// commit signals the end of a product. The C slabs that the epilogues
+// update are fetched into shared memory by bulk copies while product A
+// runs. Every wait is bounded by the global timer.
 #pragma once
 
 #include <cstdint>
@@ -64,7 +64,10 @@ constexpr uint32_t OFF_RING_A = 0;                           // product A: W reg
 constexpr uint32_t OFF_RING_BC = NP * W_PC;
 constexpr uint32_t SMEM_A = OFF_RING_A + NCH * STAGE_A;      // 147456
 constexpr uint32_t SMEM_BC = OFF_RING_BC + NCH * STAGE_BC;   // 153600
-constexpr uint32_t SMEM_BYTES = SMEM_A > SMEM_BC ? SMEM_A : SMEM_BC;
+constexpr uint32_t SLAB_BYTES = WMAX * NB * 4;                  // one C slab (64 columns of 128)
+constexpr uint32_t OFF_TOP = SMEM_A > SMEM_BC ? SMEM_A : SMEM_BC;  // C_t slab, column-major, ld 128
+constexpr uint32_t OFF_BOT = OFF_TOP + SLAB_BYTES;                 // C_b slab
+constexpr uint32_t SMEM_BYTES = OFF_BOT + SLAB_BYTES;              // 219136
 
 // Per panel tile (i, k, GEQRT or kill) the panel task stores a "T record":
 // the FP32 factor T (128 x 128, column-major, zeros below the diagonal),
@@ -84,6 +87,7 @@ struct State {
   uint64_t full[NCH];  // chunk c staged by every thread
   uint64_t img[NCH];   // chunk c of an operand image arrived (bulk copy)
   uint64_t done;       // every MMA of a product completed
+  uint64_t slab;       // the C slabs of an update arrived (bulk copies)
   uint32_t tmem;
   int pad;
 };
@@ -193,7 +197,7 @@ __device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity, volatil
 // Parity of the chunk barriers (all flip once per product) and of the done
 // barrier, tracked identically by every thread.
 struct Phases {
-  uint32_t full = 0, img = 0, done = 0;
+  uint32_t full = 0, img = 0, done = 0, slab = 0;
 };
 
 // Element masks of the reflector block V at (row, reflector):
@@ -211,8 +215,9 @@ struct Src {
   const float *p;
   int ld;
   int transposed;
-  int rows;   // valid rows (m < rows); others are zero
-  int vmode;  // vmask mode, with (row, refl) = natural ? (k, m) : (m, k); -1: none
+  int rows;     // valid rows (m < rows); others are zero
+  int vmode;    // vmask mode, with (row, refl) = natural ? (k, m) : (m, k); -1: none
+  int shared;   // p points to shared memory (a staged slab): plain loads
 };
 
 // A piece: row m, k group kg (k = 8 kg .. 8 kg + 7 of the chunk), 8 floats.
@@ -243,8 +248,13 @@ __device__ __forceinline__ Piece load_piece(const Src &s, int c, int m, int kg) 
     r.lo4 = r.hi4 = make_float4(0.f, 0.f, 0.f, 0.f);
   } else if (!s.transposed) {
     const float *q = s.p + (size_t)m * s.ld + k0;
-    r.lo4 = ldcg4(q);
-    r.hi4 = ldcg4(q + 4);
+    if (s.shared) {
+      r.lo4 = *reinterpret_cast<const float4 *>(q);
+      r.hi4 = *reinterpret_cast<const float4 *>(q + 4);
+    } else {
+      r.lo4 = ldcg4(q);
+      r.hi4 = ldcg4(q + 4);
+    }
   } else {
     const float *q = s.p + (size_t)k0 * s.ld + m;
     r.lo4.x = __ldcg(q);
@@ -307,15 +317,6 @@ __device__ __forceinline__ void fetch_b(const Src &s, int c, Piece &r) {
   r = load_piece(s, c, m, kg);
 }
 
-// The first DT chunks of a product's operands (issued ahead).
-__device__ __forceinline__ void prefetch(const Src &sa, const Src *sb, Fetch &f) {
-#pragma unroll
-  for (int c = 0; c < DT; ++c) {
-    fetch_a(sa, c, f.a[c]);
-    if (sb) fetch_b(*sb, c, f.b[c]);
-  }
-}
-
 // The six BF16 products of one K step, small terms first, accumulating.
 __device__ __forceinline__ void issue_kstep(uint32_t tmem, uint32_t idesc, uint32_t a, uint32_t apb, uint32_t b,
                                             uint32_t bpb, uint32_t blbo, uint32_t bsbo, bool first) {
@@ -329,18 +330,28 @@ __device__ __forceinline__ void issue_kstep(uint32_t tmem, uint32_t idesc, uint3
 }
 
 // D[128 x n] = A B^T over K = 128. A is either an operand image in global
-// memory (`img`: one bulk copy per chunk, issued at once by one thread) or
-// gathered by every thread from `sa` (its first DT chunks already in `f`)
-// and split into BF16 pieces; B is streamed from `sb` (product A, split by
-// the threads) or read from the resident W^T buffer (sb == nullptr). The
-// first DT chunks of the next product's gathered operand `next` (if any)
-// are requested into free registers: at once when A is an image, else
-// while the last chunks are consumed. One thread issues each chunk's MMAs
-// once its pieces are in place. Returns false on a timeout (the CTA's abort
-// flag is set).
+// memory (`img`: one bulk copy per chunk, issued at once by one thread,
+// possibly already by the caller) or gathered by every thread from `sa`
+// (its first DT chunks already in `f`) and split into BF16 pieces; B is
+// streamed from `sb` (product A: the staged C_b slab, split by the threads)
+// or read from the resident W^T buffer (sb == nullptr). The first DT chunks
+// of the next product's gathered operand `next` (if any) are requested into
+// free registers: at once when A is an image, else while the last chunks are
+// consumed. One thread issues each chunk's MMAs once its pieces are in
+// place. Returns false on a timeout (the CTA's abort flag is set).
+// The bulk copies of an operand image into a product's stages (one thread).
+__device__ __forceinline__ void issue_image(const unsigned char *img, unsigned char *smem, uint32_t ring,
+                                            uint32_t stage_bytes, State &st) {
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    ptx::mbar_arrive_expect_tx(&st.img[c], NP * A_PC);
+    ptx::bulk_g2s(smem + ring + (uint32_t)c * stage_bytes, img + (size_t)c * NP * A_PC, NP * A_PC, &st.img[c]);
+  }
+}
+
 __device__ bool product(const Src &sa, const unsigned char *img, const Src *sb, const Src *next, Fetch &f,
                         unsigned char *smem, State &st, Phases &ph, uint32_t tmem, int n, volatile int *abort,
-                        long long limit_ns) {
+                        long long limit_ns, bool img_issued = false) {
   const int tid = threadIdx.x;
   const bool streamB = sb != nullptr, useImg = img != nullptr;
   const bool threadsWrite = !useImg || streamB;  // chunk hand-off through the "full" barriers
@@ -348,13 +359,7 @@ __device__ bool product(const Src &sa, const unsigned char *img, const Src *sb, 
   const uint32_t stage_bytes = streamB ? STAGE_A : STAGE_BC;
   const uint32_t idesc = idesc_bf16(n);
   const uint32_t sbase = ptx::smem_addr(smem);
-  if (useImg && tid == 0) {
-#pragma unroll
-    for (int c = 0; c < NCH; ++c) {
-      ptx::mbar_arrive_expect_tx(&st.img[c], NP * A_PC);
-      ptx::bulk_g2s(smem + ring + (uint32_t)c * stage_bytes, img + (size_t)c * NP * A_PC, NP * A_PC, &st.img[c]);
-    }
-  }
+  if (useImg && !img_issued && tid == 0) issue_image(img, smem, ring, stage_bytes, st);
   if (useImg && next)
 #pragma unroll
     for (int c = 0; c < DT; ++c) fetch_a(*next, c, f.a[c]);
@@ -432,36 +437,19 @@ __device__ __forceinline__ void tmem_sum16(uint32_t taddr, float (&v)[16]) {
 
 // Accumulator elements of this thread in the epilogues: lane m = 32 (warp
 // & 3) + laneid, columns 16 g .. 16 g + 15 for the column groups g = (warp >>
-// 2) + 2 e, e = 0, 1 (n <= 64).
-struct Slab {
-  float v[2][16];
-};
+// 2) + 2 e, e = 0, 1 (n <= 64). The C slabs sit in shared memory (column
+// col of a slab at col * 128 floats), fetched at the start of the task.
 
-// C(m, col) of this thread's elements (zero outside the slab), read once.
-__device__ __forceinline__ void load_slab(const float *c, int n, int cw, Slab &x) {
-  const int warp = threadIdx.x >> 5, m = 32 * (warp & 3) + (threadIdx.x & 31);
-#pragma unroll
-  for (int e = 0; e < 2; ++e) {
-    const int g = (warp >> 2) + 2 * e;
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int col = 16 * g + q;
-      x.v[e][q] = (g < n / 16 && col < cw) ? __ldcg(c + (size_t)col * NB + m) : 0.f;
-    }
-  }
+// Request the slab's cw columns (512 bytes each) with bulk copies on `bar`
+// (warp 0; the first lane posts the byte count).
+__device__ __forceinline__ void fetch_slab(const float *c, int cw, float *dst, uint64_t *bar) {
+  for (int col = threadIdx.x; col < cw; col += 32)
+    ptx::bulk_g2s(dst + (size_t)col * NB, c + (size_t)col * NB, NB * 4, bar);
 }
 
-__device__ __forceinline__ void store_slab(float *c, int n, int cw, const Slab &x) {
-  const int warp = threadIdx.x >> 5, m = 32 * (warp & 3) + (threadIdx.x & 31);
-#pragma unroll
-  for (int e = 0; e < 2; ++e) {
-    const int g = (warp >> 2) + 2 * e;
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int col = 16 * g + q;
-      if (g < n / 16 && col < cw) __stcg(c + (size_t)col * NB + m, x.v[e][q]);
-    }
-  }
+// Coalesced write-back of a slab from shared memory.
+__device__ __forceinline__ void store_slab(float *c, int cw, const float *src) {
+  for (int e = threadIdx.x; e < cw * NB; e += NTHR) __stcg(c + e, src[e]);
 }
 
 // Offset of element (n = column, k = reflector) in a piece of the resident
@@ -470,9 +458,10 @@ __device__ __forceinline__ uint32_t woff(int n, int k) {
   return (uint32_t)(n & 7) * 16 + (uint32_t)(n >> 3) * SBO_W + (uint32_t)(k & 7) * 2 + (uint32_t)(k >> 3) * LBO_W;
 }
 
-// Epilogue of products A and B: W = D (+ add), optionally sub -= W, and W^T
-// (three BF16 pieces) to the resident buffer for the next product.
-__device__ void epilogue_w(uint32_t tmem, int n, int cw, const Slab *add, Slab *sub, unsigned char *smem) {
+// Epilogue of products A and B: W = D (+ add), optionally sub -= W (slabs in
+// shared memory), and W^T (three BF16 pieces) to the resident buffer for the
+// next product.
+__device__ void epilogue_w(uint32_t tmem, int n, int cw, const float *add, float *sub, unsigned char *smem) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m = 32 * (warp & 3) + lane;
   const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
@@ -485,9 +474,12 @@ __device__ void epilogue_w(uint32_t tmem, int n, int cw, const Slab *add, Slab *
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int col = 16 * g + q;
-      float x = col < cw ? v[q] : 0.f;
-      if (add) x += add->v[e][q];
-      if (sub) sub->v[e][q] -= x;
+      float x = 0.f;
+      if (col < cw) {
+        x = v[q];
+        if (add) x += add[col * NB + m];
+        if (sub) sub[col * NB + m] -= x;
+      }
       uint32_t p0, p1, p2;
       split3(x, p0, p1, p2);
       unsigned char *dst = smem + OFF_W + woff(col, m);
@@ -498,9 +490,10 @@ __device__ void epilogue_w(uint32_t tmem, int n, int cw, const Slab *add, Slab *
   }
 }
 
-// Epilogue of product C: C_b -= D.
-__device__ void epilogue_c(uint32_t tmem, int n, Slab &cb) {
-  const int warp = threadIdx.x >> 5;
+// Epilogue of product C: C_b -= D (slab in shared memory).
+__device__ void epilogue_c(uint32_t tmem, int n, int cw, float *cb) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m = 32 * (warp & 3) + lane;
   const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
@@ -509,7 +502,10 @@ __device__ void epilogue_c(uint32_t tmem, int n, Slab &cb) {
     float v[16];
     tmem_sum16(tl + 16 * g, v);
 #pragma unroll
-    for (int q = 0; q < 16; ++q) cb.v[e][q] -= v[q];
+    for (int q = 0; q < 16; ++q) {
+      const int col = 16 * g + q;
+      if (col < cw) cb[col * NB + m] -= v[q];
+    }
   }
 }
 
@@ -528,39 +524,49 @@ __device__ bool update(int mode, int trans, const float *V, const float *Trec, f
   const int n = (cw + 15) & ~15;
   const uint32_t tmem = st.tmem;
   const unsigned char *rec = reinterpret_cast<const unsigned char *>(Trec);
-  const Src sva{V, NB, 0, NB, mode == 0 ? -1 : mode};  // V^T (reflector, row): image REC_VA
-  const Src scb{cb, NB, 0, cw, -1};                     // C_b^T (column, row)
-  const Src stt{Trec, NB, 1, NB, -1};                   // T (Q): gathered; T^T (Q^T): image REC_TB
-  const Src svc{V, NB, 1, NB, mode == 0 ? -1 : mode};  // V (row, reflector): image REC_VC
-  fence_async_smem();  // earlier generic writes of the stages before the bulk copies
+  float *top = reinterpret_cast<float *>(smem + OFF_TOP), *bot = reinterpret_cast<float *>(smem + OFF_BOT);
+  const Src sva{V, NB, 0, NB, mode == 0 ? -1 : mode, 0};  // V^T (reflector, row): image REC_VA
+  const Src scb{bot, NB, 0, cw, -1, 1};                    // C_b^T (column, row) from the staged slab
+  const Src stt{Trec, NB, 1, NB, -1, 0};                   // T (Q): gathered; T^T (Q^T): image REC_TB
+  const Src svc{V, NB, 1, NB, mode == 0 ? -1 : mode, 0};  // V (row, reflector): image REC_VC
+  fence_async_smem();  // earlier generic accesses of the stages and slabs before the bulk copies
   __syncthreads();
+  if (threadIdx.x < 32) {  // the slabs and product A's V^T image, all in flight at once
+    if (threadIdx.x == 0) {
+      ptx::mbar_arrive_expect_tx(&st.slab, (uint32_t)((ct ? 2 : 1) * cw * NB * 4));
+      issue_image(rec + REC_VA, smem, OFF_RING_A, STAGE_A, st);
+    }
+    __syncwarp();
+    if (ct) fetch_slab(ct, cw, top, &st.slab);
+    fetch_slab(cb, cw, bot, &st.slab);
+  }
+  if (!wait_bar(&st.slab, ph.slab & 1u, abort, limit_ns)) return false;
+  ph.slab ^= 1u;
   Fetch f;
 #pragma unroll
   for (int c = 0; c < DT; ++c) fetch_b(scb, c, f.b[c]);
-  Slab top, bot;
-  if (ct) load_slab(ct, n, cw, top);  // in flight during product A
-  if (!product(sva, rec + REC_VA, &scb, trans ? nullptr : &stt, f, smem, st, ph, tmem, n, abort, limit_ns))
+  if (!product(sva, rec + REC_VA, &scb, trans ? nullptr : &stt, f, smem, st, ph, tmem, n, abort, limit_ns, true))
     return false;
-  epilogue_w(tmem, n, cw, ct ? &top : nullptr, nullptr, smem);
+  epilogue_w(tmem, n, cw, ct ? top : nullptr, nullptr, smem);
   tc_fence_before();
   fence_async_smem();
   __syncthreads();
   tc_fence_after();
-  load_slab(cb, n, cw, bot);  // in flight during products B and C
   if (!product(stt, trans ? rec + REC_TB : nullptr, nullptr, nullptr, f, smem, st, ph, tmem, n, abort, limit_ns))
     return false;
-  epilogue_w(tmem, n, cw, nullptr, ct ? &top : nullptr, smem);
-  if (ct) store_slab(ct, n, cw, top);
+  epilogue_w(tmem, n, cw, nullptr, ct ? top : nullptr, smem);
   tc_fence_before();
   fence_async_smem();
   __syncthreads();
   tc_fence_after();
+  if (ct) store_slab(ct, cw, top);
   if (!product(svc, rec + REC_VC, nullptr, nullptr, f, smem, st, ph, tmem, n, abort, limit_ns)) return false;
-  epilogue_c(tmem, n, bot);
-  store_slab(cb, n, cw, bot);
+  epilogue_c(tmem, n, cw, bot);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  store_slab(cb, cw, bot);
+  __syncthreads();
   return true;
 }
 
@@ -604,6 +610,14 @@ struct PanelSmem {
 constexpr uint32_t PANEL_SMEM = sizeof(PanelSmem);
 
 __device__ __forceinline__ int rsoff(int r, int c) { return c * (c + 1) / 2 + r; }
+
+// Sums of the eight per-warp partials as a fixed tree (shorter dependence chain).
+__device__ __forceinline__ float sum8s(const float *p, int stride) {
+  const float a = p[0] + p[stride], b = p[2 * stride] + p[3 * stride];
+  const float c = p[4 * stride] + p[5 * stride], d = p[6 * stride] + p[7 * stride];
+  return (a + b) + (c + d);
+}
+__device__ __forceinline__ float sum8(const float *p) { return sum8s(p, 1); }
 
 // Split image (chunk layout of the update stages) of a 128 x 128 operand
 // whose element (m, k) is value(m, k); written once per panel tile. Piece
@@ -685,14 +699,19 @@ __device__ void panel(int mode, float *X, float *Rg, float *Tg, unsigned char *s
         sm.part[buf][warp][lane + 32 * q] = s;
       }
       if (lane == 0) sm.pss[buf][warp] = ss;
-      if (mode == 1 && warp == (j >> 4)) {
-        const int ij = j & 15;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          float v = 0.f;
-#pragma unroll
-          for (int i = 0; i < 16; ++i) v = (i == ij) ? x[i][q] : v;
-          sm.prow[buf][lane + 32 * q] = v;
+      if (mode == 1 && warp == (j >> 4)) {  // row j of the tile (a jump on its register row)
+        float *pr = sm.prow[buf] + lane;
+        switch (j & 15) {
+#define HQR_PROW(I) \
+  case I:           \
+    pr[0] = x[I][0]; \
+    pr[32] = x[I][1]; \
+    pr[64] = x[I][2]; \
+    pr[96] = x[I][3]; \
+    break;
+          HQR_PROW(0) HQR_PROW(1) HQR_PROW(2) HQR_PROW(3) HQR_PROW(4) HQR_PROW(5) HQR_PROW(6) HQR_PROW(7)
+          HQR_PROW(8) HQR_PROW(9) HQR_PROW(10) HQR_PROW(11) HQR_PROW(12) HQR_PROW(13) HQR_PROW(14) HQR_PROW(15)
+#undef HQR_PROW
         }
       }
       __syncthreads();
@@ -705,9 +724,7 @@ __device__ void panel(int mode, float *X, float *Rg, float *Tg, unsigned char *s
         }
         if (lane == 0) sm.rs[rsoff(prev_j, prev_j)] = prev_beta;
       }
-      float sst = 0.f;
-#pragma unroll
-      for (int w = 0; w < 8; ++w) sst += sm.pss[buf][w];
+      const float sst = sum8(sm.pss[buf]);
       const float alpha = mode == 1 ? sm.prow[buf][j] : sm.rs[rsoff(j, j)];
       float snorm;
       bool rescaled = false;
@@ -765,9 +782,7 @@ __device__ void panel(int mode, float *X, float *Rg, float *Tg, unsigned char *s
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int c = lane + 32 * q;
-        float s = 0.f;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) s += sm.part[buf][w][c];
+        const float s = sum8s(&sm.part[buf][0][c], NB);
         rowc[q] = mode == 1 ? sm.prow[buf][c] : (c > j ? sm.rs[rsoff(j, c)] : 0.f);
         const float vta = rowc[q] + pscale * s;  // v_j^T a_c (GE, TS), v_j^T v_c for c < j
         wc[q] = c > j ? t * vta : 0.f;
@@ -829,8 +844,67 @@ __device__ void panel(int mode, float *X, float *Rg, float *Tg, unsigned char *s
   for (int e = tid; e < NB; e += NTHR) sm.tg[e * LDT + e] = sm.tau[e];
   __syncthreads();
   for (int s = 1; s < NB; s *= 2) {
+    if (s >= 16) {  // 4 x 4 output blocks per thread: 16 FMAs per 8 shared loads
+      const int nbk = s / 4, per = nbk * nbk, nblocks = (NB / (2 * s)) * per;
+      const bool act = tid < nblocks;
+      int a = 0, l0 = 0, j0 = 0;
+      if (act) {
+        const int pr = tid / per, rem = tid - pr * per;
+        a = pr * 2 * s;
+        l0 = a + (rem % nbk) * 4;
+        j0 = a + s + (rem / nbk) * 4;
+      }
+      float acc[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+      if (act)  // X = G_AB T_B (T_B upper triangular: m <= j)
+        for (int m = a + s; m <= j0 + 3; ++m) {
+          float gv[4], tv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) gv[u] = sm.tg[m + (l0 + u) * LDT];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) tv[v] = m <= j0 + v ? sm.tg[m + (j0 + v) * LDT] : 0.f;
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(gv[u], tv[v], acc[u][v]);
+        }
+      __syncthreads();
+      if (act)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) sm.tg[(l0 + u) + (j0 + v) * LDT] = acc[u][v];
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+      if (act)  // T_AB = -T_A X (T_A upper triangular: m >= l)
+        for (int m = l0; m < a + s; ++m) {
+          float ta[4], xv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) ta[u] = m >= l0 + u ? sm.tg[(l0 + u) + m * LDT] : 0.f;
+#pragma unroll
+          for (int v = 0; v < 4; ++v) xv[v] = sm.tg[m + (j0 + v) * LDT];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(ta[u], xv[v], acc[u][v]);
+        }
+      __syncthreads();
+      if (act)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) sm.tg[(l0 + u) + (j0 + v) * LDT] = -acc[u][v];
+      __syncthreads();
+      continue;
+    }
     const int per = s * s, total = (NB / (2 * s)) * per;  // outputs: (pairs) x s x s
-    float acc[16];
+    float acc[2];  // s < 16: at most 2 outputs per thread
     // X = G_AB T_B (rows l in A, columns j in B)
     int nout = 0;
     for (int o = tid; o < total; o += NTHR, ++nout) {
