@@ -491,6 +491,7 @@ def main():
         extras["batched"] = batched(torch, hqr, dev)
         extras["square_mixed"] = square_mixed(torch, hqr, dev)
         extras["serving"] = serving(torch, hqr, dev, seconds=args.serve_seconds)
+        extras["serving_200"] = serving(torch, hqr, dev, rate=200.0, seconds=args.serve_seconds)
 
     if rank != 0:
         return 0

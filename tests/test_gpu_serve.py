@@ -39,10 +39,15 @@ def wait_all(srv, tickets, done, timeout=60.0):
     assert not pending
 
 
-def test_server_mix_equals_alone_and_oracle():
-    shapes = [(300, 100), (64, 64), (1000, 200), (2048, 96), (150, 33), (700, 512), (4096, 256), (128, 32)]
+@pytest.mark.parametrize("tensor", [False, True])
+def test_server_mix_equals_alone_and_oracle(tensor):
+    """tensor=True: the requests whose default tile is 128 (here 4096 x 256,
+    2048 x 300, 3000 x 129) run on the tensor-core kernels, the others on the
+    FP32 CUDA-core kernels, all in the same resident launch."""
+    shapes = [(300, 100), (64, 64), (1000, 200), (2048, 96), (150, 33), (700, 512), (4096, 256), (128, 32),
+              (2048, 300), (3000, 129)]
     probs = [problem(M, N, 200 + q) for q, (M, N) in enumerate(shapes)]
-    srv = hqr.Server(torch.float32, refine_iters=5, max_live=4, hbm_budget=1 << 30)
+    srv = hqr.Server(torch.float32, refine_iters=5, max_live=4, hbm_budget=2 << 30, tensor=tensor)
     srv.start()
     try:
         tickets, queue, done = [], list(range(len(probs))), set()
@@ -63,7 +68,7 @@ def test_server_mix_equals_alone_and_oracle():
         xo = lstsq_unblocked(A.astype(np.float64), b)
         assert np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo) <= 1e-12
         x1 = torch.zeros_like(x)
-        plan = hqr.LSPlan([(Ad, bd, x1)], refine_iters=5)
+        plan = hqr.LSPlan([(Ad, bd, x1)], refine_iters=5, tensor=tensor)
         plan.run()
         assert plan.status() == 0
         assert torch.equal(x1, x), q
