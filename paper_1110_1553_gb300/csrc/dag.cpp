@@ -306,28 +306,36 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
       }
       inverted = true;
     }
+    // The update of the next diagonal tile's vector is its last writer before the inverse is
+    // applied, so that task applies the inverse too (tgt = 1): one task and one hop less per step
+    // of the chain. Tile 0 (forward) and n - 1 (backward) have their own inverse task.
+    auto ftask = [&](int op, int i, int j, int fused) { return make_task(op, 1, i, i, 0, j, 0, 0, 1, fused, pid); };
     if (transposed_first) {  // R^T y = g, forward
+      tr.read(ires(0), d);
+      tr.write(gres(0), d);
+      b.add(vtask(OP_TRSV_TD, 0, 0));
       for (int i = 0; i < n; ++i) {
-        tr.read(ires(i), d);
-        tr.write(gres(i), d);
-        b.add(vtask(OP_TRSV_TD, i, i));
-        for (int j = i + 1; j < n; ++j) {
+        for (int j = n - 1; j > i; --j) {  // the next tile's update last, when the others are done
+          const int fused = j == i + 1;
           read_r(i, j);
           tr.read(gres(i), d);
+          if (fused) tr.read(ires(j), d);
           tr.write(gres(j), d);
-          b.add(vtask(OP_TRSV_TU, i, j));
+          b.add(ftask(OP_TRSV_TU, i, j, fused));
         }
       }
     }
-    for (int i = n - 1; i >= 0; --i) {  // R d = y, backward
-      tr.read(ires(i), d);
-      tr.write(gres(i), d);
-      b.add(vtask(OP_TRSV_D, i, i));
+    tr.read(ires(n - 1), d);  // R d = y, backward
+    tr.write(gres(n - 1), d);
+    b.add(vtask(OP_TRSV_D, n - 1, n - 1));
+    for (int i = n - 1; i >= 0; --i) {
       for (int j = 0; j < i; ++j) {
+        const int fused = j == i - 1;
         read_r(j, i);
         tr.read(gres(i), d);
+        if (fused) tr.read(ires(j), d);
         tr.write(gres(j), d);
-        b.add(vtask(OP_TRSV_U, i, j));
+        b.add(ftask(OP_TRSV_U, i, j, fused));
       }
     }
     for (int j = 0; j < n; ++j) {

@@ -755,25 +755,24 @@ __device__ __forceinline__ void dot2_merge(double &s1, double &c1, double s2, do
 }
 
 // sum over q = q0, q0 + step, ... < q1 of M(q, o) g_q (transposed) or M(o, q) g_q, M column-major
-// with leading dimension ld, in FP64 with four independent chains. M is final for the whole launch
+// with leading dimension ld, in FP64 with eight independent chains. M is final for the whole launch
 // (R tiles after their factorization, the inverses after their TRINV task), so its loads may use L1.
 template <typename M>
 __device__ __forceinline__ double tile_dot(const M *__restrict__ m, int ld, bool transposed, int o, int q0, int q1,
                                            int step, const double *g) {
   const M *base = transposed ? m + (size_t)o * ld : m + o;
   const size_t qs = transposed ? 1 : (size_t)ld;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   int q = q0;
-  for (; q + 3 * step < q1; q += 4 * step) {
-    const double m0 = (double)base[q * qs], m1 = (double)base[(q + step) * qs];
-    const double m2 = (double)base[(q + 2 * step) * qs], m3 = (double)base[(q + 3 * step) * qs];
-    a0 = fma(m0, g[q], a0);
-    a1 = fma(m1, g[q + step], a1);
-    a2 = fma(m2, g[q + 2 * step], a2);
-    a3 = fma(m3, g[q + 3 * step], a3);
+  for (; q + 7 * step < q1; q += 8 * step) {  // eight loads in flight per thread
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = (double)base[(size_t)(q + u * step) * qs];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = fma(v[u], g[q + u * step], a[u]);
   }
-  for (; q < q1; q += step) a0 = fma((double)base[q * qs], g[q], a0);
-  return (a0 + a1) + (a2 + a3);
+  for (; q < q1; q += step) a[0] = fma((double)base[(size_t)q * qs], g[q], a[0]);
+  return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 }
 
 template <typename Real>
@@ -969,7 +968,30 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
       if (tid < n_out) {
         double v = 0.0;
         for (int q = 0; q < H; ++q) v += part[q * nb + tid];
-        go[tid] = diag ? v : __ldcg(go + tid) - v;
+        v = diag ? v : __ldcg(go + tid) - v;
+        if (!diag && t.tgt)
+          gs[tid] = v;  // fused step: the inverse of tile j follows
+        else
+          go[tid] = v;
+      }
+      __syncthreads();
+      if (!diag && t.tgt) {  // g_j <- X_j^T g_j (after TU) or X_j g_j (after U), X_j = R_jj^{-1}
+        for (int k = tid; k < nb; k += NT)
+          if (k >= n_out) gs[k] = 0.0;
+        __syncthreads();
+        acc = 0.0;
+        if (o < n_out && h < H) {
+          const int qlo = transposed ? 0 : o, qhi = transposed ? o + 1 : n_out;
+          acc = tile_dot(P.rinv + (size_t)j * nb * nb, nb, transposed, o, qlo + h, qhi, H, gs);
+        }
+        if (h < H) part[h * nb + o] = acc;
+        __syncthreads();
+        if (tid < n_out) {
+          double v = 0.0;
+          for (int q = 0; q < H; ++q) v += part[q * nb + tid];
+          go[tid] = v;
+        }
+        __syncthreads();
       }
       __syncthreads();
       break;
