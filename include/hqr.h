@@ -404,6 +404,11 @@ int hqr_server_stats(const hqr_server *server, int64_t *submitted, int64_t *comp
  * kernel is running. cap >= 5. */
 int hqr_server_counters(const hqr_server *server, uint32_t *out, int cap);
 
+/* hqr_server_progress -- tasks completed and tasks in total of the live
+ * request `ticket` (a snapshot read from the device; *done may lag). Returns
+ * HQR_ERR_INTERNAL when no live request has that ticket. */
+int hqr_server_progress(const hqr_server *server, int64_t ticket, int *done, int *total);
+
 /* hqr_server_stop -- let the kernel finish all admitted work and exit;
  * returns its status. */
 int hqr_server_stop(hqr_server *server);

@@ -107,8 +107,9 @@ struct alignas(16) Problem {
   double *rinv;       // inverses of the diagonal R tiles, n tiles of nb x nb, column-major
   int *status;        // per-problem status word (HQR_ERR_SINGULAR)
   int tc;             // FP32 tiles of 128 on the tensor-core kernels (ib = nb: one full T per tile)
-  int tstr;           // elements per T record (ib * nb; tensor-core problems: T plus split images)
-  int pad_[2];
+  int tstr;           // elements per T record (ib * nb; tensor-core problems: split images [+ T])
+  int t32;            // tensor-core problems: the records keep the FP32 T (apply Q, read T)
+  int pad_;
 };
 static_assert(sizeof(Problem) % 16 == 0, "Problem is read in 16-byte pieces");
 
@@ -142,11 +143,11 @@ struct Shared {
 template <typename Real>
 struct Geo {
   Real *A, *T, *B;
-  int m, n, nb, ib, w, wt, vc, wb, lds, ldt;
+  int m, n, nb, ib, w, wt, vc, wb, lds, ldt, t32;
   size_t tstr;
   __device__ explicit Geo(const Problem &P)
       : A((Real *)P.A), T((Real *)P.T), B((Real *)P.B), m(P.m), n(P.n), nb(P.nb), ib(P.ib), w(P.w),
-        wt(P.wt), vc(P.vc), wb(P.wb), lds(P.nb + smem_pad<Real>()), ldt(P.ib + smem_pad<Real>()),
+        wt(P.wt), vc(P.vc), wb(P.wb), lds(P.nb + smem_pad<Real>()), ldt(P.ib + smem_pad<Real>()), t32(P.t32),
         tstr(P.tstr > 0 ? (size_t)P.tstr : (size_t)P.ib * P.nb) {}
   __device__ Real *tile(int i, int j) const { return A + ((size_t)j * m + i) * (size_t)nb * nb; }
   __device__ Real *tfac(int which, int i, int k) const { return T + (((size_t)k * m + i) * 2 + which) * tstr; }
@@ -1038,51 +1039,104 @@ __device__ __forceinline__ void push_ready(const EngineParams &p, int task) {
   ptx::st_release(&p.slots[(size_t)qs * shard_cap(p.ntasks) + idx], task + 1);
 }
 
-// Claim the next ready task (thread 0 only). -1: finished or failed.
-// `pending` counts tasks this CTA completed but has not yet added to the
-// global done counter; it is flushed whenever the queues look empty.
-__device__ int pop_ready(const EngineParams &p, unsigned &pending) {
-  const uint64_t t0 = ptx::globaltimer();
-  const int cap = shard_cap(p.ntasks);
-  const int home = blockIdx.x % kShards;
-  unsigned sleep_ns = 32;
+// Warp-wide claim on NQ priority classes x kShards ready rings (ring id =
+// class * kShards + shard; within a class this CTA's home shard first).
+// Each lane reads the head and tail of NQ / 4 rings at once, a ballot picks
+// the highest-priority non-empty ring, and the lane that saw it claims that
+// ring's head. All lanes return the ring (-1: every ring looked empty) and
+// `pos`, the claimed position. Called by all 32 lanes of one warp.
+template <int NQ>
+__device__ __forceinline__ int warp_claim(CtlLine *head, const CtlLine *tail, unsigned &pos) {
+  static_assert(NQ % 4 == 0 && kShards == 8, "a warp covers 4 classes x 8 shards per round");
+  constexpr int G = NQ / 4;
+  const int lane = threadIdx.x & 31;
+  const int ring0 = (lane >> 3) * kShards + ((lane + (int)blockIdx.x) & (kShards - 1));
   while (true) {
-    if (ptx::ld_relaxed((const int *)&p.ctl->status.v) != 0) return -1;
-    for (int q = 0; q < kNumQueues; ++q) {
-      for (int k = 0; k < kShards; ++k) {
-        const int qs = q * kShards + (home + k) % kShards;
-        unsigned h = ptx::ld_relaxed_u32(&p.ctl->head[qs].v);
-        while (h < ptx::ld_relaxed_u32(&p.ctl->tail[qs].v)) {
-          const unsigned old = atomicCAS(&p.ctl->head[qs].v, h, h + 1);
-          if (old == h) {
-            const int *slot = &p.slots[(size_t)qs * cap + h];
-            int v = ptx::ld_acquire(slot);
-            const uint64_t t1 = ptx::globaltimer();
-            while (v == 0) {
-              if (ptx::globaltimer() - t1 > (uint64_t)p.timeout_ns) {
-                set_error(p, HQR_ERR_TIMEOUT, -1);
-                return -1;
-              }
-              __nanosleep(32);
-              v = ptx::ld_acquire(slot);
-            }
-            __threadfence();
-            return v - 1;
+    unsigned h[G], tl[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      h[g] = ptx::ld_relaxed_u32(&head[g * 32 + ring0].v);
+      tl[g] = ptx::ld_relaxed_u32(&tail[g * 32 + ring0].v);
+    }
+    bool contended = false;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const unsigned m = __ballot_sync(0xffffffffu, h[g] < tl[g]);
+      if (m == 0) continue;
+      const int w = __ffs(m) - 1;
+      int ok = 0;
+      unsigned hh = h[g];
+      if (lane == w) {
+        while (hh < tl[g]) {
+          const unsigned old = atomicCAS(&head[g * 32 + ring0].v, hh, hh + 1);
+          if (old == hh) {
+            ok = 1;
+            break;
           }
-          h = old;
+          hh = old;
         }
       }
+      if (__shfl_sync(0xffffffffu, ok, w)) {
+        pos = __shfl_sync(0xffffffffu, hh, w);
+        return g * 32 + __shfl_sync(0xffffffffu, ring0, w);
+      }
+      contended = true;  // another CTA took it: look again
+      break;
     }
-    if (pending) {
-      __threadfence();
-      atomicAdd(&p.ctl->done.v, pending);
-      pending = 0;
-    }
-    if (ptx::ld_relaxed_u32(&p.ctl->done.v) >= (unsigned)p.ntasks) return -1;
-    if (ptx::globaltimer() - t0 > (uint64_t)p.timeout_ns) {
+    if (!contended) return -1;
+  }
+}
+
+// Wait (bounded) for the task id a pusher stores into a claimed ring slot.
+// Returns the task, or -1 after setting HQR_ERR_TIMEOUT.
+__device__ __forceinline__ int take_slot(const EngineParams &p, int *slot) {
+  int v = ptx::ld_acquire(slot);
+  const uint64_t t1 = ptx::globaltimer();
+  while (v == 0) {
+    if (ptx::globaltimer() - t1 > (uint64_t)p.timeout_ns) {
       set_error(p, HQR_ERR_TIMEOUT, -1);
       return -1;
     }
+    __nanosleep(32);
+    v = ptx::ld_acquire(slot);
+  }
+  __threadfence();
+  return v - 1;
+}
+
+// Claim the next ready task (warp 0, all lanes; the result in every lane).
+// -1: finished or failed. `pending` (lane 0's) counts tasks this CTA
+// completed but has not yet added to the global done counter; it is
+// flushed whenever the queues look empty.
+__device__ int pop_ready(const EngineParams &p, unsigned &pending) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t t0 = ptx::globaltimer();
+  const int cap = shard_cap(p.ntasks);
+  unsigned sleep_ns = 32;
+  while (true) {
+    if (__shfl_sync(0xffffffffu, lane == 0 ? ptx::ld_relaxed((const int *)&p.ctl->status.v) : 0, 0) != 0) return -1;
+    unsigned h = 0;
+    const int qs = warp_claim<kNumQueues>(p.ctl->head, p.ctl->tail, h);
+    if (qs >= 0) {
+      int v = 0;
+      if (lane == 0) v = take_slot(p, &p.slots[(size_t)qs * cap + h]);
+      return __shfl_sync(0xffffffffu, v, 0);
+    }
+    int fin = 0;
+    if (lane == 0) {
+      if (pending) {
+        __threadfence();
+        atomicAdd(&p.ctl->done.v, pending);
+        pending = 0;
+      }
+      if (ptx::ld_relaxed_u32(&p.ctl->done.v) >= (unsigned)p.ntasks) {
+        fin = 1;
+      } else if (ptx::globaltimer() - t0 > (uint64_t)p.timeout_ns) {
+        set_error(p, HQR_ERR_TIMEOUT, -1);
+        fin = 1;
+      }
+    }
+    if (__shfl_sync(0xffffffffu, fin, 0)) return -1;
     __nanosleep(sleep_ns);
     if (sleep_ns < 1024) sleep_ns *= 2;
   }
@@ -1131,7 +1185,7 @@ __device__ bool tc_task(const EngineParams &p, const Geo<Real> &g, const Task &t
   if constexpr (TC && sizeof(Real) == 4) {
     if (t.op == OP_GEQRT || t.op == OP_TSQRT || t.op == OP_TTQRT) {
       const int mode = t.op == OP_GEQRT ? 1 : (t.op == OP_TSQRT ? 0 : 2);
-      tc::panel(mode, g.tile(t.i, t.k), g.tile(t.r, t.k), g.tfac(mode == 1 ? 0 : 1, t.i, t.k), dyn);
+      tc::panel(mode, g.tile(t.i, t.k), g.tile(t.r, t.k), g.tfac(mode == 1 ? 0 : 1, t.i, t.k), g.t32 != 0, dyn);
       return true;
     }
     const int mode = t.op == OP_UNMQR ? 1 : (t.op == OP_TSMQR ? 0 : 2);
@@ -1160,7 +1214,10 @@ __global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_sched(EngineParams p) {
   tc::Phases tph;
   unsigned pending = 0;
   while (true) {
-    if (threadIdx.x == 0) sh.task = pop_ready(p, pending);
+    if (threadIdx.x < 32) {
+      const int v = pop_ready(p, pending);
+      if (threadIdx.x == 0) sh.task = v;
+    }
     __syncthreads();
     const int tid = sh.task;
     if (tid < 0) break;
@@ -1216,8 +1273,20 @@ __global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_sched(EngineParams p) {
 // (slots cleared after use). The kernel exits once the host has set `stop`
 // and no task is outstanding.
 
+// Server ready rings: kAgeClasses request-age classes x kNumQueues
+// critical-path classes x kShards. The age class of a request is its rank
+// among the requests not yet finished, in admission order (0-1: 0, 2-7: 1,
+// 8-31: 2, else 3), taken when a task is released: the oldest requests
+// run first and newer ones fill the CTAs they leave idle, so that requests
+// complete roughly in arrival order under overload instead of all sharing
+// the GPU until the end.
+constexpr int kAgeClasses = 4;
+constexpr int kServeQueues = kAgeClasses * kNumQueues;
+
 struct ServeCtl {
-  CtlLine inbox_head, inbox_tail, stop, outstanding;
+  CtlLine inbox_head, inbox_tail, stop, outstanding, finished;
+  CtlLine head[kServeQueues * kShards];
+  CtlLine tail[kServeQueues * kShards];
 };
 
 struct InboxEntry {
@@ -1254,11 +1323,18 @@ __device__ __forceinline__ Task load_task_cg(const Task *tp) {
   return t;
 }
 
-__device__ __forceinline__ void serve_push(const ServeParams &sp, int task) {
+// Rank estimate: requests admitted before this one minus requests finished
+// (negative when later requests finished first: the oldest class then).
+__device__ __forceinline__ int age_class(const ServeParams &sp, int slot) {
+  const int rank = (int)((unsigned)(__ldcg(sp.req_seq + slot) - 1) - ptx::ld_relaxed_u32(&sp.sc->finished.v));
+  return rank < 2 ? 0 : rank < 8 ? 1 : rank < 32 ? 2 : 3;
+}
+
+__device__ __forceinline__ void serve_push(const ServeParams &sp, int task, int age) {
   const int2 head = __ldcg(reinterpret_cast<const int2 *>(sp.e.tasks + task));
   const int prio = (int)(signed char)((head.x >> 8) & 0xff);  // byte 1 of the task record
-  const int qs = prio * kShards + task % kShards;
-  const unsigned idx = atomicAdd(&sp.e.ctl->tail[qs].v, 1u);
+  const int qs = (age * kNumQueues + prio) * kShards + task % kShards;
+  const unsigned idx = atomicAdd(&sp.sc->tail[qs].v, 1u);
   ptx::st_release(&sp.e.slots[(size_t)qs * sp.ring_cap + (idx & (unsigned)(sp.ring_cap - 1))], task + 1);
 }
 
@@ -1267,74 +1343,80 @@ __device__ __forceinline__ void serve_push(const ServeParams &sp, int task) {
 // the kernel when new work arrives.
 constexpr uint64_t kIdleExitNs = 1000000000ull;
 
+// Claim the next ready task or inbox entry (warp 0, all lanes; the task in
+// every lane, -1 to leave).
 __device__ int serve_pop(const ServeParams &sp, unsigned &pending) {
   const EngineParams &p = sp.e;
-  const int home = blockIdx.x % kShards;
+  const int lane = threadIdx.x & 31;
   unsigned sleep_ns = 64;
   const uint64_t idle_since = ptx::globaltimer();
   unsigned seen_out = 0xffffffffu;  // watchdog: outstanding count last seen and since when
   uint64_t seen_at = idle_since;
   while (true) {
-    if (ptx::ld_relaxed((const int *)&p.ctl->status.v) != 0) return -1;
-    for (int q = 0; q < kNumQueues; ++q) {
-      for (int k = 0; k < kShards; ++k) {
-        const int qs = q * kShards + (home + k) % kShards;
-        unsigned h = ptx::ld_relaxed_u32(&p.ctl->head[qs].v);
-        while (h < ptx::ld_relaxed_u32(&p.ctl->tail[qs].v)) {
-          const unsigned old = atomicCAS(&p.ctl->head[qs].v, h, h + 1);
-          if (old == h) {
-            int *slot = &p.slots[(size_t)qs * sp.ring_cap + (h & (unsigned)(sp.ring_cap - 1))];
-            int v = ptx::ld_acquire(slot);
-            const uint64_t t1 = ptx::globaltimer();
-            while (v == 0) {
-              if (ptx::globaltimer() - t1 > (uint64_t)p.timeout_ns) {
-                set_error(p, HQR_ERR_TIMEOUT, -1);
-                return -1;
-              }
-              __nanosleep(32);
-              v = ptx::ld_acquire(slot);
-            }
-            *slot = 0;  // the ring slot can be reused
-            __threadfence();
-            return v - 1;
-          }
-          h = old;
+    if (__shfl_sync(0xffffffffu, lane == 0 ? ptx::ld_relaxed((const int *)&p.ctl->status.v) : 0, 0) != 0) return -1;
+    unsigned h = 0;
+    const int qs = warp_claim<kServeQueues>(sp.sc->head, sp.sc->tail, h);
+    if (qs >= 0) {
+      int v = 0;
+      if (lane == 0) {
+        int *slot = &p.slots[(size_t)qs * sp.ring_cap + (h & (unsigned)(sp.ring_cap - 1))];
+        v = take_slot(p, slot);
+        if (v >= 0) {
+          *slot = 0;  // the ring slot can be reused
+          __threadfence();
+        }
+      }
+      return __shfl_sync(0xffffffffu, v, 0);
+    }
+    // new request? (lane 0 claims the entry, the warp releases its initial tasks)
+    int base = 0, ninit = -1, age = 0;
+    if (lane == 0) {
+      const unsigned ih = ptx::ld_relaxed_u32(&sp.sc->inbox_head.v);
+      if (ih < (unsigned)ld_acquire_sys_u32(&sp.sc->inbox_tail.v)) {
+        ninit = 0;
+        if (atomicCAS(&sp.sc->inbox_head.v, ih, ih + 1) == ih) {
+          const InboxEntry *en = sp.inbox + (ih & (unsigned)(sp.inbox_cap - 1));
+          const int nt = __ldcg(&en->ntasks);
+          base = __ldcg(&en->task_base);
+          ninit = __ldcg(&en->ninit);
+          age = age_class(sp, __ldcg(&en->slot));
+          atomicAdd(&sp.sc->outstanding.v, (unsigned)nt);
         }
       }
     }
-    // new request?
-    unsigned ih = ptx::ld_relaxed_u32(&sp.sc->inbox_head.v);
-    if (ih < (unsigned)ld_acquire_sys_u32(&sp.sc->inbox_tail.v)) {
-      if (atomicCAS(&sp.sc->inbox_head.v, ih, ih + 1) == ih) {
-        const InboxEntry *en = sp.inbox + (ih & (unsigned)(sp.inbox_cap - 1));
-        const int base = __ldcg(&en->task_base), ninit = __ldcg(&en->ninit), nt = __ldcg(&en->ntasks);
-        atomicAdd(&sp.sc->outstanding.v, (unsigned)nt);
-        for (int k = 0; k < ninit; ++k) serve_push(sp, __ldcg(sp.initlist + base + k));
-      }
+    ninit = __shfl_sync(0xffffffffu, ninit, 0);
+    if (ninit >= 0) {
+      base = __shfl_sync(0xffffffffu, base, 0);
+      age = __shfl_sync(0xffffffffu, age, 0);
+      for (int k = lane; k < ninit; k += 32) serve_push(sp, __ldcg(sp.initlist + base + k), age);
       continue;
     }
-    if (pending) {
-      __threadfence();
-      atomicSub(&sp.sc->outstanding.v, pending);
-      pending = 0;
-    }
-    const unsigned outst = ptx::ld_relaxed_u32(&sp.sc->outstanding.v);
-    const uint64_t now = ptx::globaltimer();
-    if (outst != seen_out) {
-      seen_out = outst;
-      seen_at = now;
-    }
-    if (outst == 0 && ld_acquire_sys_u32(&sp.sc->stop.v) != 0 &&
-        ptx::ld_relaxed_u32(&sp.sc->inbox_head.v) == (unsigned)ld_acquire_sys_u32(&sp.sc->inbox_tail.v))
-      return -1;
-    if (outst != 0) {  // work outstanding but no task finished for the whole limit: a lost dependency
-      if (now - seen_at > (uint64_t)p.timeout_ns) {
-        set_error(p, HQR_ERR_TIMEOUT, -1);
-        return -1;
+    int leave = 0;
+    if (lane == 0) {
+      if (pending) {
+        __threadfence();
+        atomicSub(&sp.sc->outstanding.v, pending);
+        pending = 0;
       }
-    } else if (now - idle_since > kIdleExitNs) {
-      return -1;  // idle: leave; the host relaunches on new work
+      const unsigned outst = ptx::ld_relaxed_u32(&sp.sc->outstanding.v);
+      const uint64_t now = ptx::globaltimer();
+      if (outst != seen_out) {
+        seen_out = outst;
+        seen_at = now;
+      }
+      if (outst == 0 && ld_acquire_sys_u32(&sp.sc->stop.v) != 0 &&
+          ptx::ld_relaxed_u32(&sp.sc->inbox_head.v) == (unsigned)ld_acquire_sys_u32(&sp.sc->inbox_tail.v)) {
+        leave = 1;
+      } else if (outst != 0) {  // work outstanding but no task finished for the whole limit: a lost dependency
+        if (now - seen_at > (uint64_t)p.timeout_ns) {
+          set_error(p, HQR_ERR_TIMEOUT, -1);
+          leave = 1;
+        }
+      } else if (now - idle_since > kIdleExitNs) {
+        leave = 1;  // idle: leave; the host relaunches on new work
+      }
     }
+    if (__shfl_sync(0xffffffffu, leave, 0)) return -1;
     __nanosleep(sleep_ns);
     if (sleep_ns < 4096) sleep_ns *= 2;
   }
@@ -1358,7 +1440,10 @@ __global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_serve(ServeParams sp) {
   tc::Phases tph;
   unsigned pending = 0;
   while (true) {
-    if (threadIdx.x == 0) sh.task = serve_pop(sp, pending);
+    if (threadIdx.x < 32) {
+      const int v = serve_pop(sp, pending);
+      if (threadIdx.x == 0) sh.task = v;
+    }
     __syncthreads();
     const int tid = sh.task;
     if (tid < 0) break;
@@ -1382,9 +1467,12 @@ __global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_serve(ServeParams sp) {
     if (threadIdx.x < 32) {  // warp 0 releases the successors, 32 at a time
       ptx::fence_proxy_async();
       __threadfence();
-      for (int e = t.succ_begin + (int)threadIdx.x; e < t.succ_end; e += 32) {
-        const int s = __ldcg(p.succ + e);
-        if (atomicSub(&p.indeg[s], 1) == 1) serve_push(sp, s);
+      if (t.succ_end > t.succ_begin) {
+        const int age = __shfl_sync(0xffffffffu, threadIdx.x == 0 ? age_class(sp, t.pid) : 0, 0);
+        for (int e = t.succ_begin + (int)threadIdx.x; e < t.succ_end; e += 32) {
+          const int s = __ldcg(p.succ + e);
+          if (atomicSub(&p.indeg[s], 1) == 1) serve_push(sp, s, age);
+        }
       }
     }
     if (threadIdx.x == 0) {
@@ -1392,6 +1480,7 @@ __global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_serve(ServeParams sp) {
         __threadfence_system();
         sp.comp[t.pid] = __ldcg(sp.req_seq + t.pid);
         __threadfence_system();
+        atomicAdd(&sp.sc->finished.v, 1u);  // later requests move up an age rank
       }
       if (++pending >= 32) {  // keep the outstanding count current for the watchdogs
         __threadfence();

@@ -56,6 +56,15 @@ struct DevGraph {
   }
 };
 
+// Setup copies and fills go through the legacy default stream, while the
+// kernels may run on any stream, non-blocking ones (and the server's own)
+// included, which that stream does not order: setup waits for it before
+// anything is launched.
+int setup_done() {
+  CK(cudaStreamSynchronize(cudaStreamLegacy));
+  return HQR_SUCCESS;
+}
+
 int upload_graph(const Graph &g, DevGraph &d) {
   const int nt = (int)g.tasks.size();
   d.ntasks = nt;
@@ -79,7 +88,7 @@ int upload_graph(const Graph &g, DevGraph &d) {
   CK(cudaMemcpy(d.indeg0, g.indeg.data(), sizeof(int) * nt, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(d.slots0, slots.data(), sizeof(int) * slots.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(d.ctl0, &ctl, sizeof(Ctl), cudaMemcpyHostToDevice));
-  return HQR_SUCCESS;
+  return setup_done();
 }
 
 // Tile-major packing of a column-major matrix, zero padded to whole tiles.
@@ -258,11 +267,22 @@ int eff_ib(int prec, int nb, int ib) { return use_tc(prec, nb) ? nb : ib; }
 
 // Elements of one T record (the T factor; tensor-core tiles add the split
 // operand images of their updates).
-size_t t_record(int prec, int nb, int ib) { return use_tc(prec, nb) ? (size_t)tc::T_RECORD : (size_t)ib * nb; }
+size_t t_record(int prec, int nb, int ib, bool t32 = true) {
+  if (!use_tc(prec, nb)) return (size_t)ib * nb;
+  return t32 ? (size_t)tc::T_RECORD : (size_t)tc::T_RECORD_IMG;
+}
+
+// Least-squares problems (plans, server) apply only Q^T: their tensor-core T
+// records leave out the FP32 T.
+void drop_t32(int prec, Problem &P) {
+  P.t32 = 0;
+  P.tstr = (int)t_record(prec, P.nb, P.ib, false);
+}
 
 void choose_widths(int prec, int nb, int ib, Problem &P) {
   P.wb = std::min(16, nb);
   P.tc = use_tc(prec, nb) ? 1 : 0;
+  P.t32 = 1;
   P.tstr = (int)t_record(prec, nb, ib);
   if (P.tc) {
     P.w = tc::WMAX;
@@ -372,7 +392,7 @@ int push_problem(hqr_factors *F) {
   F->prob.B = F->dBw;
   if (!F->dprob) CK(cudaMalloc(&F->dprob, sizeof(Problem)));
   CK(cudaMemcpy(F->dprob, &F->prob, sizeof(Problem), cudaMemcpyHostToDevice));
-  return HQR_SUCCESS;
+  return setup_done();
 }
 
 }  // namespace
@@ -545,9 +565,9 @@ int hqr_get_t(const hqr_factors *F, void *dT, void *stream) {
   const size_t stride = t_record(F->prec, F->nb, F->ib), nrec = (size_t)F->m * F->n * 2;
   if (stride == rec)
     CK(cudaMemcpyAsync(dT, F->dT, es * rec * nrec, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
-  else  // the T factor is the first part of each record
-    CK(cudaMemcpy2DAsync(dT, es * rec, F->dT, es * stride, es * rec, nrec, cudaMemcpyDeviceToDevice,
-                         (cudaStream_t)stream));
+  else  // tensor-core records: the T factor follows the split images
+    CK(cudaMemcpy2DAsync(dT, es * rec, (const unsigned char *)F->dT + tc::REC_T32, es * stride, es * rec, nrec,
+                         cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
   return HQR_SUCCESS;
 }
 
@@ -734,6 +754,7 @@ int hqr_debug_block_task(hqr_factors *F, int64_t task, int extra) {
   }
   const int v = F->debug_base + extra;
   CK(cudaMemcpy(F->fg.indeg0 + task, &v, sizeof(int), cudaMemcpyHostToDevice));
+  if (setup_done()) return HQR_ERR_CUDA;
   if (extra == 0) {
     F->debug_task = -1;
     F->debug_base = -1;
@@ -962,6 +983,7 @@ int hqr_ls_plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_
     pb.m = (pr.M + c.nb - 1) / c.nb;
     pb.n = (pr.N + c.nb - 1) / c.nb;
     choose_widths(prec, c.nb, c.ib, pb);
+    drop_t32(prec, pb);
     pb.wb = 1;
     pb.M = pr.M;
     pb.N = pr.N;
@@ -972,7 +994,7 @@ int hqr_ls_plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_
     off_tiles[q] = arena_elems;
     arena_elems += (Mp * Np + 3) & ~(size_t)3;
     off_t[q] = arena_elems;
-    arena_elems += ((size_t)pb.m * pb.n * 2 * t_record(prec, c.nb, c.ib) + 3) & ~(size_t)3;
+    arena_elems += ((size_t)pb.m * pb.n * 2 * t_record(prec, c.nb, c.ib, false) + 3) & ~(size_t)3;
     off_b[q] = arena_elems;
     arena_elems += (Mp + 3) & ~(size_t)3;
     off_vec[q] = vec_elems;
@@ -1452,7 +1474,7 @@ int hqr_server_create(const hqr_server_opts *o, hqr_server **out) {
   const size_t TP = (size_t)o->task_pool, EP = (size_t)o->edge_pool, L = (size_t)o->max_live;
   S->ring_cap = (int)pow2_at_least(TP / kShards + L + 64);
   S->inbox_cap = (int)pow2_at_least(2 * L);
-  const size_t nslots = (size_t)kNumQueues * kShards * S->ring_cap;
+  const size_t nslots = (size_t)kServeQueues * kShards * S->ring_cap;
   int st = HQR_SUCCESS;
   if (!cuda_ok(cudaMalloc(&S->tasks, sizeof(Task) * TP), "server tasks") ||
       !cuda_ok(cudaMalloc(&S->succ, sizeof(int) * EP), "server succ") ||
@@ -1477,6 +1499,7 @@ int hqr_server_create(const hqr_server_opts *o, hqr_server **out) {
       !cuda_ok(cudaStreamCreateWithFlags(&S->kstream, cudaStreamNonBlocking), "stream") ||
       !cuda_ok(cudaStreamCreateWithFlags(&S->cstream, cudaStreamNonBlocking), "stream"))
     st = HQR_ERR_NOMEM;
+  if (!st && setup_done()) st = HQR_ERR_CUDA;  // the fills above land before the kernel or a submission runs
   if (st) {
     server_release(S);
     delete S;
@@ -1569,6 +1592,7 @@ int hqr_server_submit(hqr_server *S, const hqr_ls_problem_t *pr, int64_t *ticket
   pb.m = (pr->M + c.nb - 1) / c.nb;
   pb.n = (pr->N + c.nb - 1) / c.nb;
   choose_widths(prec, c.nb, c.ib, pb);
+  drop_t32(prec, pb);
   pb.wb = 1;
   // graph of this shape and configuration (cached)
   std::vector<int> key = {pr->M, pr->N, c.nb, c.ib, c.a, c.p, c.low_tree, c.high_tree};
@@ -1592,7 +1616,7 @@ int hqr_server_submit(hqr_server *S, const hqr_ls_problem_t *pr, int64_t *ticket
   const size_t nt = cg.g.tasks.size(), ne = std::max<size_t>(cg.g.succ.size(), 1);
   const size_t Mp = (size_t)pb.m * c.nb, Np = (size_t)pb.n * c.nb, es = S->es;
   auto r256 = [](size_t b) { return (b + 255) / 256; };
-  const size_t a_tiles = r256(es * Mp * Np), a_t = r256(es * (size_t)pb.m * pb.n * 2 * t_record(prec, c.nb, c.ib)),
+  const size_t a_tiles = r256(es * Mp * Np), a_t = r256(es * (size_t)pb.m * pb.n * 2 * t_record(prec, c.nb, c.ib, false)),
                a_b = r256(es * Mp), a_r = r256(8 * Mp), a_g = r256(8 * Np),
                a_gp = r256(16 * (size_t)atr_chunks(pb.m) * Np), a_rp = r256(16 * (size_t)res_chunks(pb.n) * Mp),
                a_ri = r256(8 * (size_t)pb.n * c.nb * c.nb);
@@ -1720,6 +1744,19 @@ int hqr_server_counters(const hqr_server *S, uint32_t *out, int cap) {
   return HQR_SUCCESS;
 }
 
+int hqr_server_progress(const hqr_server *S, int64_t ticket, int *done, int *total) {
+  if (!S) return -1;
+  if (!done || !total) return -3;
+  for (size_t slot = 0; slot < S->live.size(); ++slot) {
+    const hqr_server::Live &lv = S->live[slot];
+    if (!lv.live || lv.seq != ticket) continue;
+    CK(cudaMemcpy(done, S->req_done + slot, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(total, S->req_total + slot, sizeof(int), cudaMemcpyDeviceToHost));
+    return HQR_SUCCESS;
+  }
+  return HQR_ERR_INTERNAL;
+}
+
 int hqr_server_stats(const hqr_server *S, int64_t *submitted, int64_t *completed, int *live, size_t *bytes_in_use) {
   if (!S) return -1;
   if (submitted) *submitted = S->submitted;
@@ -1745,6 +1782,7 @@ int hqr_server_stop(hqr_server *S) {
   CK(cudaMemcpy(&stl, &S->ctl->status, sizeof(CtlLine), cudaMemcpyDeviceToHost));
   const unsigned zero = 0;  // a later start serves again
   CK(cudaMemcpy(&S->sc->stop.v, &zero, sizeof(unsigned), cudaMemcpyHostToDevice));
+  if (setup_done()) return HQR_ERR_CUDA;
   return (int)stl.v;
 }
 

@@ -70,17 +70,21 @@ constexpr uint32_t OFF_BOT = OFF_TOP + SLAB_BYTES;                 // C_b slab
 constexpr uint32_t SMEM_BYTES = OFF_BOT + SLAB_BYTES;              // 219136
 
 // Per panel tile (i, k, GEQRT or kill) the panel task stores a "T record":
-// the FP32 factor T (128 x 128, column-major, zeros below the diagonal),
-// then the three update operands already split into BF16 pieces in the
-// chunk layout of the shared-memory stages (chunk c: pieces 0, 1, 2 of
-// 128 x 32 elements), so that an update stages each chunk with one bulk
-// copy: T^T (reflector, reflector'), V^T (reflector, row), V (row,
-// reflector), with V masked to its structure (unit lower, upper, full).
+// the three update operands already split into BF16 pieces in the chunk
+// layout of the shared-memory stages (chunk c: pieces 0, 1, 2 of 128 x 32
+// elements), so that an update stages each chunk with one bulk copy: T^T
+// (reflector, reflector'), V^T (reflector, row), V (row, reflector), with V
+// masked to its structure (unit lower, upper, full); then, for
+// factorizations that keep it (apply Q, read T), the FP32 factor T (128 x
+// 128, column-major, zeros below the diagonal). Least-squares problems only
+// apply Q^T and leave it out.
 constexpr uint32_t IMG_BYTES = NCH * NP * A_PC;                  // 98304
-constexpr uint32_t REC_TB = NB * NB * 4;                         // byte offsets in a record
+constexpr uint32_t REC_TB = 0;                                   // byte offsets in a record
 constexpr uint32_t REC_VA = REC_TB + IMG_BYTES;
 constexpr uint32_t REC_VC = REC_VA + IMG_BYTES;
-constexpr uint32_t T_RECORD = (REC_VC + IMG_BYTES) / 4;          // floats per record: 90112
+constexpr uint32_t REC_T32 = REC_VC + IMG_BYTES;
+constexpr uint32_t T_RECORD_IMG = REC_T32 / 4;                   // floats per record without T: 73728
+constexpr uint32_t T_RECORD = (REC_T32 + NB * NB * 4) / 4;       // with T: 90112
 
 // Per-CTA state of the tensor path (in the kernel's static shared memory).
 struct State {
@@ -527,7 +531,7 @@ __device__ bool update(int mode, int trans, const float *V, const float *Trec, f
   float *top = reinterpret_cast<float *>(smem + OFF_TOP), *bot = reinterpret_cast<float *>(smem + OFF_BOT);
   const Src sva{V, NB, 0, NB, mode == 0 ? -1 : mode, 0};  // V^T (reflector, row): image REC_VA
   const Src scb{bot, NB, 0, cw, -1, 1};                    // C_b^T (column, row) from the staged slab
-  const Src stt{Trec, NB, 1, NB, -1, 0};                   // T (Q): gathered; T^T (Q^T): image REC_TB
+  const Src stt{Trec + REC_T32 / 4, NB, 1, NB, -1, 0};     // T (Q): gathered; T^T (Q^T): image REC_TB
   const Src svc{V, NB, 1, NB, mode == 0 ? -1 : mode, 0};  // V (row, reflector): image REC_VC
   fence_async_smem();  // earlier generic accesses of the stages and slabs before the bulk copies
   __syncthreads();
@@ -646,7 +650,7 @@ __device__ void write_image(unsigned char *dst, F value) {
   }
 }
 
-__device__ void panel(int mode, float *X, float *Rg, float *Tg, unsigned char *smem_raw) {
+__device__ void panel(int mode, float *X, float *Rg, float *Tg, bool with_t32, unsigned char *smem_raw) {
   PanelSmem &sm = *reinterpret_cast<PanelSmem *>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int rb = warp * 16;  // first row of this warp
@@ -956,12 +960,13 @@ __device__ void panel(int mode, float *X, float *Rg, float *Tg, unsigned char *s
     }
     __syncthreads();
   }
-  // ---- write T (zeros below the diagonal) and its split image T^T
-  for (int e = tid; e < NB * NB; e += NTHR) {
-    const int c = e >> 7, r = e & 127;
-    __stcg(Tg + e, r <= c ? sm.tg[r + c * LDT] : 0.f);
-  }
+  // ---- write T (zeros below the diagonal, if kept) and its split image T^T
   unsigned char *rec = reinterpret_cast<unsigned char *>(Tg);
+  if (with_t32)
+    for (int e = tid; e < NB * NB; e += NTHR) {
+      const int c = e >> 7, r = e & 127;
+      __stcg(reinterpret_cast<float *>(rec + REC_T32) + e, r <= c ? sm.tg[r + c * LDT] : 0.f);
+    }
   write_image(rec + REC_TB, [&](int m, int k) { return k <= m ? sm.tg[k + m * LDT] : 0.f; });
   __syncthreads();
   // ---- V / R, and the split images V^T and V (masked to V's structure)

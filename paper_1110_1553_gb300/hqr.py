@@ -32,7 +32,7 @@ EXPORTS = ["hqr_elim_list", "hqr_validate_list", "hqr_geqrf", "hqr_refactor", "h
            "hqr_gels", "hqr_geqrf_r_noalloc", "hqr_ls_plan_create", "hqr_ls_plan_run",
            "hqr_ls_plan_capture", "hqr_ls_plan_status", "hqr_ls_plan_info", "hqr_ls_plan_config",
            "hqr_ls_plan_free", "hqr_ls_plan_trace", "hqr_set_tuning", "hqr_autotune", "hqr_server_create", "hqr_server_start",
-           "hqr_server_submit", "hqr_server_poll", "hqr_server_stats", "hqr_server_counters", "hqr_server_stop", "hqr_server_free", "hqr_debug_block_task", "hqr_factors_free", "hqr_set_timeout_ms", "hqr_strerror", "hqr_last_error", "hqr_set_slab_widths",
+           "hqr_server_submit", "hqr_server_poll", "hqr_server_stats", "hqr_server_progress", "hqr_server_counters", "hqr_server_stop", "hqr_server_free", "hqr_debug_block_task", "hqr_factors_free", "hqr_set_timeout_ms", "hqr_strerror", "hqr_last_error", "hqr_set_slab_widths",
            "hqr_set_priority_policy",
            "hqr_last_launches"]
 
@@ -101,6 +101,7 @@ def load(build_if_missing=False):
     lib.hqr_server_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32),
                                      ctypes.POINTER(sz)]
     lib.hqr_server_counters.argtypes = [vp, vp, i32]
+    lib.hqr_server_progress.argtypes = [vp, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.hqr_server_stop.argtypes = [vp]
     lib.hqr_server_free.argtypes = [vp]
     lib.hqr_server_free.restype = None
@@ -553,6 +554,13 @@ class Server:
         _check(load().hqr_server_stats(self._h, ctypes.byref(s), ctypes.byref(c), ctypes.byref(lv), ctypes.byref(by)),
                "hqr_server_stats")
         return {"submitted": s.value, "completed": c.value, "live": lv.value, "bytes_in_use": by.value}
+
+    def progress(self, ticket):
+        """(tasks completed, tasks in total) of a live request."""
+        d, t = ctypes.c_int(0), ctypes.c_int(0)
+        _check(load().hqr_server_progress(self._h, ctypes.c_int64(ticket), ctypes.byref(d), ctypes.byref(t)),
+               "hqr_server_progress")
+        return d.value, t.value
 
     def counters(self):
         out = (ctypes.c_uint32 * 5)()

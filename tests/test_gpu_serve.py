@@ -74,6 +74,61 @@ def test_server_mix_equals_alone_and_oracle(tensor):
         assert torch.equal(x1, x), q
 
 
+def test_server_burst_runs_oldest_first():
+    """A burst of equal requests admitted at once, more than the GPU runs
+    side by side: the server runs the oldest requests first (age classes over
+    the critical-path classes) and fills idle CTAs with newer ones, so
+    completion times rise with submission order instead of every request
+    sharing the GPU to the end. Results do not depend on the order (bitwise
+    equal to a plan of the same problem)."""
+    n = 48
+    probs = [problem(4096, 512, 400 + q) for q in range(n)]
+    srv = hqr.Server(torch.float32, refine_iters=5, max_live=64, hbm_budget=8 << 30)
+    srv.start()
+    try:
+        tickets = [srv.submit(*p[2:]) for p in probs]
+        assert all(t is not None for t in tickets)
+        when, t0 = {}, time.perf_counter()
+        while len(when) < n and time.perf_counter() - t0 < 60:
+            for t in srv.poll():
+                when[t] = time.perf_counter() - t0
+    finally:
+        srv.stop()
+    assert len(when) == n
+    done_at = np.array([when[t] for t in tickets])
+    rho = np.corrcoef(np.arange(n), done_at)[0, 1]
+    assert rho > 0.5 and done_at[:8].mean() < done_at[-8:].mean(), (rho, done_at)
+    for q in (0, n - 1):
+        A, b, Ad, bd, x = probs[q]
+        x1 = torch.zeros_like(x)
+        plan = hqr.LSPlan([(Ad, bd, x1)], refine_iters=5)
+        plan.run()
+        assert plan.status() == 0
+        assert torch.equal(x1, x), q
+
+
+def test_server_fresh_servers_back_to_back():
+    """Servers created one after another, each fed a burst at once: the
+    device fills of a new server land before its kernel or any submission
+    runs (every request completes, inbox counters match)."""
+    probs = [problem(1024, 256, 500 + q) for q in range(16)]
+    for rep in range(3):
+        srv = hqr.Server(torch.float32, refine_iters=2, max_live=32, hbm_budget=4 << 30, task_pool=4 << 20)
+        srv.start()
+        try:
+            tickets = [srv.submit(*p[2:]) for p in probs]
+            assert all(t is not None for t in tickets)
+            done, t0 = set(), time.time()
+            while len(done) < len(tickets) and time.time() - t0 < 30:
+                done.update(srv.poll())
+            assert done == set(tickets), rep
+            c = srv.counters()
+            assert c["inbox_claimed"] == c["inbox_posted"] == len(tickets), c
+        finally:
+            srv.stop()
+        del srv
+
+
 def test_server_budget_admission():
     srv = hqr.Server(torch.float32, refine_iters=2, max_live=2, hbm_budget=4 << 20)
     srv.start()
