@@ -756,29 +756,61 @@ __device__ __forceinline__ void dot2_merge(double &s1, double &c1, double s2, do
 }
 
 // sum over q = q0, q0 + step, ... < q1 of M(q, o) g_q (transposed) or M(o, q) g_q, M column-major
-// with leading dimension ld, in FP64 with eight independent chains. M is final for the whole launch
-// (R tiles after their factorization, the inverses after their TRINV task), so its loads may use L1.
+// with leading dimension ld (in shared memory when staged, else global: M is final for the whole
+// launch, R tiles after their factorization, the inverses after their TRINV task), in FP64 with
+// four chains. In the transposed walk every thread reads its own column, so each starts at its
+// own offset (the lane index, cyclically): the lanes of a warp then read different rows and
+// shared-memory banks. The order of the terms depends only on (o, q0, q1, step), never on where
+// M is, so staged and unstaged runs give the same bits.
 template <typename M>
-__device__ __forceinline__ double tile_dot(const M *__restrict__ m, int ld, bool transposed, int o, int q0, int q1,
-                                           int step, const double *g) {
-  const M *base = transposed ? m + (size_t)o * ld : m + o;
-  const size_t qs = transposed ? 1 : (size_t)ld;
-  double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  int q = q0;
-  for (; q + 7 * step < q1; q += 8 * step) {  // eight loads in flight per thread
-    double v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = (double)base[(size_t)(q + u * step) * qs];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) a[u] = fma(v[u], g[q + u * step], a[u]);
+__device__ __forceinline__ double tile_dot(const M *m, int ld, bool transposed, int o, int q0, int q1, int step,
+                                           const double *g) {
+  const int K = q1 > q0 ? (q1 - q0 + step - 1) / step : 0;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  if (transposed) {
+    const M *col = m + (size_t)o * ld;
+    int k = K > 0 ? (o & 31) % K : 0;
+    auto term = [&](double acc) {
+      const int q = q0 + k * step;
+      acc = fma((double)col[q], g[q], acc);
+      if (++k == K) k = 0;
+      return acc;
+    };
+    int c = 0;
+    for (; c + 3 < K; c += 4) {
+      a0 = term(a0);
+      a1 = term(a1);
+      a2 = term(a2);
+      a3 = term(a3);
+    }
+    for (; c < K; ++c) a0 = term(a0);
+  } else {
+    const M *row = m + o;
+    const size_t qs = (size_t)step * ld;
+    const M *p = row + (size_t)q0 * ld;
+    const double *gq = g + q0;
+    int c = 0;
+    for (; c + 3 < K; c += 4, p += 4 * qs, gq += 4 * step) {
+      a0 = fma((double)p[0], gq[0], a0);
+      a1 = fma((double)p[qs], gq[step], a1);
+      a2 = fma((double)p[2 * qs], gq[2 * step], a2);
+      a3 = fma((double)p[3 * qs], gq[3 * step], a3);
+    }
+    for (; c < K; ++c, p += qs, gq += step) a0 = fma((double)p[0], gq[0], a0);
   }
-  for (; q < q1; q += step) a[0] = fma((double)base[(size_t)q * qs], g[q], a[0]);
-  return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+  return (a0 + a1) + (a2 + a3);
 }
+
+__device__ __forceinline__ bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
+// Byte offset of the tiles a triangular-solve step stages in shared memory
+// (after g_i and the partial sums: nb + NT doubles at most).
+constexpr uint32_t kVecStageOff = 4096;
+static_assert((128 + NT) * 8 <= kVecStageOff, "vector scratch overlaps the staged tiles");
 
 template <typename Real>
 __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<Real> &g, const Task &t,
-                            double *sm) {
+                            double *sm, Shared<Real> &sh, uint32_t &phase) {
   const int nb = g.nb, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const Real *A0 = (const Real *)P.A0;
   switch (t.op) {
@@ -950,8 +982,44 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
       double *go = P.g + (size_t)j * nb;
       double *gs = sm;         // g_i
       double *part = sm + nb;  // partial sums, (NT / nb) x nb
+      // the step's tiles (R(i, j) or R(j, i); the FP64 inverse it applies) are staged in shared
+      // memory with one bulk copy each, issued before anything else, where the launch has room
+      const Real *rt = diag ? nullptr : (transposed ? g.tile(i, j) : g.tile(j, i));
+      const double *xt = diag ? P.rinv + (size_t)i * nb * nb : (t.tgt ? P.rinv + (size_t)j * nb * nb : nullptr);
+      const uint32_t rbytes = (uint32_t)(nb * nb * sizeof(Real)), xbytes = (uint32_t)(nb * nb * sizeof(double));
+      unsigned char *stg = reinterpret_cast<unsigned char *>(sm) + kVecStageOff;
+      const uint32_t room = ptx::dynamic_smem_bytes();
+      const bool st_r = rt && aligned16(rt) && kVecStageOff + rbytes <= room;
+      const uint32_t xoff = st_r ? rbytes : 0;
+      const bool st_x = xt && aligned16(xt) && kVecStageOff + xoff + xbytes <= room;
+      const Real *mr = st_r ? reinterpret_cast<const Real *>(stg) : rt;
+      const double *mx = st_x ? reinterpret_cast<const double *>(stg + xoff) : xt;
+      if ((st_r || st_x) && threadIdx.x == 0) {
+        ptx::fence_proxy_async();
+        ptx::mbar_arrive_expect_tx(&sh.bar, (st_r ? rbytes : 0) + (st_x ? xbytes : 0));
+        if (st_r) ptx::bulk_g2s(stg, rt, rbytes, &sh.bar);
+        if (st_x) ptx::bulk_g2s(stg + xoff, xt, xbytes, &sh.bar);
+      }
       for (int k = tid; k < nb; k += NT) gs[k] = k < n_i ? __ldcg(gi + k) : 0.0;
+      if (st_r || st_x) {  // bounded wait for the staged tiles
+        if (!ptx::mbar_try_wait(&sh.bar, phase)) {
+          const uint64_t t0 = ptx::globaltimer();
+          while (!ptx::mbar_try_wait(&sh.bar, phase)) {
+            if (ptx::globaltimer() - t0 > (uint64_t)p.timeout_ns) {
+              sh.abort = 1;
+              break;
+            }
+          }
+        }
+        phase ^= 1u;
+      }
       __syncthreads();
+      if (sh.abort) {
+        if (tid == 0) set_error(p, HQR_ERR_TIMEOUT, -1);
+        break;
+      }
+      // every thread owns one output and 1/H of its sum (no FP64 cross-lane reductions: a
+      // warp-wide FP64 operation takes 16 cycles of the FP64 pipe)
       const int o = tid % nb, h = tid / nb, H = NT / nb;  // output index, part of the sum
       double acc = 0.0;
       if (o < n_out && h < H) {
@@ -960,9 +1028,9 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
         const int qlo = (diag && !transposed) ? o : 0;
         const int qhi = (diag && transposed) ? o + 1 : n_i;
         if (diag)
-          acc = tile_dot(P.rinv + (size_t)i * nb * nb, nb, transposed, o, qlo + h, qhi, H, gs);
+          acc = tile_dot(mx, nb, transposed, o, qlo + h, qhi, H, gs);
         else
-          acc = tile_dot(transposed ? g.tile(i, j) : g.tile(j, i), nb, transposed, o, qlo + h, qhi, H, gs);
+          acc = tile_dot(mr, nb, transposed, o, qlo + h, qhi, H, gs);
       }
       if (h < H) part[h * nb + o] = acc;
       __syncthreads();
@@ -983,7 +1051,7 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
         acc = 0.0;
         if (o < n_out && h < H) {
           const int qlo = transposed ? 0 : o, qhi = transposed ? o + 1 : n_out;
-          acc = tile_dot(P.rinv + (size_t)j * nb * nb, nb, transposed, o, qlo + h, qhi, H, gs);
+          acc = tile_dot(mx, nb, transposed, o, qlo + h, qhi, H, gs);
         }
         if (h < H) part[h * nb + o] = acc;
         __syncthreads();
@@ -1231,7 +1299,7 @@ __global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_sched(EngineParams p) {
     else if (t.op <= OP_TTMQR)
       task_update(p, g, t, sh, dyn, phase);
     else
-      task_vector(p, p.probs[t.pid], g, t, reinterpret_cast<double *>(dyn_raw));
+      task_vector(p, p.probs[t.pid], g, t, reinterpret_cast<double *>(dyn_raw), sh, phase);
     __syncthreads();
     if (threadIdx.x < 32) {  // warp 0 releases the successors, 32 at a time (most critical first)
       if (threadIdx.x == 0 && p.trace) {
@@ -1462,7 +1530,7 @@ __global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_serve(ServeParams sp) {
     else if (t.op <= OP_TTMQR)
       task_update(p, g, t, sh, dyn, phase);
     else
-      task_vector(p, P, g, t, reinterpret_cast<double *>(dyn_raw));
+      task_vector(p, P, g, t, reinterpret_cast<double *>(dyn_raw), sh, phase);
     __syncthreads();
     if (threadIdx.x < 32) {  // warp 0 releases the successors, 32 at a time
       ptx::fence_proxy_async();
