@@ -30,7 +30,16 @@ WORKLOAD = dict(M=131072, N=2048, nb=256, ib=32, a=4, p=16, low="greedy", high="
 WORKLOAD_NAME = "hqr_fp64_tall_skinny_131072x2048_nb256_ib32_a4_p16_greedy_fibonacci"
 SAMPLE_M = 4096  # oracle sample: the first 16 tile rows, all 2048 columns
 PROFILE = os.path.join(ROOT, "profiles", "hqr_sched_fp64_tall_skinny.md")
-ENGINE_SRC = os.path.join(ROOT, "paper_1110_1553_gb300", "csrc", "engine.cuh")
+# the task kernels are compiled from these headers; the committed DRAM counters
+# hold for the kernels built from the hashed versions only
+KERNEL_SRCS = [os.path.join(ROOT, "paper_1110_1553_gb300", "csrc", f) for f in ("engine.cuh", "ptx.cuh", "tc.cuh")]
+
+
+def kernel_sources_sha256():
+    h = hashlib.sha256()
+    for f in KERNEL_SRCS:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
 
 
 def qr_flops(M, N):
@@ -167,11 +176,11 @@ def ncu_traffic():
     if not os.path.exists(PROFILE):
         return None, None
     txt = open(PROFILE).read()
-    m_sha = re.search(r"engine_sha256:\s*([0-9a-f]{64})", txt)
+    m_sha = re.search(r"kernel_sources_sha256:\s*([0-9a-f]{64})", txt)
     m_b = re.search(r"dram_bytes_per_launch_full:\s*([0-9.eE+]+)", txt)
     if not m_sha or not m_b:
         return None, None
-    cur = hashlib.sha256(open(ENGINE_SRC, "rb").read()).hexdigest()
+    cur = kernel_sources_sha256()
     if cur != m_sha.group(1):
         return None, "stale"
     return float(m_b.group(1)), None
