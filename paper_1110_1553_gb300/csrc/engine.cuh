@@ -433,25 +433,28 @@ __device__ void gemm_nn_sub(Real *Cm, int ldc, const Real *V, int ldv, const Rea
   __syncthreads();
 }
 
-// W <- T^T W (trans) or T W, T an ib x ib upper triangle (ld ib).
+// W <- T^T W (trans) or T W in place, T an ib x ib upper triangle (ld ib), ib <= 32: each warp takes
+// 32 / ib columns of W at a time, lane group g holding column j0 + g (lane i of the group: W(i, j))
+// and forming its outputs from the group's values by shuffles. Lane i walks the terms from its own
+// offset, so the lanes of a group read T from different shared-memory banks.
 template <typename Real>
-__device__ void trmm_tw(Real *W, int ldw, const Real *Tq, int ib, int Nj, int trans, Real *tmp) {
-  const int O = ib * Nj;
-  for (int o = threadIdx.x; o < O; o += NT) {
-    const int i = o % ib, j = o / ib;
-    const Real *w = W + (size_t)j * ldw;
+__device__ void trmm_tw(Real *W, int ldw, const Real *Tq, int ib, int Nj, int trans) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int G = 32 / ib, grp = lane / ib, i = lane - grp * ib;
+  for (int j0 = warp * G; j0 < Nj; j0 += NWARP * G) {
+    const int j = j0 + grp;
+    const bool on = grp < G && j < Nj;
+    Real *w = W + (size_t)j * ldw;
+    const Real wl = on ? w[i] : Real(0);
     Real s = 0;
-    if (trans) {
-      for (int l = 0; l <= i; ++l) s = fma(Tq[l + (size_t)i * ib], w[l], s);
-    } else {
-      for (int l = i; l < ib; ++l) s = fma(Tq[i + (size_t)l * ib], w[l], s);
+    for (int u = 0; u < ib; ++u) {
+      int l = i + u;
+      if (l >= ib) l -= ib;
+      const Real wv = __shfl_sync(0xffffffffu, wl, (grp * ib + l) & 31);
+      if (on && (trans ? l <= i : l >= i)) s = fma(trans ? Tq[l + (size_t)i * ib] : Tq[i + (size_t)l * ib], wv, s);
     }
-    tmp[o] = s;
-  }
-  __syncthreads();
-  for (int o = threadIdx.x; o < O; o += NT) {
-    const int i = o % ib, j = o / ib;
-    W[i + (size_t)j * ldw] = tmp[o];
+    __syncwarp();
+    if (on) w[i] = s;
   }
   __syncthreads();
 }
@@ -636,7 +639,7 @@ __device__ void task_update(const EngineParams &p, const Geo<Real> &g, const Tas
       shape_v(Vc, lds, L, VC, mode, c * VC, q0);
       gemm_tn(W + c * VC, ib, Vc, lds, Cb, lds, L, VC, cw, pair ? Ct + c * VC : nullptr, lds, scr);
     }
-    trmm_tw(W, ib, Tq, ib, cw, t.trans, scr);
+    trmm_tw(W, ib, Tq, ib, cw, t.trans);
     if (pair) sub_top(Ct, lds, W, ib, ib, cw);
     for (int c = 0; c < nchunk; ++c) {
       if (nchunk > 1) {
@@ -708,7 +711,7 @@ __device__ void task_panel(const EngineParams &p, const Geo<Real> &g, const Task
         Copy<Real> cp[1] = {{Cb, lds, XB + (size_t)c0 * nb + q0, nb, L, wc}};
         stage(p, sh, cp, 1, phase);
         gemm_tn(W, ib, P, lds, Cb, lds, L, ib, wc, (const Real *)nullptr, 0, scr);
-        trmm_tw(W, ib, Tq, ib, wc, 1, scr);
+        trmm_tw(W, ib, Tq, ib, wc, 1);
         gemm_nn_sub(Cb, lds, P, lds, W, ib, L, ib, wc);
         store_cols(XB + (size_t)c0 * nb + q0, nb, Cb, lds, L, wc, 0, 0);
       } else {
@@ -716,7 +719,7 @@ __device__ void task_panel(const EngineParams &p, const Geo<Real> &g, const Task
                             {Cb, lds, XB + (size_t)c0 * nb, nb, L, wc}};
         stage(p, sh, cp, 2, phase);
         gemm_tn(W, ib, P, lds, Cb, lds, L, ib, wc, (const Real *)Ct, ldt, scr);
-        trmm_tw(W, ib, Tq, ib, wc, 1, scr);
+        trmm_tw(W, ib, Tq, ib, wc, 1);
         sub_top(Ct, ldt, W, ib, ib, wc);
         gemm_nn_sub(Cb, lds, P, lds, W, ib, L, ib, wc);
         store_cols(XR + (size_t)c0 * nb + q0, nb, Ct, ldt, ib, wc, 0, 0);
@@ -1578,8 +1581,8 @@ inline size_t engine_smem_bytes(int nb, int ib, int w, int wt, int vc) {
   const int lds = nb + smem_pad<Real>(), ldt = ib + smem_pad<Real>();
   // scratch: FP32 GEMMs keep up to 4 K-groups of partial output blocks
   const size_t fac = sizeof(Real) == 4 ? 4 : 1;
-  const size_t scr_u = std::max<size_t>({(size_t)NT, (size_t)ib * w, fac * (((vc + 3) / 4) * ((w + 3) / 4) * 16)});
-  const size_t scr_p = std::max<size_t>({(size_t)NT, (size_t)ib * wt, fac * (((ib + 3) / 4) * ((wt + 3) / 4) * 16),
+  const size_t scr_u = std::max<size_t>({(size_t)NT, fac * (((vc + 3) / 4) * ((w + 3) / 4) * 16)});
+  const size_t scr_p = std::max<size_t>({(size_t)NT, fac * (((ib + 3) / 4) * ((wt + 3) / 4) * 16),
                                          fac * (((ib + 3) / 4) * ((ib + 3) / 4) * 16)});
   const size_t upd = (size_t)lds * (2 * w + vc) + (size_t)ib * ib + (size_t)ib * w + scr_u;
   const size_t cbg = (size_t)(lds * wt > ib * ib ? lds * wt : ib * ib);
