@@ -118,68 +118,98 @@ Task make_task(int op, int prio, int i, int r, int k, int j, int c0, int cw, int
   t.r = r;
   t.k = k;
   t.j = j;
-  t.c0 = c0;
-  t.cw = cw;
+  t.c0 = (int16_t)c0;
+  t.cw = (int16_t)cw;
+  t.blk = 0;
+  t.pad_ = 0;
   t.succ_begin = t.succ_end = 0;
   return t;
 }
 
-}  // namespace
+// Storage pieces of the tile workspace for dependency tracking: for every
+// tile (i, j) and column slab s (w columns), its upper part (rows <= column:
+// R, or TTQRT's V) and its strict lower part (GEQRT's V). Updates write whole
+// slabs; a panel's V and R are parts of all its slabs (or of one block's).
+struct TilePieces {
+  int m, S;
+  size_t count(int n) const { return (size_t)m * n * S * 2; }
+  size_t u(int i, int j, int s) const { return (((size_t)j * m + i) * S + s) * 2; }
+  size_t l(int i, int j, int s) const { return u(i, j, s) + 1; }
+};
 
-Graph build_factor_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int w, int pid) {
-  const int S = (nb + w - 1) / w;  // column slabs per tile
-  const size_t per_tile = (size_t)S + 2;
-  // storage pieces of tile (i, j): S column slabs, then U (upper triangle
-  // with the diagonal: R, or TTQRT's V2) and L (strict lower: GEQRT's V)
-  auto slab = [&](int i, int j, int s) { return ((size_t)j * m + i) * per_tile + (size_t)s; };
-  auto upart = [&](int i, int j) { return ((size_t)j * m + i) * per_tile + (size_t)S; };
-  auto lpart = [&](int i, int j) { return ((size_t)j * m + i) * per_tile + (size_t)S + 1; };
-  Builder b((size_t)m * n * per_tile);
+// The factorization part of a graph (panels and their updates, Alg. 2).
+void add_factor_tasks(Builder &b, const std::vector<PanelOp> &ops, const TilePieces &P, int n, int nb, int w,
+                      int pid, int split_ib) {
   Tracker &tr = b.tr();
   std::vector<int32_t> &d = b.deps();
+  const int S = P.S;
+  const bool split = split_ib > 0;
+  const int nq = split ? nb / split_ib : 1, spb = split ? split_ib / w : S;  // blocks, slabs per block
+  auto wr_u = [&](int i, int j, int s) { tr.write(P.u(i, j, s), d); };
+  auto wr_slab = [&](int i, int j, int s) {
+    tr.write(P.u(i, j, s), d);
+    tr.write(P.l(i, j, s), d);
+  };
   for (const PanelOp &o : ops) {
-    const int k = o.k;
-    if (o.kind == 0) {  // GEQRT(i, k) and UNMQR(i, k, j) for j > k
-      for (int s = 0; s < S; ++s) tr.write(slab(o.i, k, s), d);
-      tr.write(upart(o.i, k), d);
-      tr.write(lpart(o.i, k), d);
-      b.add(make_task(OP_GEQRT, 0, o.i, o.i, k, k, 0, nb, 1, 0, pid));
-      for (int j = k + 1; j < n; ++j)
-        for (int s = 0; s < S; ++s) {
-          tr.read(lpart(o.i, k), d);
-          tr.write(slab(o.i, j, s), d);
-          b.add(make_task(OP_UNMQR, j == k + 1 ? 1 : 2, o.i, o.i, k, j, s * w,
-                          std::min(w, nb - s * w), 1, 0, pid));
+    const int k = o.k, kind = o.kind;
+    const int pop = kind == 0 ? OP_GEQRT : (kind == 1 ? OP_TSQRT : OP_TTQRT);
+    const int uop = kind == 0 ? OP_UNMQR : (kind == 1 ? OP_TSMQR : OP_TTMQR);
+    // what the panel (or its block) writes in slabs [s0, s1) of column k
+    auto panel_writes = [&](int s0, int s1) {
+      for (int s = s0; s < s1; ++s) {
+        if (kind == 0) {
+          wr_slab(o.i, k, s);
+        } else if (kind == 1) {
+          wr_u(o.r, k, s);
+          wr_slab(o.i, k, s);
+        } else {
+          wr_u(o.r, k, s);
+          wr_u(o.i, k, s);
         }
-    } else if (o.kind == 1) {  // TSQRT(i, r, k), TSMQR(i, r, k, j)
-      tr.write(upart(o.r, k), d);
-      for (int s = 0; s < S; ++s) tr.write(slab(o.i, k, s), d);
-      tr.write(upart(o.i, k), d);
-      tr.write(lpart(o.i, k), d);
-      b.add(make_task(OP_TSQRT, 0, o.i, o.r, k, k, 0, nb, 1, 0, pid));
-      for (int j = k + 1; j < n; ++j)
-        for (int s = 0; s < S; ++s) {
-          tr.read(upart(o.i, k), d);
-          tr.read(lpart(o.i, k), d);
-          tr.write(slab(o.r, j, s), d);
-          tr.write(slab(o.i, j, s), d);
-          b.add(make_task(OP_TSMQR, j == k + 1 ? 1 : 2, o.i, o.r, k, j, s * w,
-                          std::min(w, nb - s * w), 1, 0, pid));
+      }
+    };
+    // the reflectors of slabs [s0, s1): GEQRT's V below the diagonal, TSQRT's the whole tile,
+    // TTQRT's the upper part
+    auto v_reads = [&](int s0, int s1) {
+      for (int s = s0; s < s1; ++s) {
+        if (kind != 2) tr.read(P.l(o.i, k, s), d);
+        if (kind != 0) tr.read(P.u(o.i, k, s), d);
+      }
+    };
+    if (!split) {
+      panel_writes(0, S);
+      b.add(make_task(pop, 0, o.i, o.r, k, k, 0, nb, 1, 0, pid));
+    } else {
+      for (int q = 0; q < nq; ++q) {
+        panel_writes(q * spb, (q + 1) * spb);
+        Task tp = make_task(pop, 0, o.i, o.r, k, k, q * split_ib, split_ib, 1, 0, pid);
+        tp.blk = (int16_t)(q + 1);
+        b.add(tp);
+        for (int s = (q + 1) * spb; s < S; ++s) {  // block q applied to the trailing slab s
+          v_reads(q * spb, (q + 1) * spb);
+          panel_writes(s, s + 1);
+          Task tu = make_task(uop, 0, o.i, o.r, k, k, s * w, std::min(w, nb - s * w), 1, 0, pid);
+          tu.blk = (int16_t)(q + 1);
+          b.add(tu);
         }
-    } else {  // TTQRT(i, r, k), TTMQR(i, r, k, j)
-      tr.write(upart(o.r, k), d);
-      tr.write(upart(o.i, k), d);
-      b.add(make_task(OP_TTQRT, 0, o.i, o.r, k, k, 0, nb, 1, 0, pid));
-      for (int j = k + 1; j < n; ++j)
-        for (int s = 0; s < S; ++s) {
-          tr.read(upart(o.i, k), d);
-          tr.write(slab(o.r, j, s), d);
-          tr.write(slab(o.i, j, s), d);
-          b.add(make_task(OP_TTMQR, j == k + 1 ? 1 : 2, o.i, o.r, k, j, s * w,
-                          std::min(w, nb - s * w), 1, 0, pid));
-        }
+      }
     }
+    for (int j = k + 1; j < n; ++j)
+      for (int s = 0; s < S; ++s) {
+        v_reads(0, S);
+        if (kind != 0) wr_slab(o.r, j, s);
+        wr_slab(o.i, j, s);
+        b.add(make_task(uop, j == k + 1 ? 1 : 2, o.i, o.r, k, j, s * w, std::min(w, nb - s * w), 1, 0, pid));
+      }
   }
+}
+
+}  // namespace
+
+Graph build_factor_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int w, int pid, int split_ib) {
+  const TilePieces P{m, (nb + w - 1) / w};
+  Builder b(P.count(n));
+  add_factor_tasks(b, ops, P, n, nb, w, pid, split_ib);
   return b.finish();
 }
 
@@ -207,13 +237,10 @@ Graph build_apply_graph(const std::vector<PanelOp> &ops, int m, int nslab, int w
 }
 
 Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int w, int iters, int pid,
-                     bool pack) {
+                     bool pack, int split_ib) {
   const int S = (nb + w - 1) / w;
-  const size_t per_tile = (size_t)S + 2;
-  const size_t ntile_res = (size_t)m * n * per_tile;
-  auto slab = [&](int i, int j, int s) { return ((size_t)j * m + i) * per_tile + (size_t)s; };
-  auto upart = [&](int i, int j) { return ((size_t)j * m + i) * per_tile + (size_t)S; };
-  auto lpart = [&](int i, int j) { return ((size_t)j * m + i) * per_tile + (size_t)S + 1; };
+  const TilePieces P{m, S};
+  const size_t ntile_res = P.count(n);
   // vector pieces: x (n tiles), r (m tiles), g (n tiles), rhs block (m tiles)
   auto xres = [&](int j) { return ntile_res + (size_t)j; };
   auto rres = [&](int i) { return ntile_res + (size_t)n + (size_t)i; };
@@ -235,11 +262,11 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
   std::vector<int32_t> &d = b.deps();
   if (pack) {
     for (int j = 0; j < n; ++j) {
-      for (int i = 0; i < m; ++i) {
-        for (int s = 0; s < S; ++s) tr.write(slab(i, j, s), d);
-        tr.write(upart(i, j), d);
-        tr.write(lpart(i, j), d);
-      }
+      for (int i = 0; i < m; ++i)
+        for (int s = 0; s < S; ++s) {
+          tr.write(P.u(i, j, s), d);
+          tr.write(P.l(i, j, s), d);
+        }
       if (j == 0) {
         for (int i = 0; i < m; ++i) tr.write(bres(i), d);
         for (int jj = 0; jj < n; ++jj) tr.write(xres(jj), d);
@@ -247,53 +274,13 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
       b.add(make_task(OP_PACK, 0, 0, 0, 0, j, 0, 0, 1, 0, pid));
     }
   }
-  for (const PanelOp &o : ops) {
-    const int k = o.k;
-    if (o.kind == 0) {
-      for (int s = 0; s < S; ++s) tr.write(slab(o.i, k, s), d);
-      tr.write(upart(o.i, k), d);
-      tr.write(lpart(o.i, k), d);
-      b.add(make_task(OP_GEQRT, 0, o.i, o.i, k, k, 0, nb, 1, 0, pid));
-      for (int j = k + 1; j < n; ++j)
-        for (int s = 0; s < S; ++s) {
-          tr.read(lpart(o.i, k), d);
-          tr.write(slab(o.i, j, s), d);
-          b.add(make_task(OP_UNMQR, j == k + 1 ? 1 : 2, o.i, o.i, k, j, s * w, std::min(w, nb - s * w), 1, 0,
-                          pid));
-        }
-    } else if (o.kind == 1) {
-      tr.write(upart(o.r, k), d);
-      for (int s = 0; s < S; ++s) tr.write(slab(o.i, k, s), d);
-      tr.write(upart(o.i, k), d);
-      tr.write(lpart(o.i, k), d);
-      b.add(make_task(OP_TSQRT, 0, o.i, o.r, k, k, 0, nb, 1, 0, pid));
-      for (int j = k + 1; j < n; ++j)
-        for (int s = 0; s < S; ++s) {
-          tr.read(upart(o.i, k), d);
-          tr.read(lpart(o.i, k), d);
-          tr.write(slab(o.r, j, s), d);
-          tr.write(slab(o.i, j, s), d);
-          b.add(make_task(OP_TSMQR, j == k + 1 ? 1 : 2, o.i, o.r, k, j, s * w, std::min(w, nb - s * w), 1, 0,
-                          pid));
-        }
-    } else {
-      tr.write(upart(o.r, k), d);
-      tr.write(upart(o.i, k), d);
-      b.add(make_task(OP_TTQRT, 0, o.i, o.r, k, k, 0, nb, 1, 0, pid));
-      for (int j = k + 1; j < n; ++j)
-        for (int s = 0; s < S; ++s) {
-          tr.read(upart(o.i, k), d);
-          tr.write(slab(o.r, j, s), d);
-          tr.write(slab(o.i, j, s), d);
-          b.add(make_task(OP_TTMQR, j == k + 1 ? 1 : 2, o.i, o.r, k, j, s * w, std::min(w, nb - s * w), 1, 0,
-                          pid));
-        }
-    }
-  }
+  add_factor_tasks(b, ops, P, n, nb, w, pid, split_ib);
   // R tiles (i, j), j >= i, are final after their last writers
   auto read_r = [&](int i, int j) {
-    for (int s = 0; s < S; ++s) tr.read(slab(i, j, s), d);
-    tr.read(upart(i, j), d);
+    for (int s = 0; s < S; ++s) {
+      tr.read(P.u(i, j, s), d);
+      tr.read(P.l(i, j, s), d);
+    }
   };
   auto vtask = [&](int op, int i, int j) { return make_task(op, 1, i, i, 0, j, 0, 0, 1, 0, pid); };
   bool inverted = false;
@@ -348,12 +335,14 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
     // Q^T b on the right-hand-side block, replaying the factorization forward
     for (const PanelOp &o : ops) {
       if (o.kind == 0) {
-        tr.read(lpart(o.i, o.k), d);
+        for (int s = 0; s < S; ++s) tr.read(P.l(o.i, o.k, s), d);
         tr.write(bres(o.i), d);
         b.add(make_task(OP_UNMQR, 1, o.i, o.i, o.k, 0, 0, 1, 1, 1, pid));
       } else {
-        tr.read(upart(o.i, o.k), d);
-        if (o.kind == 1) tr.read(lpart(o.i, o.k), d);
+        for (int s = 0; s < S; ++s) {
+          tr.read(P.u(o.i, o.k, s), d);
+          if (o.kind == 1) tr.read(P.l(o.i, o.k, s), d);
+        }
         tr.write(bres(o.r), d);
         tr.write(bres(o.i), d);
         b.add(make_task(o.kind == 1 ? OP_TSMQR : OP_TTMQR, 1, o.i, o.r, o.k, 0, 0, 1, 1, 1, pid));
@@ -407,13 +396,15 @@ void critical_path_priorities(Graph &g, int nb) {
   // percent), so that the solve chains keep their place ahead of the next round's residuals
   auto cost = [&](const Task &t) {
     const double slab = t.cw > 0 ? (double)t.cw / nb : 1.0;
+    // a block task of a split panel: about one block's share of its panel (or of one update slab)
+    const double part = t.blk > 0 ? 0.125 : 1.0;
     switch (t.op) {
-      case OP_GEQRT: return 4.0;
-      case OP_TSQRT: return 6.0;
-      case OP_TTQRT: return 2.0;
-      case OP_UNMQR: return 6.0 * slab;
-      case OP_TSMQR: return 12.0 * slab;
-      case OP_TTMQR: return 6.0 * slab;
+      case OP_GEQRT: return 4.0 * part;
+      case OP_TSQRT: return 6.0 * part;
+      case OP_TTQRT: return 2.0 * part;
+      case OP_UNMQR: return 6.0 * slab * part;
+      case OP_TSMQR: return 12.0 * slab * part;
+      case OP_TTMQR: return 6.0 * slab * part;
       case OP_RESID:
       case OP_ATR: return t.tgt ? 3.5 : 0.7;
       case OP_TRINV: return 12.0;

@@ -626,6 +626,7 @@ __device__ void task_update(const EngineParams &p, const Geo<Real> &g, const Tas
   const int nq = nb / ib;
   for (int qq = 0; qq < nq; ++qq) {
     const int q = t.trans ? qq : nq - 1 - qq;
+    if (t.blk > 0 && q != t.blk - 1) continue;  // one block of a split panel, on the panel's own tiles
     const int q0 = q * ib;
     const int vr0 = (mode == PANEL_GE) ? q0 : 0;
     const int L = (mode == PANEL_GE) ? nb - q0 : (mode == PANEL_TS ? nb : q0 + ib);
@@ -673,7 +674,10 @@ __device__ void task_panel(const EngineParams &p, const Geo<Real> &g, const Task
   Real *XB = g.tile(t.i, t.k);
   Real *Tg = g.tfac(mode == PANEL_GE ? 0 : 1, t.i, t.k);
   const int nq = nb / ib;
-  for (int q = 0; q < nq; ++q) {
+  // a block task of a split panel factors its block only; separate update tasks apply it to the
+  // trailing slabs
+  const int qa = t.blk > 0 ? t.blk - 1 : 0, qb = t.blk > 0 ? t.blk : nq;
+  for (int q = qa; q < qb; ++q) {
     const int q0 = q * ib;
     const int L = (mode == PANEL_GE) ? nb - q0 : (mode == PANEL_TS ? nb : q0 + ib);
     const int br0 = (mode == PANEL_GE) ? q0 : 0;  // first tile row held in P
@@ -703,6 +707,7 @@ __device__ void task_panel(const EngineParams &p, const Geo<Real> &g, const Task
     gemm_tn(G, ib, P, lds, P, lds, L, ib, ib, (const Real *)nullptr, 0, scr);
     build_t(Tq, G, ib, sh);
     store_cols(Tg + (size_t)q * ib * ib, ib, Tq, ib, ib, ib, 0, 0);
+    if (t.blk > 0) break;
     // trailing columns of the tile(s): block reflector applied with Q^T
     for (int c0 = q0 + ib; c0 < nb; c0 += wt) {
       const int wc = min(wt, nb - c0);

@@ -251,6 +251,16 @@ int launch_sched(int prec, const EngineParams &p, size_t smem, cudaStream_t s) {
 int g_w_override = 0, g_wt_override = 0, g_vc_override = 0;
 // Priority policy of task graphs (hqr_set_priority_policy).
 int g_priority_policy = 1;
+// CUDA-core panels of tiles with nb >= this are split into block tasks (hqr_set_panel_split; 0: never).
+int g_split_min_nb = 256;
+
+// Block size of a split panel for a problem, or 0 to keep whole panel tasks: the tensor-core
+// kernels keep whole panels (one block per tile), and the blocks must be whole update slabs.
+int split_ib_for(const Problem &P) {
+  if (P.tc || g_split_min_nb <= 0 || P.nb < g_split_min_nb) return 0;
+  if (P.w <= 0 || P.ib % P.w != 0 || P.nb / P.ib < 2) return 0;
+  return P.ib;
+}
 
 // Tuning of the column-slab widths for a tile size and precision. FP64 work
 // is bound by the FP64 pipe, so narrow slabs (more parallel tasks) cost
@@ -407,6 +417,12 @@ int hqr_set_priority_policy(int policy) {
   return HQR_SUCCESS;
 }
 
+int hqr_set_panel_split(int min_nb) {
+  if (min_nb < 0) return -1;
+  g_split_min_nb = min_nb;
+  return HQR_SUCCESS;
+}
+
 int hqr_set_slab_widths(int w, int wt, int vc) {
   if (w < 0 || w % 2) return -1;
   if (wt < 0 || wt % 2) return -2;
@@ -483,7 +499,7 @@ int hqr_geqrf(const void *dA, int M, int N, int lda, int prec, int nb, int ib, c
     }
   }
   F->ops = expand_ops(F->list.data(), F->list.size(), F->m, F->n);
-  Graph g = build_factor_graph(F->ops, F->m, F->n, nb, F->prob.w);
+  Graph g = build_factor_graph(F->ops, F->m, F->n, nb, F->prob.w, 0, split_ib_for(F->prob));
   if (g_priority_policy == 1) critical_path_priorities(g, nb);
   int st = upload_graph(g, F->fg);
   const size_t es = elem_size(prec);
@@ -1008,7 +1024,7 @@ int hqr_ls_plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_
       return HQR_ERR_INTERNAL;
     }
     std::vector<PanelOp> ops = expand_ops(lst.data(), lst.size(), pb.m, pb.n);
-    append_graph(merged, build_ls_graph(ops, pb.m, pb.n, c.nb, pb.w, refine_iters, q));
+    append_graph(merged, build_ls_graph(ops, pb.m, pb.n, c.nb, pb.w, refine_iters, q, false, split_ib_for(pb)));
     smem = std::max(smem, smem_for(prec, pb));
     if (pb.tc) P->any_tc = 1;
     P->probs.push_back(pb);
@@ -1605,7 +1621,7 @@ int hqr_server_submit(hqr_server *S, const hqr_ls_problem_t *pr, int64_t *ticket
       return HQR_ERR_INTERNAL;
     CachedGraph cg;
     cg.g = build_ls_graph(expand_ops(lst.data(), lst.size(), pb.m, pb.n), pb.m, pb.n, c.nb, pb.w,
-                          S->o.refine_iters, 0, true);
+                          S->o.refine_iters, 0, true, split_ib_for(pb));
     if (g_priority_policy == 1) critical_path_priorities(cg.g, c.nb);
     for (size_t t = 0; t < cg.g.tasks.size(); ++t)
       if (cg.g.indeg[t] == 0) cg.init.push_back((int)t);
@@ -1911,8 +1927,10 @@ Task na_task(int op, int prio, int i, int r, int k, int j, int c0, int cw) {
   t.r = r;
   t.k = k;
   t.j = j;
-  t.c0 = c0;
-  t.cw = cw;
+  t.c0 = (int16_t)c0;
+  t.cw = (int16_t)cw;
+  t.blk = 0;
+  t.pad_ = 0;
   t.succ_begin = t.succ_end = 0;
   return t;
 }

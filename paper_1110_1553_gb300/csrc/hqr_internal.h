@@ -55,8 +55,12 @@ struct Task {
   int32_t r;      // killer row (TS/TT); equals i for GEQRT/UNMQR
   int32_t k;      // panel
   int32_t j;      // target tile column (updates) or right-hand-side block
-  int32_t c0;     // first column of the slab inside the target block
-  int32_t cw;     // slab width
+  int16_t c0;     // first column of the slab inside the target block
+  int16_t cw;     // slab width
+  int16_t blk;    // 0: every ib block of the panel; q + 1: only block q (a panel split into block
+                  // tasks: the panel task factors block q, an update task on the panel's own
+                  // tiles applies block q to the trailing slab [c0, c0 + cw))
+  int16_t pad_;
   int32_t pid;    // problem index (several problems can share one graph)
   int32_t succ_begin, succ_end;  // successor range in the CSR array
 };
@@ -84,7 +88,12 @@ std::vector<PanelOp> expand_ops(const hqr_elim_t *list, size_t count, int m, int
 
 // Factorization graph: every op expanded into its panel task and its update
 // tasks over the tile columns j > k, each split into column slabs of width w.
-Graph build_factor_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int w, int pid = 0);
+// With split_ib > 0 (a multiple of w dividing nb) every panel becomes nb /
+// split_ib block tasks, block q followed by the updates of the panel's own
+// trailing slabs with block q, so that a panel's trailing work spreads over
+// several CTAs and the next block starts as soon as its own slabs are done.
+Graph build_factor_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int w, int pid = 0,
+                         int split_ib = 0);
 
 // Q^T (trans = 1) or Q (trans = 0) applied to a right-hand side split into
 // row tiles and `nslab` column slabs of width w: the update kernels replayed
@@ -100,7 +109,7 @@ Graph build_apply_graph(const std::vector<PanelOp> &ops, int m, int nslab, int w
 // copies the caller's matrix into the workspace (for runs where no separate
 // preparation kernel can be launched).
 Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int w, int iters, int pid,
-                     bool pack = false);
+                     bool pack = false, int split_ib = 0);
 
 // Priorities from the critical path: every task gets its bottom level (its
 // own estimated cost plus the longest chain of estimated costs after it)

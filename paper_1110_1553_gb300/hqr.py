@@ -33,7 +33,7 @@ EXPORTS = ["hqr_elim_list", "hqr_validate_list", "hqr_geqrf", "hqr_refactor", "h
            "hqr_ls_plan_capture", "hqr_ls_plan_status", "hqr_ls_plan_info", "hqr_ls_plan_config",
            "hqr_ls_plan_free", "hqr_ls_plan_trace", "hqr_set_tuning", "hqr_autotune", "hqr_server_create", "hqr_server_start",
            "hqr_server_submit", "hqr_server_poll", "hqr_server_stats", "hqr_server_progress", "hqr_server_counters", "hqr_server_stop", "hqr_server_free", "hqr_debug_block_task", "hqr_factors_free", "hqr_set_timeout_ms", "hqr_strerror", "hqr_last_error", "hqr_set_slab_widths",
-           "hqr_set_priority_policy",
+           "hqr_set_priority_policy", "hqr_set_panel_split",
            "hqr_last_launches"]
 
 
@@ -112,6 +112,7 @@ def load(build_if_missing=False):
     lib.hqr_factors_free.restype = None
     lib.hqr_set_slab_widths.argtypes = [i32, i32, i32]
     lib.hqr_set_priority_policy.argtypes = [i32]
+    lib.hqr_set_panel_split.argtypes = [i32]
     lib.hqr_set_timeout_ms.argtypes = [i64]
     lib.hqr_set_timeout_ms.restype = None
     lib.hqr_strerror.argtypes = [i32]
@@ -165,6 +166,11 @@ def validate_list(m, n, records):
 
 def set_slab_widths(w=0, wt=0, vc=0):
     _check(load().hqr_set_slab_widths(int(w), int(wt), int(vc)), "hqr_set_slab_widths")
+
+
+def set_panel_split(min_nb):
+    """Split CUDA-core panels of tiles with nb >= min_nb into block tasks (0: never)."""
+    _check(load().hqr_set_panel_split(int(min_nb)), "hqr_set_panel_split")
 
 
 def set_priority_policy(policy):
