@@ -426,11 +426,11 @@ void hqr_factors_free(hqr_factors *F);
 int hqr_set_slab_widths(int w, int wt, int vc);
 
 /* hqr_set_panel_split -- panels of factorizations, plans and server requests
- * created afterwards whose tiles have nb >= min_nb (CUDA-core kernels, ib a
- * multiple of the update slab width) run as one task per ib block plus the
- * updates of the panel's own trailing slabs, block by block, so that a
+ * created afterwards whose tiles have nb >= min_nb (CUDA-core kernels, at
+ * least two ib blocks per tile) run as one task per ib block plus the
+ * updates of the panel's own trailing columns with that block, so that a
  * panel's trailing work spreads over several CTAs. 0 keeps whole panel tasks
- * everywhere; default 256. Returns -1 for min_nb < 0. */
+ * everywhere; default 64. Returns -1 for min_nb < 0. */
 int hqr_set_panel_split(int min_nb);
 
 /* hqr_set_priority_policy -- ready-queue priorities of task graphs created

@@ -144,7 +144,8 @@ void add_factor_tasks(Builder &b, const std::vector<PanelOp> &ops, const TilePie
   std::vector<int32_t> &d = b.deps();
   const int S = P.S;
   const bool split = split_ib > 0;
-  const int nq = split ? nb / split_ib : 1, spb = split ? split_ib / w : S;  // blocks, slabs per block
+  const int nq = split ? nb / split_ib : 1;
+  auto slab_of = [&](int col) { return col / w; };
   auto wr_u = [&](int i, int j, int s) { tr.write(P.u(i, j, s), d); };
   auto wr_slab = [&](int i, int j, int s) {
     tr.write(P.u(i, j, s), d);
@@ -180,17 +181,23 @@ void add_factor_tasks(Builder &b, const std::vector<PanelOp> &ops, const TilePie
       panel_writes(0, S);
       b.add(make_task(pop, 0, o.i, o.r, k, k, 0, nb, 1, 0, pid));
     } else {
+      // block q covers columns [q0, q1); its trailing columns [q1, nb) go in pieces no wider than
+      // a slab and never across one (slab s0 of a block wider than its block ends the first piece)
       for (int q = 0; q < nq; ++q) {
-        panel_writes(q * spb, (q + 1) * spb);
-        Task tp = make_task(pop, 0, o.i, o.r, k, k, q * split_ib, split_ib, 1, 0, pid);
+        const int q0 = q * split_ib, q1 = q0 + split_ib;
+        const int s0 = slab_of(q0), s1 = slab_of(q1 - 1) + 1;  // slabs holding block q
+        panel_writes(s0, s1);
+        Task tp = make_task(pop, 0, o.i, o.r, k, k, q0, split_ib, 1, 0, pid);
         tp.blk = (int16_t)(q + 1);
         b.add(tp);
-        for (int s = (q + 1) * spb; s < S; ++s) {  // block q applied to the trailing slab s
-          v_reads(q * spb, (q + 1) * spb);
+        for (int c = q1; c < nb;) {  // block q applied to trailing columns [c, ce)
+          const int s = slab_of(c), ce = std::min(nb, (s + 1) * w);
+          v_reads(s0, s1);
           panel_writes(s, s + 1);
-          Task tu = make_task(uop, 0, o.i, o.r, k, k, s * w, std::min(w, nb - s * w), 1, 0, pid);
+          Task tu = make_task(uop, 0, o.i, o.r, k, k, c, ce - c, 1, 0, pid);
           tu.blk = (int16_t)(q + 1);
           b.add(tu);
+          c = ce;
         }
       }
     }

@@ -252,13 +252,17 @@ int g_w_override = 0, g_wt_override = 0, g_vc_override = 0;
 // Priority policy of task graphs (hqr_set_priority_policy).
 int g_priority_policy = 1;
 // CUDA-core panels of tiles with nb >= this are split into block tasks (hqr_set_panel_split; 0: never).
-int g_split_min_nb = 256;
+int g_split_min_nb = 64;
 
-// Block size of a split panel for a problem, or 0 to keep whole panel tasks: the tensor-core
-// kernels keep whole panels (one block per tile), and the blocks must be whole update slabs.
-int split_ib_for(const Problem &P) {
+// Block size of a split panel for a problem, or 0 to keep whole panel tasks. The tensor-core
+// kernels keep whole panels (one block per tile). FP32 panels on CUDA cores are cheap next to
+// their updates: they are split only where a block spans whole update slabs (measured: splitting
+// blocks narrower than the 64-column FP32 slabs cost 1024 uneven problems 5 %); FP64 panels are
+// split at any slab width (512^2 FP64 QR + Q: -25 % latency).
+int split_ib_for(int prec, const Problem &P) {
   if (P.tc || g_split_min_nb <= 0 || P.nb < g_split_min_nb) return 0;
-  if (P.w <= 0 || P.ib % P.w != 0 || P.nb / P.ib < 2) return 0;
+  if (P.w <= 0 || P.nb / P.ib < 2) return 0;
+  if (prec != HQR_FP64 && P.ib % P.w != 0) return 0;
   return P.ib;
 }
 
@@ -499,7 +503,7 @@ int hqr_geqrf(const void *dA, int M, int N, int lda, int prec, int nb, int ib, c
     }
   }
   F->ops = expand_ops(F->list.data(), F->list.size(), F->m, F->n);
-  Graph g = build_factor_graph(F->ops, F->m, F->n, nb, F->prob.w, 0, split_ib_for(F->prob));
+  Graph g = build_factor_graph(F->ops, F->m, F->n, nb, F->prob.w, 0, split_ib_for(prec, F->prob));
   if (g_priority_policy == 1) critical_path_priorities(g, nb);
   int st = upload_graph(g, F->fg);
   const size_t es = elem_size(prec);
@@ -1024,7 +1028,7 @@ int hqr_ls_plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_
       return HQR_ERR_INTERNAL;
     }
     std::vector<PanelOp> ops = expand_ops(lst.data(), lst.size(), pb.m, pb.n);
-    append_graph(merged, build_ls_graph(ops, pb.m, pb.n, c.nb, pb.w, refine_iters, q, false, split_ib_for(pb)));
+    append_graph(merged, build_ls_graph(ops, pb.m, pb.n, c.nb, pb.w, refine_iters, q, false, split_ib_for(prec, pb)));
     smem = std::max(smem, smem_for(prec, pb));
     if (pb.tc) P->any_tc = 1;
     P->probs.push_back(pb);
@@ -1621,7 +1625,7 @@ int hqr_server_submit(hqr_server *S, const hqr_ls_problem_t *pr, int64_t *ticket
       return HQR_ERR_INTERNAL;
     CachedGraph cg;
     cg.g = build_ls_graph(expand_ops(lst.data(), lst.size(), pb.m, pb.n), pb.m, pb.n, c.nb, pb.w,
-                          S->o.refine_iters, 0, true, split_ib_for(pb));
+                          S->o.refine_iters, 0, true, split_ib_for(prec, pb));
     if (g_priority_policy == 1) critical_path_priorities(cg.g, c.nb);
     for (size_t t = 0; t < cg.g.tasks.size(); ++t)
       if (cg.g.indeg[t] == 0) cg.init.push_back((int)t);

@@ -88,7 +88,7 @@ std::vector<PanelOp> expand_ops(const hqr_elim_t *list, size_t count, int m, int
 
 // Factorization graph: every op expanded into its panel task and its update
 // tasks over the tile columns j > k, each split into column slabs of width w.
-// With split_ib > 0 (a multiple of w dividing nb) every panel becomes nb /
+// With split_ib > 0 (dividing nb) every panel becomes nb /
 // split_ib block tasks, block q followed by the updates of the panel's own
 // trailing slabs with block q, so that a panel's trailing work spreads over
 // several CTAs and the next block starts as soon as its own slabs are done.

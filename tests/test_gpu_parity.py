@@ -242,41 +242,44 @@ def test_tree_pairs_fp32_and_apply_q(low, high):
 
 
 # ------------------------------------------------------- split panels --
-# CUDA-core panels of large tiles run as one task per ib block plus the
-# updates of the panel's own trailing slabs (forced here at nb = 64). Same
-# tolerances as whole panels; R also against a whole-panel run.
+# CUDA-core panels of tiles with nb >= 64 run as one task per ib block plus
+# the updates of the panel's own trailing columns. Same tolerances as whole
+# panels; R also against a whole-panel run (split turned off).
 
-@pytest.mark.parametrize("low,high,a,p", [(FLAT, FLAT, 4, 1), (GREEDY, FIBONACCI, 2, 2), (BINARY, GREEDY, 1, 3)])
-def test_split_panels_fp64(low, high, a, p):
-    nb, ib, m, n = 64, 16, 7, 4
+@pytest.mark.parametrize("low,high,a,p,ib", [(FLAT, FLAT, 4, 1, 16), (GREEDY, FIBONACCI, 2, 2, 16),
+                                             (BINARY, GREEDY, 1, 3, 16), (GREEDY, GREEDY, 2, 1, 8)])
+def test_split_panels_fp64(low, high, a, p, ib):
+    """ib = 8: blocks narrower than the 16-column update slabs (a block's trailing work starts
+    inside its own slab)."""
+    nb, m, n = 64, 7, 4
     A = inputs.gaussian(m * nb, n * nb - 3, seed=61 + a)  # ragged last tile column
     recs = hqr_elim_list(m, n, a, p, low, high)
-    hqr.set_panel_split(64)
-    try:
-        Fo, Fs = run_both(A, nb, ib, recs)
-    finally:
-        hqr.set_panel_split(256)
+    Fo, Fs = run_both(A, nb, ib, recs)
     compare_factors(Fo, Fs, pad(A, nb))
     B = inputs.gaussian(A.shape[0], 3, seed=62)
     for trans in (True, False):
         out = Fs.apply_q(torch.from_numpy(B.copy()).cuda(), trans=trans).cpu().numpy()
         ref = o_apply_q(Fo, B, trans=trans)
         assert np.max(np.abs(out - ref)) <= 1e-12 * np.linalg.norm(B)
-    Fw = hqr.geqrf(torch.from_numpy(np.ascontiguousarray(A)).cuda(), nb, ib, recs)
+    hqr.set_panel_split(0)
+    try:
+        Fw = hqr.geqrf(torch.from_numpy(np.ascontiguousarray(A)).cuda(), nb, ib, recs)
+    finally:
+        hqr.set_panel_split(64)
     assert np.max(np.abs(Fs.R().cpu().numpy() - Fw.R().cpu().numpy())) <= 1e-13 * np.linalg.norm(A)
 
 
-def test_split_panels_fp32():
-    nb, ib, m, n = 128, 32, 6, 3
-    hqr.set_slab_widths(32, 0, 0)
-    hqr.set_panel_split(128)
+@pytest.mark.parametrize("nb,ib", [(128, 16), (128, 32), (256, 32)])
+def test_split_panels_fp32(nb, ib):
+    """FP32 panels are split where a block spans whole update slabs (here slabs of 16)."""
+    m, n = 6, 3
+    A = inputs.gaussian(m * nb, n * nb, seed=63 + ib).astype(np.float32)
+    recs = hqr_elim_list(m, n, 2, 2, GREEDY, FIBONACCI)
+    Fo = tile_qr(A.astype(np.float64), nb, ib, recs)
+    hqr.set_slab_widths(16, 0, 0)
     try:
-        A = inputs.gaussian(m * nb, n * nb, seed=63).astype(np.float32)
-        recs = hqr_elim_list(m, n, 2, 2, GREEDY, FIBONACCI)
-        Fo = tile_qr(A.astype(np.float64), nb, ib, recs)
         Fg = hqr.geqrf(torch.from_numpy(A).cuda(), nb, ib, recs)
     finally:
-        hqr.set_panel_split(256)
         hqr.set_slab_widths(0, 0, 0)
     nrm = np.linalg.norm(A.astype(np.float64))
     assert np.max(np.abs(Fg.R().cpu().numpy().astype(np.float64) - Fo.R())) <= 5e-6 * nrm
@@ -289,14 +292,10 @@ def test_split_panels_least_squares_plan():
     nb, ib = 64, 16
     A = inputs.gaussian(700, 190, seed=64)
     b = inputs.rng(64, 1).standard_normal(700)
-    hqr.set_panel_split(64)
-    try:
-        x = torch.zeros(190, dtype=torch.float64, device="cuda")
-        plan = hqr.LSPlan([(torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda(), x)], refine_iters=0,
-                          configs=[hqr.tile_config(nb, ib, 2, 2, "greedy", "fibonacci")])
-        plan.run()
-        assert plan.status() == 0
-    finally:
-        hqr.set_panel_split(256)
+    x = torch.zeros(190, dtype=torch.float64, device="cuda")
+    plan = hqr.LSPlan([(torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda(), x)], refine_iters=0,
+                      configs=[hqr.tile_config(nb, ib, 2, 2, "greedy", "fibonacci")])
+    plan.run()
+    assert plan.status() == 0
     xo = lstsq_unblocked(A, b)
     assert np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo) <= 1e-12
