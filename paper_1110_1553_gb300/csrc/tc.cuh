@@ -48,8 +48,9 @@ constexpr int KC = 32;           // K extent of one chunk (two MMA K steps of 16
 constexpr int NCH = NB / KC;     // chunks per product (each in its own stage)
 constexpr int DT = 2;            // chunks loaded ahead in registers
 constexpr int NP = 3;            // BF16 pieces of an FP32 value
-constexpr int NACC = NCH * (KC / 16);  // accumulators: one per MMA K step
-constexpr int TMEM_COLS = NACC * WMAX;   // 512 columns: the whole tensor memory of the SM
+constexpr int KS_ACC = 2;                  // MMA K steps (of 16) chained in one accumulator
+constexpr int NACC = NCH * (KC / 16) / KS_ACC;  // accumulators: one per K chunk of 32
+constexpr int TMEM_COLS = NACC * WMAX;   // 256 columns: half the tensor memory of the SM
 constexpr int NTHR = 256;
 
 constexpr uint32_t LBO_C = 128, SBO_C = (KC / 8) * 128;      // chunk buffers: 8-row groups of 512 B
@@ -404,13 +405,15 @@ __device__ bool product(const Src &sa, const unsigned char *img, const Src *sb, 
         const uint32_t a = sbase + ring + (uint32_t)c * stage_bytes;
 #pragma unroll
         for (int ks = 0; ks < KC / 16; ++ks) {
-          const uint32_t dk = tmem + (uint32_t)(c * (KC / 16) + ks) * WMAX;  // this K step's accumulator
+          const int acc = (c * (KC / 16) + ks) / KS_ACC;  // this K step's accumulator
+          const bool first = (c * (KC / 16) + ks) % KS_ACC == 0;
+          const uint32_t dk = tmem + (uint32_t)acc * WMAX;
           const uint32_t ak = a + (uint32_t)ks * 2 * LBO_C;
           if (streamB)
-            issue_kstep(dk, idesc, ak, A_PC, a + NP * A_PC + (uint32_t)ks * 2 * LBO_C, B_PC, LBO_C, SBO_C, true);
+            issue_kstep(dk, idesc, ak, A_PC, a + NP * A_PC + (uint32_t)ks * 2 * LBO_C, B_PC, LBO_C, SBO_C, first);
           else
             issue_kstep(dk, idesc, ak, A_PC, sbase + OFF_W + (uint32_t)(c * KC / 8 + ks * 2) * LBO_W, W_PC,
-                        LBO_W, SBO_W, true);
+                        LBO_W, SBO_W, first);
         }
       }
     }
@@ -424,9 +427,9 @@ __device__ bool product(const Src &sa, const unsigned char *img, const Src *sb, 
   return ok && !*abort;
 }
 
-// Sum of the K-step accumulators (columns col, col + 64, ...) of 16
+// Sum of the K-chunk accumulators (columns col, col + 64, ...) of 16
 // columns, in K order with round-to-nearest FP32 additions: each
-// accumulator takes the six MMAs of one K step only, which keeps the
+// accumulator takes the MMAs of KS_ACC K steps only, which keeps the
 // accumulation error of the tensor cores over a short chain.
 __device__ __forceinline__ void tmem_sum16(uint32_t taddr, float (&v)[16]) {
   tmem_ld16(taddr, v);
