@@ -12,7 +12,7 @@
 // bf16(x - b0 - b1), all rounded to nearest, |x - b0 - b1 - b2| <= 2^-27 |x|)
 // and six products per K step (b0 b0' + b0 b1' + b1 b0' + b0 b2' + b1 b1' +
 // b2 b0'; the dropped terms are below 2^-26 of |x x'|), accumulating in FP32
-// in tensor memory (one accumulator per K step of 16, summed in FP32 in the
+// in tensor memory (one accumulator per K chunk of 32, summed in FP32 in the
 // epilogue). The updates thus keep FP32 accuracy, which the
 // corrected semi-normal-equation refinement needs, at the tensor-core cost
 // of three tf32 products.
