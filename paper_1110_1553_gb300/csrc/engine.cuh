@@ -227,17 +227,23 @@ __device__ __forceinline__ Real warp_sum(Real v) {
   return v;
 }
 
-// Sum over the CTA; every thread gets the same value (fixed order).
+// Sum over the CTA; every thread gets the same value (fixed order). One
+// thread adds the warps' partial sums and broadcasts the total: in FP64 a
+// warp-wide add occupies the SM's FP64 pipe for 16 cycles whether or not
+// its lanes need the result.
 template <typename Real>
 __device__ Real block_sum(Real v, Shared<Real> &sh) {
   v = warp_sum(v);
   if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5] = v;
   __syncthreads();
-  Real t = 0;
+  if (threadIdx.x == 0) {
+    Real t = 0;
 #pragma unroll
-  for (int q = 0; q < NWARP; ++q) t += sh.red[q];
+    for (int q = 0; q < NWARP; ++q) t += sh.red[q];
+    sh.red[NWARP] = t;
+  }
   __syncthreads();
-  return t;
+  return sh.red[NWARP];
 }
 
 template <typename Real>
@@ -246,11 +252,14 @@ __device__ Real block_max(Real v, Shared<Real> &sh) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5] = v;
   __syncthreads();
-  Real t = 0;
+  if (threadIdx.x == 0) {
+    Real t = 0;
 #pragma unroll
-  for (int q = 0; q < NWARP; ++q) t = fmax(t, sh.red[q]);
+    for (int q = 0; q < NWARP; ++q) t = fmax(t, sh.red[q]);
+    sh.red[NWARP] = t;
+  }
   __syncthreads();
-  return t;
+  return sh.red[NWARP];
 }
 
 // FP32 versions of the two GEMM phases with register blocking and 16-byte
