@@ -227,13 +227,14 @@ __device__ __forceinline__ Real warp_sum(Real v) {
   return v;
 }
 
-// Sum over the CTA; every thread gets the same value (fixed order). One
-// thread adds the warps' partial sums and broadcasts the total: in FP64 a
-// warp-wide add occupies the SM's FP64 pipe for 16 cycles whether or not
-// its lanes need the result.
+// Sum over the CTA; every thread gets the same value (fixed order). Only
+// threads below `nact` hold nonzero values, so warps beyond them skip their
+// reduction, and one thread adds the warps' partial sums and broadcasts the
+// total: in FP64 a warp-wide add occupies the SM's FP64 pipe for 16 cycles
+// whether or not its lanes need the result.
 template <typename Real>
-__device__ Real block_sum(Real v, Shared<Real> &sh) {
-  v = warp_sum(v);
+__device__ Real block_sum(Real v, Shared<Real> &sh, int nact = NT) {
+  if ((int)(threadIdx.x & ~31u) < nact) v = warp_sum(v);
   if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -247,9 +248,10 @@ __device__ Real block_sum(Real v, Shared<Real> &sh) {
 }
 
 template <typename Real>
-__device__ Real block_max(Real v, Shared<Real> &sh) {
+__device__ Real block_max(Real v, Shared<Real> &sh, int nact = NT) {
+  if ((int)(threadIdx.x & ~31u) < nact)
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -494,16 +496,17 @@ __device__ void factor_block(int mode, Real *P, int ld, int L, int ib, Real *Rt,
     const int r0 = (mode == PANEL_GE) ? jj + 1 : 0;
     const int r1 = (mode == PANEL_TT) ? min(L, q0 + jj + 1) : L;
     Real *col = P + (size_t)jj * ld;
+    const int nact = min(NT, r1 - r0);  // threads holding rows of the column
     Real ss = 0;
     for (int k = r0 + tid; k < r1; k += NT) ss = fma(col[k], col[k], ss);
-    ss = block_sum(ss, sh);
+    ss = block_sum(ss, sh, nact);
     Real snorm;
     if (ss > RealTraits<Real>::tiny && ss < RealTraits<Real>::huge) {
       snorm = sqrt(ss);
     } else {
       Real am = 0;
       for (int k = r0 + tid; k < r1; k += NT) am = fmax(am, fabs(col[k]));
-      am = block_max(am, sh);
+      am = block_max(am, sh, nact);
       if (am == Real(0)) {
         snorm = 0;
       } else {
@@ -513,7 +516,7 @@ __device__ void factor_block(int mode, Real *P, int ld, int L, int ib, Real *Rt,
           const Real x = col[k] * inv;
           s2 = fma(x, x, s2);
         }
-        s2 = block_sum(s2, sh);
+        s2 = block_sum(s2, sh, nact);
         snorm = am * sqrt(s2);
       }
     }
@@ -537,19 +540,25 @@ __device__ void factor_block(int mode, Real *P, int ld, int L, int ib, Real *Rt,
     for (int k = r0 + tid; k < r1; k += NT) col[k] *= scale;
     __syncthreads();
     if (t == Real(0)) continue;  // identity reflector: nothing to apply
-    // w_c = top(jj,c) + v^T P(:,c) for the block's later columns
-    for (int c = jj + 1 + warp; c < ib; c += NWARP) {
-      const Real *pc = P + (size_t)c * ld;
+    // w_c = top(jj,c) + v^T P(:,c) for the block's later columns; short columns share a warp
+    // (LPC lanes per column, 32 / LPC columns per warp), which saves shuffle-add levels
+    const int nr = r1 - r0, ncl = ib - jj - 1;
+    const int LPC = nr > 64 ? 32 : (nr > 32 ? 16 : 8), CPW = 32 / LPC;
+    const int sub = lane / LPC, sl = lane - sub * LPC;
+    for (int cw0 = jj + 1 + warp * CPW; cw0 < ib; cw0 += NWARP * CPW) {
+      const int c = cw0 + sub;
+      const bool on = c < ib;
+      const Real *pc = P + (size_t)(on ? c : jj) * ld;
       Real s = 0;
-      for (int k = r0 + lane; k < r1; k += 32) s = fma(col[k], pc[k], s);
-      s = warp_sum(s);
-      if (lane == 0) {
+      if (on)
+        for (int k = r0 + sl; k < r1; k += LPC) s = fma(col[k], pc[k], s);
+      for (int o = LPC >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (on && sl == 0) {
         const Real top = (mode == PANEL_GE) ? pc[jj] : Rt[jj + (size_t)c * ldt];
         sh.wv[c] = t * (top + s);
       }
     }
     __syncthreads();
-    const int nr = r1 - r0, ncl = ib - jj - 1;
     for (int e = tid; e < nr * ncl; e += NT) {
       const int c = jj + 1 + e / nr, k = r0 + e % nr;
       Real *pc = P + (size_t)c * ld;
