@@ -458,6 +458,40 @@ const char *hqr_strerror(int status) {
   }
 }
 
+int hqr_task_graph(int m, int n, int nb, int ib, int prec, const hqr_elim_t *list, size_t count,
+                   int32_t *tasks, int64_t task_cap, int64_t *succ_ptr, int32_t *succ, int64_t succ_cap,
+                   int64_t *ntasks, int64_t *nedges) {
+  if (m < 1) return -1;
+  if (n < 1 || n > m) return -2;
+  if (!prec_ok(prec)) return -5;
+  if (nb < 8 || nb > 256 || nb % 8 || (prec == HQR_FP32_BF16X3 && nb != tc::NB)) return -3;
+  ib = eff_ib(prec, nb, ib);
+  if (!valid_tile_sizes(prec, nb, ib)) return -4;
+  if (!list && count) return -6;
+  if (!ntasks || !nedges) return -13;
+  if (hqr_validate_list(m, n, list, count) != HQR_SUCCESS) return HQR_ERR_INVALID_LIST;
+  Problem P{};
+  P.m = m;
+  P.n = n;
+  P.nb = nb;
+  P.ib = ib;
+  choose_widths(prec, nb, ib, P);
+  const Graph g = build_factor_graph(expand_ops(list, count, m, n), m, n, nb, P.w, 0, split_ib_for(prec, P));
+  *ntasks = (int64_t)g.tasks.size();
+  *nedges = (int64_t)g.succ.size();
+  if (!tasks) return HQR_SUCCESS;
+  if (task_cap < *ntasks || !succ_ptr || (*nedges > 0 && (!succ || succ_cap < *nedges))) return HQR_ERR_CAPACITY;
+  for (size_t q = 0; q < g.tasks.size(); ++q) {
+    const Task &t = g.tasks[q];
+    const int32_t row[8] = {t.op, t.blk, t.i, t.r, t.k, t.j, t.c0, t.cw};
+    std::memcpy(tasks + 8 * q, row, sizeof(row));
+    succ_ptr[q] = t.succ_begin;
+  }
+  succ_ptr[g.tasks.size()] = (int64_t)g.succ.size();
+  if (!g.succ.empty()) std::memcpy(succ, g.succ.data(), sizeof(int32_t) * g.succ.size());
+  return HQR_SUCCESS;
+}
+
 int hqr_geqrf(const void *dA, int M, int N, int lda, int prec, int nb, int ib, const hqr_elim_t *list,
               size_t count, hqr_factors **out, void *stream) {
   g_launches = 0;

@@ -27,7 +27,7 @@ FP64, FP32, FP32_BF16X3 = 0, 1, 2
 ELIM_DTYPE = np.dtype([("k", np.int32), ("i", np.int32), ("killer", np.int32), ("kind", np.int32),
                        ("level", np.int32), ("step", np.int32)])
 
-EXPORTS = ["hqr_elim_list", "hqr_validate_list", "hqr_geqrf", "hqr_refactor", "hqr_refactor_async",
+EXPORTS = ["hqr_elim_list", "hqr_validate_list", "hqr_task_graph", "hqr_geqrf", "hqr_refactor", "hqr_refactor_async",
            "hqr_status", "hqr_get_r", "hqr_get_tiles", "hqr_get_t", "hqr_factors_info", "hqr_kernel_ms", "hqr_trace", "hqr_apply_q",
            "hqr_gels", "hqr_geqrf_r_noalloc", "hqr_ls_plan_create", "hqr_ls_plan_run",
            "hqr_ls_plan_capture", "hqr_ls_plan_status", "hqr_ls_plan_info", "hqr_ls_plan_config",
@@ -70,6 +70,8 @@ def load(build_if_missing=False):
     pf = ctypes.POINTER(vp)
     lib.hqr_elim_list.argtypes = [i32, i32, i32, i32, i32, i32, vp, sz, ctypes.POINTER(sz)]
     lib.hqr_validate_list.argtypes = [i32, i32, vp, sz]
+    lib.hqr_task_graph.argtypes = [i32, i32, i32, i32, i32, vp, sz, vp, i64, vp, vp, i64, ctypes.POINTER(i64),
+                                   ctypes.POINTER(i64)]
     lib.hqr_geqrf.argtypes = [vp, i32, i32, i32, i32, i32, i32, vp, sz, pf, vp]
     lib.hqr_refactor.argtypes = [vp, vp, i32, vp]
     lib.hqr_refactor_async.argtypes = [vp, vp, i32, vp]
@@ -162,6 +164,28 @@ def validate_list(m, n, records):
     arr = records if isinstance(records, np.ndarray) else to_array(records)
     arr = np.ascontiguousarray(arr, dtype=ELIM_DTYPE)
     return lib.hqr_validate_list(m, n, arr.ctypes.data if len(arr) else None, len(arr))
+
+
+TASK_OPS = ("GEQRT", "UNMQR", "TSQRT", "TSMQR", "TTQRT", "TTMQR")
+
+
+def task_graph(m, n, nb, ib, records, prec=FP64):
+    """Task graph of hqr_geqrf for an m x n tile matrix (host only): an int32
+    array of (op, blk, i, r, k, j, c0, cw) per task in a topological order,
+    and the successors as CSR (offsets, ids)."""
+    lib = load()
+    arr = records if isinstance(records, np.ndarray) else to_array(records)
+    arr = np.ascontiguousarray(arr, dtype=ELIM_DTYPE)
+    lp = arr.ctypes.data if len(arr) else None
+    nt, ne = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib.hqr_task_graph(m, n, nb, ib, prec, lp, len(arr), None, 0, None, None, 0, ctypes.byref(nt),
+                              ctypes.byref(ne)), "hqr_task_graph")
+    tasks = np.zeros((nt.value, 8), dtype=np.int32)
+    ptr = np.zeros(nt.value + 1, dtype=np.int64)
+    succ = np.zeros(max(ne.value, 1), dtype=np.int32)
+    _check(lib.hqr_task_graph(m, n, nb, ib, prec, lp, len(arr), tasks.ctypes.data, nt.value, ptr.ctypes.data,
+                              succ.ctypes.data, len(succ), ctypes.byref(nt), ctypes.byref(ne)), "hqr_task_graph")
+    return tasks, ptr, succ[:ne.value]
 
 
 def set_slab_widths(w=0, wt=0, vc=0):
