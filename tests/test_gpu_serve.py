@@ -129,6 +129,42 @@ def test_server_fresh_servers_back_to_back():
         del srv
 
 
+def test_fp64_server_split_panels_equal_plan_and_oracle():
+    """FP64 requests with tiles of 64 and 128 run split panels (one task per ib block plus the
+    updates of the panel's own columns) inside the server's request graphs: every result equals
+    the same problem in a plan (bitwise) and the oracle's least-squares solution (1e-12)."""
+    shapes = [(300, 100), (700, 190), (2048, 300), (1500, 64)]
+    probs = []
+    for q, (M, N) in enumerate(shapes):
+        A = inputs.gaussian(M, N, seed=600 + q)
+        b = inputs.rng(600 + q, 1).standard_normal(M)
+        Ad = torch.from_numpy(np.asfortranarray(A).T.copy()).cuda().t()
+        probs.append((A, b, Ad, torch.from_numpy(b).cuda(), torch.zeros(N, dtype=torch.float64, device="cuda")))
+    srv = hqr.Server(torch.float64, refine_iters=0, max_live=4, hbm_budget=2 << 30)
+    srv.start()
+    try:
+        tickets, done = [], set()
+        for pr in probs:
+            t, t0 = None, time.time()
+            while t is None and time.time() - t0 < 60:
+                t = srv.submit(*pr[2:])
+                if t is None:
+                    done.update(srv.poll())
+            assert t is not None
+            tickets.append(t)
+        wait_all(srv, tickets, done)
+    finally:
+        srv.stop()
+    for q, (A, b, Ad, bd, x) in enumerate(probs):
+        xo = lstsq_unblocked(A, b)
+        assert np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo) <= 1e-12, q
+        x1 = torch.zeros_like(x)
+        plan = hqr.LSPlan([(Ad, bd, x1)], refine_iters=0)
+        plan.run()
+        assert plan.status() == 0
+        assert torch.equal(x1, x), q
+
+
 def test_server_budget_admission():
     srv = hqr.Server(torch.float32, refine_iters=2, max_live=2, hbm_budget=4 << 20)
     srv.start()
