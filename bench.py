@@ -355,6 +355,7 @@ def square_mixed(torch, hqr, dev, n=16384, refine=20):
     cross = ((x - ref).norm() / ref.norm()).item()
     return {"workload": "square_mixed_ls_16384_kappa1e6", "ms": ms, "solves_per_s": 1e3 / ms,
             "qr_tflops": info["qr_flops"] / (ms * 1e-3) / 1e12, "refine_iters": refine, "status": st,
+            "last_rel_correction": plan.correction(0),
             "rel_diff_vs_cusolver_fp64_qr": cross, "tasks": info["tasks"]}
 
 

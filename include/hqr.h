@@ -331,6 +331,13 @@ int hqr_ls_plan_capture(hqr_ls_plan *plan, void *stream);
  * diagonal (that problem's x is then not meaningful). */
 int hqr_ls_plan_status(hqr_ls_plan *plan, void *stream);
 
+/* hqr_ls_plan_correction -- size of the last refinement correction of
+ * problem idx after a run: *rel = max_i |d_i| / max_i |x_i|, d the
+ * correction the last CSNE round added to x. A value at the FP64 rounding
+ * level says the refinement has converged; -1 when the plan has no
+ * refinement rounds. Synchronizes `stream` (the one the plan ran on). */
+int hqr_ls_plan_correction(hqr_ls_plan *plan, int idx, double *rel, void *stream);
+
 /* hqr_ls_plan_info -- tasks of the merged graph, the paper's QR flop count
  * sum of 2 M N^2 - 2/3 N^3, and the device time of the last run (the task
  * kernel alone; the whole captured graph when it was launched). */

@@ -956,6 +956,30 @@ struct hqr_ls_plan {
 
 namespace {
 
+// out[0] = max_i |d_i|, out[1] = max_i |x_i| over i < n (one block).
+__global__ void vec_absmax2(const double *__restrict__ d, const double *__restrict__ x, int n, double *out) {
+  __shared__ double sd[256], sx[256];
+  double md = 0.0, mx = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    md = fmax(md, fabs(d[i]));
+    mx = fmax(mx, fabs(x[i]));
+  }
+  sd[threadIdx.x] = md;
+  sx[threadIdx.x] = mx;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      sd[threadIdx.x] = fmax(sd[threadIdx.x], sd[threadIdx.x + h]);
+      sx[threadIdx.x] = fmax(sx[threadIdx.x], sx[threadIdx.x + h]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = sd[0];
+    out[1] = sx[0];
+  }
+}
+
 int plan_enqueue(hqr_ls_plan *P, cudaStream_t s, bool timed) {
   if (P->prec == HQR_FP64)
     ls_prepare<double><<<grid_for(P->prep_total), 256, 0, s>>>(P->dprep, P->count, P->prep_total);
@@ -1217,6 +1241,27 @@ int hqr_ls_plan_status(hqr_ls_plan *P, void *stream) {
   CK(cudaMemcpy(stv.data(), P->dstatus, sizeof(int) * P->count, cudaMemcpyDeviceToHost));
   for (int v : stv)
     if (v) return v;
+  return HQR_SUCCESS;
+}
+
+int hqr_ls_plan_correction(hqr_ls_plan *P, int idx, double *rel, void *stream) {
+  if (!P) return -1;
+  if (idx < 0 || idx >= P->count) return -2;
+  if (!rel) return -3;
+  *rel = -1.0;
+  if (P->iters == 0) return HQR_SUCCESS;
+  const Problem &pb = P->probs[idx];
+  double *out = nullptr;
+  if (!cuda_ok(cudaMalloc(&out, 2 * sizeof(double)), "cudaMalloc(correction)")) return HQR_ERR_NOMEM;
+  cudaStream_t s = (cudaStream_t)stream;
+  vec_absmax2<<<1, 256, 0, s>>>(pb.g, pb.x, pb.N, out);
+  double h[2] = {0.0, 0.0};
+  const bool ok = cuda_ok(cudaGetLastError(), "correction kernel") &&
+                  cuda_ok(cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, s), "copy correction") &&
+                  cuda_ok(cudaStreamSynchronize(s), "sync correction");
+  cudaFree(out);
+  if (!ok) return HQR_ERR_CUDA;
+  *rel = h[1] > 0.0 ? h[0] / h[1] : (h[0] > 0.0 ? INFINITY : 0.0);
   return HQR_SUCCESS;
 }
 

@@ -30,7 +30,7 @@ ELIM_DTYPE = np.dtype([("k", np.int32), ("i", np.int32), ("killer", np.int32), (
 EXPORTS = ["hqr_elim_list", "hqr_validate_list", "hqr_task_graph", "hqr_geqrf", "hqr_refactor", "hqr_refactor_async",
            "hqr_status", "hqr_get_r", "hqr_get_tiles", "hqr_get_t", "hqr_factors_info", "hqr_kernel_ms", "hqr_trace", "hqr_apply_q",
            "hqr_gels", "hqr_geqrf_r_noalloc", "hqr_ls_plan_create", "hqr_ls_plan_run",
-           "hqr_ls_plan_capture", "hqr_ls_plan_status", "hqr_ls_plan_info", "hqr_ls_plan_config",
+           "hqr_ls_plan_capture", "hqr_ls_plan_status", "hqr_ls_plan_correction", "hqr_ls_plan_info", "hqr_ls_plan_config",
            "hqr_ls_plan_free", "hqr_ls_plan_trace", "hqr_set_tuning", "hqr_autotune", "hqr_server_create", "hqr_server_start",
            "hqr_server_submit", "hqr_server_poll", "hqr_server_stats", "hqr_server_progress", "hqr_server_counters", "hqr_server_stop", "hqr_server_free", "hqr_debug_block_task", "hqr_factors_free", "hqr_set_timeout_ms", "hqr_strerror", "hqr_last_error", "hqr_set_slab_widths",
            "hqr_set_priority_policy", "hqr_set_panel_split",
@@ -92,6 +92,7 @@ def load(build_if_missing=False):
     lib.hqr_ls_plan_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_float)]
     lib.hqr_ls_plan_config.argtypes = [vp, i32, vp]
+    lib.hqr_ls_plan_correction.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double), vp]
     lib.hqr_ls_plan_trace.argtypes = [vp, i32, vp, sz, ctypes.POINTER(sz)]
     lib.hqr_ls_plan_free.argtypes = [vp]
     lib.hqr_ls_plan_free.restype = None
@@ -476,6 +477,13 @@ class LSPlan:
 
     def status(self, stream=None):
         return load().hqr_ls_plan_status(self._h, _stream_ptr(stream))
+
+    def correction(self, idx=0, stream=None):
+        """max |d| / max |x| of the last refinement correction of problem idx (-1: no rounds)."""
+        rel = ctypes.c_double(0)
+        _check(load().hqr_ls_plan_correction(self._h, int(idx), ctypes.byref(rel), _stream_ptr(stream)),
+               "hqr_ls_plan_correction")
+        return rel.value
 
     def info(self):
         nt, fl, ms = ctypes.c_int64(0), ctypes.c_double(0), ctypes.c_float(0)

@@ -49,6 +49,8 @@ def test_batched_solves_match_oracle(mixed):
     plan = hqr.LSPlan(probs, refine_iters=6 if mixed else 0)
     plan.run()
     assert plan.status() == 0
+    if not mixed:  # no refinement rounds: no correction to report
+        assert plan.correction(0) == -1.0
     for (A, b), (_, _, x) in zip(host, probs):
         xo = lstsq_unblocked(A, b)
         err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
@@ -127,3 +129,9 @@ def test_mixed_square_conditioned_matches_oracle(kappa, iters):
     xo = lstsq_unblocked(A.double().cpu().numpy(), b.cpu().numpy())
     err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
     assert err <= 1e-12, err
+    # converged: the last correction is at the rounding level of x; two rounds are not enough
+    assert 0.0 <= plan.correction(0) <= 1e-11
+    x2 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    plan2 = hqr.LSPlan([(A, b, x2)], refine_iters=2, configs=[hqr.tile_config(128, 16, 4, 1)])
+    plan2.run()
+    assert plan2.status() == 0 and plan2.correction(0) > 1e-9
