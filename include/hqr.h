@@ -120,24 +120,29 @@ int hqr_elim_list(int m, int n, int a, int p, int low_tree, int high_tree,
 int hqr_validate_list(int m, int n, const hqr_elim_t *list, size_t count);
 
 /*
- * hqr_task_graph -- the task graph hqr_geqrf builds for an m x n tile matrix
- * and a valid list (Alg. 2 expansion with the current slab widths and panel
- * split setting), for inspection. Host only, no device work.
+ * hqr_task_graph -- a task graph the library builds for an m x n tile
+ * matrix and a valid list (Alg. 2 expansion and its dependencies, with the
+ * current slab widths and panel split setting), for inspection. Host only,
+ * no device work.
  *   nb, ib, prec  as in hqr_geqrf.
- *   tasks    caller array of 8 int32 per task: op (0 GEQRT, 1 UNMQR, 2 TSQRT,
- *            3 TSMQR, 4 TTQRT, 5 TTMQR), blk (0: the whole panel / every
- *            block; q + 1: block q of a split panel), i (killed or GEQRT
- *            row), r (killer; i for GEQRT / UNMQR), k (panel), j (target tile
- *            column), c0, cw (target columns [c0, c0 + cw)); tasks are in a
+ *   kind     0: the factorization (hqr_geqrf); 1: Q^T applied to a right-
+ *            hand side of `param` column slabs (hqr_apply_q, trans = 1);
+ *            2: Q applied (trans = 0); 3: a least-squares problem of a plan
+ *            with `param` refinement rounds (0: QR solve).
+ *   tasks    caller array of 10 int32 per task: op (0 GEQRT, 1 UNMQR,
+ *            2 TSQRT, 3 TSMQR, 4 TTQRT, 5 TTMQR, 6.. the vector tasks of
+ *            least-squares graphs), blk (0: the whole panel / every block;
+ *            q + 1: block q of a split panel), i, r, k, j, c0, cw, trans,
+ *            tgt (fields of the device task record); tasks are in a
  *            topological order.
  *   succ_ptr caller array of ntasks + 1 offsets into succ (CSR successors).
  *   succ     caller array of nedges successor ids.
- * With tasks == NULL (or a capacity too small) only *ntasks and *nedges are
- * set (HQR_ERR_CAPACITY when buffers were given but are too small).
- * Returns HQR_ERR_INVALID_LIST for an invalid list, -k for bad arguments.
+ * With tasks == NULL only *ntasks and *nedges are set (HQR_ERR_CAPACITY
+ * when buffers were given but are too small). Returns
+ * HQR_ERR_INVALID_LIST for an invalid list, -k for bad arguments.
  */
-int hqr_task_graph(int m, int n, int nb, int ib, int prec, const hqr_elim_t *list, size_t count,
-                   int32_t *tasks, int64_t task_cap, int64_t *succ_ptr, int32_t *succ, int64_t succ_cap,
+int hqr_task_graph(int m, int n, int nb, int ib, int prec, const hqr_elim_t *list, size_t count, int kind,
+                   int param, int32_t *tasks, int64_t task_cap, int64_t *succ_ptr, int32_t *succ, int64_t succ_cap,
                    int64_t *ntasks, int64_t *nedges);
 
 /*

@@ -458,8 +458,8 @@ const char *hqr_strerror(int status) {
   }
 }
 
-int hqr_task_graph(int m, int n, int nb, int ib, int prec, const hqr_elim_t *list, size_t count,
-                   int32_t *tasks, int64_t task_cap, int64_t *succ_ptr, int32_t *succ, int64_t succ_cap,
+int hqr_task_graph(int m, int n, int nb, int ib, int prec, const hqr_elim_t *list, size_t count, int kind,
+                   int param, int32_t *tasks, int64_t task_cap, int64_t *succ_ptr, int32_t *succ, int64_t succ_cap,
                    int64_t *ntasks, int64_t *nedges) {
   if (m < 1) return -1;
   if (n < 1 || n > m) return -2;
@@ -468,7 +468,9 @@ int hqr_task_graph(int m, int n, int nb, int ib, int prec, const hqr_elim_t *lis
   ib = eff_ib(prec, nb, ib);
   if (!valid_tile_sizes(prec, nb, ib)) return -4;
   if (!list && count) return -6;
-  if (!ntasks || !nedges) return -13;
+  if (kind < 0 || kind > 3) return -8;
+  if (param < 0 || ((kind == 1 || kind == 2) && param < 1)) return -9;
+  if (!ntasks || !nedges) return -16;
   if (hqr_validate_list(m, n, list, count) != HQR_SUCCESS) return HQR_ERR_INVALID_LIST;
   Problem P{};
   P.m = m;
@@ -476,15 +478,22 @@ int hqr_task_graph(int m, int n, int nb, int ib, int prec, const hqr_elim_t *lis
   P.nb = nb;
   P.ib = ib;
   choose_widths(prec, nb, ib, P);
-  const Graph g = build_factor_graph(expand_ops(list, count, m, n), m, n, nb, P.w, 0, split_ib_for(prec, P));
+  const std::vector<PanelOp> ops = expand_ops(list, count, m, n);
+  Graph g;
+  if (kind == 0)
+    g = build_factor_graph(ops, m, n, nb, P.w, 0, split_ib_for(prec, P));
+  else if (kind == 3)
+    g = build_ls_graph(ops, m, n, nb, P.w, param, 0, false, split_ib_for(prec, P));
+  else
+    g = build_apply_graph(ops, m, param, P.wb, kind == 1 ? 1 : 0);
   *ntasks = (int64_t)g.tasks.size();
   *nedges = (int64_t)g.succ.size();
   if (!tasks) return HQR_SUCCESS;
   if (task_cap < *ntasks || !succ_ptr || (*nedges > 0 && (!succ || succ_cap < *nedges))) return HQR_ERR_CAPACITY;
   for (size_t q = 0; q < g.tasks.size(); ++q) {
     const Task &t = g.tasks[q];
-    const int32_t row[8] = {t.op, t.blk, t.i, t.r, t.k, t.j, t.c0, t.cw};
-    std::memcpy(tasks + 8 * q, row, sizeof(row));
+    const int32_t row[10] = {t.op, t.blk, t.i, t.r, t.k, t.j, t.c0, t.cw, t.trans, t.tgt};
+    std::memcpy(tasks + 10 * q, row, sizeof(row));
     succ_ptr[q] = t.succ_begin;
   }
   succ_ptr[g.tasks.size()] = (int64_t)g.succ.size();

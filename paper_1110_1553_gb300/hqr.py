@@ -70,8 +70,8 @@ def load(build_if_missing=False):
     pf = ctypes.POINTER(vp)
     lib.hqr_elim_list.argtypes = [i32, i32, i32, i32, i32, i32, vp, sz, ctypes.POINTER(sz)]
     lib.hqr_validate_list.argtypes = [i32, i32, vp, sz]
-    lib.hqr_task_graph.argtypes = [i32, i32, i32, i32, i32, vp, sz, vp, i64, vp, vp, i64, ctypes.POINTER(i64),
-                                   ctypes.POINTER(i64)]
+    lib.hqr_task_graph.argtypes = [i32, i32, i32, i32, i32, vp, sz, i32, i32, vp, i64, vp, vp, i64,
+                                   ctypes.POINTER(i64), ctypes.POINTER(i64)]
     lib.hqr_geqrf.argtypes = [vp, i32, i32, i32, i32, i32, i32, vp, sz, pf, vp]
     lib.hqr_refactor.argtypes = [vp, vp, i32, vp]
     lib.hqr_refactor_async.argtypes = [vp, vp, i32, vp]
@@ -167,25 +167,30 @@ def validate_list(m, n, records):
     return lib.hqr_validate_list(m, n, arr.ctypes.data if len(arr) else None, len(arr))
 
 
-TASK_OPS = ("GEQRT", "UNMQR", "TSQRT", "TSMQR", "TTQRT", "TTMQR")
+GRAPH_KINDS = {"factor": 0, "qt": 1, "q": 2, "ls": 3}
 
 
-def task_graph(m, n, nb, ib, records, prec=FP64):
-    """Task graph of hqr_geqrf for an m x n tile matrix (host only): an int32
-    array of (op, blk, i, r, k, j, c0, cw) per task in a topological order,
-    and the successors as CSR (offsets, ids)."""
+def task_graph(m, n, nb, ib, records, prec=FP64, kind="factor", param=0):
+    """A task graph of the library for an m x n tile matrix (host only): kind
+    "factor" (hqr_geqrf), "qt" / "q" (Q^T / Q applied to `param` column
+    slabs), "ls" (a plan's least-squares problem with `param` refinement
+    rounds). Returns an int32 array of (op, blk, i, r, k, j, c0, cw, trans,
+    tgt) per task in a topological order, and the successors as CSR
+    (offsets, ids)."""
     lib = load()
     arr = records if isinstance(records, np.ndarray) else to_array(records)
     arr = np.ascontiguousarray(arr, dtype=ELIM_DTYPE)
     lp = arr.ctypes.data if len(arr) else None
+    kd = GRAPH_KINDS[kind]
     nt, ne = ctypes.c_int64(0), ctypes.c_int64(0)
-    _check(lib.hqr_task_graph(m, n, nb, ib, prec, lp, len(arr), None, 0, None, None, 0, ctypes.byref(nt),
-                              ctypes.byref(ne)), "hqr_task_graph")
-    tasks = np.zeros((nt.value, 8), dtype=np.int32)
+    _check(lib.hqr_task_graph(m, n, nb, ib, prec, lp, len(arr), kd, int(param), None, 0, None, None, 0,
+                              ctypes.byref(nt), ctypes.byref(ne)), "hqr_task_graph")
+    tasks = np.zeros((nt.value, 10), dtype=np.int32)
     ptr = np.zeros(nt.value + 1, dtype=np.int64)
     succ = np.zeros(max(ne.value, 1), dtype=np.int32)
-    _check(lib.hqr_task_graph(m, n, nb, ib, prec, lp, len(arr), tasks.ctypes.data, nt.value, ptr.ctypes.data,
-                              succ.ctypes.data, len(succ), ctypes.byref(nt), ctypes.byref(ne)), "hqr_task_graph")
+    _check(lib.hqr_task_graph(m, n, nb, ib, prec, lp, len(arr), kd, int(param), tasks.ctypes.data, nt.value,
+                              ptr.ctypes.data, succ.ctypes.data, len(succ), ctypes.byref(nt), ctypes.byref(ne)),
+           "hqr_task_graph")
     return tasks, ptr, succ[:ne.value]
 
 

@@ -17,7 +17,9 @@ from oracle.elim_list import BINARY, FIBONACCI, FLAT, GREEDY, hqr_elim_list
 hqr = pytest.importorskip("paper_1110_1553_gb300.hqr")
 
 GEQRT, UNMQR, TSQRT, TSMQR, TTQRT, TTMQR = range(6)
+RESID, ATR, TRSV_TD, TRSV_TU, TRSV_D, TRSV_U, XUPD, BTOG, PACK, ATRR, TRINV, RESR = range(6, 18)
 WEIGHT = {GEQRT: 4, UNMQR: 6, TSQRT: 6, TSMQR: 12, TTQRT: 2, TTMQR: 6}  # units of b^3 / 3 (Sec. 2)
+CHUNK = 8  # tiles per chunk of the residual / A^T r partial sums
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -30,11 +32,46 @@ def _lib():
     hqr.set_slab_widths(0, 0, 0)
 
 
-def accesses(task, nb, ib):
-    """(reads, writes) of one task as sets of (row tile, tile column, column, part)."""
-    op, blk, i, r, k, j, c0, cw = (int(x) for x in task)
-    block = range((blk - 1) * ib, blk * ib) if blk > 0 else range(nb)
+def tile(row, col, nb):
+    """Every (column, part) piece of one tile."""
+    return {(row, col, c, part) for c in range(nb) for part in "UL"}
+
+
+def accesses(task, nb, ib, m=0, n=0):
+    """(reads, writes) of one task: tile pieces (row tile, tile column, column, part), right-hand-side
+    blocks ("rhs", row, slab) and the least-squares vectors ("x" / "r" / "g" / "inv", tile),
+    ("res", row tile, column chunk), ("atr", row chunk, column tile)."""
+    op, blk, i, r, k, j, c0, cw, trans, tgt = (int(x) for x in task)
     reads, writes = set(), set()
+    if op >= RESID:  # vector tasks of a least-squares graph
+        nrc, nch = -(-n // CHUNK), -(-m // CHUNK)
+        if op == RESID:  # partial sums of A x over row tile i and column chunk j
+            reads = {("x", q) for q in range(j * CHUNK, min(n, (j + 1) * CHUNK))}
+            writes = {("res", i, j)}
+        elif op == RESR:  # r_i = b_i - sum over the chunks
+            reads, writes = {("res", i, c) for c in range(nrc)}, {("r", i)}
+        elif op == ATR:  # partial sums of A^T r over row chunk i for column tile j
+            reads = {("r", q) for q in range(i * CHUNK, min(m, (i + 1) * CHUNK))}
+            writes = {("atr", i, j)}
+        elif op == ATRR:
+            reads, writes = {("atr", c, j) for c in range(nch)}, {("g", j)}
+        elif op == TRINV:  # inverse of the diagonal R tile
+            reads, writes = tile(i, i, nb), {("inv", i)}
+        elif op in (TRSV_TD, TRSV_D):
+            reads, writes = {("inv", i), ("g", i)}, {("g", i)}
+        elif op in (TRSV_TU, TRSV_U):  # g_j -= R(i,j)^T g_i (TU) or R(j,i) g_i (U); fused: then X_j
+            reads = (tile(i, j, nb) if op == TRSV_TU else tile(j, i, nb)) | {("g", i)}
+            if tgt:
+                reads.add(("inv", j))
+            writes = {("g", j)}
+        elif op == XUPD:
+            reads, writes = {("g", j)}, {("x", j)}
+        elif op == BTOG:
+            reads, writes = {("rhs", i, 0)}, {("g", i)}
+        else:
+            raise AssertionError("unexpected task %d" % op)
+        return reads, writes
+    block = range((blk - 1) * ib, blk * ib) if blk > 0 else range(nb)
     if op in (GEQRT, TSQRT, TTQRT):  # a panel (or one block of it)
         for c in block:
             if op == GEQRT:
@@ -49,6 +86,10 @@ def accesses(task, nb, ib):
             reads.add((i, k, c, "L"))
         if op != UNMQR:
             reads.add((i, k, c, "U"))
+    rows = (i,) if op == UNMQR else (r, i)
+    if tgt:  # a right-hand-side slab
+        writes |= {("rhs", row, j) for row in rows}
+        return reads, writes
     for c in range(c0, c0 + cw):
         if blk > 0:  # a panel block applied to the panel's own trailing columns
             if op == UNMQR:
@@ -58,13 +99,12 @@ def accesses(task, nb, ib):
             else:
                 writes |= {(r, k, c, "U"), (i, k, c, "U")}
         else:  # whole target slabs of tile column j
-            rows = (i,) if op == UNMQR else (r, i)
             for row in rows:
                 writes |= {(row, j, c, "U"), (row, j, c, "L")}
     return reads, writes
 
 
-def check_no_races(tasks, ptr, succ, nb, ib):
+def check_no_races(tasks, ptr, succ, nb, ib, m=0, n=0):
     nt = len(tasks)
     preds = [[] for _ in range(nt)]
     for a in range(nt):
@@ -74,17 +114,17 @@ def check_no_races(tasks, ptr, succ, nb, ib):
     anc = [0] * nt
     last_w, readers = {}, {}
     for t in range(nt):
-        m = 0
+        before = 0  # bit q set: task q is an ancestor of t
         for p in preds[t]:
-            m |= anc[p] | (1 << p)
-        anc[t] = m
-        rd, wr = accesses(tasks[t], nb, ib)
+            before |= anc[p] | (1 << p)
+        anc[t] = before
+        rd, wr = accesses(tasks[t], nb, ib, m, n)
         for x in rd | wr:
             w = last_w.get(x)
-            assert w is None or (m >> w) & 1, ("unordered with the last writer", t, w, x)
+            assert w is None or (before >> w) & 1, ("unordered with the last writer", t, w, x)
         for x in wr:
             for q in readers.get(x, ()):
-                assert q == t or (m >> q) & 1, ("write unordered with an earlier read", t, q, x)
+                assert q == t or (before >> q) & 1, ("write unordered with an earlier read", t, q, x)
         for x in rd - wr:
             readers.setdefault(x, []).append(t)
         for x in wr:
@@ -92,8 +132,11 @@ def check_no_races(tasks, ptr, succ, nb, ib):
             readers[x] = []
 
 
-@pytest.mark.parametrize("low,high,a,p", [(FLAT, FLAT, 6, 1), (GREEDY, FIBONACCI, 2, 2), (BINARY, GREEDY, 1, 3),
-                                          (FIBONACCI, BINARY, 3, 2), (GREEDY, GREEDY, 1, 1)])
+TREE_CASES = [(FLAT, FLAT, 6, 1), (GREEDY, FIBONACCI, 2, 2), (BINARY, GREEDY, 1, 3), (FIBONACCI, BINARY, 3, 2),
+              (GREEDY, GREEDY, 1, 1)]
+
+
+@pytest.mark.parametrize("low,high,a,p", TREE_CASES)
 @pytest.mark.parametrize("nb,ib,split", [(64, 16, 64), (64, 8, 64), (64, 16, 0), (256, 32, 64)])
 def test_graph_has_no_races(low, high, a, p, nb, ib, split):
     """nb 64 / ib 8: blocks narrower than the 16-column update slabs."""
@@ -146,7 +189,7 @@ def test_split_panel_structure(nb, ib):
     blocks = [t for t in split if t[0] in (GEQRT, TSQRT, TTQRT)]
     assert all(t[1] == 0 for t in panels) and len(blocks) == nq * len(panels)
     own = [t for t in split if t[0] in (UNMQR, TSMQR, TTMQR) and t[1] > 0]
-    for (op, blk, i, r, k, j, c0, cw) in own:
+    for (op, blk, i, r, k, j, c0, cw, _, _) in own:
         assert j == k and c0 >= blk * ib and c0 // w == (c0 + cw - 1) // w
     for (op, i, r, k) in {(int(t[0]), int(t[2]), int(t[3]), int(t[4])) for t in blocks}:
         for q in range(1, nq + 1):
@@ -155,3 +198,56 @@ def test_split_panel_structure(nb, ib):
             assert cols == list(range(q * ib, nb))
     later = lambda g: sorted(tuple(int(x) for x in t) for t in g if t[0] in (UNMQR, TSMQR, TTMQR) and t[1] == 0)
     assert later(whole) == later(split)
+
+
+@pytest.mark.parametrize("low,high,a,p", TREE_CASES[:3])
+@pytest.mark.parametrize("iters,split", [(0, 64), (3, 64), (3, 0)])
+def test_least_squares_graph_has_no_races(low, high, a, p, iters, split):
+    """A plan's graph: the factorization, then Q^T b and the triangular solve (iters = 0) or
+    CSNE rounds (residual and A^T r partial sums, inverses of the diagonal tiles, fused solve
+    steps, x updates)."""
+    m, n, nb, ib = 9, 9, 64, 16
+    hqr.set_panel_split(split)
+    tasks, ptr, succ = hqr.task_graph(m, n, nb, ib, hqr_elim_list(m, n, a, p, low, high), kind="ls",
+                                      param=iters)
+    check_no_races(tasks, ptr, succ, nb, ib, m, n)
+    ops = tasks[:, 0]
+    assert (ops == XUPD).sum() == n * max(iters, 1)
+    if iters:
+        assert (ops == RESID).sum() == iters * m * -(-n // CHUNK)
+        # one fused solve step per tile pair of the chain (next tile) in each direction
+        assert ((ops == TRSV_TU) & (tasks[:, 9] == 1)).sum() == iters * (n - 1)
+        assert ((ops == TRSV_U) & (tasks[:, 9] == 1)).sum() == iters * (n - 1)
+
+
+@pytest.mark.parametrize("low,high,a,p", TREE_CASES[:3])
+def test_apply_graphs_replay_the_factorization(low, high, a, p):
+    """Q^T and Q on a right-hand side of 3 slabs: no races, and on every slab the updates
+    replay the factorization's panels in their order (Q^T) or in reverse (Q), Sec. 5.1."""
+    m, n, nb, ib = 7, 4, 64, 16
+    recs = hqr_elim_list(m, n, a, p, low, high)
+    hqr.set_panel_split(0)
+    fac, _, _ = hqr.task_graph(m, n, nb, ib, recs)
+    panels = [(int(t[0]) + 1, int(t[2]), int(t[3]), int(t[4])) for t in fac if t[0] in (GEQRT, TSQRT, TTQRT)]
+    for kind, trans in (("qt", 1), ("q", 0)):
+        tasks, ptr, succ = hqr.task_graph(m, n, nb, ib, recs, kind=kind, param=3)
+        check_no_races(tasks, ptr, succ, nb, ib)
+        assert (tasks[:, 8] == trans).all() and (tasks[:, 9] == 1).all()
+        for slab in range(3):
+            seq = [(int(t[0]), int(t[2]), int(t[3]), int(t[4])) for t in tasks if t[5] == slab]
+            assert seq == (panels if trans else panels[::-1])
+
+
+def test_race_check_catches_a_dropped_refinement_edge():
+    """The vector-task model: without the edges out of an x update, the next round's residual
+    reads x unordered, and the check reports it."""
+    m, n, nb, ib = 9, 9, 64, 16
+    tasks, ptr, succ = hqr.task_graph(m, n, nb, ib, hqr_elim_list(m, n, 2, 2, GREEDY, FIBONACCI), kind="ls",
+                                      param=2)
+    check_no_races(tasks, ptr, succ, nb, ib, m, n)
+    a = next(t for t in range(len(tasks)) if tasks[t, 0] == XUPD)
+    succ2 = np.concatenate([succ[:ptr[a]], succ[ptr[a + 1]:]])
+    ptr2 = ptr.copy()
+    ptr2[a + 1:] -= ptr[a + 1] - ptr[a]
+    with pytest.raises(AssertionError):
+        check_no_races(tasks, ptr2, succ2, nb, ib, m, n)
