@@ -251,3 +251,42 @@ def test_race_check_catches_a_dropped_refinement_edge():
     ptr2[a + 1:] -= ptr[a + 1] - ptr[a]
     with pytest.raises(AssertionError):
         check_no_races(tasks, ptr2, succ2, nb, ib, m, n)
+
+
+@pytest.mark.parametrize("prec,nb,ib,split", [
+    (hqr.FP64, 64, 16, True), (hqr.FP64, 256, 32, True), (hqr.FP64, 32, 8, False),  # FP64 from nb 64
+    (hqr.FP32, 128, 16, False), (hqr.FP32, 256, 32, True),  # FP32: only blocks spanning whole slabs
+    (hqr.FP32_BF16X3, 128, 128, False),  # tensor-core tiles keep whole panels (one block)
+])
+def test_panel_split_policy(prec, nb, ib, split):
+    recs = hqr_elim_list(3, 2, 2, 1, GREEDY, GREEDY)
+    hqr.set_panel_split(64)
+    tasks, _, _ = hqr.task_graph(3, 2, nb, ib, recs, prec=prec)
+    assert (tasks[:, 1] > 0).any() == split
+    hqr.set_panel_split(0)
+    tasks, _, _ = hqr.task_graph(3, 2, nb, ib, recs, prec=prec)
+    assert not (tasks[:, 1] > 0).any()
+    hqr.set_panel_split(64)
+
+
+def test_task_graph_arguments():
+    import ctypes
+    lib = hqr.load()
+    recs = hqr.to_array(hqr_elim_list(4, 2, 2, 1, GREEDY, GREEDY))
+    nt, ne = ctypes.c_int64(0), ctypes.c_int64(0)
+
+    def call(m=4, n=2, nb=64, ib=16, prec=0, lst=recs, kind=0, param=0, tasks=None, cap=0, ptr=None, succ=None,
+             scap=0):
+        return lib.hqr_task_graph(m, n, nb, ib, prec, lst.ctypes.data if len(lst) else None, len(lst), kind, param,
+                                  tasks, cap, ptr, succ, scap, ctypes.byref(nt), ctypes.byref(ne))
+    assert call() == 0 and nt.value > 0 and ne.value > 0
+    assert call(m=0) == -1 and call(n=5) == -2 and call(nb=12) == -3 and call(ib=5) == -4
+    assert call(kind=4) == -8 and call(kind=1, param=0) == -9
+    bad = recs.copy()
+    bad[0]["killer"] = bad[0]["i"]  # a row cannot kill itself
+    assert call(lst=bad) == hqr.ERR_INVALID_LIST
+    small = np.zeros((1, 10), dtype=np.int32)
+    ptr = np.zeros(2, dtype=np.int64)
+    succ = np.zeros(1, dtype=np.int32)
+    assert call(tasks=small.ctypes.data, cap=1, ptr=ptr.ctypes.data, succ=succ.ctypes.data, scap=1) == \
+        hqr.ERR_CAPACITY
