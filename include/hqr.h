@@ -451,6 +451,12 @@ void hqr_server_free(hqr_server *server);
 /* hqr_factors_free -- release a factorization (NULL is allowed). */
 void hqr_factors_free(hqr_factors *F);
 
+/* Process-wide settings (hqr_set_slab_widths, hqr_set_panel_split,
+ * hqr_set_priority_policy, hqr_set_timeout_ms, hqr_set_tuning): read when a
+ * factorization, plan or server request is created (the time limit: when a
+ * kernel is launched). They are plain globals: set them before, not while,
+ * other threads create work. */
+
 /* hqr_set_slab_widths -- engine tuning for factorizations and plans created
  * afterwards: column-slab width of an update task (w), of the trailing
  * update inside a panel task (wt), and V columns staged per chunk (vc,
