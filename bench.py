@@ -53,6 +53,19 @@ def dist_env():
     return rank, world, local
 
 
+def whole_job_rate(torch, dist, ms_local, flops_per_step, steps, world, device):
+    """Whole-job TFLOP/s over the slowest rank: every rank processed `steps`
+    steps of `flops_per_step` in its own `ms_local`; the job took the maximum
+    over ranks (all-reduce MAX when a process group is given). Returns
+    (TFLOP/s, that maximum in ms)."""
+    ms = float(ms_local)
+    if dist is not None and world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+    return flops_per_step * steps * world / (ms * 1e-3) / 1e12, ms
+
+
 def oracle_rate(M, N, wl, repeats=1):
     """CPU oracle (as it stands) on an M x N sample: (TFLOP/s, seconds)."""
     from oracle.elim_list import TREE_NAMES, hqr_elim_list
@@ -456,13 +469,8 @@ def main():
     st = F.status()
     if st != 0:
         raise RuntimeError("factorization failed with status %d" % st)
-    ms_total = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = t.item()
     flops = qr_flops(M, N)
-    value = flops * args.steps * world / (ms_total * 1e-3) / 1e12
+    value, ms_total = whole_job_rate(torch, dist, e0.elapsed_time(e1), flops, args.steps, world, dev)
     kern_tflops = flops / (statistics.mean(kernel_ms) * 1e-3) / 1e12
 
     # end to end through the public API with host buffers, pipelined as a
@@ -511,8 +519,7 @@ def main():
         R_host.copy_(R, non_blocking=True)
     t1.record(stream)
     torch.cuda.synchronize(dev)
-    e2e_ms = t0.elapsed_time(t1)
-    e2e_value = flops * k_e2e * world / (e2e_ms * 1e-3) / 1e12
+    e2e_value, _ = whole_job_rate(torch, dist, t0.elapsed_time(t1), flops, k_e2e, world, dev)
     del A_dev, A_host
 
     peak = measured_dgemm_tflops(torch, dev) if rank == 0 else None
