@@ -128,7 +128,8 @@ int hqr_validate_list(int m, int n, const hqr_elim_t *list, size_t count);
  *   kind     0: the factorization (hqr_geqrf); 1: Q^T applied to a right-
  *            hand side of `param` column slabs (hqr_apply_q, trans = 1);
  *            2: Q applied (trans = 0); 3: a least-squares problem of a plan
- *            with `param` refinement rounds (0: QR solve).
+ *            with `param` refinement rounds (0: QR solve); 4: the same as a
+ *            server request (packing tasks first).
  *   tasks    caller array of 10 int32 per task: op (0 GEQRT, 1 UNMQR,
  *            2 TSQRT, 3 TSMQR, 4 TTQRT, 5 TTMQR, 6.. the vector tasks of
  *            least-squares graphs), blk (0: the whole panel / every block;

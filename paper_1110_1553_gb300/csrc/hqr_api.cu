@@ -468,7 +468,7 @@ int hqr_task_graph(int m, int n, int nb, int ib, int prec, const hqr_elim_t *lis
   ib = eff_ib(prec, nb, ib);
   if (!valid_tile_sizes(prec, nb, ib)) return -4;
   if (!list && count) return -6;
-  if (kind < 0 || kind > 3) return -8;
+  if (kind < 0 || kind > 4) return -8;
   if (param < 0 || ((kind == 1 || kind == 2) && param < 1)) return -9;
   if (!ntasks || !nedges) return -16;
   if (hqr_validate_list(m, n, list, count) != HQR_SUCCESS) return HQR_ERR_INVALID_LIST;
@@ -482,8 +482,8 @@ int hqr_task_graph(int m, int n, int nb, int ib, int prec, const hqr_elim_t *lis
   Graph g;
   if (kind == 0)
     g = build_factor_graph(ops, m, n, nb, P.w, 0, split_ib_for(prec, P));
-  else if (kind == 3)
-    g = build_ls_graph(ops, m, n, nb, P.w, param, 0, false, split_ib_for(prec, P));
+  else if (kind >= 3)
+    g = build_ls_graph(ops, m, n, nb, P.w, param, 0, kind == 4, split_ib_for(prec, P));
   else
     g = build_apply_graph(ops, m, param, P.wb, kind == 1 ? 1 : 0);
   *ntasks = (int64_t)g.tasks.size();

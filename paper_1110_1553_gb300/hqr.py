@@ -167,14 +167,14 @@ def validate_list(m, n, records):
     return lib.hqr_validate_list(m, n, arr.ctypes.data if len(arr) else None, len(arr))
 
 
-GRAPH_KINDS = {"factor": 0, "qt": 1, "q": 2, "ls": 3}
+GRAPH_KINDS = {"factor": 0, "qt": 1, "q": 2, "ls": 3, "request": 4}
 
 
 def task_graph(m, n, nb, ib, records, prec=FP64, kind="factor", param=0):
     """A task graph of the library for an m x n tile matrix (host only): kind
     "factor" (hqr_geqrf), "qt" / "q" (Q^T / Q applied to `param` column
     slabs), "ls" (a plan's least-squares problem with `param` refinement
-    rounds). Returns an int32 array of (op, blk, i, r, k, j, c0, cw, trans,
+    rounds), "request" (the same as a server request, packing first). Returns an int32 array of (op, blk, i, r, k, j, c0, cw, trans,
     tgt) per task in a topological order, and the successors as CSR
     (offsets, ids)."""
     lib = load()

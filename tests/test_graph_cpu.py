@@ -68,6 +68,10 @@ def accesses(task, nb, ib, m=0, n=0):
             reads, writes = {("g", j)}, {("x", j)}
         elif op == BTOG:
             reads, writes = {("rhs", i, 0)}, {("g", i)}
+        elif op == PACK:  # tile column j from the caller's matrix; column 0 also b and x = 0
+            writes = set().union(*(tile(row, j, nb) for row in range(m)))
+            if j == 0:
+                writes |= {("rhs", row, 0) for row in range(m)} | {("x", q) for q in range(n)}
         else:
             raise AssertionError("unexpected task %d" % op)
         return reads, writes
@@ -201,15 +205,16 @@ def test_split_panel_structure(nb, ib):
 
 
 @pytest.mark.parametrize("low,high,a,p", TREE_CASES[:3])
-@pytest.mark.parametrize("iters,split", [(0, 64), (3, 64), (3, 0)])
-def test_least_squares_graph_has_no_races(low, high, a, p, iters, split):
+@pytest.mark.parametrize("iters,split,kind", [(0, 64, "ls"), (3, 64, "ls"), (3, 0, "ls"), (2, 64, "request")])
+def test_least_squares_graph_has_no_races(low, high, a, p, iters, split, kind):
     """A plan's graph: the factorization, then Q^T b and the triangular solve (iters = 0) or
     CSNE rounds (residual and A^T r partial sums, inverses of the diagonal tiles, fused solve
-    steps, x updates)."""
+    steps, x updates); a server request's graph packs the caller's matrix first."""
     m, n, nb, ib = 9, 9, 64, 16
     hqr.set_panel_split(split)
-    tasks, ptr, succ = hqr.task_graph(m, n, nb, ib, hqr_elim_list(m, n, a, p, low, high), kind="ls",
+    tasks, ptr, succ = hqr.task_graph(m, n, nb, ib, hqr_elim_list(m, n, a, p, low, high), kind=kind,
                                       param=iters)
+    assert ((tasks[:, 0] == PACK).sum() == n) == (kind == "request")
     check_no_races(tasks, ptr, succ, nb, ib, m, n)
     ops = tasks[:, 0]
     assert (ops == XUPD).sum() == n * max(iters, 1)
@@ -281,7 +286,7 @@ def test_task_graph_arguments():
                                   tasks, cap, ptr, succ, scap, ctypes.byref(nt), ctypes.byref(ne))
     assert call() == 0 and nt.value > 0 and ne.value > 0
     assert call(m=0) == -1 and call(n=5) == -2 and call(nb=12) == -3 and call(ib=5) == -4
-    assert call(kind=4) == -8 and call(kind=1, param=0) == -9
+    assert call(kind=5) == -8 and call(kind=1, param=0) == -9
     bad = recs.copy()
     bad[0]["killer"] = bad[0]["i"]  # a row cannot kill itself
     assert call(lst=bad) == hqr.ERR_INVALID_LIST
