@@ -110,6 +110,19 @@ int hqr_elim_list(int m, int n, int a, int p, int low_tree, int high_tree,
                   hqr_elim_t *out, size_t cap, size_t *count);
 
 /*
+ * hqr_elim_list_domino -- hqr_elim_list with the coupling level of Sec. 4.2
+ * (level 2, "domino"): in panel k, the TS domains and the low-level tree of
+ * domain c reduce only its rows on and below its local diagonal (local index
+ * k, tile row k p + c), to that diagonal row; the rows between the domain's
+ * top and its local diagonal (the diagonal row included) are then killed by
+ * the top, one after the other in ascending order, with TT kernels (records
+ * with level 2); the high-level tree reduces the tops as before. With p = 1
+ * the list equals hqr_elim_list's. Same arguments and returns.
+ */
+int hqr_elim_list_domino(int m, int n, int a, int p, int low_tree, int high_tree,
+                         hqr_elim_t *out, size_t cap, size_t *count);
+
+/*
  * hqr_validate_list -- check a list against the validity rules of Sec. 2:
  * every tile (i, k), i > k, killed exactly once; both rows ready (zeroed in
  * every earlier panel before this record); the killer not yet zeroed in this

@@ -13,9 +13,9 @@ A record is ``(k, i, killer, kind, level, step)``:
                 the same operation);
 * ``kind``   -- 0 = TS (a triangle kills a square), 1 = TT (a triangle kills a
                 triangle), Sec. 2 and Alg. 2;
-* ``level``  -- 0 = TS level, 1 = low level (intra-domain tree), 3 = high level
-                (tree over the p virtual domains), Sec. 4.1-4.2. Level 2
-                (domino coupling) is not generated;
+* ``level``  -- 0 = TS level, 1 = low level (intra-domain tree), 2 = coupling
+                level ("domino", only when asked for), 3 = high level (tree
+                over the p virtual domains), Sec. 4.1-4.2;
 * ``step``   -- the time step of the coarse unit-time model of Sec. 3.1-3.2
                 (every elimination takes one time unit).
 
@@ -30,6 +30,12 @@ Hierarchy (Sec. 4.1, Sec. 4.2, readings recorded in the design notes):
   domain, whose survivor is the domain's top;
 * high level: a TT reduction tree of the chosen shape over the tops of all
   domains, whose survivor is row k.
+
+With the coupling level (Sec. 4.2, "Working out an example"): levels 0 and 1
+of domain c reduce only its rows on and below its local diagonal, the row of
+local index k (global row k p + c), to that row; level 2 then kills the rows
+between the top (excluded) and the local diagonal (included) with the top as
+killer, in ascending order, TT kernels; level 3 is unchanged.
 
 Tree shapes over an ordered leaf list x0 < x1 < ... (survivor x0):
 
@@ -47,7 +53,7 @@ Tree shapes over an ordered leaf list x0 < x1 < ... (survivor x0):
 Steps: ``busy[r]`` is the step of the last elimination row r took part in.
 A fixed-shape tree's eliminations are visited in the tree's order and get
 ``step = max(busy[i], busy[killer]) + 1``. GREEDY runs the time loop itself and
-the step is the loop time. Levels are processed in the order 0, 1, 3 and the
+the step is the loop time. Levels are processed in the order 0, 1, 2, 3 and the
 records of a panel are sorted by (step, i).
 """
 
@@ -155,11 +161,11 @@ def _tree(tree, leaves, busy):
     return out
 
 
-def hqr_elim_list(m, n, a, p, low, high):
+def hqr_elim_list(m, n, a, p, low, high, domino=False):
     """Elimination list of HQR for an m x n tile matrix (m >= n), TS domains of
     a tiles, p virtual domains, low-level tree ``low`` and high-level tree
-    ``high`` (Sec. 4.1-4.2). Returns records (k, i, killer, kind, level, step)
-    sorted by (k, step, i)."""
+    ``high`` (Sec. 4.1-4.2), with the coupling level if ``domino``. Returns
+    records (k, i, killer, kind, level, step) sorted by (k, step, i)."""
     if m < 1 or n < 1 or m < n:
         raise ValueError("need m >= n >= 1")
     if a < 1 or p < 1:
@@ -173,19 +179,34 @@ def hqr_elim_list(m, n, a, p, low, high):
             rows = [i for i in range(k, m) if i % p == c]
             if not rows:
                 continue
-            heads = rows[::a]
+            top = rows[0]
+            # the local reduction starts at the local diagonal (local index k) with the
+            # coupling level, at the top without it
+            diag = k * p + c if domino else top
+            local = [i for i in rows if i >= diag]
+            coupled = [i for i in rows if top < i < diag]
+            if local and local[0] != top:
+                coupled.append(local[0])
+            heads = local[::a]
             # level 0: each head kills the a-1 rows below it with TS kernels
-            for h in range(0, len(rows), a):
-                head = rows[h]
-                for i in rows[h + 1:h + a]:
+            for h in range(0, len(local), a):
+                head = local[h]
+                for i in local[h + 1:h + a]:
                     step = max(busy[i], busy[head]) + 1
                     busy[i] = step
                     busy[head] = step
                     panel.append((k, i, head, TS, 0, step))
-            # level 1: tree over the heads; survivor = domain top
+            # level 1: tree over the heads; survivor = the local diagonal (the top
+            # without the coupling level)
             for kd, kr, step in _tree(low, heads, busy):
                 panel.append((k, kd, kr, TT, 1, step))
-            tops.append(rows[0])
+            # level 2 (domino): the top kills the coupled rows one after the other
+            for i in coupled:
+                step = max(busy[i], busy[top]) + 1
+                busy[i] = step
+                busy[top] = step
+                panel.append((k, i, top, TT, 2, step))
+            tops.append(top)
         tops.sort()
         # level 3: tree over the domain tops; survivor = row k
         for kd, kr, step in _tree(high, tops, busy):

@@ -2,8 +2,8 @@
 //
 // Sec. 4.1-4.2 compose the list from per-panel reduction trees: TS domains of
 // `a` tiles (level 0), a low-level tree over the TS heads of each of the p
-// virtual domains (level 1), and a high-level tree over the domain tops
-// (level 3). Tree shapes follow Sec. 3.1 (flat, binary), Sec. 3.2 (greedy,
+// virtual domains (level 1), optionally the coupling ("domino") level
+// (level 2), and a high-level tree over the domain tops (level 3). Tree shapes follow Sec. 3.1 (flat, binary), Sec. 3.2 (greedy,
 // Table 4) and the Modi-Clarke "Fibonacci" scheme that Sec. 3.3 names.
 // Steps follow the unit-time model of Sec. 3.1-3.2.
 #include <algorithm>
@@ -124,8 +124,18 @@ void run_tree(int tree, const std::vector<int> &leaves, std::vector<int> &busy,
 
 }  // namespace
 
-extern "C" int hqr_elim_list(int m, int n, int a, int p, int low_tree, int high_tree,
-                             hqr_elim_t *out, size_t cap, size_t *count) {
+namespace {
+
+// The list of Sec. 4.1-4.2. In panel k the active rows of domain c are its
+// rows >= k; its top is the first of them. Without the coupling level the TS
+// domains and the low-level tree reduce all active rows to the top. With it
+// (Sec. 4.2, level 2) they reduce only the rows on and below the domain's
+// local diagonal (local index k, row k p + c), whose survivor is that
+// diagonal row; the rows between the top and the local diagonal (the
+// diagonal row included) are then killed by the top, one after the other in
+// ascending order, with TT kernels (the domino tree).
+int elim_list(int m, int n, int a, int p, int low_tree, int high_tree, bool domino, hqr_elim_t *out,
+              size_t cap, size_t *count) {
   if (m < 1) return -1;
   if (n < 1 || n > m) return -2;
   if (a < 1) return -3;
@@ -141,7 +151,7 @@ extern "C" int hqr_elim_list(int m, int n, int a, int p, int low_tree, int high_
 
   std::vector<int> busy(m, 0);
   std::vector<hqr_elim_t> panel;
-  std::vector<int> rows, heads, tops;
+  std::vector<int> rows, local, coupled, heads, tops;
   std::vector<Emit> em;
   size_t pos = 0;
   for (int k = 0; k < n; ++k) {
@@ -153,12 +163,23 @@ extern "C" int hqr_elim_list(int m, int n, int a, int p, int low_tree, int high_
       int first = k + ((c - k % p) % p + p) % p;
       for (int i = first; i < m; i += p) rows.push_back(i);
       if (rows.empty()) continue;
+      const int top = rows[0];
+      const long long base = domino ? (long long)k * p + c : top;  // first row of the local reduction
+      local.clear();
+      coupled.clear();
+      for (int i : rows) {
+        if (i >= base)
+          local.push_back(i);
+        else if (i > top)
+          coupled.push_back(i);
+      }
+      if (!local.empty() && local[0] != top) coupled.push_back(local[0]);  // the local survivor
       heads.clear();
-      for (size_t h = 0; h < rows.size(); h += (size_t)a) {
-        heads.push_back(rows[h]);
-        const int head = rows[h];
-        for (size_t q = h + 1; q < h + (size_t)a && q < rows.size(); ++q) {
-          const int i = rows[q];
+      for (size_t h = 0; h < local.size(); h += (size_t)a) {
+        heads.push_back(local[h]);
+        const int head = local[h];
+        for (size_t q = h + 1; q < h + (size_t)a && q < local.size(); ++q) {
+          const int i = local[q];
           const int step = std::max(busy[i], busy[head]) + 1;
           busy[i] = step;
           busy[head] = step;
@@ -168,7 +189,13 @@ extern "C" int hqr_elim_list(int m, int n, int a, int p, int low_tree, int high_
       em.clear();
       run_tree(low_tree, heads, busy, em);
       for (const Emit &e : em) panel.push_back({k, e.killed, e.killer, HQR_KIND_TT, 1, e.step});
-      tops.push_back(rows[0]);
+      for (int i : coupled) {  // level 2: the top kills the coupled rows in ascending order
+        const int step = std::max(busy[i], busy[top]) + 1;
+        busy[i] = step;
+        busy[top] = step;
+        panel.push_back({k, i, top, HQR_KIND_TT, 2, step});
+      }
+      tops.push_back(top);
     }
     std::sort(tops.begin(), tops.end());
     em.clear();
@@ -180,6 +207,18 @@ extern "C" int hqr_elim_list(int m, int n, int a, int p, int low_tree, int high_
     for (const hqr_elim_t &r : panel) out[pos++] = r;
   }
   return pos == need ? HQR_SUCCESS : HQR_ERR_INTERNAL;
+}
+
+}  // namespace
+
+extern "C" int hqr_elim_list(int m, int n, int a, int p, int low_tree, int high_tree,
+                             hqr_elim_t *out, size_t cap, size_t *count) {
+  return elim_list(m, n, a, p, low_tree, high_tree, false, out, cap, count);
+}
+
+extern "C" int hqr_elim_list_domino(int m, int n, int a, int p, int low_tree, int high_tree,
+                                    hqr_elim_t *out, size_t cap, size_t *count) {
+  return elim_list(m, n, a, p, low_tree, high_tree, true, out, cap, count);
 }
 
 extern "C" int hqr_validate_list(int m, int n, const hqr_elim_t *list, size_t count) {

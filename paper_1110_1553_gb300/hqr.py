@@ -27,7 +27,7 @@ FP64, FP32, FP32_BF16X3 = 0, 1, 2
 ELIM_DTYPE = np.dtype([("k", np.int32), ("i", np.int32), ("killer", np.int32), ("kind", np.int32),
                        ("level", np.int32), ("step", np.int32)])
 
-EXPORTS = ["hqr_elim_list", "hqr_validate_list", "hqr_task_graph", "hqr_geqrf", "hqr_refactor", "hqr_refactor_async",
+EXPORTS = ["hqr_elim_list", "hqr_elim_list_domino", "hqr_validate_list", "hqr_task_graph", "hqr_geqrf", "hqr_refactor", "hqr_refactor_async",
            "hqr_status", "hqr_get_r", "hqr_get_tiles", "hqr_get_t", "hqr_factors_info", "hqr_kernel_ms", "hqr_trace", "hqr_apply_q",
            "hqr_gels", "hqr_geqrf_r_noalloc", "hqr_ls_plan_create", "hqr_ls_plan_run",
            "hqr_ls_plan_capture", "hqr_ls_plan_status", "hqr_ls_plan_correction", "hqr_ls_plan_info", "hqr_ls_plan_config",
@@ -69,6 +69,7 @@ def load(build_if_missing=False):
     vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
     pf = ctypes.POINTER(vp)
     lib.hqr_elim_list.argtypes = [i32, i32, i32, i32, i32, i32, vp, sz, ctypes.POINTER(sz)]
+    lib.hqr_elim_list_domino.argtypes = [i32, i32, i32, i32, i32, i32, vp, sz, ctypes.POINTER(sz)]
     lib.hqr_validate_list.argtypes = [i32, i32, vp, sz]
     lib.hqr_task_graph.argtypes = [i32, i32, i32, i32, i32, vp, sz, i32, i32, vp, i64, vp, vp, i64,
                                    ctypes.POINTER(i64), ctypes.POINTER(i64)]
@@ -133,19 +134,20 @@ def _check(status, where):
 
 # ----------------------------------------------------------- host only --
 
-def elim_list(m, n, a, p, low, high):
+def elim_list(m, n, a, p, low, high, domino=False):
     """HQR elimination list as a structured numpy array (fields k, i,
-    killer, kind, level, step), sorted by (k, step, i)."""
+    killer, kind, level, step), sorted by (k, step, i); with domino=True the
+    coupling level of Sec. 4.2 is included (hqr_elim_list_domino)."""
     lib = load()
+    fn = lib.hqr_elim_list_domino if domino else lib.hqr_elim_list
     low = TREES.get(low, low)
     high = TREES.get(high, high)
     cnt = ctypes.c_size_t(0)
-    st = lib.hqr_elim_list(m, n, a, p, low, high, None, 0, ctypes.byref(cnt))
+    st = fn(m, n, a, p, low, high, None, 0, ctypes.byref(cnt))
     if st not in (0, ERR_CAPACITY):
         _check(st, "hqr_elim_list")
     out = np.zeros(cnt.value, dtype=ELIM_DTYPE)
-    st = lib.hqr_elim_list(m, n, a, p, low, high, out.ctypes.data if cnt.value else None, cnt.value,
-                           ctypes.byref(cnt))
+    st = fn(m, n, a, p, low, high, out.ctypes.data if cnt.value else None, cnt.value, ctypes.byref(cnt))
     _check(st, "hqr_elim_list")
     return out
 

@@ -295,3 +295,15 @@ def test_task_graph_arguments():
     succ = np.zeros(1, dtype=np.int32)
     assert call(tasks=small.ctypes.data, cap=1, ptr=ptr.ctypes.data, succ=succ.ctypes.data, scap=1) == \
         hqr.ERR_CAPACITY
+
+
+@pytest.mark.parametrize("split", [64, 0])
+def test_graph_with_coupling_level_has_no_races(split):
+    """Lists with the coupling (domino) level: level-2 TT kills by the domain tops."""
+    m, n, nb, ib = 10, 5, 64, 16
+    hqr.set_panel_split(split)
+    for low, high, a, p in ((GREEDY, FIBONACCI, 2, 3), (FLAT, BINARY, 1, 4)):
+        recs = hqr_elim_list(m, n, a, p, low, high, domino=True)
+        assert any(r[4] == 2 for r in recs)
+        tasks, ptr, succ = hqr.task_graph(m, n, nb, ib, recs)
+        check_no_races(tasks, ptr, succ, nb, ib)

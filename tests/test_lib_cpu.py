@@ -63,6 +63,21 @@ def test_lists_bit_exact_workload_shapes(lib, m, n, a, p):
             assert hqr.validate_list(m, n, got) == 0
 
 
+def test_domino_lists_bit_exact(lib):
+    trees = (FLAT, BINARY, GREEDY, FIBONACCI)
+    for m in range(1, 8):
+        for n in range(1, m + 1):
+            for a in range(1, m + 1):
+                for p in range(1, m + 1):
+                    for lo, hi in itertools.product(trees, trees):
+                        got = hqr.as_records(hqr.elim_list(m, n, a, p, lo, hi, domino=True))
+                        assert got == [tuple(r) for r in hqr_elim_list(m, n, a, p, lo, hi, domino=True)]
+    for (m, n, a, p) in [(24, 10, 2, 3), (512, 8, 4, 16), (100, 37, 3, 7)]:
+        got = hqr.elim_list(m, n, a, p, GREEDY, FIBONACCI, domino=True)
+        assert hqr.as_records(got) == [tuple(r) for r in hqr_elim_list(m, n, a, p, GREEDY, FIBONACCI, domino=True)]
+        assert hqr.validate_list(m, n, got) == 0
+
+
 def test_capacity_and_argument_errors(lib):
     import ctypes
     cnt = ctypes.c_size_t(0)

@@ -219,3 +219,88 @@ def test_triangle_rows():
     L = hqr_elim_list(8, 8, 8, 1, FLAT, FLAT)
     for k in range(8):
         assert triangle_rows(L, k, 8, 8) == {k}
+
+
+# ----------------------------------------------------- coupling level --
+# Sec. 4.2 ("Working out an example", m = 24, n = 10, p = 3, a = 2): tiles
+# (4, 1) and (5, 1) are level-2 ("domino") tiles killed by their clusters' top
+# tiles (1, 1) and (2, 1), after the inter-cluster eliminations elim(1, 0, 0)
+# and elim(2, 0, 0) updated those tops; the last local killer of cluster P0 in
+# panel 2 is its local diagonal tile (6, 2).
+
+def _domino_structure(L, m, n, a, p):
+    assert validate(L, m, n) is None
+    assert L == sorted(L, key=lambda r: (r[0], r[5], r[1]))
+    last = {}
+    for (k, i, killer, kind, level, step) in L:
+        for r in (i, killer):
+            assert last.get(r, 0) < step
+            last[r] = step
+    for k in range(n):
+        recs = [r for r in L if r[0] == k]
+        assert {r[1] for r in recs} == set(range(k + 1, m))
+        for c in range(p):
+            rows = [i for i in range(k, m) if i % p == c]
+            if not rows:
+                continue
+            top, diag = rows[0], k * p + c
+            local = [i for i in rows if i >= diag]
+            mine = [r for r in recs if r[1] % p == c and r[4] in (0, 1, 2)]
+            for (kk, i, killer, kind, level, step) in mine:
+                if level == 2:  # coupled rows: between the top and the local diagonal, killed by the top
+                    assert killer == top and kind == TT and top < i <= diag
+                else:  # local rows: on or below the local diagonal, reduced to it
+                    assert i > diag and killer >= diag and killer % p == c
+            coupled = sorted(r[1] for r in mine if r[4] == 2)
+            assert coupled == [i for i in rows if top < i < diag] + ([local[0]] if local and local[0] != top else [])
+            steps = [r[5] for r in sorted((r for r in mine if r[4] == 2), key=lambda r: r[1])]
+            assert steps == sorted(steps)  # ascending, one after the other
+    assert total_weight(L, m, n) == 6 * m * n * n - 2 * n ** 3
+
+
+@pytest.mark.parametrize("high", [FLAT, BINARY])
+def test_domino_example_facts(high):
+    for low in TREES:
+        L = hqr_elim_list(24, 10, 2, 3, low, high, domino=True)
+        rec = {(r[0], r[1], r[2]): r for r in L}
+        assert rec[(1, 4, 1)][4] == 2 and rec[(1, 5, 2)][4] == 2
+        assert rec[(0, 1, 0)][4] == 3 and rec[(0, 2, 0)][4] == 3
+        assert rec[(1, 4, 1)][5] > rec[(0, 1, 0)][5]
+        assert rec[(1, 5, 2)][5] > rec[(0, 2, 0)][5]
+        local = [r for r in L if r[0] == 2 and r[1] % 3 == 0 and r[4] in (0, 1)]
+        assert max(local, key=lambda r: r[5])[2] == 6
+        assert all(r[1] != 6 for r in local)
+        _domino_structure(L, 24, 10, 2, 3)
+
+
+def test_domino_with_one_domain_is_the_plain_list():
+    for m, n, a in ((8, 8, 1), (9, 4, 3), (16, 5, 16)):
+        for low, high in itertools.product(TREES, TREES):
+            assert hqr_elim_list(m, n, a, 1, low, high, domino=True) == hqr_elim_list(m, n, a, 1, low, high)
+
+
+def test_domino_bruteforce_small_shapes():
+    count = 0
+    for m in range(1, 8):
+        for n in range(1, m + 1):
+            for a in range(1, m + 1):
+                for p in range(1, m + 1):
+                    for low, high in itertools.product(TREES, TREES):
+                        _domino_structure(hqr_elim_list(m, n, a, p, low, high, domino=True), m, n, a, p)
+                        count += 1
+    assert count > 10000
+
+
+def test_domino_medium_and_level_counts():
+    m, n, a, p = 64, 8, 4, 16
+    L = hqr_elim_list(m, n, a, p, GREEDY, FIBONACCI, domino=True)
+    _domino_structure(L, m, n, a, p)
+    # the number of coupled rows grows with the panel: k - (local index of the top) per domain
+    for k in range(n):
+        want = 0
+        for c in range(p):
+            rows = [i for i in range(k, m) if i % p == c]
+            if rows:
+                want += len([i for i in rows if rows[0] < i <= k * p + c])
+        assert sum(1 for r in L if r[0] == k and r[4] == 2) == want
+    assert not any(r[4] == 2 for r in hqr_elim_list(m, n, a, p, GREEDY, FIBONACCI))

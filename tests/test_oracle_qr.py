@@ -129,6 +129,18 @@ def test_tile_qr_matches_unblocked(low, high):
         assert np.max(np.abs(_rt(F.R()) - Ru)) <= 1e-12 * nrm
 
 
+@pytest.mark.parametrize("low,high", [(FLAT, FLAT), (GREEDY, FIBONACCI), (BINARY, GREEDY)])
+def test_tile_qr_with_coupling_level_matches_unblocked(low, high):
+    """Lists with the coupling (domino) level of Sec. 4.2 are valid factorization orders too."""
+    b, ib, m, n = 8, 3, 12, 6
+    A = rng(15).standard_normal((m * b, n * b))
+    Ru = _rt(householder_qr(A)[0])
+    nrm = np.linalg.norm(A)
+    for a, p in ((1, 3), (2, 3), (2, 4)):
+        F = tile_qr(A, b, ib, hqr_elim_list(m, n, a, p, low, high, domino=True))
+        assert np.max(np.abs(_rt(F.R()) - Ru)) <= 1e-12 * nrm
+
+
 def test_unblocked_matches_lapack():
     A = rng(6).standard_normal((50, 20))
     assert np.allclose(_rt(householder_qr(A)[0]), _rt(np.linalg.qr(A)[1]), atol=1e-13)
