@@ -9,6 +9,7 @@ checks: each builds its seeded synthetic input, runs the operation once
 Cases:
   fp64_tall_skinny  FP64 HQR of rows x 2048 (nb 256, ib 32, a 4, p 16,
                     greedy / Fibonacci), the benchmark's configuration
+                    (--domino: with the coupling level of Sec. 4.2)
   fp32_tc_square    FP32 tile QR of n x n on the tensor-core kernels
                     (nb 128, a 16, greedy / greedy)
   fp32_cc_square    the same on the CUDA-core FP32 kernels (ib 16)
@@ -26,6 +27,7 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=6144)
     ap.add_argument("--iters", type=int, default=16)
     ap.add_argument("--once", action="store_true", help="no untimed first run")
+    ap.add_argument("--domino", action="store_true", help="fp64_tall_skinny: list with the coupling level (Sec. 4.2)")
     a = ap.parse_args(argv)
     import torch
 
@@ -38,7 +40,7 @@ def main(argv=None):
     if a.case == "fp64_tall_skinny":
         M, N, nb = a.rows, 2048, 256
         A = inputs.gaussian_torch(M, N, seed=1, device=dev)
-        recs = hqr.elim_list(M // nb, N // nb, 4, 16, "greedy", "fibonacci")
+        recs = hqr.elim_list(M // nb, N // nb, 4, 16, "greedy", "fibonacci", domino=a.domino)
         F = hqr.geqrf(A, nb, 32, recs)
         for _ in range(runs - 1):
             F.refactor(A)
