@@ -46,9 +46,10 @@ typedef enum { HQR_FLAT = 0, HQR_BINARY = 1, HQR_GREEDY = 2, HQR_FIBONACCI = 3 }
 typedef enum { HQR_KIND_TS = 0, HQR_KIND_TT = 1 } hqr_kind_t;
 
 /* One elimination elim(i, killer, k) of Sec. 2: tile (i, k) is zeroed by
- * tile (killer, k). level: 0 = TS level, 1 = low level, 3 = high level
- * (Sec. 4.2; level 2, the domino level, is not generated). step: time step
- * of the unit-time model of Sec. 3.1-3.2. 24 bytes, no padding surprises. */
+ * tile (killer, k). level: 0 = TS level, 1 = low level, 2 = coupling
+ * ("domino") level, only in lists from hqr_elim_list_domino, 3 = high level
+ * (Sec. 4.2). step: time step of the unit-time model of Sec. 3.1-3.2.
+ * 24 bytes, no padding surprises. */
 typedef struct {
   int32_t k;
   int32_t i;
@@ -100,8 +101,10 @@ typedef struct hqr_factors hqr_factors;
  *   count     receives the number of records, sum_{k<n} (m-k-1).
  * Records are written sorted by (k, step, i). If cap is too small nothing is
  * written, *count is set and HQR_ERR_CAPACITY is returned.
- * Readings of the paper (also in the design notes): heads are every a-th
- * active row counted from the domain top; GREEDY takes readiness into account
+ * Where the paper leaves a rule open (Sec. 3.3 names FIBONACCI without
+ * defining it; Sec. 4.1 refers to a lost figure for the TS domain alignment),
+ * this library reads it as follows: heads are every a-th active row counted
+ * from the domain top; GREEDY takes readiness into account
  * (a row is a candidate at step t once its last elimination is before t);
  * FIBONACCI cuts the leaves below the survivor into groups of 1, 2, 3, ...
  * killed by the same number of leaves right above them, bottom group first.
@@ -286,6 +289,10 @@ int hqr_debug_block_task(hqr_factors *F, int64_t task, int extra);
  * scratch array that is a static device variable of the library: it is
  * reserved on every GPU that loads the library until the process exits.
  * Larger problems return HQR_ERR_TOO_LARGE before any device work.
+ * The schedule is a simpler one than hqr_geqrf's: fixed priority classes
+ * (panels, then updates of the next tile column, then the rest) and whole
+ * panel tasks (no split panels); the arithmetic of each task is the same.
+ * An invalid list returns -7 (argument 7, as every -k code names argument k).
  * No cudaMalloc, cudaFree or other allocating call is made. The first call
  * on each device looks up that device's scratch address (a one-time set-up);
  * make that first call before any stream capture. All calls share the one

@@ -19,7 +19,8 @@ A record is ``(k, i, killer, kind, level, step)``:
 * ``step``   -- the time step of the coarse unit-time model of Sec. 3.1-3.2
                 (every elimination takes one time unit).
 
-Hierarchy (Sec. 4.1, Sec. 4.2, readings recorded in the design notes):
+Hierarchy (Sec. 4.1, Sec. 4.2; where the paper is silent, the reading taken
+is stated with the rule):
 
 * tile row i belongs to virtual domain ``i mod p`` (cyclic distribution);
 * in panel k the active rows of a domain are its rows ``>= k``, ascending, and

@@ -67,3 +67,40 @@ def test_properties_at_full_size(fullsize):
     nb0 = b.norm(dim=0)
     F.apply_q(b, trans=True)
     assert ((b.norm(dim=0) - nb0).abs() / nb0).max().item() <= 1e-13
+
+
+# ------------------------------------------------- with the coupling level --
+# The same workload with the coupling ("domino") level of Sec. 4.2. Panel 0
+# has no coupled rows, so R[:512, :512] (panels 0 and 1 on the first two tile
+# columns) is compared with the oracle; properties that hold at any size are
+# checked on the whole result.
+
+@pytest.fixture(scope="module")
+def fullsize_domino(fullsize):
+    A, Ad, _ = fullsize
+    recs = hqr.elim_list(M // NB, N // NB, A_, P_, "greedy", "fibonacci", domino=True)
+    assert any(int(r["level"]) == 2 for r in recs)
+    return A, Ad, hqr.geqrf(Ad, NB, IB, recs)
+
+
+def test_domino_first_two_tile_columns_match_oracle(fullsize_domino):
+    A, Ad, F = fullsize_domino
+    recs2 = hqr_elim_list(M // NB, 2, A_, P_, GREEDY, FIBONACCI, domino=True)
+    full = hqr.as_records(hqr.elim_list(M // NB, N // NB, A_, P_, "greedy", "fibonacci", domino=True))
+    assert [r for r in full if r[0] < 2] == [tuple(r) for r in recs2]
+    Fo = tile_qr(A[:, :2 * NB], NB, IB, recs2)
+    Rg = F.R()[:2 * NB, :2 * NB].cpu().numpy()
+    assert np.max(np.abs(Rg - Fo.R())) <= 1e-11 * np.linalg.norm(A[:, :2 * NB])
+
+
+def test_domino_properties_at_full_size(fullsize_domino):
+    A, Ad, F = fullsize_domino
+    R = F.R()
+    cn = (R.norm(dim=0) - Ad.norm(dim=0)).abs() / Ad.norm(dim=0)
+    assert cn.max().item() <= 1e-13
+    x = torch.randn(N, 2, dtype=torch.float64, device="cuda")
+    y = (Ad @ x).t().contiguous().t()
+    F.apply_q(y, trans=True)
+    rx = R @ x
+    assert ((y[:N] - rx).abs().max() / rx.abs().max()).item() <= 1e-12
+    assert (y[N:].abs().max() / rx.abs().max()).item() <= 1e-12

@@ -56,3 +56,24 @@ def test_noalloc_rejects_oversized_problems():
     A = torch.zeros((256, 128), dtype=torch.float64, device="cuda")
     R = hqr.empty_colmajor(128, 128)
     assert hqr.geqrf_r_noalloc(A, 128, 16, recs, R) == hqr.ERR_TOO_LARGE  # nb > 64
+
+
+def test_noalloc_layout_over_the_scratch_size_then_a_normal_call():
+    # 64 x 4 tiles of 64 with ib = 32: within the tile-count limits, but the
+    # tiles (8 MiB) and T factors (8 MiB) with the task graph exceed the
+    # 16 MiB scratch: rejected before any device work
+    nb, ib = 64, 32
+    M, N = 64 * nb, 4 * nb
+    recs = hqr.elim_list(64, 4, 4, 1, "greedy", "greedy")
+    A = torch.zeros((M, N), dtype=torch.float64, device="cuda")
+    R = hqr.empty_colmajor(N, N)
+    assert hqr.geqrf_r_noalloc(A, nb, ib, recs, R) == hqr.ERR_TOO_LARGE
+    # the next call that fits still gives the regular factorization's R
+    M, N = 512, 256
+    recs = hqr.elim_list(M // nb, N // nb, 2, 2, "greedy", "fibonacci")
+    A = torch.from_numpy(inputs.gaussian(M, N, seed=33)).cuda()
+    R = hqr.empty_colmajor(N, N)
+    R.fill_(np.nan)
+    assert hqr.geqrf_r_noalloc(A, nb, ib, recs, R) == 0
+    Rref = hqr.geqrf(A, nb, ib, recs).R()
+    assert ((R - Rref).abs().max() / torch.linalg.norm(A)).item() <= R_TOL
