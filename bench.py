@@ -199,7 +199,7 @@ def ncu_traffic():
     return float(m_b.group(1)), None
 
 
-def latency_square(torch, hqr, inputs, dev, reps=100):
+def latency_square(torch, hqr, inputs, dev, reps=100, peak=None):
     """512 x 512 FP64 (nb 64, ib 16, flat TS a = 8): QR plus Q applied to I,
     device time per call, p50 / p99 over `reps` calls."""
     A = inputs.gaussian_torch(512, 512, seed=11, device=dev)
@@ -220,12 +220,60 @@ def latency_square(torch, hqr, inputs, dev, reps=100):
             times.append(e0.elapsed_time(e1) * 1e3)
     times.sort()
     fl = 2 * 512 ** 3 - 2 / 3 * 512 ** 3
-    return {"workload": "fp64_square_512_nb64_ib16_flat_ts", "p50_us": times[len(times) // 2],
-            "p99_us": times[min(len(times) - 1, int(0.99 * len(times)))], "qr_flops": fl,
-            "includes": "tile QR + Q applied to I (apply-Q graph), per call"}
+    fq = 4.0 * 512 * 512 * 512 - 2.0 * 512 * 512 * 512  # Q applied to I: 4 M N r - 2 N^2 r, r = N
+    p50 = times[len(times) // 2]
+    out = {"workload": "fp64_square_512_nb64_ib16_flat_ts", "p50_us": p50,
+           "p99_us": times[min(len(times) - 1, int(0.99 * len(times)))], "qr_flops": fl, "q_flops": fq,
+           "includes": "tile QR + Q applied to I (apply-Q graph), per call"}
+    if peak:
+        tf = (fl + fq) / (p50 * 1e-6) / 1e12
+        out["roofline"] = {"bound": "latency", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                           "peak_source": "in-run FP64 DGEMM (context: the case is bound by its critical path)"}
+    return out
 
 
-def batched(torch, hqr, dev, count=1024, refine=4, tune=True):
+def batched_buckets(torch, hqr, plan, probs, shapes, dtype, iters, tensor, peaks, reps=3):
+    """The batch split by the tile size its configuration chose (32, 64, 128),
+    each bucket solved alone in one launch (CUDA graph): QR TFLOP/s (paper's
+    flop count over the whole solve, refinement included) against the
+    bucket's roofline: the update arithmetic (FP32 FFMA, BF16x3 tensor or
+    the FP64 pipe) or HBM at the updates' intensity (nb / (element size)
+    flop/B)."""
+    cfgs = [plan.config(q) for q in range(len(probs))]
+    out = {}
+    for nb in sorted({c[0] for c in cfgs}):
+        idx = [q for q, c in enumerate(cfgs) if c[0] == nb]
+        sub = [probs[q] for q in idx]
+        sp = hqr.LSPlan(sub, refine_iters=iters, configs=[hqr.tile_config(*cfgs[q]) for q in idx], tensor=tensor)
+        s = torch.cuda.Stream()
+        sp.capture(s)
+        sp.run(s)
+        s.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            sp.run(s)
+        e1.record(s)
+        e1.synchronize()
+        st = sp.status(s)
+        ms = e0.elapsed_time(e1) / reps
+        fl = sp.info()["qr_flops"]
+        tf = fl / (ms * 1e-3) / 1e12
+        if dtype == torch.float64:
+            hbm = peaks["hbm_gbs"] * 1e9 * nb / 8.0 / 1e12
+            alu = 2 * FP64_OPS_PER_S / 1e12
+            bound, pk = ("hbm", hbm) if hbm < alu else ("alu", alu)
+        else:
+            bound, pk = fp32_qr_bound(peaks, nb, tensor and nb == 128)
+        out["nb%d" % nb] = {"problems": len(idx), "solves_per_s": len(idx) / (ms * 1e-3), "ms": ms,
+                            "qr_tflops": tf, "status": st,
+                            "roofline": {"bound": bound, "achieved": tf, "peak": pk, "unit": "TFLOP/s",
+                                         "frac": tf / pk}}
+        del sp
+    return out
+
+
+def batched(torch, hqr, dev, count=1024, refine=4, tune=True, peaks=None):
     """1024 uneven least-squares problems in one persistent launch: mixed
     (FP32 QR + FP64 CSNE) and plain FP64 (QR + Q^T b + back substitution)."""
     from paper_1110_1553_gb300 import workloads
@@ -267,6 +315,9 @@ def batched(torch, hqr, dev, count=1024, refine=4, tune=True):
                       "refine_iters": iters, "status": st, "launches_per_batch": 3, "cuda_graph": True,
                       "tensor_cores": tensor}
         out["_x_" + label] = [p[2] for p in probs[:8]]
+        if peaks is not None:
+            out[label]["buckets"] = batched_buckets(torch, hqr, plan, probs, shapes, dtype, iters, tensor, peaks)
+        del plan
         hqr.set_tuning({})
     out["mixed_over_fp64"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
     out["mixed_tc_over_fp64"] = out["mixed_tc"]["solves_per_s"] / out["fp64"]["solves_per_s"]
@@ -274,7 +325,7 @@ def batched(torch, hqr, dev, count=1024, refine=4, tune=True):
     return out
 
 
-def serving(torch, hqr, dev, rate=2000.0, seconds=5.0, refine=5):
+def serving(torch, hqr, dev, rate=2000.0, seconds=5.0, refine=5, peaks=None):
     """Poisson request stream at `rate` req/s for `seconds`: 90 % uneven
     batched-like shapes, 10 % 32768 x 1024 FP32 with kappa = 1e4. Mixed server
     vs plain FP64 server on the same arrivals."""
@@ -304,6 +355,7 @@ def serving(torch, hqr, dev, rate=2000.0, seconds=5.0, refine=5):
                          task_pool=16 << 20, edge_pool=64 << 20, tensor=tensor)
         srv.start()
         lat, inflight, queue = [], {}, deque()
+        done_flops = 0.0
         t0 = time.perf_counter()
         i = 0
         try:
@@ -319,12 +371,14 @@ def serving(torch, hqr, dev, rate=2000.0, seconds=5.0, refine=5):
                     t = srv.submit(A, b, x)
                     if t is None:
                         break
-                    inflight[t] = arrivals[q]
+                    inflight[t] = (arrivals[q], qr_flops(A.shape[0], A.shape[1]))
                     queue.popleft()
                 done = srv.poll()
                 now = time.perf_counter() - t0
                 for t in done:
-                    lat.append(now - inflight.pop(t))
+                    arr, fl = inflight.pop(t)
+                    lat.append(now - arr)
+                    done_flops += fl
                 if now > seconds * 4:  # a saturated server: stop at 4x the arrival window
                     break
             wall = time.perf_counter() - t0
@@ -335,12 +389,70 @@ def serving(torch, hqr, dev, rate=2000.0, seconds=5.0, refine=5):
                       "solves_per_s": len(lat) / wall, "wall_s": wall,
                       "p50_ms": 1e3 * lat[len(lat) // 2] if lat else None,
                       "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None,
-                      "refine_iters": iters, "tensor_cores": tensor}
+                      "refine_iters": iters, "tensor_cores": tensor,
+                      "qr_tflops": done_flops / wall / 1e12}
+        if peaks is not None:
+            pk = peaks["bf16_tflops_sustained"] / 6.0 if tensor else 2 * FP64_OPS_PER_S / 1e12
+            out[label]["roofline"] = {
+                "bound": "tensor" if tensor else "alu", "achieved": done_flops / wall / 1e12, "peak": pk,
+                "unit": "TFLOP/s", "frac": done_flops / wall / 1e12 / pk,
+                "peak_source": ("%s BF16 sustained / 6 (BF16x3)" % peaks["source"]) if tensor else
+                               "FP64 pipe: 152 SMs x 2 FMA/cycle x 2.07 GHz"}
         del srv
     return out
 
 
-def square_mixed(torch, hqr, dev, n=16384, refine=20):
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# unit-count peaks at the maximum SM clock (2.07 GHz, 152 SMs): FP32 FFMA
+# 128 lanes per SM (2 flops each); FP64 pipe 2 thread-operations per cycle
+# per SM (an FMA or any other FP64 operation, incl. FP32 -> FP64 conversions)
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_OPS_PER_S = 152 * 2 * 2.07e9
+
+
+def pool_peaks():
+    """HBM GB/s and BF16 tensor TFLOP/s (burst and sustained) measured on this
+    pool's GPUs, else the machine's fallback figures; `source` says which."""
+    try:
+        d = json.load(open(PEAKS_FILE))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d["bf16_tflops_sustained"]), "source": "measured"}
+    except (OSError, ValueError, KeyError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+def fp32_qr_bound(peaks, nb, tensor, sustained=False):
+    """Roofline of an FP32 tile QR with tiles of nb: the update arithmetic
+    (BF16x3 = six BF16 products on the tensor pipe, or FP32 FFMA) against HBM
+    at the updates' intensity of nb / 4 flop per byte (the killer tile kept on
+    chip along a TS chain, FP32 elements). Returns (bound, peak TFLOP/s)."""
+    alu = (peaks["bf16_tflops_sustained" if sustained else "bf16_tflops"] / 6.0) if tensor else FP32_ALU_TFLOPS
+    hbm = peaks["hbm_gbs"] * 1e9 * nb / 4.0 / 1e12
+    return ("hbm", hbm) if hbm < alu else (("tensor" if tensor else "alu"), alu)
+
+
+def refine_fp64_ops(n_rows, n_cols, plain_rounds, comp_rounds):
+    """FP64 pipe operations of the refinement rounds of one M x N problem:
+    a plain round = r = b - A x and A^T r with one FMA and one FP32 -> FP64
+    conversion per element of A (4 M N), plus the two triangular solves with
+    the FP32 R (N^2 / 2 FMAs and conversions each: 2 N^2); a compensated round
+    = 11 operations per element of A for each product (TwoProduct 2, TwoSum 6,
+    accumulation 2, conversion 1: 22 M N) plus the solves."""
+    mn, nn = float(n_rows) * n_cols, float(n_cols) * n_cols
+    return plain_rounds * (4 * mn + 2 * nn) + comp_rounds * (22 * mn + 2 * nn)
+
+
+def trace_phases(tr):
+    """QR phase (kernel start to the end of the last packing / tile task) and
+    refinement phase (the rest) of a traced least-squares plan run, in ms."""
+    ops = tr[:, 3] >> np.uint64(24)
+    qr = (ops <= 5) | (ops == 14)
+    t0 = tr[:, 0].min()
+    qr_end = tr[qr, 1].max()
+    return float(qr_end - t0) * 1e-6, float(tr[:, 1].max() - qr_end) * 1e-6
+
+
+def square_mixed(torch, hqr, dev, peaks, n=16384, refine=20):
     """16384^2 FP32 least squares, A = U diag(s) V^T, s geometric 1 .. 1e-6,
     b = A x_true + 1e-8 N(0,1): FP32 tile QR with tensor-core updates
     (BF16x3) + FP64 CSNE."""
@@ -351,7 +463,8 @@ def square_mixed(torch, hqr, dev, n=16384, refine=20):
     xt = torch.randn(n, dtype=torch.float64, device=dev, generator=g)
     b = A.double() @ xt + 1e-8 * torch.randn(n, dtype=torch.float64, device=dev, generator=g)
     x = torch.zeros(n, dtype=torch.float64, device=dev)
-    cfg = [hqr.tile_config(128, 128, 16, 1, "greedy", "greedy")]
+    nb = 128
+    cfg = [hqr.tile_config(nb, nb, 16, 1, "greedy", "greedy")]
     plan = hqr.LSPlan([(A, b, x)], refine_iters=refine, configs=cfg, tensor=True)
     plan.run()
     plan.status()
@@ -363,13 +476,110 @@ def square_mixed(torch, hqr, dev, n=16384, refine=20):
     st = plan.status()
     ms = e0.elapsed_time(e1)
     info = plan.info()
+    # one traced run for the split between the QR and the refinement
+    plan.trace(True)
+    plan.run()
+    plan.status()
+    qr_ms, ref_ms = trace_phases(plan.trace())
+    plan.trace(False)
+    ncomp = min(refine, max(4, (2 * refine + 4) // 5))
+    bound, qpeak = fp32_qr_bound(peaks, nb, True)
+    qr_tf = info["qr_flops"] / (qr_ms * 1e-3) / 1e12
+    rops = refine_fp64_ops(n, n, refine - ncomp, ncomp)
     # independent cross-check (a library FP64 QR solve, itself accurate to about kappa * u64)
     ref = torch.linalg.lstsq(A.double(), b.unsqueeze(1), driver="gels").solution[:, 0]
     cross = ((x - ref).norm() / ref.norm()).item()
     return {"workload": "square_mixed_ls_16384_kappa1e6", "ms": ms, "solves_per_s": 1e3 / ms,
             "qr_tflops": info["qr_flops"] / (ms * 1e-3) / 1e12, "refine_iters": refine, "status": st,
             "last_rel_correction": plan.correction(0),
-            "rel_diff_vs_cusolver_fp64_qr": cross, "tasks": info["tasks"]}
+            "rel_diff_vs_cusolver_fp64_qr": cross, "tasks": info["tasks"],
+            "phases_ms": {"qr": qr_ms, "refinement": ref_ms, "from": "one traced run (per-task %globaltimer)"},
+            "roofline": {
+                "qr": {"bound": bound, "achieved": qr_tf, "peak": qpeak, "unit": "TFLOP/s", "frac": qr_tf / qpeak,
+                       "tensor_peak": peaks["bf16_tflops"] / 6.0,
+                       "hbm_peak": peaks["hbm_gbs"] * 1e9 * nb / 4 / 1e12,
+                       "peak_source": "%s BF16 burst / 6 (BF16x3) and HBM x nb/4 flop/B" % peaks["source"]},
+                "refinement": {"bound": "alu", "achieved": rops / (ref_ms * 1e-3) / 1e9, "peak": FP64_OPS_PER_S / 1e9,
+                               "unit": "G FP64-ops/s", "frac": rops / (ref_ms * 1e-3) / FP64_OPS_PER_S,
+                               "ops": rops, "plain_rounds": refine - ncomp, "compensated_rounds": ncomp,
+                               "peak_source": "FP64 pipe: 152 SMs x 2 ops/cycle x 2.07 GHz"}}}
+
+
+def list_stats(recs):
+    """Records, coupling-level records and the unit-time critical path (the
+    largest step) of a list."""
+    steps = [int(r["step"]) for r in recs]
+    return {"records": len(recs), "level2_records": int(sum(1 for r in recs if int(r["level"]) == 2)),
+            "unit_time_steps": max(steps) if steps else 0}
+
+
+def time_list(torch, hqr, A, nb, ib, recs, reps):
+    """Factor A with the list (a first run, then `reps` timed runs back to
+    back): mean task-kernel ms, status, max relative column-norm error of R."""
+    F = hqr.geqrf(A, nb, ib, recs)
+    F.kernel_times()
+    for _ in range(reps):
+        F.refactor_async(A)
+    ms = F.kernel_times()
+    st = F.status()
+    R = F.R()
+    cn = ((R.norm(dim=0) - A.norm(dim=0)).abs() / A.norm(dim=0)).max().item()
+    del F, R
+    torch.cuda.empty_cache()
+    return statistics.mean(ms), st, cn
+
+
+def list_variants(torch, hqr, A, peak, wl, headline_ms, reps=2):
+    """The tall-skinny workload factored with other elimination lists on the
+    same kernels (the comparisons of Sec. 5): Flat and Binary low-level trees,
+    the coupling ("domino") level of Sec. 4.2, and the prior-art lists
+    [SLHD10] (p = 1, TS domains of m / 16 tiles, binary tree) and [BBD+10]
+    (the flat tile QR: p = 1, one TS domain)."""
+    M, N, nb, ib = wl["M"], wl["N"], wl["nb"], wl["ib"]
+    m, n = M // nb, N // nb
+    fl = qr_flops(M, N)
+    out = {"workload": "fp64_tall_skinny_%dx%d_nb%d_ib%d" % (M, N, nb, ib), "peak_tflops": peak,
+           "peak_source": "FP64 cuBLAS DGEMM measured in this run", "reps": reps}
+    head = hqr.elim_list(m, n, wl["a"], wl["p"], wl["low"], wl["high"])
+    out["greedy_fibonacci_a4_p16"] = dict(list_stats(head), ms=headline_ms, tflops=fl / (headline_ms * 1e-3) / 1e12,
+                                          frac_of_dgemm=fl / (headline_ms * 1e-3) / 1e12 / peak, headline=True)
+    variants = [
+        ("greedy_fibonacci_a4_p16_domino", (wl["a"], wl["p"], "greedy", "fibonacci", True)),
+        ("flat_fibonacci_a4_p16", (wl["a"], wl["p"], "flat", "fibonacci", False)),
+        ("binary_fibonacci_a4_p16", (wl["a"], wl["p"], "binary", "fibonacci", False)),
+        ("fibonacci_fibonacci_a4_p16_domino", (wl["a"], wl["p"], "fibonacci", "fibonacci", True)),
+        ("slhd10_p1_a%d_binary" % (m // 16), (m // 16, 1, "binary", "flat", False)),
+        ("bbd10_flat_p1_a%d" % m, (m, 1, "flat", "flat", False)),
+    ]
+    for label, (a, p, low, high, domino) in variants:
+        recs = hqr.elim_list(m, n, a, p, low, high, domino=domino)
+        ms, st, cn = time_list(torch, hqr, A, nb, ib, recs, reps)
+        tf = fl / (ms * 1e-3) / 1e12
+        out[label] = dict(list_stats(recs), a=a, p=p, low=low, high=high, domino=domino, ms=ms, tflops=tf,
+                          frac_of_dgemm=tf / peak, status=st, max_rel_colnorm_err=cn)
+    return out
+
+
+def square_fp64(torch, hqr, inputs, dev, peak, n=16384, nb=256, ib=32):
+    """A large square FP64 factorization (Sec. 5's square runs): 16384^2
+    N(0, 1), tiles of 256, low-level Fibonacci tree, high-level Flat tree,
+    a = 4 (the paper's best square setting), p = 4; with and without the
+    coupling level (Sec. 5 reports that it hurts large square matrices)."""
+    A = inputs.gaussian_torch(n, n, seed=12, device=dev)
+    m = n // nb
+    fl = qr_flops(n, n)
+    out = {"workload": "fp64_square_%d_nb%d_ib%d" % (n, nb, ib), "qr_flops": fl, "peak_tflops": peak,
+           "peak_source": "FP64 cuBLAS DGEMM measured in this run"}
+    for label, domino in (("fibonacci_flat_a4_p4", False), ("fibonacci_flat_a4_p4_domino", True)):
+        recs = hqr.elim_list(m, m, 4, 4, "fibonacci", "flat", domino=domino)
+        ms, st, cn = time_list(torch, hqr, A, nb, ib, recs, 1)
+        tf = fl / (ms * 1e-3) / 1e12
+        out[label] = dict(list_stats(recs), ms=ms, tflops=tf, status=st, max_rel_colnorm_err=cn,
+                          roofline={"bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+                                    "frac": tf / peak, "peak_source": "in-run FP64 DGEMM"})
+    del A
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_reference(args):
@@ -451,8 +661,8 @@ def main():
     for _ in range(args.warmup):
         F.refactor_async(A)
     torch.cuda.synchronize(dev)
+    F.kernel_times()  # drop the warm-up runs
 
-    kernel_ms = []
     launches = 0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
@@ -460,12 +670,15 @@ def main():
         torch.cuda.synchronize(dev)
         e0.record(stream)
         for _ in range(args.steps):
-            F.refactor_async(A)
+            F.refactor_async(A)  # back to back: no host wait inside the timed loop
             launches += hqr.last_launches()
-            kernel_ms.append(F.kernel_ms())
         e1.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
+    # per-step device time of the task kernel (events recorded by the library
+    # on the launching stream around each launch)
+    kernel_ms = F.kernel_times()
+    assert len(kernel_ms) == args.steps
     st = F.status()
     if st != 0:
         raise RuntimeError("factorization failed with status %d" % st)
@@ -529,12 +742,17 @@ def main():
     torch.cuda.empty_cache()
 
     extras = {}
-    if not args.no_extras and M == WORKLOAD["M"]:
-        extras["latency_square"] = latency_square(torch, hqr, inputs, dev)
-        extras["batched"] = batched(torch, hqr, dev)
-        extras["square_mixed"] = square_mixed(torch, hqr, dev)
-        extras["serving"] = serving(torch, hqr, dev, seconds=args.serve_seconds)
-        extras["serving_200"] = serving(torch, hqr, dev, rate=200.0, seconds=args.serve_seconds)
+    if not args.no_extras and M == WORKLOAD["M"] and world == 1:
+        peaks = pool_peaks()
+        extras["list_variants"] = list_variants(torch, hqr, A, peak, wl, statistics.mean(kernel_ms))
+        del A
+        torch.cuda.empty_cache()
+        extras["square_fp64"] = square_fp64(torch, hqr, inputs, dev, peak)
+        extras["latency_square"] = latency_square(torch, hqr, inputs, dev, peak=peak)
+        extras["batched"] = batched(torch, hqr, dev, peaks=peaks)
+        extras["square_mixed"] = square_mixed(torch, hqr, dev, peaks)
+        extras["serving"] = serving(torch, hqr, dev, seconds=args.serve_seconds, peaks=peaks)
+        extras["serving_200"] = serving(torch, hqr, dev, rate=200.0, seconds=args.serve_seconds, peaks=peaks)
 
     if rank != 0:
         return 0

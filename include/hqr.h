@@ -228,6 +228,13 @@ int hqr_get_t(const hqr_factors *F, void *dT, void *stream);
  * Waits for that kernel to finish. */
 int hqr_kernel_ms(hqr_factors *F, float *ms);
 
+/* hqr_kernel_times -- device times (CUDA events on each run's stream) of
+ * the persistent task kernel of every factorization or apply-Q run on F
+ * since the previous call (at most the last 64 runs), oldest first, into
+ * ms[0 .. *count). Waits for the last of those kernels. cap too small:
+ * HQR_ERR_CAPACITY with *count = the number needed. */
+int hqr_kernel_times(hqr_factors *F, float *ms, int cap, int *count);
+
 /*
  * hqr_trace -- per-task timing of the persistent kernel (for analysis).
  * enable = 1: record from the next run on (allocates a device buffer of

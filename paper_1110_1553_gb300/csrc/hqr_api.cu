@@ -341,6 +341,10 @@ struct hqr_factors {
   Ctl *last_ctl = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool timed = false;
+  // start / end events of the last kRing task-kernel runs (hqr_kernel_times)
+  static constexpr int kRing = 64;
+  std::vector<cudaEvent_t> ring;
+  int64_t ring_runs = 0, ring_read = 0;
   unsigned long long *dtrace = nullptr;
   size_t trace_cap = 0;
   int64_t debug_task = -1;
@@ -369,10 +373,18 @@ int run_graph(hqr_factors *F, DevGraph &g, cudaStream_t s) {
     CK(cudaEventCreate(&F->ev0));
     CK(cudaEventCreate(&F->ev1));
   }
+  if (F->ring.empty()) {
+    F->ring.assign(2 * hqr_factors::kRing, nullptr);
+    for (cudaEvent_t &e : F->ring) CK(cudaEventCreate(&e));
+  }
+  const int slot = (int)(F->ring_runs % hqr_factors::kRing);
   CK(cudaEventRecord(F->ev0, s));
+  CK(cudaEventRecord(F->ring[2 * slot], s));
   int st = launch_sched(F->prec, p, smem, s);
   if (st) return st;
   CK(cudaEventRecord(F->ev1, s));
+  CK(cudaEventRecord(F->ring[2 * slot + 1], s));
+  F->ring_runs += 1;
   F->timed = true;
   F->last_ctl = g.ctl;
   return HQR_SUCCESS;
@@ -643,6 +655,29 @@ int hqr_kernel_ms(hqr_factors *F, float *ms) {
   return HQR_SUCCESS;
 }
 
+int hqr_kernel_times(hqr_factors *F, float *ms, int cap, int *count) {
+  if (!F) return -1;
+  if (!ms) return -2;
+  if (cap < 1) return -3;
+  if (!count) return -4;
+  const int64_t first = std::max(F->ring_read, F->ring_runs - (int64_t)hqr_factors::kRing);
+  const int avail = (int)(F->ring_runs - first);
+  if (avail > cap) {
+    *count = avail;
+    return HQR_ERR_CAPACITY;
+  }
+  *count = avail;
+  if (avail == 0) return HQR_SUCCESS;
+  const int last = (int)((F->ring_runs - 1) % hqr_factors::kRing);
+  CK(cudaEventSynchronize(F->ring[2 * last + 1]));
+  for (int q = 0; q < avail; ++q) {
+    const int slot = (int)((first + q) % hqr_factors::kRing);
+    CK(cudaEventElapsedTime(ms + q, F->ring[2 * slot], F->ring[2 * slot + 1]));
+  }
+  F->ring_read = F->ring_runs;
+  return HQR_SUCCESS;
+}
+
 int hqr_trace(hqr_factors *F, int enable, uint64_t *host, size_t cap, size_t *count) {
   if (!F) return -1;
   if (enable == 1) {
@@ -836,6 +871,8 @@ void hqr_factors_free(hqr_factors *F) {
   cudaFree(F->dtrace);
   if (F->ev0) cudaEventDestroy(F->ev0);
   if (F->ev1) cudaEventDestroy(F->ev1);
+  for (cudaEvent_t e : F->ring)
+    if (e) cudaEventDestroy(e);
   delete F;
 }
 

@@ -28,7 +28,7 @@ ELIM_DTYPE = np.dtype([("k", np.int32), ("i", np.int32), ("killer", np.int32), (
                        ("level", np.int32), ("step", np.int32)])
 
 EXPORTS = ["hqr_elim_list", "hqr_elim_list_domino", "hqr_validate_list", "hqr_task_graph", "hqr_geqrf", "hqr_refactor", "hqr_refactor_async",
-           "hqr_status", "hqr_get_r", "hqr_get_tiles", "hqr_get_t", "hqr_factors_info", "hqr_kernel_ms", "hqr_trace", "hqr_apply_q",
+           "hqr_status", "hqr_get_r", "hqr_get_tiles", "hqr_get_t", "hqr_factors_info", "hqr_kernel_ms", "hqr_kernel_times", "hqr_trace", "hqr_apply_q",
            "hqr_gels", "hqr_geqrf_r_noalloc", "hqr_ls_plan_create", "hqr_ls_plan_run",
            "hqr_ls_plan_capture", "hqr_ls_plan_status", "hqr_ls_plan_correction", "hqr_ls_plan_info", "hqr_ls_plan_config",
            "hqr_ls_plan_free", "hqr_ls_plan_trace", "hqr_set_tuning", "hqr_autotune", "hqr_server_create", "hqr_server_start",
@@ -83,6 +83,7 @@ def load(build_if_missing=False):
     ip = ctypes.POINTER(i32)
     lib.hqr_factors_info.argtypes = [vp, ip, ip, ip, ip, ip, ip, ctypes.POINTER(i64)]
     lib.hqr_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    lib.hqr_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32, ctypes.POINTER(i32)]
     lib.hqr_trace.argtypes = [vp, i32, vp, sz, ctypes.POINTER(sz)]
     lib.hqr_apply_q.argtypes = [vp, i32, vp, i32, i32, vp]
     lib.hqr_gels.argtypes = [vp, i32, i32, i32, vp, i32, i32, vp, i32, i32, i32, i32, vp, sz, vp]
@@ -311,6 +312,15 @@ class Factors:
         ms = ctypes.c_float(0)
         _check(load().hqr_kernel_ms(self._h, ctypes.byref(ms)), "hqr_kernel_ms")
         return ms.value
+
+    def kernel_times(self):
+        """Device times (ms) of the task-kernel runs since the previous call
+        (at most the last 64), oldest first."""
+        lib = load()
+        buf = (ctypes.c_float * 64)()
+        cnt = ctypes.c_int32(0)
+        _check(lib.hqr_kernel_times(self._h, buf, 64, ctypes.byref(cnt)), "hqr_kernel_times")
+        return [buf[q] for q in range(cnt.value)]
 
     def trace(self, enable=None):
         """enable=True/False switches per-task tracing; with no argument,
