@@ -82,7 +82,8 @@ enum {
   HQR_ERR_INTERNAL = 7,  /* internal consistency check failed */
   HQR_ERR_TOO_LARGE = 8, /* problem exceeds the fixed limits of hqr_geqrf_r_noalloc */
   HQR_ERR_BUSY = 9,      /* server: no slot, memory or pool space free right now; retry later */
-  HQR_ERR_BUDGET = 10    /* server: the request can never fit the server's budget */
+  HQR_ERR_BUDGET = 10,   /* server: the request can never fit the server's budget */
+  HQR_ERR_NOCONV = 11    /* refinement did not reach the tolerance within its rounds */
 };
 
 /* Opaque factorization: owns the tile workspace (V and R), the T factors,
@@ -145,7 +146,10 @@ int hqr_validate_list(int m, int n, const hqr_elim_t *list, size_t count);
  *            hand side of `param` column slabs (hqr_apply_q, trans = 1);
  *            2: Q applied (trans = 0); 3: a least-squares problem of a plan
  *            with `param` refinement rounds (0: QR solve); 4: the same as a
- *            server request (packing tasks first).
+ *            server request (packing tasks first); 5: a problem of a plan
+ *            from hqr_ls_plan_create_tol with at most `param` rounds (round
+ *            tasks carry trans = 2 and k = the round; op 18 is a round's
+ *            convergence check).
  *   tasks    caller array of 10 int32 per task: op (0 GEQRT, 1 UNMQR,
  *            2 TSQRT, 3 TSMQR, 4 TTQRT, 5 TTMQR, 6.. the vector tasks of
  *            least-squares graphs), blk (0: the whole panel / every block;
@@ -259,7 +263,8 @@ int hqr_factors_info(const hqr_factors *F, int *Mp, int *Np, int *m, int *n,
 int hqr_apply_q(hqr_factors *F, int trans, void *dB, int ldb, int nrhs, void *stream);
 
 /*
- * hqr_gels -- least squares min ||b - A x||_2 for M >= N, full rank:
+ * hqr_gels_qr -- least squares min ||b - A x||_2 for M >= N, full rank, in
+ * the storage precision, for many right-hand sides and a given list:
  * factor, c = Q^T b, x = R^{-1} c[0:N] (problem of Sec. 2 with the
  * application of Sec. 5.1).
  *   db      device, M x nrhs, ldb >= M; read only.
@@ -267,9 +272,48 @@ int hqr_apply_q(hqr_factors *F, int trans, void *dB, int ldb, int nrhs, void *st
  *   list    as in hqr_geqrf (NULL = default).
  * Returns HQR_ERR_SINGULAR if a diagonal entry of R is exactly zero.
  */
-int hqr_gels(const void *dA, int M, int N, int lda, const void *db, int ldb, int nrhs,
-             void *dx, int ldx, int prec, int nb, int ib, const hqr_elim_t *list,
-             size_t count, void *stream);
+int hqr_gels_qr(const void *dA, int M, int N, int lda, const void *db, int ldb, int nrhs,
+                void *dx, int ldx, int prec, int nb, int ib, const hqr_elim_t *list,
+                size_t count, void *stream);
+
+/* Outcome of hqr_gels. */
+typedef struct {
+  int iters;               /* refinement rounds applied (0 when max_iter = 0) */
+  int converged;           /* 1: the tolerance was met (always 1 when max_iter = 0) */
+  double rel_correction;   /* max|d| / max|x| of the last applied correction d; -1 without refinement */
+  double backward_error;   /* ||b - A x||_2 / (||A||_F ||x||_2 + ||b||_2), FP64 on the device */
+  double normal_residual;  /* ||A^T (b - A x)||_2 / (||A||_F ||b - A x||_2): near rounding level at a
+                              least-squares solution even when b - A x itself is large */
+  int64_t singular_index;  /* first column with an exact zero on R's diagonal, -1 if none */
+} hqr_gels_info;
+
+/*
+ * hqr_gels -- least squares min ||b - A x||_2 for one M x N matrix, M >= N,
+ * solved through the tile QR (the problem of Sec. 2; Q^T applied by
+ * replaying the trees, Sec. 5.1), with the tolerance-stopped refinement of
+ * hqr_ls_plan_create_tol.
+ *   dA, lda   device, column-major, lda >= M, in the storage precision of
+ *             `prec` (double for HQR_FP64, float otherwise); read only.
+ *   db        device, M doubles; read only.
+ *   dx        device, N doubles; receives x.
+ *   prec      HQR_FP64: FP64 tile QR. HQR_FP32 / HQR_FP32_BF16X3: the
+ *             mixed-precision solve: FP32 tile QR (tiles of 128 on the tensor
+ *             cores with BF16X3), FP64 only in the refinement (residual,
+ *             A^T r, triangular solves with the low-precision R).
+ *   tol       stop the refinement at the first compensated round whose
+ *             correction has max|d| <= tol max|x| (tol >= 0).
+ *   max_iter  refinement rounds at most, 0 <= max_iter <= 64. With 0, x is
+ *             the plain QR solve R^{-1} (Q^T b)[0:N] in the storage precision.
+ *   info      NULL, or receives the outcome (also on HQR_ERR_NOCONV and
+ *             HQR_ERR_SINGULAR).
+ * Tile configuration: the autotuner table (hqr_set_tuning / hqr_autotune)
+ * or the built-in heuristic. Allocates and frees its own workspace and
+ * synchronizes `stream`. Returns HQR_ERR_NOCONV when max_iter rounds did not
+ * meet tol (x is then the last iterate) and HQR_ERR_SINGULAR when R has an
+ * exact zero on its diagonal (info->singular_index names the column).
+ */
+int hqr_gels(const void *dA, int M, int N, int lda, const double *db, double *dx, int prec, double tol,
+             int max_iter, hqr_gels_info *info, void *stream);
 
 /*
  * hqr_debug_block_task -- testing aid for the device-side time limits: add
@@ -349,6 +393,30 @@ typedef struct hqr_ls_plan hqr_ls_plan;
 int hqr_ls_plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_config_t *cfg, int prec,
                        int refine_iters, hqr_ls_plan **plan);
 
+/*
+ * hqr_ls_plan_create_tol -- as hqr_ls_plan_create with refinement rounds
+ * that stop at a tolerance (corrected semi-normal equations as above): at
+ * most max_iter rounds (1 .. 64); each problem stops after the first round
+ * whose correction d has max|d| <= tol max|x| and whose residual and A^T r
+ * were compensated. Rounds start with plain FP64 sums and switch to
+ * compensated ones when the corrections stop halving from round to round or
+ * reach tol (decided on the device, two rounds ahead). The rounds after a
+ * problem's last one are skipped on the device. A problem that does not meet
+ * tol reports HQR_ERR_NOCONV (hqr_ls_plan_status); see
+ * hqr_ls_plan_refine_info.
+ */
+int hqr_ls_plan_create_tol(int count, const hqr_ls_problem_t *probs, const hqr_tile_config_t *cfg, int prec,
+                           int max_iter, double tol, hqr_ls_plan **plan);
+
+/* hqr_ls_plan_refine_info -- outcome of problem idx after a run of a plan
+ * from hqr_ls_plan_create_tol: rounds applied, the last applied correction
+ * max|d| / max|x|, whether tol was met, and the first column with an exact
+ * zero on R's diagonal (-1: none). Plans from hqr_ls_plan_create report
+ * their fixed round count, -1, 0 and -1. Any output may be NULL.
+ * Synchronizes `stream`. */
+int hqr_ls_plan_refine_info(hqr_ls_plan *plan, int idx, int *iters, double *rel_correction, int *converged,
+                            int64_t *singular_index, void *stream);
+
 /* hqr_ls_plan_run -- solve all problems (asynchronous on `stream`): one
  * preparation kernel (tile packing, b, x = 0), the persistent task kernel,
  * one kernel copying every x out. If hqr_ls_plan_capture was called, the
@@ -360,8 +428,10 @@ int hqr_ls_plan_run(hqr_ls_plan *plan, void *stream);
 int hqr_ls_plan_capture(hqr_ls_plan *plan, void *stream);
 
 /* hqr_ls_plan_status -- synchronize `stream`; 0, the device status of the
- * last run, or HQR_ERR_SINGULAR if any problem's R had an exact zero
- * diagonal (that problem's x is then not meaningful). */
+ * last run, HQR_ERR_SINGULAR if a problem's R had an exact zero diagonal
+ * (that problem's x is then not meaningful), or HQR_ERR_NOCONV if a problem
+ * of a tolerance plan did not meet its tolerance (the first problem's code
+ * when several failed). */
 int hqr_ls_plan_status(hqr_ls_plan *plan, void *stream);
 
 /* hqr_ls_plan_correction -- size of the last refinement correction of

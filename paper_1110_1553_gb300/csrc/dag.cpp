@@ -74,6 +74,7 @@ class Builder {
   explicit Builder(size_t nres) : tr_(nres) {}
   Tracker &tr() { return tr_; }
   std::vector<int32_t> &deps() { return deps_; }
+  int32_t next_id() const { return (int32_t)g_.tasks.size(); }
   void add(const Task &t) {
     const int32_t id = (int32_t)g_.tasks.size();
     std::sort(deps_.begin(), deps_.end());
@@ -244,7 +245,7 @@ Graph build_apply_graph(const std::vector<PanelOp> &ops, int m, int nslab, int w
 }
 
 Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int w, int iters, int pid,
-                     bool pack, int split_ib) {
+                     bool pack, int split_ib, bool tol_mode) {
   const int S = (nb + w - 1) / w;
   const TilePieces P{m, S};
   const size_t ntile_res = P.count(n);
@@ -289,21 +290,38 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
       tr.read(P.l(i, j, s), d);
     }
   };
-  auto vtask = [&](int op, int i, int j) { return make_task(op, 1, i, i, 0, j, 0, 0, 1, 0, pid); };
+  // tasks of refinement round `round` (-1: not a round task) carry k = round and, with
+  // tol_mode, trans = 2 (see the header)
+  int round = -1;
+  auto rmark = [&](Task t) {
+    if (round >= 0) {
+      t.k = round;
+      if (tol_mode) t.trans = 2;
+    }
+    return t;
+  };
+  auto vtask = [&](int op, int i, int j) { return rmark(make_task(op, 1, i, i, 0, j, 0, 0, 1, 0, pid)); };
+  int32_t check = -1;  // the previous round's check task (tol_mode)
+  std::vector<int32_t> xupd;  // this round's x updates
   bool inverted = false;
   auto solve_r = [&](bool transposed_first) {
     if (!inverted) {  // inverses of the diagonal tiles, once per factorization
+      const int rsave = round;
+      round = -1;
       for (int i = 0; i < n; ++i) {
         read_r(i, i);
         tr.write(ires(i), d);
         b.add(vtask(OP_TRINV, i, i));
       }
+      round = rsave;
       inverted = true;
     }
     // The update of the next diagonal tile's vector is its last writer before the inverse is
     // applied, so that task applies the inverse too (tgt = 1): one task and one hop less per step
     // of the chain. Tile 0 (forward) and n - 1 (backward) have their own inverse task.
-    auto ftask = [&](int op, int i, int j, int fused) { return make_task(op, 1, i, i, 0, j, 0, 0, 1, fused, pid); };
+    auto ftask = [&](int op, int i, int j, int fused) {
+      return rmark(make_task(op, 1, i, i, 0, j, 0, 0, 1, fused, pid));
+    };
     if (transposed_first) {  // R^T y = g, forward
       tr.read(ires(0), d);
       tr.write(gres(0), d);
@@ -332,10 +350,19 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
         b.add(ftask(OP_TRSV_U, i, j, fused));
       }
     }
+    xupd.clear();
     for (int j = 0; j < n; ++j) {
       tr.read(gres(j), d);
       tr.write(xres(j), d);
+      if (tol_mode && check >= 0) d.push_back(check);  // applied only if no earlier round met the tolerance
+      xupd.push_back(b.next_id());
       b.add(vtask(OP_XUPD, j, j));
+    }
+    if (tol_mode && round >= 0) {  // the round's check, after all its x updates
+      for (int32_t u : xupd) d.push_back(u);
+      if (check >= 0) d.push_back(check);
+      check = b.next_id();
+      b.add(vtask(OP_RCHK, 0, 0));
     }
   };
   if (iters == 0) {
@@ -367,8 +394,9 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
   // element instead of ~10 FP64 operations). Vector tasks carry the choice in `tgt`.
   const int ncomp = std::min(iters, std::max(4, (2 * iters + 4) / 5));
   for (int it = 0; it < iters; ++it) {
-    const int comp = it >= iters - ncomp ? 1 : 0;
-    auto rtask = [&](int op, int i, int j) { return make_task(op, 1, i, i, 0, j, 0, 0, 1, comp, pid); };
+    round = it;
+    const int comp = (!tol_mode && it >= iters - ncomp) ? 1 : 0;
+    auto rtask = [&](int op, int i, int j) { return rmark(make_task(op, 1, i, i, 0, j, 0, 0, 1, comp, pid)); };
     for (int i = 0; i < m; ++i) {
       for (int c = 0; c < nrc; ++c) {
         for (int j = c * kResChunk; j < std::min(n, (c + 1) * kResChunk); ++j) tr.read(xres(j), d);

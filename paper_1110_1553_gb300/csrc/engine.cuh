@@ -109,7 +109,9 @@ struct alignas(16) Problem {
   int tc;             // FP32 tiles of 128 on the tensor-core kernels (ib = nb: one full T per tile)
   int tstr;           // elements per T record (ib * nb; tensor-core problems: split images [+ T])
   int t32;            // tensor-core problems: the records keep the FP32 T (apply Q, read T)
-  int pad_;
+  int maxit;          // tolerance-stopped refinement: rounds at most (0: fixed rounds)
+  double tol;         // tolerance-stopped refinement: stop when max |d| / max |x| <= tol
+  RefineState *rs;    // tolerance-stopped refinement state (nullptr otherwise)
 };
 static_assert(sizeof(Problem) % 16 == 0, "Problem is read in 16-byte pieces");
 
@@ -131,6 +133,7 @@ struct Shared {
   uint64_t bar;
   int task;
   int abort;
+  int vskip, vcomp;  // vector tasks of tolerance-stopped rounds: skip the task, compensated sums
   Real red[2 * NWARP];
   Real tau[IBMAX];
   Real wv[IBMAX];
@@ -839,6 +842,22 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
                             double *sm, Shared<Real> &sh, uint32_t &phase) {
   const int nb = g.nb, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const Real *A0 = (const Real *)P.A0;
+  // a round of a tolerance-stopped refinement: nothing to do once an earlier round met the
+  // tolerance (the x updates and checks are ordered after the check that decided it; the
+  // other tasks of the round right after it may read the flag early or late, and only
+  // write scratch vectors that no later task reads)
+  const bool tolm = t.trans == 2;
+  bool comp = t.tgt != 0;  // residual and A^T r: compensated (Dot2) or plain FP64 sums
+  if (tolm) {  // one thread reads the state, so that the whole CTA takes the same branch
+    if (tid == 0) {
+      const int conv = __ldcg(&P.rs->conv);
+      sh.vskip = conv != 0 && t.k >= conv;
+      sh.vcomp = __ldcg(&P.rs->mode[t.k]) != 0;
+    }
+    __syncthreads();
+    if (sh.vskip) return;
+    comp = sh.vcomp != 0;
+  }
   switch (t.op) {
     case OP_RESID: {  // partial sums of A(rows of tile i, columns of chunk t.j) x
       const int r0 = t.i * nb, nr = min(nb, P.M - r0);
@@ -846,7 +865,7 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
       const int G = NT / nb;  // column groups
       const int rr = tid % nb, gi = tid / nb;
       double s = 0.0, c = 0.0;
-      if (rr < nr && gi < G && !t.tgt) {  // plain FP64 round: four independent FMA chains
+      if (rr < nr && gi < G && !comp) {  // plain FP64 round: four independent FMA chains
         const Real *arow = A0 + r0 + rr;
         double s1 = 0.0, s2 = 0.0, s3 = 0.0;
         int j = clo + gi;
@@ -916,6 +935,7 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
         const double djj = (double)__ldcg(R + (size_t)j * nb + j);
         if (djj == 0.0) {
           atomicExch(P.status, HQR_ERR_SINGULAR);
+          if (P.rs) atomicMax(&P.rs->sing, ~(unsigned)(i * nb + j));
           continue;
         }
         xj[j] = 1.0 / djj;
@@ -925,6 +945,7 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
           const double dkk = (double)__ldcg(R + (size_t)k * nb + k);
           if (dkk == 0.0) {
             atomicExch(P.status, HQR_ERR_SINGULAR);
+            if (P.rs) atomicMax(&P.rs->sing, ~(unsigned)(i * nb + k));
             break;
           }
           xj[k] = -s / dkk;
@@ -940,7 +961,7 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
         const Real *acol = A0 + (long long)(c0 + cc) * P.lda0;
         double s = 0.0, c = 0.0, s1 = 0.0, c1 = 0.0, s2 = 0.0, c2 = 0.0, s3 = 0.0, c3 = 0.0;
         int i = rlo + lane;
-        if (!t.tgt) {  // plain FP64 round: FMA chains, then a plain warp sum
+        if (!comp) {  // plain FP64 round: FMA chains, then a plain warp sum
           for (; i + 96 < rhi; i += 128) {
             s = fma((double)__ldcg(acol + i), __ldcg(P.r + i), s);
             s1 = fma((double)__ldcg(acol + i + 32), __ldcg(P.r + i + 32), s1);
@@ -1093,8 +1114,58 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
     }
     case OP_XUPD: {
       const int j = t.j, n_j = min(nb, P.N - j * nb);
-      for (int c = tid; c < n_j; c += NT)
-        P.x[(size_t)j * nb + c] = __ldcg(P.x + (size_t)j * nb + c) + __ldcg(P.g + (size_t)j * nb + c);
+      double md = 0.0, mx = 0.0;
+      for (int c = tid; c < n_j; c += NT) {
+        const double d = __ldcg(P.g + (size_t)j * nb + c);
+        const double xn = __ldcg(P.x + (size_t)j * nb + c) + d;
+        P.x[(size_t)j * nb + c] = xn;
+        md = fmax(md, fabs(d));
+        mx = fmax(mx, fabs(xn));
+      }
+      if (tolm) {  // fold this tile's max |d| and max |x| into the round's
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
+          mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+        if (lane == 0) {
+          sm[warp] = md;
+          sm[NWARP + warp] = mx;
+        }
+        __syncthreads();
+        if (tid == 0) {
+          for (int w = 1; w < NWARP; ++w) {
+            md = fmax(md, sm[w]);
+            mx = fmax(mx, sm[NWARP + w]);
+          }
+          // NaN stays visible: its bit pattern is above every finite one
+          atomicMax(&P.rs->dmax[t.k], (unsigned long long)__double_as_longlong(md));
+          atomicMax(&P.rs->xmax[t.k], (unsigned long long)__double_as_longlong(mx));
+        }
+        __syncthreads();
+      }
+      break;
+    }
+    case OP_RCHK: {  // after every x update of round k: tolerance met? compensate round k + 2?
+      if (tid == 0) {
+        RefineState *rs = P.rs;
+        const int k = t.k;
+        const double d = __longlong_as_double((long long)__ldcg(&rs->dmax[k]));
+        const double x = __longlong_as_double((long long)__ldcg(&rs->xmax[k]));
+        const double c = x > 0.0 ? d / x : (d > 0.0 ? INFINITY : 0.0);
+        rs->cval[k] = c;
+        const int comp_k = __ldcg(&rs->mode[k]);
+        if ((comp_k && c <= P.tol) || c == 0.0) {
+          rs->conv = k + 1;
+        } else {
+          // plain rounds until their corrections stop shrinking (by half per round) or reach
+          // the tolerance; from then on compensated residuals, which can certify it
+          if (k + 2 < P.maxit)
+            rs->mode[k + 2] = (__ldcg(&rs->mode[k + 1]) || c <= P.tol || (k >= 1 && !(c <= 0.5 * rs->cval[k - 1])))
+                                  ? 1 : 0;
+          if (k == P.maxit - 1) atomicCAS(P.status, 0, HQR_ERR_NOCONV);
+        }
+      }
       break;
     }
     case OP_BTOG: {

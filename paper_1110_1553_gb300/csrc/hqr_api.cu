@@ -466,6 +466,7 @@ const char *hqr_strerror(int status) {
     case HQR_ERR_TOO_LARGE: return "problem exceeds the limits of the allocation-free entry point";
     case HQR_ERR_BUSY: return "no room for the request right now";
     case HQR_ERR_BUDGET: return "request exceeds the server's budget";
+    case HQR_ERR_NOCONV: return "refinement did not reach the tolerance";
     default: return status < 0 ? "invalid argument" : "unknown status";
   }
 }
@@ -480,7 +481,7 @@ int hqr_task_graph(int m, int n, int nb, int ib, int prec, const hqr_elim_t *lis
   ib = eff_ib(prec, nb, ib);
   if (!valid_tile_sizes(prec, nb, ib)) return -4;
   if (!list && count) return -6;
-  if (kind < 0 || kind > 4) return -8;
+  if (kind < 0 || kind > 5) return -8;
   if (param < 0 || ((kind == 1 || kind == 2) && param < 1)) return -9;
   if (!ntasks || !nedges) return -16;
   if (hqr_validate_list(m, n, list, count) != HQR_SUCCESS) return HQR_ERR_INVALID_LIST;
@@ -495,7 +496,7 @@ int hqr_task_graph(int m, int n, int nb, int ib, int prec, const hqr_elim_t *lis
   if (kind == 0)
     g = build_factor_graph(ops, m, n, nb, P.w, 0, split_ib_for(prec, P));
   else if (kind >= 3)
-    g = build_ls_graph(ops, m, n, nb, P.w, param, 0, kind == 4, split_ib_for(prec, P));
+    g = build_ls_graph(ops, m, n, nb, P.w, param, 0, kind == 4, split_ib_for(prec, P), kind == 5);
   else
     g = build_apply_graph(ops, m, param, P.wb, kind == 1 ? 1 : 0);
   *ntasks = (int64_t)g.tasks.size();
@@ -777,8 +778,8 @@ int hqr_apply_q(hqr_factors *F, int trans, void *dB, int ldb, int nrhs, void *st
   return read_status(F, s);
 }
 
-int hqr_gels(const void *dA, int M, int N, int lda, const void *db, int ldb, int nrhs, void *dx, int ldx,
-             int prec, int nb, int ib, const hqr_elim_t *list, size_t count, void *stream) {
+int hqr_gels_qr(const void *dA, int M, int N, int lda, const void *db, int ldb, int nrhs, void *dx, int ldx,
+                int prec, int nb, int ib, const hqr_elim_t *list, size_t count, void *stream) {
   if (!db) return -5;
   if (ldb < M) return -6;
   if (nrhs < 1) return -7;
@@ -979,6 +980,9 @@ __global__ void ls_finish(const PrepDesc *__restrict__ d, int count) {
 
 struct hqr_ls_plan {
   int count = 0, prec = 0, iters = 0;
+  int tol_mode = 0;                 // refinement rounds stop at a tolerance (hqr_ls_plan_create_tol)
+  double tol = 0.0;
+  RefineState *drs = nullptr;       // per-problem refinement state (tol_mode)
   int any_tc = 0;          // some problem runs on the tensor-core kernels
   std::vector<hqr_tile_config_t> cfg;
   std::vector<Problem> probs;
@@ -1033,6 +1037,7 @@ int plan_enqueue(hqr_ls_plan *P, cudaStream_t s, bool timed) {
     ls_prepare<float><<<grid_for(P->prep_total), 256, 0, s>>>(P->dprep, P->count, P->prep_total);
   CK(cudaGetLastError());
   CK(cudaMemsetAsync(P->dstatus, 0, sizeof(int) * P->count, s));
+  if (P->drs) CK(cudaMemsetAsync(P->drs, 0, sizeof(RefineState) * P->count, s));
   DevGraph &g = P->graph;
   CK(cudaMemcpyAsync(g.indeg, g.indeg0, sizeof(int) * g.ntasks, cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(g.slots, g.slots0, sizeof(int) * slot_count(g.ntasks), cudaMemcpyDeviceToDevice, s));
@@ -1069,19 +1074,20 @@ int hqr_set_tuning(int count, const int *keys, const hqr_tile_config_t *cfgs) {
   return HQR_SUCCESS;
 }
 
-int hqr_ls_plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_config_t *cfg, int prec,
-                       int refine_iters, hqr_ls_plan **plan) {
-  if (count < 1) return -1;
-  if (!probs) return -2;
-  if (!prec_ok(prec)) return -4;
-  if (refine_iters < 0 || refine_iters > 64) return -5;
-  if (!plan) return -6;
+}  // extern "C"
+
+namespace {
+
+int plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_config_t *cfg, int prec,
+                int refine_iters, bool tol_mode, double tol, hqr_ls_plan **plan) {
   *plan = nullptr;
   hqr_ls_plan *P = new (std::nothrow) hqr_ls_plan();
   if (!P) return HQR_ERR_NOMEM;
   P->count = count;
   P->prec = prec;
   P->iters = refine_iters;
+  P->tol_mode = tol_mode && refine_iters > 0;
+  P->tol = tol;
   const size_t es = elem_size(prec);
   // tile configurations, lists, sizes
   std::vector<size_t> off_tiles(count), off_t(count), off_b(count), off_vec(count);
@@ -1132,7 +1138,12 @@ int hqr_ls_plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_
       return HQR_ERR_INTERNAL;
     }
     std::vector<PanelOp> ops = expand_ops(lst.data(), lst.size(), pb.m, pb.n);
-    append_graph(merged, build_ls_graph(ops, pb.m, pb.n, c.nb, pb.w, refine_iters, q, false, split_ib_for(prec, pb)));
+    append_graph(merged, build_ls_graph(ops, pb.m, pb.n, c.nb, pb.w, refine_iters, q, false, split_ib_for(prec, pb),
+                                        P->tol_mode != 0));
+    if (P->tol_mode) {
+      pb.maxit = refine_iters;
+      pb.tol = tol;
+    }
     smem = std::max(smem, smem_for(prec, pb));
     if (pb.tc) P->any_tc = 1;
     P->probs.push_back(pb);
@@ -1143,6 +1154,7 @@ int hqr_ls_plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_
   if (!cuda_ok(cudaMalloc(&P->arena, es * std::max<size_t>(arena_elems, 1)), "cudaMalloc(arena)") ||
       !cuda_ok(cudaMalloc(&P->vec, sizeof(double) * std::max<size_t>(vec_elems, 1)), "cudaMalloc(vec)") ||
       !cuda_ok(cudaMalloc(&P->dstatus, sizeof(int) * count), "cudaMalloc(status)") ||
+      (tol_mode && !cuda_ok(cudaMalloc(&P->drs, sizeof(RefineState) * count), "cudaMalloc(refine state)")) ||
       !cuda_ok(cudaMemset(P->arena, 0, es * std::max<size_t>(arena_elems, 1)), "memset(arena)"))
     st = HQR_ERR_NOMEM;
   if (!st) {
@@ -1160,6 +1172,7 @@ int hqr_ls_plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_
       pb.rp = pb.gp + 2 * (size_t)atr_chunks(pb.m) * pb.n * pb.nb;
       pb.rinv = pb.rp + 2 * (size_t)res_chunks(pb.n) * pb.m * pb.nb;
       pb.status = P->dstatus + q;
+      pb.rs = P->drs ? P->drs + q : nullptr;
       PrepDesc d;
       d.A = probs[q].dA;
       d.lda = probs[q].lda;
@@ -1200,6 +1213,68 @@ int hqr_ls_plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_
   for (size_t t = 0; t < merged.tasks.size(); ++t)
     P->task_kind[t] = ((int32_t)merged.tasks[t].op << 24) | merged.tasks[t].pid;
   *plan = P;
+  return HQR_SUCCESS;
+}
+
+// Refinement outcome of problem idx (synchronizes s): rounds applied, the
+// last applied correction max |d| / max |x| (-1 without refinement), whether
+// the tolerance was met, and the first column with a zero diagonal entry of R
+// (-1: none; tolerance plans only).
+int plan_refine_state(hqr_ls_plan *P, int idx, cudaStream_t s, int *iters, double *rel, int *met, int64_t *sing) {
+  *iters = P->iters;
+  *rel = -1.0;
+  *met = 0;
+  *sing = -1;
+  if (!P->drs) return HQR_SUCCESS;
+  RefineState h;
+  CK(cudaMemcpyAsync(&h, P->drs + idx, sizeof(RefineState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *sing = h.sing ? (int64_t)(~h.sing) : -1;
+  if (!P->tol_mode) return HQR_SUCCESS;
+  *met = h.conv != 0;
+  *iters = h.conv ? h.conv : P->iters;
+  *rel = *iters > 0 ? h.cval[*iters - 1] : -1.0;
+  return HQR_SUCCESS;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hqr_ls_plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_config_t *cfg, int prec,
+                       int refine_iters, hqr_ls_plan **plan) {
+  if (count < 1) return -1;
+  if (!probs) return -2;
+  if (!prec_ok(prec)) return -4;
+  if (refine_iters < 0 || refine_iters > kMaxRounds) return -5;
+  if (!plan) return -6;
+  return plan_create(count, probs, cfg, prec, refine_iters, false, 0.0, plan);
+}
+
+int hqr_ls_plan_create_tol(int count, const hqr_ls_problem_t *probs, const hqr_tile_config_t *cfg, int prec,
+                           int max_iter, double tol, hqr_ls_plan **plan) {
+  if (count < 1) return -1;
+  if (!probs) return -2;
+  if (!prec_ok(prec)) return -4;
+  if (max_iter < 1 || max_iter > kMaxRounds) return -5;
+  if (!(tol >= 0.0)) return -6;
+  if (!plan) return -7;
+  return plan_create(count, probs, cfg, prec, max_iter, true, tol, plan);
+}
+
+int hqr_ls_plan_refine_info(hqr_ls_plan *P, int idx, int *iters, double *rel_correction, int *converged,
+                            int64_t *singular_index, void *stream) {
+  if (!P) return -1;
+  if (idx < 0 || idx >= P->count) return -2;
+  int it = 0, met = 0;
+  double rel = -1.0;
+  int64_t sing = -1;
+  const int st = plan_refine_state(P, idx, (cudaStream_t)stream, &it, &rel, &met, &sing);
+  if (st) return st;
+  if (iters) *iters = it;
+  if (rel_correction) *rel_correction = rel;
+  if (converged) *converged = met;
+  if (singular_index) *singular_index = sing;
   return HQR_SUCCESS;
 }
 
@@ -1296,6 +1371,11 @@ int hqr_ls_plan_correction(hqr_ls_plan *P, int idx, double *rel, void *stream) {
   if (!rel) return -3;
   *rel = -1.0;
   if (P->iters == 0) return HQR_SUCCESS;
+  if (P->tol_mode) {  // the last applied round's (later rounds may leave scratch vectors behind)
+    int it = 0, met = 0;
+    int64_t sing = -1;
+    return plan_refine_state(P, idx, (cudaStream_t)stream, &it, rel, &met, &sing);
+  }
   const Problem &pb = P->probs[idx];
   double *out = nullptr;
   if (!cuda_ok(cudaMalloc(&out, 2 * sizeof(double)), "cudaMalloc(correction)")) return HQR_ERR_NOMEM;
@@ -1341,6 +1421,7 @@ void hqr_ls_plan_free(hqr_ls_plan *P) {
   cudaFree(P->arena);
   cudaFree(P->vec);
   cudaFree(P->dstatus);
+  cudaFree(P->drs);
   cudaFree(P->dprobs);
   cudaFree(P->dprep);
   cudaFree(P->dtrace);
@@ -1350,6 +1431,179 @@ void hqr_ls_plan_free(hqr_ls_plan *P) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// hqr_gels: one least-squares solve through a plan, with its diagnostics.
+namespace {
+
+// Partial sums of b - A x over column chunk blockIdx.y of `cw` columns, one
+// thread per row: part[chunk * M + row] (plain FP64 FMAs; a diagnostic).
+template <typename Real>
+__global__ void diag_resid_part(const Real *__restrict__ A, long long lda, int M, int N, int cw,
+                                const double *__restrict__ x, double *__restrict__ part) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= M) return;
+  const int c0 = blockIdx.y * cw, c1 = min(N, c0 + cw);
+  double s = 0.0;
+  for (int c = c0; c < c1; ++c) s = fma((double)A[(long long)c * lda + row], x[c], s);
+  part[(size_t)blockIdx.y * M + row] = s;
+}
+
+// r = b - (sum of the chunk partials, in chunk order).
+__global__ void diag_resid_sum(const double *__restrict__ part, int nch, int M, const double *__restrict__ b,
+                               double *__restrict__ r) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= M) return;
+  double s = 0.0;
+  for (int c = 0; c < nch; ++c) s += part[(size_t)c * M + row];
+  r[row] = b[row] - s;
+}
+
+// out[col] = sum of squares of column col of A (one warp per column), and
+// out[N + col] = (A^T r)_col.
+template <typename Real>
+__global__ void diag_cols(const Real *__restrict__ A, long long lda, int M, int N, const double *__restrict__ r,
+                          double *__restrict__ out) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= N) return;
+  const Real *col = A + (long long)warp * lda;
+  double ss = 0.0, d = 0.0;
+  for (int i = lane; i < M; i += 32) {
+    const double a = (double)col[i];
+    ss = fma(a, a, ss);
+    d = fma(a, r[i], d);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    d += __shfl_xor_sync(0xffffffffu, d, o);
+  }
+  if (lane == 0) {
+    out[warp] = ss;
+    out[N + warp] = d;
+  }
+}
+
+// One block: out[0] = sum v1^2 (n1 entries of v1: plain squares) ... four
+// sums in a fixed order: ||A||_F^2 (column sums), ||A^T r||^2, ||r||^2,
+// ||x||^2, ||b||^2.
+__global__ void diag_norms(const double *__restrict__ colss, const double *__restrict__ atr, int N,
+                           const double *__restrict__ r, const double *__restrict__ b, int M,
+                           const double *__restrict__ x, double *__restrict__ out) {
+  __shared__ double red[5][256];
+  double v[5] = {0, 0, 0, 0, 0};
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    v[0] += colss[i];
+    v[1] = fma(atr[i], atr[i], v[1]);
+    v[3] = fma(x[i], x[i], v[3]);
+  }
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    v[2] = fma(r[i], r[i], v[2]);
+    v[4] = fma(b[i], b[i], v[4]);
+  }
+  for (int q = 0; q < 5; ++q) red[q][threadIdx.x] = v[q];
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h)
+      for (int q = 0; q < 5; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x < 5) out[threadIdx.x] = red[threadIdx.x][0];
+}
+
+// ||b - A x||, ||A||_F, ||x||, ||b|| and ||A^T (b - A x)|| of a solved
+// problem (plain FP64 on the device): the backward error and the
+// normal-equation residual of hqr_gels_info.
+int gels_diagnostics(const void *dA, int M, int N, int lda, const double *db, const double *dx, int prec,
+                     cudaStream_t s, double *bwd, double *nres) {
+  const int cw = 256, nch = (N + cw - 1) / cw;
+  double *buf = nullptr;
+  const size_t need = (size_t)nch * M + M + 2 * (size_t)N + 8;
+  if (!cuda_ok(cudaMalloc(&buf, sizeof(double) * need), "cudaMalloc(gels diagnostics)")) return HQR_ERR_NOMEM;
+  double *part = buf, *r = part + (size_t)nch * M, *cols = r + M, *out = cols + 2 * (size_t)N;
+  const dim3 g1((M + 255) / 256, nch);
+  if (prec == HQR_FP64) {
+    diag_resid_part<double><<<g1, 256, 0, s>>>((const double *)dA, lda, M, N, cw, dx, part);
+  } else {
+    diag_resid_part<float><<<g1, 256, 0, s>>>((const float *)dA, lda, M, N, cw, dx, part);
+  }
+  diag_resid_sum<<<(M + 255) / 256, 256, 0, s>>>(part, nch, M, db, r);
+  if (prec == HQR_FP64)
+    diag_cols<double><<<(N * 32 + 255) / 256, 256, 0, s>>>((const double *)dA, lda, M, N, r, cols);
+  else
+    diag_cols<float><<<(N * 32 + 255) / 256, 256, 0, s>>>((const float *)dA, lda, M, N, r, cols);
+  diag_norms<<<1, 256, 0, s>>>(cols, cols + N, N, r, db, M, dx, out);
+  double h[5] = {0, 0, 0, 0, 0};
+  const bool ok = cuda_ok(cudaGetLastError(), "gels diagnostics") &&
+                  cuda_ok(cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, s), "copy diagnostics") &&
+                  cuda_ok(cudaStreamSynchronize(s), "sync diagnostics");
+  cudaFree(buf);
+  if (!ok) return HQR_ERR_CUDA;
+  const double na = std::sqrt(h[0]), natr = std::sqrt(h[1]), nr = std::sqrt(h[2]), nx = std::sqrt(h[3]),
+               nbv = std::sqrt(h[4]);
+  *bwd = (na * nx + nbv) > 0.0 ? nr / (na * nx + nbv) : 0.0;
+  *nres = (na * nr) > 0.0 ? natr / (na * nr) : 0.0;
+  return HQR_SUCCESS;
+}
+
+}  // namespace
+
+extern "C" int hqr_gels(const void *dA, int M, int N, int lda, const double *db, double *dx, int prec, double tol,
+                        int max_iter, hqr_gels_info *info, void *stream) {
+  if (!dA) return -1;
+  if (M < 1) return -2;
+  if (N < 1 || N > M) return -3;
+  if (lda < M) return -4;
+  if (!db) return -5;
+  if (!dx) return -6;
+  if (!prec_ok(prec)) return -7;
+  if (!(tol >= 0.0)) return -8;
+  if (max_iter < 0 || max_iter > kMaxRounds) return -9;
+  cudaStream_t s = (cudaStream_t)stream;
+  hqr_ls_problem_t pr;
+  pr.M = M;
+  pr.N = N;
+  pr.dA = dA;
+  pr.lda = lda;
+  pr.db = db;
+  pr.dx = dx;
+  hqr_ls_plan *P = nullptr;
+  int st = plan_create(1, &pr, nullptr, prec, max_iter, true, tol, &P);
+  if (st) return st;
+  st = hqr_ls_plan_run(P, stream);
+  const int64_t launches = g_launches;
+  if (!st) st = hqr_ls_plan_status(P, stream);
+  hqr_gels_info inf;
+  inf.iters = 0;
+  inf.converged = max_iter == 0 ? 1 : 0;
+  inf.rel_correction = -1.0;
+  inf.backward_error = -1.0;
+  inf.normal_residual = -1.0;
+  inf.singular_index = -1;
+  if (st == HQR_SUCCESS || st == HQR_ERR_NOCONV || st == HQR_ERR_SINGULAR) {
+    int it = 0, met = 0;
+    double rel = -1.0;
+    int64_t sing = -1;
+    const int s2 = plan_refine_state(P, 0, s, &it, &rel, &met, &sing);
+    if (s2) {
+      st = s2;
+    } else {
+      if (max_iter > 0) {
+        inf.iters = it;
+        inf.converged = met;
+        inf.rel_correction = rel;
+      }
+      inf.singular_index = sing;
+      if (st != HQR_ERR_SINGULAR) {
+        const int s3 = gels_diagnostics(dA, M, N, lda, db, dx, prec, s, &inf.backward_error, &inf.normal_residual);
+        if (s3) st = s3;
+      }
+    }
+  }
+  hqr_ls_plan_free(P);
+  g_launches = launches + 5;
+  if (info) *info = inf;
+  return st;
+}
 
 // ---------------------------------------------------------------------------
 // Measured autotuner for least-squares plans.

@@ -31,7 +31,28 @@ enum Op : int8_t {
   OP_ATRR = 15,    // g_j = sum over row chunks of the OP_ATR partial sums
   OP_TRINV = 16,   // inverse of the diagonal R tile i (FP64), used by OP_TRSV_TD / OP_TRSV_D
   OP_RESR = 17,    // r_i = b_i - sum over column chunks of the OP_RESID partial sums
+  OP_RCHK = 18,    // convergence check of one refinement round (tolerance-stopped plans)
 };
+
+// Refinement rounds of a least-squares graph at most.
+constexpr int kMaxRounds = 64;
+
+// Per-problem state of a tolerance-stopped refinement (device memory, zeroed
+// before every run). Round r's x-update tasks fold max |d_i| and max |x_i|
+// into dmax[r] / xmax[r] (bit patterns of non-negative doubles order like the
+// values, so atomicMax on them is a max of the values); round r's check task
+// (after all of them) turns them into cval[r], decides whether round r + 2
+// computes its residuals compensated, and records the round at which the
+// tolerance was met. Tasks of the rounds after that do nothing.
+struct RefineState {
+  unsigned long long dmax[kMaxRounds];
+  unsigned long long xmax[kMaxRounds];
+  double cval[kMaxRounds];  // max |d| / max |x| of round r
+  int mode[kMaxRounds];     // 1: round r's residual and A^T r compensated (Dot2)
+  int conv;                 // rounds applied when the tolerance was met (0: not met)
+  unsigned sing;            // ~c for the first column c with a zero diagonal entry of R (0: none)
+};
+static_assert(sizeof(RefineState) % 8 == 0, "RefineState layout");
 
 // Row tiles per chunk of the A^T r partial sums, column tiles per chunk of
 // the residual partial sums.
@@ -108,8 +129,16 @@ Graph build_apply_graph(const std::vector<PanelOp> &ops, int m, int nslab, int w
 // With `pack`, the graph starts with one OP_PACK task per tile column that
 // copies the caller's matrix into the workspace (for runs where no separate
 // preparation kernel can be launched).
+//
+// With tol_mode, `iters` is the largest number of rounds and the rounds stop
+// at a tolerance: every task of round r (residual, A^T r, solve steps, x
+// update) carries trans = 2 and k = r; round r ends with an OP_RCHK task after
+// all its x updates, and round r + 1's x updates follow that check, so a round
+// whose check found the tolerance met leaves x as it was (its other tasks may
+// still run on scratch vectors: harmless). Which rounds compensate their
+// residuals is decided at run time (RefineState::mode), not by `tgt`.
 Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int w, int iters, int pid,
-                     bool pack = false, int split_ib = 0);
+                     bool pack = false, int split_ib = 0, bool tol_mode = false);
 
 // Priorities from the critical path: every task gets its bottom level (its
 // own estimated cost plus the longest chain of estimated costs after it)

@@ -22,14 +22,15 @@ TS, TT = 0, 1
 FP64, FP32, FP32_BF16X3 = 0, 1, 2
 
 (SUCCESS, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_CAPACITY, ERR_INVALID_LIST, ERR_SINGULAR, ERR_INTERNAL,
- ERR_TOO_LARGE, ERR_BUSY, ERR_BUDGET) = range(11)
+ ERR_TOO_LARGE, ERR_BUSY, ERR_BUDGET, ERR_NOCONV) = range(12)
 
 ELIM_DTYPE = np.dtype([("k", np.int32), ("i", np.int32), ("killer", np.int32), ("kind", np.int32),
                        ("level", np.int32), ("step", np.int32)])
 
 EXPORTS = ["hqr_elim_list", "hqr_elim_list_domino", "hqr_validate_list", "hqr_task_graph", "hqr_geqrf", "hqr_refactor", "hqr_refactor_async",
            "hqr_status", "hqr_get_r", "hqr_get_tiles", "hqr_get_t", "hqr_factors_info", "hqr_kernel_ms", "hqr_kernel_times", "hqr_trace", "hqr_apply_q",
-           "hqr_gels", "hqr_geqrf_r_noalloc", "hqr_ls_plan_create", "hqr_ls_plan_run",
+           "hqr_gels", "hqr_gels_qr", "hqr_geqrf_r_noalloc", "hqr_ls_plan_create", "hqr_ls_plan_create_tol",
+           "hqr_ls_plan_refine_info", "hqr_ls_plan_run",
            "hqr_ls_plan_capture", "hqr_ls_plan_status", "hqr_ls_plan_correction", "hqr_ls_plan_info", "hqr_ls_plan_config",
            "hqr_ls_plan_free", "hqr_ls_plan_trace", "hqr_set_tuning", "hqr_autotune", "hqr_server_create", "hqr_server_start",
            "hqr_server_submit", "hqr_server_poll", "hqr_server_stats", "hqr_server_progress", "hqr_server_counters", "hqr_server_stop", "hqr_server_free", "hqr_debug_block_task", "hqr_factors_free", "hqr_set_timeout_ms", "hqr_strerror", "hqr_last_error", "hqr_set_slab_widths",
@@ -86,8 +87,12 @@ def load(build_if_missing=False):
     lib.hqr_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32, ctypes.POINTER(i32)]
     lib.hqr_trace.argtypes = [vp, i32, vp, sz, ctypes.POINTER(sz)]
     lib.hqr_apply_q.argtypes = [vp, i32, vp, i32, i32, vp]
-    lib.hqr_gels.argtypes = [vp, i32, i32, i32, vp, i32, i32, vp, i32, i32, i32, i32, vp, sz, vp]
+    lib.hqr_gels_qr.argtypes = [vp, i32, i32, i32, vp, i32, i32, vp, i32, i32, i32, i32, vp, sz, vp]
+    lib.hqr_gels.argtypes = [vp, i32, i32, i32, vp, vp, i32, ctypes.c_double, i32, vp, vp]
     lib.hqr_ls_plan_create.argtypes = [i32, vp, vp, i32, i32, pf]
+    lib.hqr_ls_plan_create_tol.argtypes = [i32, vp, vp, i32, i32, ctypes.c_double, pf]
+    lib.hqr_ls_plan_refine_info.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(i32), ctypes.POINTER(i64), vp]
     lib.hqr_ls_plan_run.argtypes = [vp, vp]
     lib.hqr_ls_plan_capture.argtypes = [vp, vp]
     lib.hqr_ls_plan_status.argtypes = [vp, vp]
@@ -170,7 +175,7 @@ def validate_list(m, n, records):
     return lib.hqr_validate_list(m, n, arr.ctypes.data if len(arr) else None, len(arr))
 
 
-GRAPH_KINDS = {"factor": 0, "qt": 1, "q": 2, "ls": 3, "request": 4}
+GRAPH_KINDS = {"factor": 0, "qt": 1, "q": 2, "ls": 3, "request": 4, "ls_tol": 5}
 
 
 def task_graph(m, n, nb, ib, records, prec=FP64, kind="factor", param=0):
@@ -397,8 +402,37 @@ def geqrf(A, nb, ib, records=None, stream=None, tensor=False):
     return Factors(h, M, N, A.dtype)
 
 
-def gels(A, b, nb, ib, records=None, stream=None, tensor=False):
-    """Least-squares solution x of min ||b - A x|| (b: M or M x nrhs)."""
+class GelsInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("rel_correction", ctypes.c_double),
+                ("backward_error", ctypes.c_double), ("normal_residual", ctypes.c_double),
+                ("singular_index", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def gels(A, b, tol=1e-14, max_iter=30, tensor=False, stream=None, raise_on_error=True):
+    """hqr_gels: least-squares solution x (float64, N) of min ||b - A x|| for
+    a float32 (mixed precision) or float64 A and a float64 b of M entries,
+    with tolerance-stopped refinement. Returns (x, status, info dict)."""
+    torch = _torch()
+    A, lda = colmajor(A)
+    M, N = A.shape
+    if b.dtype != torch.float64 or not b.is_contiguous() or b.numel() != M:
+        raise TypeError("b must be a contiguous float64 CUDA vector of M entries")
+    x = torch.zeros(N, dtype=torch.float64, device=A.device)
+    info = GelsInfo()
+    st = load().hqr_gels(ctypes.c_void_p(A.data_ptr()), M, N, lda, ctypes.c_void_p(b.data_ptr()),
+                         ctypes.c_void_p(x.data_ptr()), prec_of(A, tensor), float(tol), int(max_iter),
+                         ctypes.byref(info), _stream_ptr(stream))
+    if raise_on_error and st not in (SUCCESS, ERR_NOCONV, ERR_SINGULAR):
+        _check(st, "hqr_gels")
+    return x, st, info.as_dict()
+
+
+def gels_qr(A, b, nb, ib, records=None, stream=None, tensor=False):
+    """hqr_gels_qr: least-squares solution x of min ||b - A x|| in the storage
+    precision (b: M or M x nrhs)."""
     A, lda = colmajor(A)
     M, N = A.shape
     vec = b.dim() == 1
@@ -406,11 +440,11 @@ def gels(A, b, nb, ib, records=None, stream=None, tensor=False):
     nrhs = bc.shape[1]
     x = empty_colmajor(N, nrhs, dtype=A.dtype)
     ptr, cnt, keep = _list_arg(records)
-    st = load().hqr_gels(ctypes.c_void_p(A.data_ptr()), M, N, lda, ctypes.c_void_p(bc.data_ptr()), ldb, nrhs,
-                         ctypes.c_void_p(x.data_ptr()), N, prec_of(A, tensor), nb, ib, ptr, cnt,
-                         _stream_ptr(stream))
+    st = load().hqr_gels_qr(ctypes.c_void_p(A.data_ptr()), M, N, lda, ctypes.c_void_p(bc.data_ptr()), ldb,
+                            nrhs, ctypes.c_void_p(x.data_ptr()), N, prec_of(A, tensor), nb, ib, ptr, cnt,
+                            _stream_ptr(stream))
     del keep
-    _check(st, "hqr_gels")
+    _check(st, "hqr_gels_qr")
     return x[:, 0] if vec else x
 
 
@@ -455,7 +489,10 @@ class LSPlan:
     x float64 (N, written by run()). tensor=True (float32) runs tiles of
     128 on the tensor cores."""
 
-    def __init__(self, problems, refine_iters, configs=None, tensor=False):
+    def __init__(self, problems, refine_iters, configs=None, tensor=False, tol=None):
+        """tol=None: `refine_iters` fixed rounds (hqr_ls_plan_create); a
+        number: at most `refine_iters` rounds that stop at that tolerance
+        (hqr_ls_plan_create_tol)."""
         torch = _torch()
         self._keep = []
         arr = (LSProblem * len(problems))()
@@ -475,9 +512,15 @@ class LSPlan:
         if configs is not None:
             cfg = (TileConfig * len(problems))(*configs)
         h = ctypes.c_void_p(0)
-        st = load().hqr_ls_plan_create(len(problems), ctypes.byref(arr), ctypes.byref(cfg) if cfg else None,
-                                       prec_of(self._keep[0], tensor), int(refine_iters), ctypes.byref(h))
-        _check(st, "hqr_ls_plan_create")
+        if tol is None:
+            st = load().hqr_ls_plan_create(len(problems), ctypes.byref(arr), ctypes.byref(cfg) if cfg else None,
+                                           prec_of(self._keep[0], tensor), int(refine_iters), ctypes.byref(h))
+            _check(st, "hqr_ls_plan_create")
+        else:
+            st = load().hqr_ls_plan_create_tol(len(problems), ctypes.byref(arr),
+                                               ctypes.byref(cfg) if cfg else None, prec_of(self._keep[0], tensor),
+                                               int(refine_iters), float(tol), ctypes.byref(h))
+            _check(st, "hqr_ls_plan_create_tol")
         self._h = h
         self.count = len(problems)
 
@@ -494,6 +537,15 @@ class LSPlan:
 
     def status(self, stream=None):
         return load().hqr_ls_plan_status(self._h, _stream_ptr(stream))
+
+    def refine_info(self, idx=0, stream=None):
+        """(rounds applied, last applied correction, tolerance met, first zero
+        diagonal column or -1) of problem idx (hqr_ls_plan_refine_info)."""
+        it, met = ctypes.c_int32(0), ctypes.c_int32(0)
+        rel, sing = ctypes.c_double(0), ctypes.c_int64(0)
+        _check(load().hqr_ls_plan_refine_info(self._h, idx, ctypes.byref(it), ctypes.byref(rel), ctypes.byref(met),
+                                              ctypes.byref(sing), _stream_ptr(stream)), "hqr_ls_plan_refine_info")
+        return it.value, rel.value, bool(met.value), sing.value
 
     def correction(self, idx=0, stream=None):
         """max |d| / max |x| of the last refinement correction of problem idx (-1: no rounds)."""

@@ -126,7 +126,7 @@ def test_gels_matches_oracle():
     A = inputs.gaussian(m * nb, n * nb, seed=7)
     b = inputs.gaussian(m * nb, 2, seed=8)
     recs = hqr_elim_list(m, n, 2, 2, GREEDY, FIBONACCI)
-    x = hqr.gels(torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda(), nb, ib, recs).cpu().numpy()
+    x = hqr.gels_qr(torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda(), nb, ib, recs).cpu().numpy()
     for c in range(2):
         xo, _ = lstsq(A, b[:, c], nb, ib, recs)
         kappa = np.linalg.cond(A)

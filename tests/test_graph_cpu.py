@@ -17,7 +17,7 @@ from oracle.elim_list import BINARY, FIBONACCI, FLAT, GREEDY, hqr_elim_list
 hqr = pytest.importorskip("paper_1110_1553_gb300.hqr")
 
 GEQRT, UNMQR, TSQRT, TSMQR, TTQRT, TTMQR = range(6)
-RESID, ATR, TRSV_TD, TRSV_TU, TRSV_D, TRSV_U, XUPD, BTOG, PACK, ATRR, TRINV, RESR = range(6, 18)
+RESID, ATR, TRSV_TD, TRSV_TU, TRSV_D, TRSV_U, XUPD, BTOG, PACK, ATRR, TRINV, RESR, RCHK = range(6, 19)
 WEIGHT = {GEQRT: 4, UNMQR: 6, TSQRT: 6, TSMQR: 12, TTQRT: 2, TTMQR: 6}  # units of b^3 / 3 (Sec. 2)
 CHUNK = 8  # tiles per chunk of the residual / A^T r partial sums
 
@@ -66,6 +66,9 @@ def accesses(task, nb, ib, m=0, n=0):
             writes = {("g", j)}
         elif op == XUPD:
             reads, writes = {("g", j)}, {("x", j)}
+        elif op == RCHK:  # round k's convergence check (tolerance plans)
+            reads = {("stat", k), ("cval", k - 1), ("mode", k), ("mode", k + 1), ("conv",)}
+            writes = {("conv",), ("cval", k), ("mode", k + 2)}
         elif op == BTOG:
             reads, writes = {("rhs", i, 0)}, {("g", i)}
         elif op == PACK:  # tile column j from the caller's matrix; column 0 also b and x = 0
@@ -74,6 +77,13 @@ def accesses(task, nb, ib, m=0, n=0):
                 writes |= {("rhs", row, 0) for row in range(m)} | {("x", q) for q in range(n)}
         else:
             raise AssertionError("unexpected task %d" % op)
+        if trans == 2:  # a round of a tolerance-stopped refinement (round k)
+            if op in (RESID, ATR):  # plain or compensated sums, as decided two rounds before
+                reads.add(("mode", k))
+            if op == XUPD:  # applied only if no earlier round met the tolerance
+                reads.add(("conv",))
+            # every round task also reads the stop flag to skip work, but only x updates and
+            # checks act on it in an order that matters: the others write scratch vectors only
         return reads, writes
     block = range((blk - 1) * ib, blk * ib) if blk > 0 else range(nb)
     if op in (GEQRT, TSQRT, TTQRT):  # a panel (or one block of it)
@@ -108,6 +118,13 @@ def accesses(task, nb, ib, m=0, n=0):
     return reads, writes
 
 
+def accumulates(task):
+    """Commutative accumulations of a task (atomic maxima): x updates of a
+    tolerance round fold max |d| and max |x| into that round's statistics."""
+    op, k, trans = int(task[0]), int(task[4]), int(task[8])
+    return {("stat", k)} if (op == XUPD and trans == 2) else set()
+
+
 def check_no_races(tasks, ptr, succ, nb, ib, m=0, n=0):
     nt = len(tasks)
     preds = [[] for _ in range(nt)]
@@ -116,24 +133,31 @@ def check_no_races(tasks, ptr, succ, nb, ib, m=0, n=0):
             assert b > a, "task ids are not a topological order"
             preds[b].append(a)
     anc = [0] * nt
-    last_w, readers = {}, {}
+    last_w, readers, accs = {}, {}, {}
     for t in range(nt):
         before = 0  # bit q set: task q is an ancestor of t
         for p in preds[t]:
             before |= anc[p] | (1 << p)
         anc[t] = before
         rd, wr = accesses(tasks[t], nb, ib, m, n)
-        for x in rd | wr:
+        ac = accumulates(tasks[t])
+        for x in rd | wr | ac:
             w = last_w.get(x)
             assert w is None or (before >> w) & 1, ("unordered with the last writer", t, w, x)
-        for x in wr:
+        for x in wr | ac:
             for q in readers.get(x, ()):
                 assert q == t or (before >> q) & 1, ("write unordered with an earlier read", t, q, x)
+        for x in rd | wr:  # accumulations commute with each other, not with reads or writes
+            for q in accs.get(x, ()):
+                assert (before >> q) & 1, ("unordered with an accumulation", t, q, x)
         for x in rd - wr:
             readers.setdefault(x, []).append(t)
+        for x in ac:
+            accs.setdefault(x, []).append(t)
         for x in wr:
             last_w[x] = t
             readers[x] = []
+            accs[x] = []
 
 
 TREE_CASES = [(FLAT, FLAT, 6, 1), (GREEDY, FIBONACCI, 2, 2), (BINARY, GREEDY, 1, 3), (FIBONACCI, BINARY, 3, 2),
@@ -286,7 +310,7 @@ def test_task_graph_arguments():
                                   tasks, cap, ptr, succ, scap, ctypes.byref(nt), ctypes.byref(ne))
     assert call() == 0 and nt.value > 0 and ne.value > 0
     assert call(m=0) == -1 and call(n=5) == -2 and call(nb=12) == -3 and call(ib=5) == -4
-    assert call(kind=5) == -8 and call(kind=1, param=0) == -9
+    assert call(kind=6) == -8 and call(kind=1, param=0) == -9
     bad = recs.copy()
     bad[0]["killer"] = bad[0]["i"]  # a row cannot kill itself
     assert call(lst=bad) == hqr.ERR_INVALID_LIST
@@ -307,3 +331,52 @@ def test_graph_with_coupling_level_has_no_races(split):
         assert any(r[4] == 2 for r in recs)
         tasks, ptr, succ = hqr.task_graph(m, n, nb, ib, recs)
         check_no_races(tasks, ptr, succ, nb, ib)
+
+
+@pytest.mark.parametrize("low,high,a,p", TREE_CASES[:3])
+@pytest.mark.parametrize("iters,split", [(1, 64), (4, 64), (5, 0)])
+def test_tolerance_graph_has_no_races(low, high, a, p, iters, split):
+    """A plan from hqr_ls_plan_create_tol: rounds whose tasks carry trans = 2
+    and k = the round, one convergence check per round after all its x
+    updates, and the next round's x updates after that check."""
+    m, n, nb, ib = 9, 9, 64, 16
+    hqr.set_panel_split(split)
+    try:
+        tasks, ptr, succ = hqr.task_graph(m, n, nb, ib, hqr_elim_list(m, n, a, p, low, high), kind="ls_tol",
+                                          param=iters)
+    finally:
+        hqr.set_panel_split(64)
+    check_no_races(tasks, ptr, succ, nb, ib, m, n)
+    ops, ks, trans = tasks[:, 0], tasks[:, 4], tasks[:, 8]
+    assert (ops == RCHK).sum() == iters
+    assert sorted(ks[ops == RCHK]) == list(range(iters))
+    rnd = np.isin(ops, [RESID, RESR, ATR, ATRR, TRSV_TD, TRSV_TU, TRSV_D, TRSV_U, XUPD, RCHK])
+    assert (trans[rnd] == 2).all() and (trans[~rnd] != 2).all()
+    # every check follows all x updates of its round; every x update of round k + 1 follows check k
+    for q in np.nonzero(ops == RCHK)[0]:
+        k = ks[q]
+        for u in np.nonzero((ops == XUPD) & (ks == k))[0]:
+            assert q in succ[ptr[u]:ptr[u + 1]]
+        for u in np.nonzero((ops == XUPD) & (ks == k + 1))[0]:
+            assert u in succ[ptr[q]:ptr[q + 1]]
+
+
+def test_race_check_catches_a_missing_check_edge():
+    """Dropping the edge from a round's check to the next round's x update
+    must be reported (that x update could apply a correction after the
+    tolerance was met)."""
+    m, n, nb, ib = 5, 5, 64, 16
+    tasks, ptr, succ = hqr.task_graph(m, n, nb, ib, hqr_elim_list(m, n, 2, 2, GREEDY, FIBONACCI), kind="ls_tol",
+                                      param=3)
+    ops, ks = tasks[:, 0], tasks[:, 4]
+    q = int(np.nonzero((ops == RCHK) & (ks == 0))[0][0])
+    u = int(np.nonzero((ops == XUPD) & (ks == 1))[0][0])
+    s2 = list(succ[ptr[q]:ptr[q + 1]])
+    s2.remove(u)
+    succ2 = np.concatenate([succ[:ptr[q]], np.array(s2, dtype=succ.dtype), succ[ptr[q + 1]:]])
+    ptr2 = ptr.copy()
+    ptr2[q + 1:] -= 1
+    # the x update may still be ordered after the check through another path: only a
+    # missing path counts
+    with pytest.raises(AssertionError):
+        check_no_races(tasks, ptr2, succ2, nb, ib, m, n)
