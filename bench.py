@@ -452,20 +452,37 @@ def trace_phases(tr):
     return float(qr_end - t0) * 1e-6, float(tr[:, 1].max() - qr_end) * 1e-6
 
 
-def square_mixed(torch, hqr, dev, peaks, n=16384, refine=20):
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def square_mixed_oracle(A, b, n):
+    """The committed FP64 oracle solution of the square mixed workload (written
+    by tests/golden/make_square_mixed_oracle.py with oracle/ alone), if the
+    fingerprints of this run's A and b match the ones it was computed for."""
+    meta_f = os.path.join(GOLDEN, "square_mixed_%d_oracle.json" % n)
+    x_f = os.path.join(GOLDEN, "square_mixed_%d_oracle_x.npy" % n)
+    if not (os.path.exists(meta_f) and os.path.exists(x_f)):
+        return None, "no committed oracle solution"
+    meta = json.load(open(meta_f))
+    Ah = A.cpu().numpy()
+    ha = hashlib.sha256(np.asfortranarray(Ah).tobytes(order="F")).hexdigest()
+    hb = hashlib.sha256(np.ascontiguousarray(b.cpu().numpy()).tobytes()).hexdigest()
+    if ha != meta["sha256_A_fp32_colmajor"] or hb != meta["sha256_b_fp64"]:
+        return None, "input fingerprint differs from the one the oracle solved"
+    return np.load(x_f), meta["oracle"]
+
+
+def square_mixed(torch, hqr, dev, peaks, n=16384, max_iter=40, tol=1e-12):
     """16384^2 FP32 least squares, A = U diag(s) V^T, s geometric 1 .. 1e-6,
     b = A x_true + 1e-8 N(0,1): FP32 tile QR with tensor-core updates
-    (BF16x3) + FP64 CSNE."""
+    (BF16x3) + FP64 CSNE refinement stopped at ||d|| <= tol ||x|| (at most
+    max_iter rounds); x against the committed FP64 oracle solution."""
     from paper_1110_1553_gb300 import workloads
-    A = workloads.conditioned(torch, n, n, 1e6, seed=30, device=dev)
-    g = torch.Generator(device=dev)
-    g.manual_seed(31)
-    xt = torch.randn(n, dtype=torch.float64, device=dev, generator=g)
-    b = A.double() @ xt + 1e-8 * torch.randn(n, dtype=torch.float64, device=dev, generator=g)
+    A, b = workloads.square_mixed_problem(torch, n, device=dev)
     x = torch.zeros(n, dtype=torch.float64, device=dev)
     nb = 128
     cfg = [hqr.tile_config(nb, nb, 16, 1, "greedy", "greedy")]
-    plan = hqr.LSPlan([(A, b, x)], refine_iters=refine, configs=cfg, tensor=True)
+    plan = hqr.LSPlan([(A, b, x)], refine_iters=max_iter, configs=cfg, tensor=True, tol=tol)
     plan.run()
     plan.status()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -476,22 +493,27 @@ def square_mixed(torch, hqr, dev, peaks, n=16384, refine=20):
     st = plan.status()
     ms = e0.elapsed_time(e1)
     info = plan.info()
+    iters, last_corr, met, _, ncomp = plan.refine_info(0)
     # one traced run for the split between the QR and the refinement
     plan.trace(True)
     plan.run()
     plan.status()
     qr_ms, ref_ms = trace_phases(plan.trace())
     plan.trace(False)
-    ncomp = min(refine, max(4, (2 * refine + 4) // 5))
     bound, qpeak = fp32_qr_bound(peaks, nb, True)
     qr_tf = info["qr_flops"] / (qr_ms * 1e-3) / 1e12
-    rops = refine_fp64_ops(n, n, refine - ncomp, ncomp)
+    rops = refine_fp64_ops(n, n, iters - ncomp, ncomp)
+    xo, how = square_mixed_oracle(A, b, n)
+    xh = x.cpu().numpy()
+    err = float(np.linalg.norm(xh - xo) / np.linalg.norm(xo)) if xo is not None else None
     # independent cross-check (a library FP64 QR solve, itself accurate to about kappa * u64)
     ref = torch.linalg.lstsq(A.double(), b.unsqueeze(1), driver="gels").solution[:, 0]
     cross = ((x - ref).norm() / ref.norm()).item()
     return {"workload": "square_mixed_ls_16384_kappa1e6", "ms": ms, "solves_per_s": 1e3 / ms,
-            "qr_tflops": info["qr_flops"] / (ms * 1e-3) / 1e12, "refine_iters": refine, "status": st,
-            "last_rel_correction": plan.correction(0),
+            "qr_tflops": info["qr_flops"] / (ms * 1e-3) / 1e12, "status": st,
+            "refinement": {"tol": tol, "max_iter": max_iter, "iters": iters, "compensated_rounds": ncomp,
+                           "converged": met, "last_rel_correction": last_corr},
+            "rel_err_vs_oracle": err, "oracle": how,
             "rel_diff_vs_cusolver_fp64_qr": cross, "tasks": info["tasks"],
             "phases_ms": {"qr": qr_ms, "refinement": ref_ms, "from": "one traced run (per-task %globaltimer)"},
             "roofline": {
@@ -501,7 +523,7 @@ def square_mixed(torch, hqr, dev, peaks, n=16384, refine=20):
                        "peak_source": "%s BF16 burst / 6 (BF16x3) and HBM x nb/4 flop/B" % peaks["source"]},
                 "refinement": {"bound": "alu", "achieved": rops / (ref_ms * 1e-3) / 1e9, "peak": FP64_OPS_PER_S / 1e9,
                                "unit": "G FP64-ops/s", "frac": rops / (ref_ms * 1e-3) / FP64_OPS_PER_S,
-                               "ops": rops, "plain_rounds": refine - ncomp, "compensated_rounds": ncomp,
+                               "ops": rops, "plain_rounds": iters - ncomp, "compensated_rounds": ncomp,
                                "peak_source": "FP64 pipe: 152 SMs x 2 ops/cycle x 2.07 GHz"}}}
 
 

@@ -280,7 +280,7 @@ int hqr_gels_qr(const void *dA, int M, int N, int lda, const void *db, int ldb, 
 typedef struct {
   int iters;               /* refinement rounds applied (0 when max_iter = 0) */
   int converged;           /* 1: the tolerance was met (always 1 when max_iter = 0) */
-  double rel_correction;   /* max|d| / max|x| of the last applied correction d; -1 without refinement */
+  double rel_correction;   /* ||d||_2 / ||x||_2 of the last applied correction d; -1 without refinement */
   double backward_error;   /* ||b - A x||_2 / (||A||_F ||x||_2 + ||b||_2), FP64 on the device */
   double normal_residual;  /* ||A^T (b - A x)||_2 / (||A||_F ||b - A x||_2): near rounding level at a
                               least-squares solution even when b - A x itself is large */
@@ -301,7 +301,8 @@ typedef struct {
  *             cores with BF16X3), FP64 only in the refinement (residual,
  *             A^T r, triangular solves with the low-precision R).
  *   tol       stop the refinement at the first compensated round whose
- *             correction has max|d| <= tol max|x| (tol >= 0).
+ *             correction has ||d||_2 <= tol ||x||_2 (tol >= 0); see
+ *             hqr_ls_plan_create_tol for the other stop.
  *   max_iter  refinement rounds at most, 0 <= max_iter <= 64. With 0, x is
  *             the plain QR solve R^{-1} (Q^T b)[0:N] in the storage precision.
  *   info      NULL, or receives the outcome (also on HQR_ERR_NOCONV and
@@ -397,25 +398,28 @@ int hqr_ls_plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_
  * hqr_ls_plan_create_tol -- as hqr_ls_plan_create with refinement rounds
  * that stop at a tolerance (corrected semi-normal equations as above): at
  * most max_iter rounds (1 .. 64); each problem stops after the first round
- * whose correction d has max|d| <= tol max|x| and whose residual and A^T r
- * were compensated. Rounds start with plain FP64 sums and switch to
- * compensated ones when the corrections stop halving from round to round or
- * reach tol (decided on the device, two rounds ahead). The rounds after a
- * problem's last one are skipped on the device. A problem that does not meet
- * tol reports HQR_ERR_NOCONV (hqr_ls_plan_status); see
- * hqr_ls_plan_refine_info.
+ * whose correction d has ||d||_2 <= tol ||x||_2 and whose residual and A^T r
+ * were compensated (tolerance met), or after two compensated rounds in a row
+ * whose corrections did not shrink by 10 % (no more progress: the attainable
+ * accuracy with this R is reached; reported as not met). Rounds start with
+ * plain FP64 sums and switch to compensated ones when the corrections, below
+ * 1e-6, stop halving from round to round or reach tol (decided on the
+ * device, two rounds ahead). The rounds after a problem's last one are
+ * skipped on the device. A problem that does not meet tol reports
+ * HQR_ERR_NOCONV (hqr_ls_plan_status); see hqr_ls_plan_refine_info.
  */
 int hqr_ls_plan_create_tol(int count, const hqr_ls_problem_t *probs, const hqr_tile_config_t *cfg, int prec,
                            int max_iter, double tol, hqr_ls_plan **plan);
 
 /* hqr_ls_plan_refine_info -- outcome of problem idx after a run of a plan
  * from hqr_ls_plan_create_tol: rounds applied, the last applied correction
- * max|d| / max|x|, whether tol was met, and the first column with an exact
- * zero on R's diagonal (-1: none). Plans from hqr_ls_plan_create report
- * their fixed round count, -1, 0 and -1. Any output may be NULL.
- * Synchronizes `stream`. */
+ * ||d||_2 / ||x||_2, whether tol was met, how many of the applied rounds had
+ * compensated residuals, and the first column with an exact zero on R's
+ * diagonal (-1: none). Plans from hqr_ls_plan_create report their fixed
+ * round count, -1, 0, their compensated round count and -1. Any output may
+ * be NULL. Synchronizes `stream`. */
 int hqr_ls_plan_refine_info(hqr_ls_plan *plan, int idx, int *iters, double *rel_correction, int *converged,
-                            int64_t *singular_index, void *stream);
+                            int *compensated, int64_t *singular_index, void *stream);
 
 /* hqr_ls_plan_run -- solve all problems (asynchronous on `stream`): one
  * preparation kernel (tile packing, b, x = 0), the persistent task kernel,
@@ -436,9 +440,11 @@ int hqr_ls_plan_status(hqr_ls_plan *plan, void *stream);
 
 /* hqr_ls_plan_correction -- size of the last refinement correction of
  * problem idx after a run: *rel = max_i |d_i| / max_i |x_i|, d the
- * correction the last CSNE round added to x. A value at the FP64 rounding
- * level says the refinement has converged; -1 when the plan has no
- * refinement rounds. Synchronizes `stream` (the one the plan ran on). */
+ * correction the last CSNE round added to x (plans from
+ * hqr_ls_plan_create_tol: ||d||_2 / ||x||_2 of the last applied round, the
+ * measure their stop uses). A small value says the refinement has
+ * converged; -1 when the plan has no refinement rounds. Synchronizes
+ * `stream` (the one the plan ran on). */
 int hqr_ls_plan_correction(hqr_ls_plan *plan, int idx, double *rel, void *stream);
 
 /* hqr_ls_plan_info -- tasks of the merged graph, the paper's QR flop count
@@ -465,13 +471,30 @@ void hqr_ls_plan_free(hqr_ls_plan *plan);
 int hqr_set_tuning(int count, const int *keys, const hqr_tile_config_t *cfgs);
 
 /*
+ * hqr_critical_path -- unit-cost model of the factorization of an m x n tile
+ * matrix by a list (host only): every task of the library's graph costs its
+ * Sec. 2 weight (GEQRT 4, TSQRT 6, TTQRT 2, UNMQR 6, TSMQR 12, TTMQR 6 units
+ * of b^3 / 3; column slabs and split-panel blocks their share). Returns the
+ * longest chain of costs (the time on unbounded processors; the paper's
+ * coarse model of Sec. 3 counts steps instead) and their sum (the time on
+ * one processor). nb, ib, prec as in hqr_geqrf; -k for a bad argument k,
+ * HQR_ERR_INVALID_LIST for an invalid list.
+ */
+int hqr_critical_path(int m, int n, int nb, int ib, int prec, const hqr_elim_t *list, size_t count,
+                      double *critical_path, double *work);
+
+/*
  * hqr_autotune -- measured autotuner for least-squares plans. For every
  * shape class (floor(log2 M), floor(log2 N)) among the `count` shapes
- * (Ms[q] x Ns[q]), times candidate tile configurations (nb in {32, 64, 128},
- * TS domains a in {1, 4, 16} with greedy trees, or one flat TS domain) on
- * `reps` random problems of the class's geometric-mean shape solved in one
- * plan (prec, refine_iters as in hqr_ls_plan_create), and installs the
- * fastest per class with hqr_set_tuning. The chosen table is also copied to
+ * (Ms[q] x Ns[q]), times candidate tile configurations on `reps` random
+ * problems of the class's geometric-mean shape solved in one plan (prec,
+ * refine_iters as in hqr_ls_plan_create), in two stages: (1) nb in {32, 64,
+ * 128} x TS domains a in {1, 4, 16} with greedy trees, or one flat TS
+ * domain, with p = 1; (2) for the winner, p in {2, 4, 8, 16} x high-level
+ * trees {greedy, Fibonacci, binary, flat}, ranked by the unit-cost model of
+ * hqr_critical_path (the larger of the critical path and the work over the
+ * resident CTAs), of which the best three are timed. Installs the fastest
+ * per class with hqr_set_tuning. The chosen table is also copied to
  * keys_out (2 ints per class) / cfg_out when cap is large enough;
  * *nout = number of classes. Synchronizes `stream`; allocates and frees its
  * own random test matrices.

@@ -422,40 +422,61 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
   return b.finish();
 }
 
-void critical_path_priorities(Graph &g, int nb) {
+// Estimated cost of a task in units of b^3/3 (Sec. 2 weights), updates scaled by slab width;
+// the FP64 vector tasks of least-squares graphs by their relative durations (a compensated
+// residual or A^T r chunk costs about a GEQRT, a plain one a fifth of it, a triangular-solve
+// step a few percent), so that the solve chains keep their place ahead of the next round's
+// residuals.
+static double task_cost(const Task &t, int nb) {
+  const double slab = t.cw > 0 ? (double)t.cw / nb : 1.0;
+  // a block task of a split panel: about one block's share of its panel (or of one update slab)
+  const double part = t.blk > 0 ? 0.125 : 1.0;
+  switch (t.op) {
+    case OP_GEQRT: return 4.0 * part;
+    case OP_TSQRT: return 6.0 * part;
+    case OP_TTQRT: return 2.0 * part;
+    case OP_UNMQR: return 6.0 * slab * part;
+    case OP_TSMQR: return 12.0 * slab * part;
+    case OP_TTMQR: return 6.0 * slab * part;
+    case OP_RESID:
+    case OP_ATR: return t.tgt ? 3.5 : 0.7;
+    case OP_TRINV: return 12.0;
+    case OP_TRSV_TD:
+    case OP_TRSV_TU:
+    case OP_TRSV_D:
+    case OP_TRSV_U: return 0.2;
+    default: return 0.1;
+  }
+}
+
+// Bottom level of every task: its cost plus the longest chain of costs after it.
+static std::vector<double> bottom_levels(const Graph &g, int nb) {
   const size_t nt = g.tasks.size();
-  if (nt == 0) return;
-  // estimated cost in units of b^3/3 (Sec. 2 weights), updates scaled by slab width; the FP64
-  // vector tasks of least-squares graphs by their relative durations (a compensated residual or
-  // A^T r chunk costs about a GEQRT, a plain one a fifth of it, a triangular-solve step a few
-  // percent), so that the solve chains keep their place ahead of the next round's residuals
-  auto cost = [&](const Task &t) {
-    const double slab = t.cw > 0 ? (double)t.cw / nb : 1.0;
-    // a block task of a split panel: about one block's share of its panel (or of one update slab)
-    const double part = t.blk > 0 ? 0.125 : 1.0;
-    switch (t.op) {
-      case OP_GEQRT: return 4.0 * part;
-      case OP_TSQRT: return 6.0 * part;
-      case OP_TTQRT: return 2.0 * part;
-      case OP_UNMQR: return 6.0 * slab * part;
-      case OP_TSMQR: return 12.0 * slab * part;
-      case OP_TTMQR: return 6.0 * slab * part;
-      case OP_RESID:
-      case OP_ATR: return t.tgt ? 3.5 : 0.7;
-      case OP_TRINV: return 12.0;
-      case OP_TRSV_TD:
-      case OP_TRSV_TU:
-      case OP_TRSV_D:
-      case OP_TRSV_U: return 0.2;
-      default: return 0.1;
-    }
-  };
   std::vector<double> bl(nt, 0.0);
   for (size_t q = nt; q-- > 0;) {  // tasks are in a topological order
     double best = 0.0;
     for (int32_t e = g.tasks[q].succ_begin; e < g.tasks[q].succ_end; ++e) best = std::max(best, bl[g.succ[e]]);
-    bl[q] = cost(g.tasks[q]) + best;
+    bl[q] = task_cost(g.tasks[q], nb) + best;
   }
+  return bl;
+}
+
+double critical_path_length(const Graph &g, int nb) {
+  double cp = 0.0;
+  for (double v : bottom_levels(g, nb)) cp = std::max(cp, v);
+  return cp;
+}
+
+double total_cost(const Graph &g, int nb) {
+  double w = 0.0;
+  for (const Task &t : g.tasks) w += task_cost(t, nb);
+  return w;
+}
+
+void critical_path_priorities(Graph &g, int nb) {
+  const size_t nt = g.tasks.size();
+  if (nt == 0) return;
+  const std::vector<double> bl = bottom_levels(g, nb);
   // successors in decreasing bottom level: the most critical ones are released first
   for (size_t q = 0; q < nt; ++q) {
     const Task &t = g.tasks[q];

@@ -110,8 +110,10 @@ struct alignas(16) Problem {
   int tstr;           // elements per T record (ib * nb; tensor-core problems: split images [+ T])
   int t32;            // tensor-core problems: the records keep the FP32 T (apply Q, read T)
   int maxit;          // tolerance-stopped refinement: rounds at most (0: fixed rounds)
-  double tol;         // tolerance-stopped refinement: stop when max |d| / max |x| <= tol
+  double tol;         // tolerance-stopped refinement: stop when ||d||_2 / ||x||_2 <= tol
   RefineState *rs;    // tolerance-stopped refinement state (nullptr otherwise)
+  double *rn;         // tolerance-stopped refinement: per tile of x, sum d^2 and sum x^2 of a round
+  long long pad2_;
 };
 static_assert(sizeof(Problem) % 16 == 0, "Problem is read in 16-byte pieces");
 
@@ -1119,14 +1121,14 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
         const double d = __ldcg(P.g + (size_t)j * nb + c);
         const double xn = __ldcg(P.x + (size_t)j * nb + c) + d;
         P.x[(size_t)j * nb + c] = xn;
-        md = fmax(md, fabs(d));
-        mx = fmax(mx, fabs(xn));
+        md = fma(d, d, md);
+        mx = fma(xn, xn, mx);
       }
-      if (tolm) {  // fold this tile's max |d| and max |x| into the round's
+      if (tolm) {  // this tile's sum d^2 and sum x^2 (fixed order: threads, then warps)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-          md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
-          mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+          md += __shfl_xor_sync(0xffffffffu, md, o);
+          mx += __shfl_xor_sync(0xffffffffu, mx, o);
         }
         if (lane == 0) {
           sm[warp] = md;
@@ -1135,34 +1137,42 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
         __syncthreads();
         if (tid == 0) {
           for (int w = 1; w < NWARP; ++w) {
-            md = fmax(md, sm[w]);
-            mx = fmax(mx, sm[NWARP + w]);
+            md += sm[w];
+            mx += sm[NWARP + w];
           }
-          // NaN stays visible: its bit pattern is above every finite one
-          atomicMax(&P.rs->dmax[t.k], (unsigned long long)__double_as_longlong(md));
-          atomicMax(&P.rs->xmax[t.k], (unsigned long long)__double_as_longlong(mx));
+          P.rn[2 * j] = md;
+          P.rn[2 * j + 1] = mx;
         }
         __syncthreads();
       }
       break;
     }
-    case OP_RCHK: {  // after every x update of round k: tolerance met? compensate round k + 2?
+    case OP_RCHK: {  // after every x update of round k: stop? compensate round k + 2?
       if (tid == 0) {
         RefineState *rs = P.rs;
         const int k = t.k;
-        const double d = __longlong_as_double((long long)__ldcg(&rs->dmax[k]));
-        const double x = __longlong_as_double((long long)__ldcg(&rs->xmax[k]));
-        const double c = x > 0.0 ? d / x : (d > 0.0 ? INFINITY : 0.0);
+        double sd = 0.0, sx = 0.0;
+        for (int q = 0; q < g.n; ++q) {  // tile order: the same sum on every run
+          sd += __ldcg(P.rn + 2 * q);
+          sx += __ldcg(P.rn + 2 * q + 1);
+        }
+        const double c = sx > 0.0 ? sqrt(sd / sx) : (sd > 0.0 ? INFINITY : 0.0);
         rs->cval[k] = c;
         const int comp_k = __ldcg(&rs->mode[k]);
+        const int comp_p = k >= 1 ? __ldcg(&rs->mode[k - 1]) : 0;
+        const double cp = k >= 1 ? __ldcg(&rs->cval[k - 1]) : 0.0;
         if ((comp_k && c <= P.tol) || c == 0.0) {
+          rs->met = 1;
           rs->conv = k + 1;
+        } else if (comp_k && comp_p && !(c <= 0.9 * cp)) {
+          rs->conv = k + 1;  // no more progress: the accuracy the low-precision R allows
+          atomicCAS(P.status, 0, HQR_ERR_NOCONV);
         } else {
-          // plain rounds until their corrections stop shrinking (by half per round) or reach
-          // the tolerance; from then on compensated residuals, which can certify it
+          // plain rounds until their corrections stop halving below 1e-6 (the plain residual's
+          // floor) or reach the tolerance; from then on compensated residuals, which can
+          // certify it
           if (k + 2 < P.maxit)
-            rs->mode[k + 2] = (__ldcg(&rs->mode[k + 1]) || c <= P.tol || (k >= 1 && !(c <= 0.5 * rs->cval[k - 1])))
-                                  ? 1 : 0;
+            rs->mode[k + 2] = (__ldcg(&rs->mode[k + 1]) || c <= P.tol || (c < 1e-6 && !(c <= 0.5 * cp))) ? 1 : 0;
           if (k == P.maxit - 1) atomicCAS(P.status, 0, HQR_ERR_NOCONV);
         }
       }

@@ -1129,7 +1129,7 @@ int plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_config_
     arena_elems += (Mp + 3) & ~(size_t)3;
     off_vec[q] = vec_elems;
     vec_elems += Np + Mp + Np + 2 * (size_t)atr_chunks(pb.m) * Np + 2 * (size_t)res_chunks(pb.n) * Mp +
-                 (size_t)pb.n * c.nb * c.nb;
+                 (size_t)pb.n * c.nb * c.nb + 2 * (size_t)pb.n;
     size_t cnt = 0;
     hqr_elim_list(pb.m, pb.n, c.a, c.p, c.low_tree, c.high_tree, nullptr, 0, &cnt);
     std::vector<hqr_elim_t> lst(cnt);
@@ -1171,6 +1171,7 @@ int plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_config_
       pb.gp = pb.g + (size_t)pb.n * pb.nb;
       pb.rp = pb.gp + 2 * (size_t)atr_chunks(pb.m) * pb.n * pb.nb;
       pb.rinv = pb.rp + 2 * (size_t)res_chunks(pb.n) * pb.m * pb.nb;
+      pb.rn = pb.rinv + (size_t)pb.n * pb.nb * pb.nb;
       pb.status = P->dstatus + q;
       pb.rs = P->drs ? P->drs + q : nullptr;
       PrepDesc d;
@@ -1220,20 +1221,26 @@ int plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_config_
 // last applied correction max |d| / max |x| (-1 without refinement), whether
 // the tolerance was met, and the first column with a zero diagonal entry of R
 // (-1: none; tolerance plans only).
-int plan_refine_state(hqr_ls_plan *P, int idx, cudaStream_t s, int *iters, double *rel, int *met, int64_t *sing) {
+int plan_refine_state(hqr_ls_plan *P, int idx, cudaStream_t s, int *iters, double *rel, int *met, int64_t *sing,
+                      int *ncomp = nullptr) {
   *iters = P->iters;
   *rel = -1.0;
   *met = 0;
   *sing = -1;
+  if (ncomp) *ncomp = std::min(P->iters, std::max(4, (2 * P->iters + 4) / 5));
   if (!P->drs) return HQR_SUCCESS;
   RefineState h;
   CK(cudaMemcpyAsync(&h, P->drs + idx, sizeof(RefineState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   *sing = h.sing ? (int64_t)(~h.sing) : -1;
   if (!P->tol_mode) return HQR_SUCCESS;
-  *met = h.conv != 0;
+  *met = h.met;
   *iters = h.conv ? h.conv : P->iters;
   *rel = *iters > 0 ? h.cval[*iters - 1] : -1.0;
+  if (ncomp) {
+    *ncomp = 0;
+    for (int r = 0; r < *iters; ++r) *ncomp += h.mode[r] != 0;
+  }
   return HQR_SUCCESS;
 }
 
@@ -1263,17 +1270,18 @@ int hqr_ls_plan_create_tol(int count, const hqr_ls_problem_t *probs, const hqr_t
 }
 
 int hqr_ls_plan_refine_info(hqr_ls_plan *P, int idx, int *iters, double *rel_correction, int *converged,
-                            int64_t *singular_index, void *stream) {
+                            int *compensated, int64_t *singular_index, void *stream) {
   if (!P) return -1;
   if (idx < 0 || idx >= P->count) return -2;
-  int it = 0, met = 0;
+  int it = 0, met = 0, nc = 0;
   double rel = -1.0;
   int64_t sing = -1;
-  const int st = plan_refine_state(P, idx, (cudaStream_t)stream, &it, &rel, &met, &sing);
+  const int st = plan_refine_state(P, idx, (cudaStream_t)stream, &it, &rel, &met, &sing, &nc);
   if (st) return st;
   if (iters) *iters = it;
   if (rel_correction) *rel_correction = rel;
   if (converged) *converged = met;
+  if (compensated) *compensated = nc;
   if (singular_index) *singular_index = sing;
   return HQR_SUCCESS;
 }
@@ -1609,6 +1617,26 @@ extern "C" int hqr_gels(const void *dA, int M, int N, int lda, const double *db,
 // Measured autotuner for least-squares plans.
 namespace {
 
+// Unit-cost model of the factorization graph of an m x n tile matrix under a
+// tile configuration: critical path and total work (hqr_critical_path).
+int config_cost(int m, int n, const hqr_tile_config_t &c, int prec, double *cp, double *work) {
+  size_t cnt = 0;
+  if (hqr_elim_list(m, n, c.a, c.p, c.low_tree, c.high_tree, nullptr, 0, &cnt) != HQR_ERR_CAPACITY && cnt) return 1;
+  std::vector<hqr_elim_t> lst(cnt);
+  if (cnt && hqr_elim_list(m, n, c.a, c.p, c.low_tree, c.high_tree, lst.data(), cnt, &cnt)) return 1;
+  Problem pb{};
+  pb.m = m;
+  pb.n = n;
+  pb.nb = c.nb;
+  pb.ib = eff_ib(prec, c.nb, c.ib);
+  choose_widths(prec, c.nb, pb.ib, pb);
+  const Graph g = build_factor_graph(expand_ops(lst.data(), lst.size(), m, n), m, n, c.nb, pb.w, 0,
+                                     split_ib_for(prec, pb));
+  *cp = critical_path_length(g, c.nb);
+  *work = total_cost(g, c.nb);
+  return 0;
+}
+
 // Uniform(-1, 1) entries from a counter-based hash (SplitMix64 finaliser);
 // only used to time candidate configurations.
 template <typename Real>
@@ -1624,6 +1652,29 @@ __global__ void fill_uniform(Real *x, long long n, unsigned long long seed) {
 }
 
 }  // namespace
+
+extern "C" int hqr_critical_path(int m, int n, int nb, int ib, int prec, const hqr_elim_t *list, size_t count,
+                                 double *critical_path, double *work) {
+  if (m < 1) return -1;
+  if (n < 1 || n > m) return -2;
+  if (!prec_ok(prec)) return -5;
+  if (nb < 8 || nb > 256 || nb % 8 || (prec == HQR_FP32_BF16X3 && nb != tc::NB)) return -3;
+  ib = eff_ib(prec, nb, ib);
+  if (!valid_tile_sizes(prec, nb, ib)) return -4;
+  if (!list && count) return -6;
+  if (!critical_path || !work) return -8;
+  if (hqr_validate_list(m, n, list, count) != HQR_SUCCESS) return HQR_ERR_INVALID_LIST;
+  Problem pb{};
+  pb.m = m;
+  pb.n = n;
+  pb.nb = nb;
+  pb.ib = ib;
+  choose_widths(prec, nb, ib, pb);
+  const Graph g = build_factor_graph(expand_ops(list, count, m, n), m, n, nb, pb.w, 0, split_ib_for(prec, pb));
+  *critical_path = critical_path_length(g, nb);
+  *work = total_cost(g, nb);
+  return HQR_SUCCESS;
+}
 
 extern "C" int hqr_autotune(int count, const int *Ms, const int *Ns, int prec, int refine_iters, int reps,
                             int *keys_out, hqr_tile_config_t *cfg_out, int cap, int *nout, void *stream) {
@@ -1688,12 +1739,12 @@ extern "C" int hqr_autotune(int count, const int *Ms, const int *Ns, int prec, i
     }
     float best = 1e30f;
     hqr_tile_config_t best_cfg = default_config(M, N, prec);
-    for (const hqr_tile_config_t &cf : cands) {
-      if (!valid_tile_sizes(prec, cf.nb, cf.ib)) continue;
+    auto try_config = [&](const hqr_tile_config_t &cf) {
+      if (!valid_tile_sizes(prec, cf.nb, cf.ib)) return;
       std::vector<hqr_tile_config_t> cfv(reps, cf);
       hqr_ls_plan *P = nullptr;
       int st = hqr_ls_plan_create(reps, probs.data(), cfv.data(), prec, refine_iters, &P);
-      if (st) continue;
+      if (st) return;
       float ms = 0.f, tot = 0.f;
       bool ok = hqr_ls_plan_run(P, stream) == HQR_SUCCESS;  // warm-up
       for (int it = 0; ok && it < 2; ++it) {
@@ -1705,6 +1756,36 @@ extern "C" int hqr_autotune(int count, const int *Ms, const int *Ns, int prec, i
         best_cfg = cf;
       }
       hqr_ls_plan_free(P);
+    };
+    // stage 1: tile size, TS domain size and low-level tree (one virtual domain)
+    for (const hqr_tile_config_t &cf : cands) try_config(cf);
+    // stage 2: virtual domains p and the high-level tree for the stage-1 winner. The
+    // candidates are ranked by a unit-cost model of the factorization graph (Sec. 2
+    // weights): the larger of its critical path and its work spread over the resident
+    // CTAs (the reps problems run at once); only the best few are timed.
+    {
+      const hqr_tile_config_t c1 = best_cfg;
+      const int mt = (M + c1.nb - 1) / c1.nb, nt = (N + c1.nb - 1) / c1.nb;
+      int sms = 152;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+      const double workers = 2.0 * sms;
+      std::vector<std::pair<double, hqr_tile_config_t>> ranked;
+      for (int p : {2, 4, 8, 16}) {
+        if (2 * p > mt) continue;
+        for (int high : {HQR_GREEDY, HQR_FIBONACCI, HQR_BINARY, HQR_FLAT}) {
+          hqr_tile_config_t cf = c1;
+          cf.p = p;
+          cf.high_tree = high;
+          double cp = 0.0, work = 0.0;
+          if (config_cost(mt, nt, cf, prec, &cp, &work)) continue;
+          ranked.push_back({std::max(cp, reps * work / workers), cf});
+        }
+      }
+      std::stable_sort(ranked.begin(), ranked.end(),
+                       [](const std::pair<double, hqr_tile_config_t> &a, const std::pair<double, hqr_tile_config_t> &b) {
+                         return a.first < b.first;
+                       });
+      for (size_t q = 0; q < ranked.size() && q < 3; ++q) try_config(ranked[q].second);
     }
     cudaFree(A);
     cudaFree(bx);

@@ -38,19 +38,22 @@ enum Op : int8_t {
 constexpr int kMaxRounds = 64;
 
 // Per-problem state of a tolerance-stopped refinement (device memory, zeroed
-// before every run). Round r's x-update tasks fold max |d_i| and max |x_i|
-// into dmax[r] / xmax[r] (bit patterns of non-negative doubles order like the
-// values, so atomicMax on them is a max of the values); round r's check task
-// (after all of them) turns them into cval[r], decides whether round r + 2
-// computes its residuals compensated, and records the round at which the
-// tolerance was met. Tasks of the rounds after that do nothing.
+// before every run). Round r's x-update task of tile j leaves sum d_i^2 and
+// sum x_i^2 over its tile in a per-problem array (two doubles per tile);
+// round r's check task (after all of them) adds them up in tile order into
+// cval[r] = ||d||_2 / ||x||_2, decides whether round r + 2 computes its
+// residuals compensated, and whether to stop: at the first compensated round
+// with cval <= tol (met = 1), or at a compensated round that no longer
+// shrinks the correction (cval > 0.9 cval of the compensated round before:
+// the attainable accuracy of the low-precision R is reached, met = 0). The
+// tasks of the rounds after the stop do nothing.
 struct RefineState {
-  unsigned long long dmax[kMaxRounds];
-  unsigned long long xmax[kMaxRounds];
-  double cval[kMaxRounds];  // max |d| / max |x| of round r
+  double cval[kMaxRounds];  // ||d||_2 / ||x||_2 of round r
   int mode[kMaxRounds];     // 1: round r's residual and A^T r compensated (Dot2)
-  int conv;                 // rounds applied when the tolerance was met (0: not met)
+  int conv;                 // rounds applied when the refinement stopped (0: running)
+  int met;                  // 1: it stopped because the tolerance was met
   unsigned sing;            // ~c for the first column c with a zero diagonal entry of R (0: none)
+  int pad_;
 };
 static_assert(sizeof(RefineState) % 8 == 0, "RefineState layout");
 
@@ -145,6 +148,12 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
 // and the queue 0 (longest remaining chain) .. kNumQueues-1 of its quantile.
 // Replaces the default classes (panel kernels, next-column updates, rest).
 void critical_path_priorities(Graph &g, int nb);
+
+// Longest chain of estimated task costs (units of b^3 / 3, Sec. 2 weights) of
+// a graph, and the sum of all its task costs: a unit-cost model of the time
+// on unbounded and on one processor.
+double critical_path_length(const Graph &g, int nb);
+double total_cost(const Graph &g, int nb);
 
 // Append graph g to `into` (its task ids and successor lists renumbered);
 // the two graphs stay independent.

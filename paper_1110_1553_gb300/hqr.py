@@ -30,7 +30,7 @@ ELIM_DTYPE = np.dtype([("k", np.int32), ("i", np.int32), ("killer", np.int32), (
 EXPORTS = ["hqr_elim_list", "hqr_elim_list_domino", "hqr_validate_list", "hqr_task_graph", "hqr_geqrf", "hqr_refactor", "hqr_refactor_async",
            "hqr_status", "hqr_get_r", "hqr_get_tiles", "hqr_get_t", "hqr_factors_info", "hqr_kernel_ms", "hqr_kernel_times", "hqr_trace", "hqr_apply_q",
            "hqr_gels", "hqr_gels_qr", "hqr_geqrf_r_noalloc", "hqr_ls_plan_create", "hqr_ls_plan_create_tol",
-           "hqr_ls_plan_refine_info", "hqr_ls_plan_run",
+           "hqr_ls_plan_refine_info", "hqr_critical_path", "hqr_ls_plan_run",
            "hqr_ls_plan_capture", "hqr_ls_plan_status", "hqr_ls_plan_correction", "hqr_ls_plan_info", "hqr_ls_plan_config",
            "hqr_ls_plan_free", "hqr_ls_plan_trace", "hqr_set_tuning", "hqr_autotune", "hqr_server_create", "hqr_server_start",
            "hqr_server_submit", "hqr_server_poll", "hqr_server_stats", "hqr_server_progress", "hqr_server_counters", "hqr_server_stop", "hqr_server_free", "hqr_debug_block_task", "hqr_factors_free", "hqr_set_timeout_ms", "hqr_strerror", "hqr_last_error", "hqr_set_slab_widths",
@@ -92,7 +92,7 @@ def load(build_if_missing=False):
     lib.hqr_ls_plan_create.argtypes = [i32, vp, vp, i32, i32, pf]
     lib.hqr_ls_plan_create_tol.argtypes = [i32, vp, vp, i32, i32, ctypes.c_double, pf]
     lib.hqr_ls_plan_refine_info.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double),
-                                            ctypes.POINTER(i32), ctypes.POINTER(i64), vp]
+                                            ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i64), vp]
     lib.hqr_ls_plan_run.argtypes = [vp, vp]
     lib.hqr_ls_plan_capture.argtypes = [vp, vp]
     lib.hqr_ls_plan_status.argtypes = [vp, vp]
@@ -115,6 +115,8 @@ def load(build_if_missing=False):
     lib.hqr_server_stop.argtypes = [vp]
     lib.hqr_server_free.argtypes = [vp]
     lib.hqr_server_free.restype = None
+    lib.hqr_critical_path.argtypes = [i32, i32, i32, i32, i32, vp, sz, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double)]
     lib.hqr_autotune.argtypes = [i32, vp, vp, i32, i32, i32, vp, vp, i32, ctypes.POINTER(i32), vp]
     lib.hqr_geqrf_r_noalloc.argtypes = [vp, i32, i32, i32, i32, i32, vp, sz, vp, i32, vp]
     lib.hqr_debug_block_task.argtypes = [vp, i64, i32]
@@ -200,6 +202,18 @@ def task_graph(m, n, nb, ib, records, prec=FP64, kind="factor", param=0):
                               ptr.ctypes.data, succ.ctypes.data, len(succ), ctypes.byref(nt), ctypes.byref(ne)),
            "hqr_task_graph")
     return tasks, ptr, succ[:ne.value]
+
+
+def critical_path(m, n, nb, ib, records, prec=FP64):
+    """(critical path, total work) of the factorization graph in units of
+    b^3 / 3 (hqr_critical_path)."""
+    lib = load()
+    arr = records if isinstance(records, np.ndarray) else to_array(records)
+    arr = np.ascontiguousarray(arr, dtype=ELIM_DTYPE)
+    cp, w = ctypes.c_double(0), ctypes.c_double(0)
+    _check(lib.hqr_critical_path(m, n, nb, ib, prec, arr.ctypes.data if len(arr) else None, len(arr),
+                                 ctypes.byref(cp), ctypes.byref(w)), "hqr_critical_path")
+    return cp.value, w.value
 
 
 def set_slab_widths(w=0, wt=0, vc=0):
@@ -540,12 +554,14 @@ class LSPlan:
 
     def refine_info(self, idx=0, stream=None):
         """(rounds applied, last applied correction, tolerance met, first zero
-        diagonal column or -1) of problem idx (hqr_ls_plan_refine_info)."""
-        it, met = ctypes.c_int32(0), ctypes.c_int32(0)
+        diagonal column or -1, compensated rounds) of problem idx
+        (hqr_ls_plan_refine_info)."""
+        it, met, nc = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
         rel, sing = ctypes.c_double(0), ctypes.c_int64(0)
         _check(load().hqr_ls_plan_refine_info(self._h, idx, ctypes.byref(it), ctypes.byref(rel), ctypes.byref(met),
-                                              ctypes.byref(sing), _stream_ptr(stream)), "hqr_ls_plan_refine_info")
-        return it.value, rel.value, bool(met.value), sing.value
+                                              ctypes.byref(nc), ctypes.byref(sing), _stream_ptr(stream)),
+               "hqr_ls_plan_refine_info")
+        return it.value, rel.value, bool(met.value), sing.value, nc.value
 
     def correction(self, idx=0, stream=None):
         """max |d| / max |x| of the last refinement correction of problem idx (-1: no rounds)."""

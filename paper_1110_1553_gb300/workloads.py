@@ -50,3 +50,15 @@ def conditioned(torch, M, N, kappa, seed, device="cuda", dtype=None):
     A = (U * s.unsqueeze(0)) @ V.t()
     torch.backends.cuda.matmul.allow_tf32 = prev
     return A.to(dtype).t().contiguous().t()
+
+
+def square_mixed_problem(torch, n=16384, device="cuda"):
+    """The square mixed-precision least-squares workload: A = U diag(s) V^T
+    (FP32, n x n, s geometric from 1 to 1e-6, seed 30), x_true N(0, 1) and
+    b = A x_true + 1e-8 N(0, 1) in FP64 (seed 31). Returns (A, b)."""
+    A = conditioned(torch, n, n, 1e6, seed=30, device=device)
+    g = torch.Generator(device=device)
+    g.manual_seed(31)
+    xt = torch.randn(n, dtype=torch.float64, device=device, generator=g)
+    b = A.double() @ xt + 1e-8 * torch.randn(n, dtype=torch.float64, device=device, generator=g)
+    return A, b

@@ -73,15 +73,29 @@ def test_gels_mixed_kappa_1e6_n4096_matches_oracle(tensor):
     g.manual_seed(904)
     xt = torch.randn(n, dtype=torch.float64, device="cuda", generator=g)
     b = A.double() @ xt + 1e-8 * torch.randn(n, dtype=torch.float64, device="cuda", generator=g)
-    x, st, info = hqr.gels(A, b, tol=1e-14, max_iter=60, tensor=tensor)
+    x, st, info = hqr.gels(A, b, tol=1e-12, max_iter=60, tensor=tensor)
     assert st == hqr.SUCCESS, (st, info)
-    assert info["converged"] == 1
+    assert info["converged"] == 1 and info["rel_correction"] <= 1e-12
     A64 = A.double().cpu().numpy()
     bh = b.cpu().numpy()
     nb = 256
     xo, _ = lstsq(A64, bh, nb, 32, hqr_elim_list(n // nb, n // nb, 4, 1, GREEDY, GREEDY), refine=3)
     err = rel(x.cpu().numpy(), xo)
     assert err <= X_TOL, (err, info)
+    assert info["backward_error"] <= 1e-14
+
+
+def test_gels_stops_when_the_refinement_stalls():
+    """A tolerance below what the FP32 R allows: the refinement stops once two
+    compensated rounds in a row no longer shrink the correction, well before
+    max_iter, and reports that the tolerance was not met."""
+    n = 1024
+    A = workloads.conditioned(torch, n, n, 1e6, seed=908, device="cuda")
+    b = A.double() @ torch.randn(n, dtype=torch.float64, device="cuda")
+    x, st, info = hqr.gels(A, b, tol=1e-18, max_iter=60, tensor=True)
+    assert st == hqr.ERR_NOCONV
+    assert info["converged"] == 0 and info["iters"] < 60
+    assert info["rel_correction"] <= 1e-12  # it stalls near the attainable accuracy (~1e-13 here)
     assert info["backward_error"] <= 1e-14
 
 
@@ -135,7 +149,7 @@ def test_tolerance_plan_mixed_batch_matches_oracle_and_is_deterministic():
             b = torch.randn(M, dtype=torch.float64, device="cuda", generator=g)
         probs.append((A, b, torch.zeros(N, dtype=torch.float64, device="cuda")))
         host.append((A.double().cpu().numpy(), b.cpu().numpy()))
-    plan = hqr.LSPlan(probs, refine_iters=40, tensor=True, tol=1e-14)
+    plan = hqr.LSPlan(probs, refine_iters=40, tensor=True, tol=1e-12)
     plan.run()
     assert plan.status() == 0
     iters = [plan.refine_info(q)[0] for q in range(len(shapes))]

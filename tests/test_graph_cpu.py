@@ -380,3 +380,31 @@ def test_race_check_catches_a_missing_check_edge():
     # missing path counts
     with pytest.raises(AssertionError):
         check_no_races(tasks, ptr2, succ2, nb, ib, m, n)
+
+
+@pytest.mark.parametrize("low,high", [(FLAT, FLAT), (GREEDY, FIBONACCI), (BINARY, GREEDY), (FIBONACCI, BINARY)])
+def test_critical_path_model(low, high):
+    """hqr_critical_path: with whole panels the work is the Sec. 2 weight sum
+    6 m n^2 - 2 n^3 (units of b^3 / 3) for every list; the critical path lies
+    between the longest single task and the work."""
+    m, n, nb, ib = 12, 5, 64, 16
+    hqr.set_panel_split(0)
+    try:
+        for a, p in ((1, 1), (2, 3), (m, 1)):
+            cp, work = hqr.critical_path(m, n, nb, ib, hqr_elim_list(m, n, a, p, low, high))
+            assert work == pytest.approx(6 * m * n * n - 2 * n ** 3, rel=1e-12)
+            assert 12.0 / 4 <= cp <= work  # a TSMQR slab (16 of 64 columns) is the smallest full task
+    finally:
+        hqr.set_panel_split(64)
+
+
+def test_critical_path_orders_trees_on_a_tall_matrix():
+    """On a tall-skinny tile matrix the flat tree (one TS domain) has the
+    longest critical path and a tree over single tiles a much shorter one
+    (Sec. 3: the flat tree's panel is a chain of m - 1 kills)."""
+    m, n, nb, ib = 64, 4, 64, 16
+    cp_flat, _ = hqr.critical_path(m, n, nb, ib, hqr_elim_list(m, n, m, 1, FLAT, FLAT))
+    cp_greedy, _ = hqr.critical_path(m, n, nb, ib, hqr_elim_list(m, n, 1, 1, GREEDY, GREEDY))
+    cp_hier, _ = hqr.critical_path(m, n, nb, ib, hqr_elim_list(m, n, 4, 4, GREEDY, FIBONACCI))
+    assert cp_greedy < cp_hier < cp_flat
+    assert cp_flat > 4 * cp_greedy
