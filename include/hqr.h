@@ -396,7 +396,9 @@ int hqr_ls_plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_
 
 /*
  * hqr_ls_plan_create_tol -- as hqr_ls_plan_create with refinement rounds
- * that stop at a tolerance (corrected semi-normal equations as above): at
+ * that stop at a tolerance (corrected semi-normal equations as above,
+ * started from the QR solution x0 = R^{-1} (Q^T b)[0:N] computed in the
+ * storage precision instead of x0 = 0): at
  * most max_iter rounds (1 .. 64); each problem stops after the first round
  * whose correction d has ||d||_2 <= tol ||x||_2 and whose residual and A^T r
  * were compensated (tolerance met), or after two compensated rounds in a row

@@ -365,8 +365,9 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
       b.add(vtask(OP_RCHK, 0, 0));
     }
   };
-  if (iters == 0) {
-    // Q^T b on the right-hand-side block, replaying the factorization forward
+  if (iters == 0 || tol_mode) {
+    // Q^T b on the right-hand-side block, replaying the factorization forward (with tol_mode:
+    // the starting point x0 = R^{-1} (Q^T b)[0:N] of the refinement, in place of x0 = 0)
     for (const PanelOp &o : ops) {
       if (o.kind == 0) {
         for (int s = 0; s < S; ++s) tr.read(P.l(o.i, o.k, s), d);

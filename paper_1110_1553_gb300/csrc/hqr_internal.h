@@ -133,8 +133,10 @@ Graph build_apply_graph(const std::vector<PanelOp> &ops, int m, int nslab, int w
 // copies the caller's matrix into the workspace (for runs where no separate
 // preparation kernel can be launched).
 //
-// With tol_mode, `iters` is the largest number of rounds and the rounds stop
-// at a tolerance: every task of round r (residual, A^T r, solve steps, x
+// With tol_mode, the refinement starts from the QR solution x0 = R^{-1}
+// (Q^T b)[0:N] (the iters = 0 tasks, in the storage precision), `iters` is
+// the largest number of rounds and the rounds stop at a tolerance: every
+// task of round r (residual, A^T r, solve steps, x
 // update) carries trans = 2 and k = r; round r ends with an OP_RCHK task after
 // all its x updates, and round r + 1's x updates follow that check, so a round
 // whose check found the tolerance met leaves x as it was (its other tasks may

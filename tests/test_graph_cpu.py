@@ -336,9 +336,10 @@ def test_graph_with_coupling_level_has_no_races(split):
 @pytest.mark.parametrize("low,high,a,p", TREE_CASES[:3])
 @pytest.mark.parametrize("iters,split", [(1, 64), (4, 64), (5, 0)])
 def test_tolerance_graph_has_no_races(low, high, a, p, iters, split):
-    """A plan from hqr_ls_plan_create_tol: rounds whose tasks carry trans = 2
-    and k = the round, one convergence check per round after all its x
-    updates, and the next round's x updates after that check."""
+    """A plan from hqr_ls_plan_create_tol: the QR solution as starting point,
+    then rounds whose tasks carry trans = 2 and k = the round, one
+    convergence check per round after all its x updates, and the next round's
+    x updates after that check."""
     m, n, nb, ib = 9, 9, 64, 16
     hqr.set_panel_split(split)
     try:
@@ -351,13 +352,17 @@ def test_tolerance_graph_has_no_races(low, high, a, p, iters, split):
     assert (ops == RCHK).sum() == iters
     assert sorted(ks[ops == RCHK]) == list(range(iters))
     rnd = np.isin(ops, [RESID, RESR, ATR, ATRR, TRSV_TD, TRSV_TU, TRSV_D, TRSV_U, XUPD, RCHK])
-    assert (trans[rnd] == 2).all() and (trans[~rnd] != 2).all()
+    assert rnd[trans == 2].all()  # only round tasks are marked
+    assert (trans[np.isin(ops, [RESID, RESR, ATR, ATRR, RCHK])] == 2).all()
+    # the starting point x0 = R^{-1} (Q^T b)[0:N]: Q^T b, its first N entries, one backward solve
+    assert (ops == BTOG).sum() == n
+    assert ((ops == XUPD) & (trans != 2)).sum() == n and ((ops == XUPD) & (trans == 2)).sum() == iters * n
     # every check follows all x updates of its round; every x update of round k + 1 follows check k
     for q in np.nonzero(ops == RCHK)[0]:
         k = ks[q]
-        for u in np.nonzero((ops == XUPD) & (ks == k))[0]:
+        for u in np.nonzero((ops == XUPD) & (ks == k) & (trans == 2))[0]:
             assert q in succ[ptr[u]:ptr[u + 1]]
-        for u in np.nonzero((ops == XUPD) & (ks == k + 1))[0]:
+        for u in np.nonzero((ops == XUPD) & (ks == k + 1) & (trans == 2))[0]:
             assert u in succ[ptr[q]:ptr[q + 1]]
 
 
@@ -368,9 +373,9 @@ def test_race_check_catches_a_missing_check_edge():
     m, n, nb, ib = 5, 5, 64, 16
     tasks, ptr, succ = hqr.task_graph(m, n, nb, ib, hqr_elim_list(m, n, 2, 2, GREEDY, FIBONACCI), kind="ls_tol",
                                       param=3)
-    ops, ks = tasks[:, 0], tasks[:, 4]
+    ops, ks, trans = tasks[:, 0], tasks[:, 4], tasks[:, 8]
     q = int(np.nonzero((ops == RCHK) & (ks == 0))[0][0])
-    u = int(np.nonzero((ops == XUPD) & (ks == 1))[0][0])
+    u = int(np.nonzero((ops == XUPD) & (ks == 1) & (trans == 2))[0][0])
     s2 = list(succ[ptr[q]:ptr[q + 1]])
     s2.remove(u)
     succ2 = np.concatenate([succ[:ptr[q]], np.array(s2, dtype=succ.dtype), succ[ptr[q + 1]:]])
