@@ -575,7 +575,8 @@ void hqr_server_free(hqr_server *server);
 void hqr_factors_free(hqr_factors *F);
 
 /* Process-wide settings (hqr_set_slab_widths, hqr_set_panel_split,
- * hqr_set_priority_policy, hqr_set_timeout_ms, hqr_set_tuning): read when a
+ * hqr_set_split_launch, hqr_set_priority_policy, hqr_set_timeout_ms,
+ * hqr_set_tuning): read when a
  * factorization, plan or server request is created (the time limit: when a
  * kernel is launched). They are plain globals: set them before, not while,
  * other threads create work. */
@@ -594,6 +595,16 @@ int hqr_set_slab_widths(int w, int wt, int vc);
  * panel's trailing work spreads over several CTAs. 0 keeps whole panel tasks
  * everywhere; default 64. Returns -1 for min_nb < 0. */
 int hqr_set_panel_split(int min_nb);
+
+/* hqr_set_split_launch -- least-squares plans created afterwards that hold
+ * both tensor-core problems (HQR_FP32_BF16X3 tiles of 128) and CUDA-core
+ * ones run them as two persistent launches side by side: the tensor-core
+ * kernel (one CTA per SM) on a share of the SMs and the CUDA-core kernel
+ * (two CTAs per SM) on the rest, the share set from the parts' QR flops and
+ * rebalanced from the two kernels' times after every timed run (not inside a
+ * captured graph, which keeps the share it was captured with). 1 (default):
+ * on; 0: one launch of the tensor-core kernel for every problem. */
+int hqr_set_split_launch(int on);
 
 /* hqr_set_priority_policy -- ready-queue priorities of task graphs created
  * afterwards (factorizations, plans, server requests): 1 (default) by the

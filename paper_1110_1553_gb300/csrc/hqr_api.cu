@@ -232,10 +232,11 @@ int ctas_for(int prec, bool tc, size_t smem, int ntasks, int *grid) {
   return HQR_SUCCESS;
 }
 
-int launch_sched(int prec, const EngineParams &p, size_t smem, cudaStream_t s) {
+int launch_sched(int prec, const EngineParams &p, size_t smem, cudaStream_t s, int max_ctas = 0) {
   int grid = 0;
   int st = ctas_for(prec, p.tc != 0, smem, p.ntasks, &grid);
   if (st) return st;
+  if (max_ctas > 0) grid = std::min(grid, max_ctas);
   if (prec == HQR_FP64)
     hqr_sched<double, false><<<grid, NT, smem, s>>>(p);
   else if (p.tc)
@@ -253,6 +254,8 @@ int g_w_override = 0, g_wt_override = 0, g_vc_override = 0;
 int g_priority_policy = 1;
 // CUDA-core panels of tiles with nb >= this are split into block tasks (hqr_set_panel_split; 0: never).
 int g_split_min_nb = 64;
+// Plans with tensor-core and CUDA-core problems launch them side by side (hqr_set_split_launch).
+int g_split_launch = 1;
 
 // Block size of a split panel for a problem, or 0 to keep whole panel tasks. The tensor-core
 // kernels keep whole panels (one block per tile). FP32 panels on CUDA cores are cheap next to
@@ -430,6 +433,12 @@ void hqr_set_timeout_ms(int64_t ms) { g_timeout_ns = (ms > 0 ? ms : 1) * 1000000
 int hqr_set_priority_policy(int policy) {
   if (policy != 0 && policy != 1) return -1;
   g_priority_policy = policy;
+  return HQR_SUCCESS;
+}
+
+int hqr_set_split_launch(int on) {
+  if (on < 0 || on > 1) return -1;
+  g_split_launch = on;
   return HQR_SUCCESS;
 }
 
@@ -984,6 +993,19 @@ struct hqr_ls_plan {
   double tol = 0.0;
   RefineState *drs = nullptr;       // per-problem refinement state (tol_mode)
   int any_tc = 0;          // some problem runs on the tensor-core kernels
+  // Plans with tensor-core and CUDA-core problems run them as two persistent
+  // launches side by side: the tensor-core kernel (one CTA per SM) on tc_sms
+  // SMs and the CUDA-core kernel (two CTAs per SM) on the others, so that the
+  // small problems keep two CTAs per SM. graph holds the tensor-core
+  // problems' tasks, graph2 the others'.
+  int split = 0;
+  DevGraph graph2;
+  size_t smem2 = 0;
+  int tc_sms = 0;
+  double work_tc = 0.0, work_cc = 0.0;  // relative work of the parts (SM share of the next run)
+  bool timed_split = false;             // the last run recorded the two kernels' events
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr, k0[2] = {nullptr, nullptr}, k1[2] = {nullptr, nullptr};
   std::vector<hqr_tile_config_t> cfg;
   std::vector<Problem> probs;
   std::vector<PrepDesc> prep;
@@ -1038,24 +1060,56 @@ int plan_enqueue(hqr_ls_plan *P, cudaStream_t s, bool timed) {
   CK(cudaGetLastError());
   CK(cudaMemsetAsync(P->dstatus, 0, sizeof(int) * P->count, s));
   if (P->drs) CK(cudaMemsetAsync(P->drs, 0, sizeof(RefineState) * P->count, s));
-  DevGraph &g = P->graph;
-  CK(cudaMemcpyAsync(g.indeg, g.indeg0, sizeof(int) * g.ntasks, cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpyAsync(g.slots, g.slots0, sizeof(int) * slot_count(g.ntasks), cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpyAsync(g.ctl, g.ctl0, sizeof(Ctl), cudaMemcpyDeviceToDevice, s));
-  EngineParams p{};
-  p.tc = P->any_tc;
-  p.probs = P->dprobs;
-  p.tasks = g.tasks;
-  p.ntasks = g.ntasks;
-  p.succ = g.succ;
-  p.indeg = g.indeg;
-  p.slots = g.slots;
-  p.ctl = g.ctl;
-  p.timeout_ns = g_timeout_ns;
-  p.trace = P->dtrace;
+  for (DevGraph *g : {&P->graph, &P->graph2}) {
+    if (!g->ntasks) continue;
+    CK(cudaMemcpyAsync(g->indeg, g->indeg0, sizeof(int) * g->ntasks, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(g->slots, g->slots0, sizeof(int) * slot_count(g->ntasks), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(g->ctl, g->ctl0, sizeof(Ctl), cudaMemcpyDeviceToDevice, s));
+  }
+  auto params = [&](const DevGraph &g, int tc, unsigned long long *trace) {
+    EngineParams p{};
+    p.tc = tc;
+    p.probs = P->dprobs;
+    p.tasks = g.tasks;
+    p.ntasks = g.ntasks;
+    p.succ = g.succ;
+    p.indeg = g.indeg;
+    p.slots = g.slots;
+    p.ctl = g.ctl;
+    p.timeout_ns = g_timeout_ns;
+    p.trace = trace;
+    return p;
+  };
   if (timed) CK(cudaEventRecord(P->ev0, s));
-  int st = launch_sched(P->prec, p, P->smem, s);
-  if (st) return st;
+  if (!P->split) {
+    int st = launch_sched(P->prec, params(P->graph, P->any_tc, P->dtrace), P->smem, s);
+    if (st) return st;
+  } else {
+    // the two parts side by side: tensor-core kernel on s (tc_sms CTAs), CUDA-core kernel on
+    // the side stream (two CTAs on each other SM)
+    int sms = 0, dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (P->tc_sms <= 0) {
+      const double w = P->work_tc + P->work_cc;
+      P->tc_sms = (int)std::lround(sms * (w > 0 ? P->work_tc / w : 0.5));
+    }
+    P->tc_sms = std::max(1, std::min(sms - 1, P->tc_sms));
+    CK(cudaEventRecord(P->fork, s));
+    CK(cudaStreamWaitEvent(P->side, P->fork, 0));
+    if (timed) CK(cudaEventRecord(P->k0[0], s));
+    int st = launch_sched(P->prec, params(P->graph, 1, P->dtrace), P->smem, s, P->tc_sms);
+    if (st) return st;
+    if (timed) CK(cudaEventRecord(P->k1[0], s));
+    if (timed) CK(cudaEventRecord(P->k0[1], P->side));
+    st = launch_sched(P->prec, params(P->graph2, 0, P->dtrace ? P->dtrace + 3 * (size_t)P->graph.ntasks : nullptr),
+                      P->smem2, P->side, 2 * (sms - P->tc_sms));
+    if (st) return st;
+    if (timed) CK(cudaEventRecord(P->k1[1], P->side));
+    CK(cudaEventRecord(P->join, P->side));
+    CK(cudaStreamWaitEvent(s, P->join, 0));
+    P->timed_split = timed;
+  }
   if (timed) CK(cudaEventRecord(P->ev1, s));
   ls_finish<<<std::min(P->count, 4096), 256, 0, s>>>(P->dprep, P->count);
   CK(cudaGetLastError());
@@ -1092,7 +1146,7 @@ int plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_config_
   // tile configurations, lists, sizes
   std::vector<size_t> off_tiles(count), off_t(count), off_b(count), off_vec(count);
   size_t arena_elems = 0, vec_elems = 0;
-  Graph merged;
+  Graph merged, merged2;  // with split launches: tensor-core problems, the others
   size_t smem = 0;
   for (int q = 0; q < count; ++q) {
     const hqr_ls_problem_t &pr = probs[q];
@@ -1138,18 +1192,22 @@ int plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_config_
       return HQR_ERR_INTERNAL;
     }
     std::vector<PanelOp> ops = expand_ops(lst.data(), lst.size(), pb.m, pb.n);
-    append_graph(merged, build_ls_graph(ops, pb.m, pb.n, c.nb, pb.w, refine_iters, q, false, split_ib_for(prec, pb),
-                                        P->tol_mode != 0));
+    const bool tcp = use_tc(prec, c.nb);
+    append_graph(tcp || !g_split_launch ? merged : merged2,
+                 build_ls_graph(ops, pb.m, pb.n, c.nb, pb.w, refine_iters, q, false, split_ib_for(prec, pb),
+                                P->tol_mode != 0));
     if (P->tol_mode) {
       pb.maxit = refine_iters;
       pb.tol = tol;
     }
-    smem = std::max(smem, smem_for(prec, pb));
+    if (tcp || !g_split_launch)
+      smem = std::max(smem, smem_for(prec, pb));
+    else
+      P->smem2 = std::max(P->smem2, smem_for(prec, pb));
     if (pb.tc) P->any_tc = 1;
     P->probs.push_back(pb);
     P->flops += 2.0 * pr.M * (double)pr.N * pr.N - 2.0 / 3.0 * (double)pr.N * pr.N * pr.N;
   }
-  P->smem = smem;
   int st = HQR_SUCCESS;
   if (!cuda_ok(cudaMalloc(&P->arena, es * std::max<size_t>(arena_elems, 1)), "cudaMalloc(arena)") ||
       !cuda_ok(cudaMalloc(&P->vec, sizeof(double) * std::max<size_t>(vec_elems, 1)), "cudaMalloc(vec)") ||
@@ -1202,17 +1260,46 @@ int plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_config_
                        "copy prep") ||
               !cuda_ok(cudaEventCreate(&P->ev0), "event") || !cuda_ok(cudaEventCreate(&P->ev1), "event")))
     st = HQR_ERR_CUDA;
+  if (!st && !merged2.tasks.empty() && merged.tasks.empty()) {  // no tensor-core problem after all
+    merged = std::move(merged2);
+    merged2 = Graph();
+    smem = P->smem2;
+  }
+  P->split = !merged2.tasks.empty();
   if (!st) {
     if (g_priority_policy == 1) critical_path_priorities(merged, 128);
     st = upload_graph(merged, P->graph);
   }
+  if (!st && P->split) {
+    if (g_priority_policy == 1) critical_path_priorities(merged2, 128);
+    st = upload_graph(merged2, P->graph2);
+    // first SM share: by the QR flops of each part, the tensor-core part's counted at a third
+    // (its tiles run about three times faster); rebalanced after every timed run
+    double ftc = 0.0, fcc = 0.0;
+    for (int q = 0; q < count; ++q) {
+      const double f = 2.0 * probs[q].M * (double)probs[q].N * probs[q].N;
+      if (P->probs[q].tc) ftc += f; else fcc += f;
+    }
+    P->work_tc = ftc / 3.0;
+    P->work_cc = fcc;
+    if (!st && (!cuda_ok(cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking), "side stream") ||
+                !cuda_ok(cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming), "event") ||
+                !cuda_ok(cudaEventCreateWithFlags(&P->join, cudaEventDisableTiming), "event")))
+      st = HQR_ERR_CUDA;
+    for (int q = 0; q < 2 && !st; ++q)
+      if (!cuda_ok(cudaEventCreate(&P->k0[q]), "event") || !cuda_ok(cudaEventCreate(&P->k1[q]), "event"))
+        st = HQR_ERR_CUDA;
+  }
+  P->smem = smem;
   if (st) {
     hqr_ls_plan_free(P);
     return st;
   }
-  P->task_kind.resize(merged.tasks.size());
+  P->task_kind.resize(merged.tasks.size() + merged2.tasks.size());
   for (size_t t = 0; t < merged.tasks.size(); ++t)
     P->task_kind[t] = ((int32_t)merged.tasks[t].op << 24) | merged.tasks[t].pid;
+  for (size_t t = 0; t < merged2.tasks.size(); ++t)
+    P->task_kind[merged.tasks.size() + t] = ((int32_t)merged2.tasks[t].op << 24) | merged2.tasks[t].pid;
   *plan = P;
   return HQR_SUCCESS;
 }
@@ -1288,7 +1375,7 @@ int hqr_ls_plan_refine_info(hqr_ls_plan *P, int idx, int *iters, double *rel_cor
 
 int hqr_ls_plan_trace(hqr_ls_plan *P, int enable, uint64_t *host, size_t cap, size_t *count) {
   if (!P) return -1;
-  const size_t nt = (size_t)P->graph.ntasks;
+  const size_t nt = (size_t)P->graph.ntasks + (size_t)P->graph2.ntasks;
   if (enable == 1) {
     if (!P->dtrace && !cuda_ok(cudaMalloc(&P->dtrace, 3 * sizeof(unsigned long long) * nt), "cudaMalloc(trace)"))
       return HQR_ERR_NOMEM;
@@ -1326,8 +1413,21 @@ int hqr_ls_plan_run(hqr_ls_plan *P, void *stream) {
     g_launches = 3;
     return HQR_SUCCESS;
   }
+  if (P->split && P->timed_split && cudaEventQuery(P->k1[1]) == cudaSuccess && cudaEventQuery(P->k1[0]) == cudaSuccess) {
+    // SM share from the last timed run: each part's work = its time x its SMs
+    float a = 0.f, b = 0.f;
+    if (cudaEventElapsedTime(&a, P->k0[0], P->k1[0]) == cudaSuccess &&
+        cudaEventElapsedTime(&b, P->k0[1], P->k1[1]) == cudaSuccess && a > 0.f && b > 0.f) {
+      int sms = 0, dev = 0;
+      CK(cudaGetDevice(&dev));
+      CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      P->work_tc = (double)a * P->tc_sms;
+      P->work_cc = (double)b * (sms - P->tc_sms);
+      P->tc_sms = (int)std::lround(sms * P->work_tc / (P->work_tc + P->work_cc));
+    }
+  }
   int st = plan_enqueue(P, s, true);
-  g_launches += 2;  // preparation and finishing kernels (the task kernel counted at launch)
+  g_launches += 2;  // preparation and finishing kernels (the task kernels counted at launch)
   return st;
 }
 
@@ -1343,9 +1443,10 @@ int hqr_ls_plan_capture(hqr_ls_plan *P, void *stream) {
     cudaGraphDestroy(P->cg);
     P->cg = nullptr;
   }
-  int grid = 0;  // sets the kernel's shared-memory attribute outside the capture
+  int grid = 0;  // sets the kernels' shared-memory attributes outside the capture
   int st = ctas_for(P->prec, P->any_tc != 0, P->smem, P->graph.ntasks, &grid);
   if (st) return st;
+  if (P->split && (st = ctas_for(P->prec, false, P->smem2, P->graph2.ntasks, &grid))) return st;
   CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   st = plan_enqueue(P, s, false);
   cudaGraph_t g = nullptr;
@@ -1366,6 +1467,10 @@ int hqr_ls_plan_status(hqr_ls_plan *P, void *stream) {
   CtlLine c;
   CK(cudaMemcpy(&c, &P->graph.ctl->status, sizeof(CtlLine), cudaMemcpyDeviceToHost));
   if (c.v) return (int)c.v;
+  if (P->split) {
+    CK(cudaMemcpy(&c, &P->graph2.ctl->status, sizeof(CtlLine), cudaMemcpyDeviceToHost));
+    if (c.v) return (int)c.v;
+  }
   std::vector<int> stv(P->count);
   CK(cudaMemcpy(stv.data(), P->dstatus, sizeof(int) * P->count, cudaMemcpyDeviceToHost));
   for (int v : stv)
@@ -1401,7 +1506,7 @@ int hqr_ls_plan_correction(hqr_ls_plan *P, int idx, double *rel, void *stream) {
 
 int hqr_ls_plan_info(hqr_ls_plan *P, int64_t *ntasks, double *qr_flops, float *kernel_ms) {
   if (!P) return -1;
-  if (ntasks) *ntasks = P->graph.ntasks;
+  if (ntasks) *ntasks = P->graph.ntasks + P->graph2.ntasks;
   if (qr_flops) *qr_flops = P->flops;
   if (kernel_ms) {
     *kernel_ms = 0.f;
@@ -1424,6 +1529,10 @@ int hqr_ls_plan_config(const hqr_ls_plan *P, int idx, hqr_tile_config_t *cfg) {
 void hqr_ls_plan_free(hqr_ls_plan *P) {
   if (!P) return;
   P->graph.release();
+  P->graph2.release();
+  if (P->side) cudaStreamDestroy(P->side);
+  for (cudaEvent_t e : {P->fork, P->join, P->k0[0], P->k0[1], P->k1[0], P->k1[1]})
+    if (e) cudaEventDestroy(e);
   if (P->cge) cudaGraphExecDestroy(P->cge);
   if (P->cg) cudaGraphDestroy(P->cg);
   cudaFree(P->arena);

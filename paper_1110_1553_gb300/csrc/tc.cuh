@@ -50,7 +50,7 @@ constexpr int DT = 2;            // chunks loaded ahead in registers
 constexpr int NP = 3;            // BF16 pieces of an FP32 value
 constexpr int KS_ACC = 2;                  // MMA K steps (of 16) chained in one accumulator
 constexpr int NACC = NCH * (KC / 16) / KS_ACC;  // accumulators: one per K chunk of 32
-constexpr int TMEM_COLS = NACC * WMAX;   // 256 columns: half the tensor memory of the SM
+constexpr int TMEM_COLS = 2 * NACC * WMAX;  // 512 columns: two products' accumulators (all of the SM's)
 constexpr int NTHR = 256;
 
 constexpr uint32_t LBO_C = 128, SBO_C = (KC / 8) * 128;      // chunk buffers: 8-row groups of 512 B
@@ -71,28 +71,30 @@ constexpr uint32_t OFF_BOT = OFF_TOP + SLAB_BYTES;                 // C_b slab
 constexpr uint32_t SMEM_BYTES = OFF_BOT + SLAB_BYTES;              // 219136
 
 // Per panel tile (i, k, GEQRT or kill) the panel task stores a "T record":
-// the three update operands already split into BF16 pieces in the chunk
-// layout of the shared-memory stages (chunk c: pieces 0, 1, 2 of 128 x 32
-// elements), so that an update stages each chunk with one bulk copy: T^T
-// (reflector, reflector'), V^T (reflector, row), V (row, reflector), with V
+// the update operands already split into BF16 pieces in the chunk layout of
+// the shared-memory stages (chunk c: pieces 0, 1, 2 of 128 x 32 elements),
+// so that an update stages each chunk with one bulk copy: T^T (reflector,
+// reflector'), V^T (reflector, row) and Y = V T^T (row, reflector), with V
 // masked to its structure (unit lower, upper, full); then, for
-// factorizations that keep it (apply Q, read T), the FP32 factor T (128 x
-// 128, column-major, zeros below the diagonal). Least-squares problems only
-// apply Q^T and leave it out.
+// factorizations that keep them (apply Q, read T), V (row, reflector) and the
+// FP32 factor T (128 x 128, column-major, zeros below the diagonal).
+// Least-squares problems only apply Q^T and leave those two out.
 constexpr uint32_t IMG_BYTES = NCH * NP * A_PC;                  // 98304
 constexpr uint32_t REC_TB = 0;                                   // byte offsets in a record
 constexpr uint32_t REC_VA = REC_TB + IMG_BYTES;
-constexpr uint32_t REC_VC = REC_VA + IMG_BYTES;
+constexpr uint32_t REC_Y = REC_VA + IMG_BYTES;
+constexpr uint32_t REC_VC = REC_Y + IMG_BYTES;
 constexpr uint32_t REC_T32 = REC_VC + IMG_BYTES;
-constexpr uint32_t T_RECORD_IMG = REC_T32 / 4;                   // floats per record without T: 73728
-constexpr uint32_t T_RECORD = (REC_T32 + NB * NB * 4) / 4;       // with T: 90112
+constexpr uint32_t T_RECORD_IMG = REC_VC / 4;                    // floats per record without V and T: 73728
+constexpr uint32_t T_RECORD = (REC_T32 + NB * NB * 4) / 4;       // with them: 114688
 
 // Per-CTA state of the tensor path (in the kernel's static shared memory).
 struct State {
-  uint64_t full[NCH];  // chunk c staged by every thread
-  uint64_t img[NCH];   // chunk c of an operand image arrived (bulk copy)
-  uint64_t done;       // every MMA of a product completed
-  uint64_t slab;       // the C slabs of an update arrived (bulk copies)
+  uint64_t full[NCH];   // chunk c staged by every thread
+  uint64_t img[NCH];    // chunk c of an operand image arrived (bulk copy)
+  uint64_t sfree[NCH];  // the MMAs that read stage c of the second ring completed
+  uint64_t done;        // every MMA of a product completed
+  uint64_t slab;        // the C slabs of an update arrived (bulk copies)
   uint32_t tmem;
   int pad;
 };
@@ -202,7 +204,7 @@ __device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity, volatil
 // Parity of the chunk barriers (all flip once per product) and of the done
 // barrier, tracked identically by every thread.
 struct Phases {
-  uint32_t full = 0, img = 0, done = 0, slab = 0;
+  uint32_t full = 0, img = 0, done = 0, slab = 0, sfree = 0;
 };
 
 // Element masks of the reflector block V at (row, reflector):
@@ -447,11 +449,10 @@ __device__ __forceinline__ void tmem_sum16(uint32_t taddr, float (&v)[16]) {
 // 2) + 2 e, e = 0, 1 (n <= 64). The C slabs sit in shared memory (column
 // col of a slab at col * 128 floats), fetched at the start of the task.
 
-// Request the slab's cw columns (512 bytes each) with bulk copies on `bar`
-// (warp 0; the first lane posts the byte count).
+// Request the slab's cw columns with one bulk copy on `bar`: in a tile (and a
+// right-hand-side block) the columns of a slab are contiguous (ld 128).
 __device__ __forceinline__ void fetch_slab(const float *c, int cw, float *dst, uint64_t *bar) {
-  for (int col = threadIdx.x; col < cw; col += 32)
-    ptx::bulk_g2s(dst + (size_t)col * NB, c + (size_t)col * NB, NB * 4, bar);
+  ptx::bulk_g2s(dst, c, (uint32_t)cw * NB * 4, bar);
 }
 
 // Coalesced write-back of a slab from shared memory.
@@ -516,6 +517,73 @@ __device__ void epilogue_c(uint32_t tmem, int n, int cw, float *cb) {
   }
 }
 
+// Second phase of a Q^T update from the resident W^T: D_top = T^T W (TS /
+// TT: `top`) into the accumulators at tmem, and D_bot = Y W (Y = V T^T) into
+// those at tmem + NACC * WMAX. The images stream through the four stages of
+// the second ring: the caller has issued the first image (T^T with `top`, else
+// Y); with `top`, stage c is refilled with Y's chunk c as soon as the MMAs
+// that read T^T's chunk c completed (one commit per stage). One thread issues
+// every MMA; all threads wait for the last. Returns false on a timeout.
+__device__ bool product_pair(const unsigned char *rec, bool top, unsigned char *smem, State &st, Phases &ph,
+                             uint32_t tmem, int n, volatile int *abort, long long limit_ns) {
+  const uint32_t idesc = idesc_bf16(n);
+  const uint32_t sbase = ptx::smem_addr(smem);
+  bool ok = true;
+  if (threadIdx.x == 0) {
+    const uint32_t pi = ph.img & 1u, pf = ph.sfree & 1u;
+    auto issue = [&](int c, uint32_t dbase) {
+      const uint32_t a = sbase + OFF_RING_BC + (uint32_t)c * STAGE_BC;
+#pragma unroll
+      for (int ks = 0; ks < KC / 16; ++ks) {
+        const int acc = (c * (KC / 16) + ks) / KS_ACC;
+        const bool first = (c * (KC / 16) + ks) % KS_ACC == 0;
+        issue_kstep(dbase + (uint32_t)acc * WMAX, idesc, a + (uint32_t)ks * 2 * LBO_C, A_PC,
+                    sbase + OFF_W + (uint32_t)(c * KC / 8 + ks * 2) * LBO_W, W_PC, LBO_W, SBO_W, first);
+      }
+    };
+    const uint32_t dbot = tmem + (uint32_t)(NACC * WMAX);
+    if (top) {
+      for (int c = 0; c < NCH && ok; ++c) {
+        if (!wait_bar(&st.img[c], pi, abort, limit_ns)) ok = false;
+        tc_fence_after();
+        if (ok) {
+          issue(c, tmem);
+          mma_commit(&st.sfree[c]);
+        }
+      }
+      for (int c = 0; c < NCH && ok; ++c) {  // refill each stage once its T^T chunk is consumed
+        if (!wait_bar(&st.sfree[c], pf, abort, limit_ns)) ok = false;
+        if (ok) {
+          ptx::mbar_arrive_expect_tx(&st.img[c], NP * A_PC);
+          ptx::bulk_g2s(smem + OFF_RING_BC + (uint32_t)c * STAGE_BC, rec + REC_Y + (size_t)c * NP * A_PC, NP * A_PC,
+                        &st.img[c]);
+        }
+      }
+      for (int c = 0; c < NCH && ok; ++c) {
+        if (!wait_bar(&st.img[c], pi ^ 1u, abort, limit_ns)) ok = false;
+        tc_fence_after();
+        if (ok) issue(c, dbot);
+      }
+    } else {
+      for (int c = 0; c < NCH && ok; ++c) {
+        if (!wait_bar(&st.img[c], pi, abort, limit_ns)) ok = false;
+        tc_fence_after();
+        if (ok) issue(c, dbot);
+      }
+    }
+    if (ok) mma_commit(&st.done);
+  }
+  if (top) {
+    ph.sfree ^= 1u;  // T^T then Y: every image barrier completed twice
+  } else {
+    ph.img ^= 1u;
+  }
+  if (!wait_bar(&st.done, ph.done & 1u, abort, limit_ns)) ok = false;
+  ph.done ^= 1u;
+  tc_fence_after();
+  return ok && !*abort;
+}
+
 // One update task on a column slab of cw <= 64 columns.
 //  mode: 1 UNMQR (V unit lower in tile V), 0 TSMQR (V = [I; V2], V2 the full
 //        tile), 2 TTMQR (V2 the upper triangle of the tile)
@@ -539,13 +607,11 @@ __device__ bool update(int mode, int trans, const float *V, const float *Trec, f
   fence_async_smem();  // earlier generic accesses of the stages and slabs before the bulk copies
   __syncthreads();
   if (threadIdx.x < 32) {  // the slabs and product A's V^T image, all in flight at once
-    if (threadIdx.x == 0) {
-      ptx::mbar_arrive_expect_tx(&st.slab, (uint32_t)((ct ? 2 : 1) * cw * NB * 4));
-      issue_image(rec + REC_VA, smem, OFF_RING_A, STAGE_A, st);
-    }
+    if (threadIdx.x == 0) ptx::mbar_arrive_expect_tx(&st.slab, (uint32_t)((ct ? 2 : 1) * cw * NB * 4));
     __syncwarp();
-    if (ct) fetch_slab(ct, cw, top, &st.slab);
-    fetch_slab(cb, cw, bot, &st.slab);
+    if (ct && threadIdx.x == 1) fetch_slab(ct, cw, top, &st.slab);
+    if (threadIdx.x == 2) fetch_slab(cb, cw, bot, &st.slab);
+    if (threadIdx.x == 0) issue_image(rec + REC_VA, smem, OFF_RING_A, STAGE_A, st);
   }
   if (!wait_bar(&st.slab, ph.slab & 1u, abort, limit_ns)) return false;
   ph.slab ^= 1u;
@@ -554,6 +620,28 @@ __device__ bool update(int mode, int trans, const float *V, const float *Trec, f
   for (int c = 0; c < DT; ++c) fetch_b(scb, c, f.b[c]);
   if (!product(sva, rec + REC_VA, &scb, trans ? nullptr : &stt, f, smem, st, ph, tmem, n, abort, limit_ns, true))
     return false;
+  if (trans) {
+    // Q^T: C_t -= T^T W and C_b -= Y W with W = V^T C_b (+ C_t), the two products from the
+    // same W^T; the first image (T^T, or Y for UNMQR) is requested while W^T is written
+    fence_async_smem();
+    __syncthreads();  // product A's stages are free (its MMAs completed) before the copies
+    if (threadIdx.x == 0) issue_image(rec + (ct ? REC_TB : REC_Y), smem, OFF_RING_BC, STAGE_BC, st);
+    epilogue_w(tmem, n, cw, ct ? top : nullptr, nullptr, smem);
+    tc_fence_before();
+    fence_async_smem();
+    __syncthreads();
+    tc_fence_after();
+    if (!product_pair(rec, ct != nullptr, smem, st, ph, tmem, n, abort, limit_ns)) return false;
+    if (ct) epilogue_c(tmem, n, cw, top);
+    epilogue_c(tmem + (uint32_t)(NACC * WMAX), n, cw, bot);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (ct) store_slab(ct, cw, top);
+    store_slab(cb, cw, bot);
+    __syncthreads();
+    return true;
+  }
   epilogue_w(tmem, n, cw, ct ? top : nullptr, nullptr, smem);
   tc_fence_before();
   fence_async_smem();
@@ -606,7 +694,8 @@ namespace tc {
 constexpr int LDT = NB + 1;  // shared T / G array: T upper + diagonal, G(l, j) at (j, l)
 
 struct PanelSmem {
-  float tg[NB * LDT];        // also staging of the tile for loads and stores
+  float tg[NB * LDT];        // also staging of the tile for loads
+  float sv[NB * LDT];        // the factored tile (V and R), element (r, c) at c * LDT + r
   float rs[NB * (NB + 1) / 2];  // TS / TT: packed upper triangle of R, column c at c (c + 1) / 2
   float part[2][8][NB];      // per-warp partial products of column j with every column
   float pss[2][8];           // per-warp partial squared norms
@@ -650,6 +739,59 @@ __device__ void write_image(unsigned char *dst, F value) {
 #pragma unroll
     for (int q = 0; q < NP; ++q)
       __stcg(reinterpret_cast<uint4 *>(dst + off + (uint32_t)q * A_PC), make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]));
+  }
+}
+
+// Split image of Y = V T^T (element (m, k): row m of the tile, reflector k):
+// Y(m, k) = sum over l >= k of V(m, l) T(k, l), V the masked reflectors of
+// the factored tile `sv` (column l at l * LDT), T the upper triangle of `tg`
+// (T(k, l) at k + l * LDT). Thread block: rows lane + 32 a (a < 4: the lanes
+// of a warp read consecutive words) x 8 reflectors (four pieces of the
+// image), in FP32 with the terms in ascending l.
+__device__ void write_y_image(int mode, const float *sv, const float *tg, unsigned char *dst) {
+  constexpr int RB = 4;
+#pragma unroll 1
+  for (int u = 0; u < (NB / RB) * (NB / 8) / NTHR; ++u) {
+    const int p = threadIdx.x + NTHR * u;
+    const int m0 = p & 31, kg = p >> 5;  // rows m0 + 32 a; warps: k groups
+    const int k0 = 8 * kg;
+    float acc[RB][8];
+#pragma unroll
+    for (int a = 0; a < RB; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+#pragma unroll 2
+    for (int l = k0; l < NB; ++l) {
+      float v[RB], t[8];
+#pragma unroll
+      for (int a = 0; a < RB; ++a) v[a] = vmask(mode, m0 + 32 * a, l, sv[l * LDT + m0 + 32 * a]);
+#pragma unroll
+      for (int b = 0; b < 8; ++b) t[b] = k0 + b <= l ? tg[k0 + b + l * LDT] : 0.f;
+#pragma unroll
+      for (int a = 0; a < RB; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(v[a], t[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < RB; ++a) {
+      const int m = m0 + 32 * a;
+      uint32_t w[NP][4];
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        uint32_t a0, a1, a2, b0, b1, b2;
+        split3(acc[a][e], a0, a1, a2);
+        split3(acc[a][e + 1], b0, b1, b2);
+        w[0][e / 2] = a0 | (b0 << 16);
+        w[1][e / 2] = a1 | (b1 << 16);
+        w[2][e / 2] = a2 | (b2 << 16);
+      }
+      const uint32_t off = (uint32_t)(kg >> 2) * NP * A_PC + (uint32_t)(m & 7) * 16 + (uint32_t)(m >> 3) * SBO_C +
+                           (uint32_t)(kg & 3) * LBO_C;
+#pragma unroll
+      for (int q = 0; q < NP; ++q)
+        __stcg(reinterpret_cast<uint4 *>(dst + off + (uint32_t)q * A_PC),
+               make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]));
+    }
   }
 }
 
@@ -963,7 +1105,13 @@ __device__ void panel(int mode, float *X, float *Rg, float *Tg, bool with_t32, u
     }
     __syncthreads();
   }
-  // ---- write T (zeros below the diagonal, if kept) and its split image T^T
+  // ---- the factored tile (V / R) to shared memory
+#pragma unroll
+  for (int i = 0; i < 16; ++i)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sm.sv[(lane + 32 * q) * LDT + rb + i] = x[i][q];
+  __syncthreads();
+  // ---- write T (zeros below the diagonal, if kept) and the split images T^T, Y = V T^T
   unsigned char *rec = reinterpret_cast<unsigned char *>(Tg);
   if (with_t32)
     for (int e = tid; e < NB * NB; e += NTHR) {
@@ -971,20 +1119,15 @@ __device__ void panel(int mode, float *X, float *Rg, float *Tg, bool with_t32, u
       __stcg(reinterpret_cast<float *>(rec + REC_T32) + e, r <= c ? sm.tg[r + c * LDT] : 0.f);
     }
   write_image(rec + REC_TB, [&](int m, int k) { return k <= m ? sm.tg[k + m * LDT] : 0.f; });
-  __syncthreads();
+  write_y_image(mode, sm.sv, sm.tg, rec + REC_Y);
   // ---- V / R, and the split images V^T and V (masked to V's structure)
-#pragma unroll
-  for (int i = 0; i < 16; ++i)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) sm.tg[(lane + 32 * q) * LDT + rb + i] = x[i][q];
-  __syncthreads();
   for (int e = tid; e < NB * NB; e += NTHR) {
     const int c = e >> 7, r = e & 127;
-    if (mode != 2 || r <= c) __stcg(X + e, sm.tg[c * LDT + r]);
+    if (mode != 2 || r <= c) __stcg(X + e, sm.sv[c * LDT + r]);
     if (mode != 1 && r <= c) __stcg(Rg + e, sm.rs[rsoff(r, c)]);
   }
-  write_image(rec + REC_VA, [&](int m, int k) { return vmask(mode, k, m, sm.tg[k + m * LDT]); });
-  write_image(rec + REC_VC, [&](int m, int k) { return vmask(mode, m, k, sm.tg[m + k * LDT]); });
+  write_image(rec + REC_VA, [&](int m, int k) { return vmask(mode, k, m, sm.sv[k + m * LDT]); });
+  if (with_t32) write_image(rec + REC_VC, [&](int m, int k) { return vmask(mode, m, k, sm.sv[m + k * LDT]); });
   __syncthreads();
 }
 

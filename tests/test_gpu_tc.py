@@ -178,3 +178,39 @@ def test_ls_conditioned_tc(kappa, iters):
     xo = lstsq_unblocked(A.double().cpu().numpy(), b.cpu().numpy())
     err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
     assert err <= 1e-12, err
+
+
+def test_split_launch_equals_one_launch():
+    """A plan with tensor-core and CUDA-core problems runs them as two
+    launches side by side (hqr_set_split_launch): every x is bitwise the
+    one of a single launch of the tensor-core kernel (each task's arithmetic
+    does not depend on the kernel variant that runs it), also on CUDA-graph
+    replay and after the SM share is rebalanced between runs."""
+    shapes = [(64, 32), (300, 60), (1000, 333), (2048, 256), (200, 100), (4096, 129), (90, 90)]
+    host, outs = [], {}
+    for q, (M, N) in enumerate(shapes):
+        A = inputs.gaussian(M, N, seed=780 + q).astype(np.float32)
+        host.append((A, inputs.rng(780 + q, 1).standard_normal(M)))
+    cfgs = [hqr.tile_config(128, 128, 2, 1, "greedy", "greedy") if N > 128 else hqr.tile_config(32, 16, 2, 1)
+            for (M, N) in shapes]
+    for split in (0, 1):
+        hqr.set_split_launch(split)
+        try:
+            probs = [to_dev(A, b, A.shape[1]) for A, b in host]
+            plan = hqr.LSPlan(probs, refine_iters=6, configs=cfgs, tensor=True)
+        finally:
+            hqr.set_split_launch(1)
+        for _ in range(3):  # timed runs: the split plan rebalances its SM share
+            plan.run()
+            assert plan.status() == 0
+        outs[split] = [p[2].clone() for p in probs]
+        if split:
+            s = torch.cuda.Stream()
+            plan.capture(s)
+            plan.run(s)
+            assert plan.status(s) == 0
+            assert all(torch.equal(p[2], x) for p, x in zip(probs, outs[1]))
+    assert all(torch.equal(a, b) for a, b in zip(outs[0], outs[1]))
+    for (A, b), x in zip(host, outs[1]):
+        xo = lstsq_unblocked(A.astype(np.float64), b)
+        assert np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo) <= 1e-12
