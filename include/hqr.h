@@ -430,7 +430,9 @@ int hqr_ls_plan_refine_info(hqr_ls_plan *plan, int idx, int *iters, double *rel_
 int hqr_ls_plan_run(hqr_ls_plan *plan, void *stream);
 
 /* hqr_ls_plan_capture -- capture one run on `stream` (not the legacy
- * default stream) into a CUDA graph used by later runs. */
+ * default stream) into a CUDA graph used by later runs. A plan that splits
+ * its launch (hqr_set_split_launch) keeps the SM share it has at capture:
+ * run it a few times first so that the share is set from measured times. */
 int hqr_ls_plan_capture(hqr_ls_plan *plan, void *stream);
 
 /* hqr_ls_plan_status -- synchronize `stream`; 0, the device status of the
