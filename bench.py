@@ -331,7 +331,8 @@ def batched(torch, hqr, dev, count=1024, refine=4, tune=True, peaks=None):
     return out
 
 
-def serving(torch, hqr, dev, rate=2000.0, seconds=5.0, refine=5, peaks=None):
+def serving(torch, hqr, dev, rate=2000.0, seconds=5.0, refine=5, peaks=None, labels=("mixed_tc", "fp64"),
+            stop_factor=4.0):
     """Poisson request stream at `rate` req/s for `seconds`: 90 % uneven
     batched-like shapes, 10 % 32768 x 1024 FP32 with kappa = 1e4. Mixed server
     vs plain FP64 server on the same arrivals."""
@@ -355,6 +356,8 @@ def serving(torch, hqr, dev, rate=2000.0, seconds=5.0, refine=5, peaks=None):
            "offered_per_s": rate, "requests": n_req}
     for label, dtype, iters, tensor in (("mixed_tc", torch.float32, refine, True),
                                         ("fp64", torch.float64, 0, False)):
+        if label not in labels:
+            continue
         pool_s = small if dtype == torch.float32 else [(A.double().t().contiguous().t(), b) for A, b in small]
         pool_l = large if dtype == torch.float32 else [(A.double().t().contiguous().t(), b) for A, b in large]
         srv = hqr.Server(dtype, refine_iters=iters, max_live=2048, hbm_budget=120 << 30,
@@ -385,7 +388,7 @@ def serving(torch, hqr, dev, rate=2000.0, seconds=5.0, refine=5, peaks=None):
                     arr, fl = inflight.pop(t)
                     lat.append(now - arr)
                     done_flops += fl
-                if now > seconds * 4:  # a saturated server: stop at 4x the arrival window
+                if now > seconds * stop_factor:  # a saturated server: stop at 4x the arrival window
                     break
             wall = time.perf_counter() - t0
         finally:
@@ -459,6 +462,24 @@ def trace_phases(tr):
 
 
 GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def serving_sustainable(torch, hqr, dev, peaks, seconds=3.0):
+    """Highest offered Poisson rate (of a few) that each server sustains: at
+    least 97 % of the requests completed within the window plus 50 %, with
+    p50 / p99 latency at that rate."""
+    out = {"criterion": "completed >= 97 % of the offered requests within 1.5x the %g s arrival window" % seconds}
+    for label, rates in (("mixed_tc", (250.0, 400.0, 600.0)), ("fp64", (80.0, 110.0, 140.0))):
+        best = None
+        for rate in rates:
+            r = serving(torch, hqr, dev, rate=rate, seconds=seconds, peaks=peaks, labels=(label,), stop_factor=2.0)[label]
+            ok = r["completed"] >= 0.97 * int(rate * seconds) and r["wall_s"] <= 1.5 * seconds
+            if ok:
+                best = dict(r, offered_per_s=rate)
+            else:
+                break
+        out[label] = best if best else {"offered_per_s": None, "note": "no tried rate was sustained"}
+    return out
 
 
 def square_mixed_oracle(A, b, n):
@@ -781,6 +802,7 @@ def main():
         extras["square_mixed"] = square_mixed(torch, hqr, dev, peaks)
         extras["serving"] = serving(torch, hqr, dev, seconds=args.serve_seconds, peaks=peaks)
         extras["serving_200"] = serving(torch, hqr, dev, rate=200.0, seconds=args.serve_seconds, peaks=peaks)
+        extras["serving_sustainable"] = serving_sustainable(torch, hqr, dev, peaks)
 
     if rank != 0:
         return 0

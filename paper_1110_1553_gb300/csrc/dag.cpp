@@ -394,14 +394,24 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
   // corrections are still far above the FP64 rounding level, use plain FP64 sums (1 FMA per
   // element instead of ~10 FP64 operations). Vector tasks carry the choice in `tgt`.
   const int ncomp = std::min(iters, std::max(4, (2 * iters + 4) / 5));
+  std::vector<int32_t> checks, gates;  // tol_mode: each round's check; the gates (ids)
+  int32_t gate = -1;
   for (int it = 0; it < iters; ++it) {
     round = it;
     const int comp = (!tol_mode && it >= iters - ncomp) ? 1 : 0;
     auto rtask = [&](int op, int i, int j) { return rmark(make_task(op, 1, i, i, 0, j, 0, 0, 1, comp, pid)); };
+    if (tol_mode && it >= 2) {  // the round's gate: after check it - 2 and the previous gate
+      d.push_back(checks[it - 2]);
+      if (gate >= 0) d.push_back(gate);
+      gate = b.next_id();
+      gates.push_back(gate);
+      b.add(vtask(OP_RGATE, 0, 0));
+    }
     for (int i = 0; i < m; ++i) {
       for (int c = 0; c < nrc; ++c) {
         for (int j = c * kResChunk; j < std::min(n, (c + 1) * kResChunk); ++j) tr.read(xres(j), d);
         tr.write(qres(i, c), d);
+        if (tol_mode && it >= 2) d.push_back(gate);
         b.add(rtask(OP_RESID, i, c));
       }
       for (int c = 0; c < nrc; ++c) tr.read(qres(i, c), d);
@@ -419,8 +429,11 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
       b.add(vtask(OP_ATRR, j, j));
     }
     solve_r(true);
+    if (tol_mode) checks.push_back(check);
   }
-  return b.finish();
+  Graph g = b.finish();
+  for (int32_t q : gates) g.tasks[q].j = (int32_t)g.tasks.size() - q - 1;  // tasks after the gate
+  return g;
 }
 
 // Estimated cost of a task in units of b^3/3 (Sec. 2 weights), updates scaled by slab width;

@@ -136,6 +136,7 @@ struct Shared {
   int task;
   int abort;
   int vskip, vcomp;  // vector tasks of tolerance-stopped rounds: skip the task, compensated sums
+  int norelease;     // the task released none of its successors (a gate that cancelled its rounds)
   Real red[2 * NWARP];
   Real tau[IBMAX];
   Real wv[IBMAX];
@@ -850,6 +851,20 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
   // write scratch vectors that no later task reads)
   const bool tolm = t.trans == 2;
   bool comp = t.tgt != 0;  // residual and A^T r: compensated (Dot2) or plain FP64 sums
+  if (t.op == OP_RGATE) {
+    // gate of round k: if the refinement stopped at round k - 2 or earlier, no task of rounds >= k
+    // may run; they all follow this gate, so it releases none of its successors and counts them
+    // (t.j tasks) as done
+    if (tid == 0) {
+      const int conv = __ldcg(&P.rs->conv);
+      if (conv != 0 && t.k >= conv + 1) {
+        sh.norelease = 1;
+        atomicAdd(&p.ctl->done.v, (unsigned)t.j);
+      }
+    }
+    __syncthreads();
+    return;
+  }
   if (tolm) {  // one thread reads the state, so that the whole CTA takes the same branch
     if (tid == 0) {
       const int conv = __ldcg(&P.rs->conv);
@@ -1382,6 +1397,7 @@ __global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_sched(EngineParams p) {
   if (threadIdx.x == 0) {
     ptx::mbar_init(&sh.bar, 1);
     sh.abort = 0;
+    sh.norelease = 0;
   }
   tc_setup<TC>(ts);
   __syncthreads();
@@ -1417,10 +1433,13 @@ __global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_sched(EngineParams p) {
       }
       ptx::fence_proxy_async();
       __threadfence();
-      for (int e = t.succ_begin + (int)threadIdx.x; e < t.succ_end; e += 32) {
+      const int e_end = sh.norelease ? t.succ_begin : t.succ_end;
+      for (int e = t.succ_begin + (int)threadIdx.x; e < e_end; e += 32) {
         const int s = p.succ[e];
         if (atomicSub(&p.indeg[s], 1) == 1) push_ready(p, s);
       }
+      __syncwarp();
+      if (threadIdx.x == 0) sh.norelease = 0;
       if (threadIdx.x == 0 && ++pending >= 64) {
         __threadfence();
         atomicAdd(&p.ctl->done.v, pending);
@@ -1608,6 +1627,7 @@ __global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_serve(ServeParams sp) {
   if (threadIdx.x == 0) {
     ptx::mbar_init(&sh.bar, 1);
     sh.abort = 0;
+    sh.norelease = 0;
   }
   tc_setup<TC>(ts);
   __syncthreads();

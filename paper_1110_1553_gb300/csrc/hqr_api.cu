@@ -233,6 +233,10 @@ int ctas_for(int prec, bool tc, size_t smem, int ntasks, int *grid) {
 }
 
 int launch_sched(int prec, const EngineParams &p, size_t smem, cudaStream_t s, int max_ctas = 0) {
+  if (p.tc && smem < engine_smem_bytes_tc()) {  // the tensor-core tasks lay out that much shared memory
+    g_last_error = "tensor-core launch with too little shared memory";
+    return HQR_ERR_INTERNAL;
+  }
   int grid = 0;
   int st = ctas_for(prec, p.tc != 0, smem, p.ntasks, &grid);
   if (st) return st;
@@ -1193,9 +1197,9 @@ int plan_create(int count, const hqr_ls_problem_t *probs, const hqr_tile_config_
     }
     std::vector<PanelOp> ops = expand_ops(lst.data(), lst.size(), pb.m, pb.n);
     const bool tcp = use_tc(prec, c.nb);
-    append_graph(tcp || !g_split_launch ? merged : merged2,
-                 build_ls_graph(ops, pb.m, pb.n, c.nb, pb.w, refine_iters, q, false, split_ib_for(prec, pb),
-                                P->tol_mode != 0));
+    Graph gq = build_ls_graph(ops, pb.m, pb.n, c.nb, pb.w, refine_iters, q, false, split_ib_for(prec, pb),
+                              P->tol_mode != 0);
+    append_graph(tcp || !g_split_launch ? merged : merged2, gq);
     if (P->tol_mode) {
       pb.maxit = refine_iters;
       pb.tol = tol;

@@ -32,6 +32,7 @@ enum Op : int8_t {
   OP_TRINV = 16,   // inverse of the diagonal R tile i (FP64), used by OP_TRSV_TD / OP_TRSV_D
   OP_RESR = 17,    // r_i = b_i - sum over column chunks of the OP_RESID partial sums
   OP_RCHK = 18,    // convergence check of one refinement round (tolerance-stopped plans)
+  OP_RGATE = 19,   // gate of refinement round k >= 2 (tolerance-stopped plans): cancels rounds >= k
 };
 
 // Refinement rounds of a least-squares graph at most.
@@ -141,7 +142,13 @@ Graph build_apply_graph(const std::vector<PanelOp> &ops, int m, int nslab, int w
 // all its x updates, and round r + 1's x updates follow that check, so a round
 // whose check found the tolerance met leaves x as it was (its other tasks may
 // still run on scratch vectors: harmless). Which rounds compensate their
-// residuals is decided at run time (RefineState::mode), not by `tgt`.
+// residuals is decided at run time (RefineState::mode), not by `tgt`. Every
+// round r >= 2 starts with an OP_RGATE task (after check r - 2 and gate
+// r - 1; before the round's residual tasks, which every other task of the
+// round and of later rounds follows); its `j` holds the number of tasks
+// after it in the graph (rounds >= r). A gate that finds the refinement
+// stopped at round r - 2 or earlier releases no successor and counts those
+// tasks as done, so the cancelled rounds cost nothing.
 Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int w, int iters, int pid,
                      bool pack = false, int split_ib = 0, bool tol_mode = false);
 

@@ -17,7 +17,7 @@ from oracle.elim_list import BINARY, FIBONACCI, FLAT, GREEDY, hqr_elim_list
 hqr = pytest.importorskip("paper_1110_1553_gb300.hqr")
 
 GEQRT, UNMQR, TSQRT, TSMQR, TTQRT, TTMQR = range(6)
-RESID, ATR, TRSV_TD, TRSV_TU, TRSV_D, TRSV_U, XUPD, BTOG, PACK, ATRR, TRINV, RESR, RCHK = range(6, 19)
+RESID, ATR, TRSV_TD, TRSV_TU, TRSV_D, TRSV_U, XUPD, BTOG, PACK, ATRR, TRINV, RESR, RCHK, RGATE = range(6, 20)
 WEIGHT = {GEQRT: 4, UNMQR: 6, TSQRT: 6, TSMQR: 12, TTQRT: 2, TTMQR: 6}  # units of b^3 / 3 (Sec. 2)
 CHUNK = 8  # tiles per chunk of the residual / A^T r partial sums
 
@@ -66,9 +66,11 @@ def accesses(task, nb, ib, m=0, n=0):
             writes = {("g", j)}
         elif op == XUPD:
             reads, writes = {("g", j)}, {("x", j)}
-        elif op == RCHK:  # round k's convergence check (tolerance plans)
-            reads = {("stat", k), ("cval", k - 1), ("mode", k), ("mode", k + 1), ("conv",)}
-            writes = {("conv",), ("cval", k), ("mode", k + 2)}
+        elif op == RGATE:  # round k's gate: acts on the stop decisions of the checks up to round k - 2
+            reads = {("conv", k - 2)}
+        elif op == RCHK:  # round k's convergence check (tolerance plans): its stop decision ("conv", k)
+            reads = {("stat", k), ("cval", k - 1), ("mode", k), ("mode", k + 1), ("conv", k - 1)}
+            writes = {("conv", k), ("cval", k), ("mode", k + 2)}
         elif op == BTOG:
             reads, writes = {("rhs", i, 0)}, {("g", i)}
         elif op == PACK:  # tile column j from the caller's matrix; column 0 also b and x = 0
@@ -80,8 +82,8 @@ def accesses(task, nb, ib, m=0, n=0):
         if trans == 2:  # a round of a tolerance-stopped refinement (round k)
             if op in (RESID, ATR):  # plain or compensated sums, as decided two rounds before
                 reads.add(("mode", k))
-            if op == XUPD:  # applied only if no earlier round met the tolerance
-                reads.add(("conv",))
+            if op == XUPD:  # applied only if no earlier round stopped the refinement
+                reads.add(("conv", k - 1))
             # every round task also reads the stop flag to skip work, but only x updates and
             # checks act on it in an order that matters: the others write scratch vectors only
         return reads, writes
@@ -351,12 +353,30 @@ def test_tolerance_graph_has_no_races(low, high, a, p, iters, split):
     ops, ks, trans = tasks[:, 0], tasks[:, 4], tasks[:, 8]
     assert (ops == RCHK).sum() == iters
     assert sorted(ks[ops == RCHK]) == list(range(iters))
-    rnd = np.isin(ops, [RESID, RESR, ATR, ATRR, TRSV_TD, TRSV_TU, TRSV_D, TRSV_U, XUPD, RCHK])
+    rnd = np.isin(ops, [RESID, RESR, ATR, ATRR, TRSV_TD, TRSV_TU, TRSV_D, TRSV_U, XUPD, RCHK, RGATE])
     assert rnd[trans == 2].all()  # only round tasks are marked
     assert (trans[np.isin(ops, [RESID, RESR, ATR, ATRR, RCHK])] == 2).all()
     # the starting point x0 = R^{-1} (Q^T b)[0:N]: Q^T b, its first N entries, one backward solve
     assert (ops == BTOG).sum() == n
     assert ((ops == XUPD) & (trans != 2)).sum() == n and ((ops == XUPD) & (trans == 2)).sum() == iters * n
+    # gates of rounds >= 2: after check k - 2 and gate k - 1, before every residual task of round k;
+    # j = the number of tasks after the gate, all of rounds >= k and all its descendants
+    gidx = np.nonzero(ops == RGATE)[0]
+    assert sorted(ks[gidx]) == list(range(2, iters))
+    for q in gidx:
+        k = ks[q]
+        assert tasks[q, 5] == len(tasks) - q - 1
+        assert (ks[q + 1:][trans[q + 1:] == 2] >= k).all() and (trans[q + 1:] == 2).all()
+        assert q in succ[ptr[int(np.nonzero((ops == RCHK) & (ks == k - 2))[0][0])]:ptr[int(np.nonzero((ops == RCHK) & (ks == k - 2))[0][0]) + 1]]
+        for u in np.nonzero((ops == RESID) & (ks == k) & (trans == 2))[0]:
+            assert u in succ[ptr[q]:ptr[q + 1]]
+        # every later task descends from the gate (a cancelled gate releases nothing, so none of them runs)
+        desc = np.zeros(len(tasks), bool)
+        desc[q] = True
+        for t in range(q, len(tasks)):
+            if desc[t]:
+                desc[succ[ptr[t]:ptr[t + 1]]] = True
+        assert desc[q + 1:].all()
     # every check follows all x updates of its round; every x update of round k + 1 follows check k
     for q in np.nonzero(ops == RCHK)[0]:
         k = ks[q]
