@@ -785,6 +785,7 @@ def main():
     del A_dev, A_host
 
     peak = measured_dgemm_tflops(torch, dev) if rank == 0 else None
+    pipes = hqr.fp64_pipe_rates() if rank == 0 else (None, None)
     traffic, traffic_note = ncu_traffic()
     ntasks = F.ntasks
     del F
@@ -835,6 +836,8 @@ def main():
                      "kernel": "hqr::hqr_sched<double>",
                      "peak_source": "FP64 cuBLAS DGEMM 8192^3 measured in this run (best of 3); "
                                     "no FP64 entry in MEASURED_PEAKS.json",
+                     "fp64_pipe_tflops": {"dfma": pipes[0], "dmma": pipes[1],
+                                          "from": "hqr_fp64_pipe_rates: register-only DFMA / DMMA loops"},
                      "traffic_note": traffic_note},
         "clocks": clk.summary(),
         "cpu_baseline": cpu,

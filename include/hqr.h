@@ -149,7 +149,10 @@ int hqr_validate_list(int m, int n, const hqr_elim_t *list, size_t count);
  *            server request (packing tasks first); 5: a problem of a plan
  *            from hqr_ls_plan_create_tol with at most `param` rounds (round
  *            tasks carry trans = 2 and k = the round; op 18 is a round's
- *            convergence check).
+ *            convergence check, op 19 a round's gate); 6: the graph of
+ *            hqr_geqrf_r_noalloc (FP64 only, its limits apply:
+ *            HQR_ERR_TOO_LARGE beyond them; built in the static storage that
+ *            entry point uses, so not concurrently with it).
  *   tasks    caller array of 10 int32 per task: op (0 GEQRT, 1 UNMQR,
  *            2 TSQRT, 3 TSMQR, 4 TTQRT, 5 TTMQR, 6.. the vector tasks of
  *            least-squares graphs), blk (0: the whole panel / every block;
@@ -618,6 +621,14 @@ int hqr_set_priority_policy(int policy);
 
 /* hqr_set_timeout_ms -- time limit of every device-side wait (default 20000). */
 void hqr_set_timeout_ms(int64_t ms);
+
+/* hqr_fp64_pipe_rates -- measured FP64 rates of the current GPU (TFLOP/s,
+ * a multiply-add counted as 2 flops): DFMA instructions and DMMA
+ * (mma.sync m8n8k4 f64) instructions, each from independent register
+ * chains in every warp of 4 CTAs per SM (no memory traffic); best of three
+ * timed launches after a warm-up. A reference for the FP64 kernels'
+ * roofline; the paper has no counterpart. Synchronizes the device. */
+int hqr_fp64_pipe_rates(double *dfma_tflops, double *dmma_tflops);
 
 /* hqr_strerror -- static text of a status code. */
 const char *hqr_strerror(int status);

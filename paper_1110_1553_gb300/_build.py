@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 
 GENCODE = "-gencode=arch=compute_103a,code=sm_103a"
 CXX_SRCS = ["elim_list.cpp", "dag.cpp"]
-CU_SRCS = ["hqr_api.cu"]
+CU_SRCS = ["hqr_api.cu", "peaks.cu"]
 
 
 def _nvcc():

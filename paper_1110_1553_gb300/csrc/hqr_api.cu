@@ -484,6 +484,14 @@ const char *hqr_strerror(int status) {
   }
 }
 
+}  // extern "C"
+namespace {
+int na_task_graph(int m, int n, int nb, int ib, const hqr_elim_t *list, size_t count, int32_t *tasks,
+                  int64_t task_cap, int64_t *succ_ptr, int32_t *succ, int64_t succ_cap, int64_t *ntasks,
+                  int64_t *nedges);
+}  // namespace
+extern "C" {
+
 int hqr_task_graph(int m, int n, int nb, int ib, int prec, const hqr_elim_t *list, size_t count, int kind,
                    int param, int32_t *tasks, int64_t task_cap, int64_t *succ_ptr, int32_t *succ, int64_t succ_cap,
                    int64_t *ntasks, int64_t *nedges) {
@@ -494,10 +502,13 @@ int hqr_task_graph(int m, int n, int nb, int ib, int prec, const hqr_elim_t *lis
   ib = eff_ib(prec, nb, ib);
   if (!valid_tile_sizes(prec, nb, ib)) return -4;
   if (!list && count) return -6;
-  if (kind < 0 || kind > 5) return -8;
+  if (kind < 0 || kind > 6) return -8;
+  if (kind == 6 && prec != HQR_FP64) return -5;
   if (param < 0 || ((kind == 1 || kind == 2) && param < 1)) return -9;
   if (!ntasks || !nedges) return -16;
   if (hqr_validate_list(m, n, list, count) != HQR_SUCCESS) return HQR_ERR_INVALID_LIST;
+  if (kind == 6)
+    return na_task_graph(m, n, nb, ib, list, count, tasks, task_cap, succ_ptr, succ, succ_cap, ntasks, nedges);
   Problem P{};
   P.m = m;
   P.n = n;
@@ -2550,36 +2561,13 @@ bool na_list_valid(int m, int n, const hqr_elim_t *list, size_t count) {
   return true;
 }
 
-size_t na_align(size_t x) { return (x + 255) & ~(size_t)255; }
-
-}  // namespace
-
-extern "C" int hqr_geqrf_r_noalloc(const void *dA, int M, int N, int lda, int nb, int ib,
-                                   const hqr_elim_t *list, size_t count, void *dR, int ldr, void *stream) {
-  if (!dA) return -1;
-  if (M < 1) return -2;
-  if (N < 1 || N > M) return -3;
-  if (lda < M) return -4;
-  if (nb < 8 || nb % 8) return -5;
-  if (ib < 2 || ib % 2 || nb % ib || (ib > 16 && ib != 32)) return -6;
-  if (!list) return -7;
-  if (!dR) return -9;
-  if (ldr < N) return -10;
-  if (nb > 64) return HQR_ERR_TOO_LARGE;
-  const int m = (M + nb - 1) / nb, n = (N + nb - 1) / nb;
-  if (m > kNaMaxM || n > kNaMaxN || m * n > kNaMaxTiles) return HQR_ERR_TOO_LARGE;
-  if (!na_list_valid(m, n, list, count)) return -7;
-  cudaStream_t s = (cudaStream_t)stream;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return HQR_ERR_CUDA;
-  if (dev < 0 || dev >= kNaMaxDevices) return HQR_ERR_TOO_LARGE;
-  if (!g_na_ready[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) return HQR_ERR_CUDA;
-    g_na_dev_ptr[dev] = p;
-    g_na_ready[dev] = true;
-  }
-  const int w = std::min(16, nb), wt = std::min(16, nb), vc = std::min(ib, 16);
+// The task graph of hqr_geqrf_r_noalloc for an m x n tile matrix and a
+// valid list, built in the static host storage g_na: tasks with their
+// successor ranges (succ_begin / succ_end into g_na.succ), in-degrees.
+// Returns HQR_ERR_TOO_LARGE when a static table would overflow.
+int na_build(int m, int n, int nb, int ib, const hqr_elim_t *list, size_t count) {
+  (void)ib;
+  const int w = std::min(16, nb);
   const int S = (nb + w - 1) / w;
   // operation sequence of Alg. 1 / Alg. 2 (as expand_ops)
   int nops = 0;
@@ -2658,6 +2646,66 @@ extern "C" int hqr_geqrf_r_noalloc(const void *dA, int M, int N, int lda, int nb
     g_na.tasks[t].succ_end = g_na.cnt[t + 1];
   }
   for (int e = 0; e < g_na.nedges; ++e) g_na.succ[g_na.cnt[g_na.efrom[e]]++] = g_na.eto[e];
+  return HQR_SUCCESS;
+}
+
+// hqr_task_graph kind 6: the allocation-free entry point's graph (host only).
+int na_task_graph(int m, int n, int nb, int ib, const hqr_elim_t *list, size_t count, int32_t *tasks,
+                  int64_t task_cap, int64_t *succ_ptr, int32_t *succ, int64_t succ_cap, int64_t *ntasks,
+                  int64_t *nedges) {
+  if (nb > 64 || m > kNaMaxM || n > kNaMaxN || m * n > kNaMaxTiles) return HQR_ERR_TOO_LARGE;
+  const int st = na_build(m, n, nb, ib, list, count);
+  if (st) return st;
+  *ntasks = g_na.ntasks;
+  *nedges = g_na.nedges;
+  if (!tasks) return HQR_SUCCESS;
+  if (task_cap < *ntasks || !succ_ptr || (*nedges > 0 && (!succ || succ_cap < *nedges))) return HQR_ERR_CAPACITY;
+  for (int q = 0; q < g_na.ntasks; ++q) {
+    const Task &t = g_na.tasks[q];
+    const int32_t row[10] = {t.op, t.blk, t.i, t.r, t.k, t.j, t.c0, t.cw, t.trans, t.tgt};
+    std::memcpy(tasks + 10 * (size_t)q, row, sizeof(row));
+    succ_ptr[q] = t.succ_begin;
+  }
+  succ_ptr[g_na.ntasks] = g_na.nedges;
+  if (g_na.nedges) std::memcpy(succ, g_na.succ, sizeof(int32_t) * (size_t)g_na.nedges);
+  return HQR_SUCCESS;
+}
+
+size_t na_align(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int hqr_geqrf_r_noalloc(const void *dA, int M, int N, int lda, int nb, int ib,
+                                   const hqr_elim_t *list, size_t count, void *dR, int ldr, void *stream) {
+  if (!dA) return -1;
+  if (M < 1) return -2;
+  if (N < 1 || N > M) return -3;
+  if (lda < M) return -4;
+  if (nb < 8 || nb % 8) return -5;
+  if (ib < 2 || ib % 2 || nb % ib || (ib > 16 && ib != 32)) return -6;
+  if (!list) return -7;
+  if (!dR) return -9;
+  if (ldr < N) return -10;
+  if (nb > 64) return HQR_ERR_TOO_LARGE;
+  const int m = (M + nb - 1) / nb, n = (N + nb - 1) / nb;
+  if (m > kNaMaxM || n > kNaMaxN || m * n > kNaMaxTiles) return HQR_ERR_TOO_LARGE;
+  if (!na_list_valid(m, n, list, count)) return -7;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HQR_ERR_CUDA;
+  if (dev < 0 || dev >= kNaMaxDevices) return HQR_ERR_TOO_LARGE;
+  if (!g_na_ready[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) return HQR_ERR_CUDA;
+    g_na_dev_ptr[dev] = p;
+    g_na_ready[dev] = true;
+  }
+  const int w = std::min(16, nb), wt = std::min(16, nb), vc = std::min(ib, 16);
+  {
+    const int bst = na_build(m, n, nb, ib, list, count);
+    if (bst) return bst;
+  }
+  const int nt = g_na.ntasks;
   for (size_t q = 0; q < slot_count(nt); ++q) g_na.slots[q] = 0;
   init_ready(g_na.tasks, g_na.indeg, nt, g_na.slots, g_na.ctl);
   // scratch layout

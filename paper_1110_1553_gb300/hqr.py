@@ -30,7 +30,8 @@ ELIM_DTYPE = np.dtype([("k", np.int32), ("i", np.int32), ("killer", np.int32), (
 EXPORTS = ["hqr_elim_list", "hqr_elim_list_domino", "hqr_validate_list", "hqr_task_graph", "hqr_geqrf", "hqr_refactor", "hqr_refactor_async",
            "hqr_status", "hqr_get_r", "hqr_get_tiles", "hqr_get_t", "hqr_factors_info", "hqr_kernel_ms", "hqr_kernel_times", "hqr_trace", "hqr_apply_q",
            "hqr_gels", "hqr_gels_qr", "hqr_geqrf_r_noalloc", "hqr_ls_plan_create", "hqr_ls_plan_create_tol",
-           "hqr_ls_plan_refine_info", "hqr_critical_path", "hqr_set_split_launch", "hqr_ls_plan_run",
+           "hqr_ls_plan_refine_info", "hqr_critical_path", "hqr_set_split_launch", "hqr_fp64_pipe_rates",
+           "hqr_ls_plan_run",
            "hqr_ls_plan_capture", "hqr_ls_plan_status", "hqr_ls_plan_correction", "hqr_ls_plan_info", "hqr_ls_plan_config",
            "hqr_ls_plan_free", "hqr_ls_plan_trace", "hqr_set_tuning", "hqr_autotune", "hqr_server_create", "hqr_server_start",
            "hqr_server_submit", "hqr_server_poll", "hqr_server_stats", "hqr_server_progress", "hqr_server_counters", "hqr_server_stop", "hqr_server_free", "hqr_debug_block_task", "hqr_factors_free", "hqr_set_timeout_ms", "hqr_strerror", "hqr_last_error", "hqr_set_slab_widths",
@@ -126,6 +127,7 @@ def load(build_if_missing=False):
     lib.hqr_set_priority_policy.argtypes = [i32]
     lib.hqr_set_panel_split.argtypes = [i32]
     lib.hqr_set_split_launch.argtypes = [i32]
+    lib.hqr_fp64_pipe_rates.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     lib.hqr_set_timeout_ms.argtypes = [i64]
     lib.hqr_set_timeout_ms.restype = None
     lib.hqr_strerror.argtypes = [i32]
@@ -178,7 +180,7 @@ def validate_list(m, n, records):
     return lib.hqr_validate_list(m, n, arr.ctypes.data if len(arr) else None, len(arr))
 
 
-GRAPH_KINDS = {"factor": 0, "qt": 1, "q": 2, "ls": 3, "request": 4, "ls_tol": 5}
+GRAPH_KINDS = {"factor": 0, "qt": 1, "q": 2, "ls": 3, "request": 4, "ls_tol": 5, "noalloc": 6}
 
 
 def task_graph(m, n, nb, ib, records, prec=FP64, kind="factor", param=0):
@@ -224,6 +226,13 @@ def set_slab_widths(w=0, wt=0, vc=0):
 def set_panel_split(min_nb):
     """Split CUDA-core panels of tiles with nb >= min_nb into block tasks (0: never)."""
     _check(load().hqr_set_panel_split(int(min_nb)), "hqr_set_panel_split")
+
+
+def fp64_pipe_rates():
+    """(DFMA, DMMA) FP64 TFLOP/s of the current GPU (hqr_fp64_pipe_rates)."""
+    a, b = ctypes.c_double(0), ctypes.c_double(0)
+    _check(load().hqr_fp64_pipe_rates(ctypes.byref(a), ctypes.byref(b)), "hqr_fp64_pipe_rates")
+    return a.value, b.value
 
 
 def set_split_launch(on):

@@ -312,7 +312,7 @@ def test_task_graph_arguments():
                                   tasks, cap, ptr, succ, scap, ctypes.byref(nt), ctypes.byref(ne))
     assert call() == 0 and nt.value > 0 and ne.value > 0
     assert call(m=0) == -1 and call(n=5) == -2 and call(nb=12) == -3 and call(ib=5) == -4
-    assert call(kind=6) == -8 and call(kind=1, param=0) == -9
+    assert call(kind=7) == -8 and call(kind=1, param=0) == -9
     bad = recs.copy()
     bad[0]["killer"] = bad[0]["i"]  # a row cannot kill itself
     assert call(lst=bad) == hqr.ERR_INVALID_LIST
@@ -433,3 +433,29 @@ def test_critical_path_orders_trees_on_a_tall_matrix():
     cp_hier, _ = hqr.critical_path(m, n, nb, ib, hqr_elim_list(m, n, 4, 4, GREEDY, FIBONACCI))
     assert cp_greedy < cp_hier < cp_flat
     assert cp_flat > 4 * cp_greedy
+
+
+@pytest.mark.parametrize("nb,ib", [(16, 4), (32, 8), (64, 16)])
+@pytest.mark.parametrize("low,high,a,p,domino", [(FLAT, FLAT, 4, 1, False), (GREEDY, FIBONACCI, 2, 2, False),
+                                                 (BINARY, GREEDY, 1, 3, False), (GREEDY, FLAT, 2, 3, True),
+                                                 (FIBONACCI, BINARY, 1, 4, True)])
+def test_noalloc_graph_has_no_races(nb, ib, low, high, a, p, domino):
+    """The allocation-free entry point builds its own task graph in static
+    storage (coarser dependency pieces than the main builder: slab, upper and
+    lower part per tile); the same independent race check applies to it, for
+    TS and TT lists and lists with the coupling level."""
+    m, n = 12, 5
+    recs = hqr_elim_list(m, n, a, p, low, high, domino=domino)
+    tasks, ptr, succ = hqr.task_graph(m, n, nb, ib, recs, kind="noalloc")
+    check_no_races(tasks, ptr, succ, nb, ib, m, n)
+    # one panel task per op of the expansion and one update per (op, later column, slab)
+    S = -(-nb // min(16, nb))
+    nops = (tasks[:, 0] % 2 == 0).sum()
+    assert len(tasks) == nops + S * sum(n - 1 - t[4] for t in tasks if t[0] % 2 == 0 and t[0] <= 4)
+
+
+def test_noalloc_graph_limits():
+    recs = hqr_elim_list(65, 1, 1, 1, FLAT, FLAT)
+    with pytest.raises(hqr.HQRError) as e:
+        hqr.task_graph(65, 1, 16, 4, recs, kind="noalloc")
+    assert e.value.status == hqr.ERR_TOO_LARGE
