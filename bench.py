@@ -453,7 +453,9 @@ def refine_fp64_ops(n_rows, n_cols, plain_rounds, comp_rounds):
 
 def trace_phases(tr):
     """QR phase (kernel start to the end of the last packing / tile task) and
-    refinement phase (the rest) of a traced least-squares plan run, in ms."""
+    refinement phase (the rest) of a traced least-squares plan run, in ms.
+    Tasks of cancelled refinement rounds never ran and have no timestamps."""
+    tr = tr[tr[:, 1] > 0]
     ops = tr[:, 3] >> np.uint64(24)
     qr = (ops <= 5) | (ops == 14)
     t0 = tr[:, 0].min()
