@@ -1349,10 +1349,8 @@ __device__ __forceinline__ void tc_setup(tc::State &ts) {
       for (int c = 0; c < tc::NCH; ++c) {
         ptx::mbar_init(&ts.full[c], NT);
         ptx::mbar_init(&ts.img[c], 1);
-        ptx::mbar_init(&ts.sfree[c], 1);
       }
       ptx::mbar_init(&ts.done, 1);
-      ptx::mbar_init(&ts.slab, 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (threadIdx.x < 32) tc::tmem_alloc(&ts.tmem);

@@ -1,12 +1,13 @@
 // Tensor-core (tcgen05) tile kernels of the FP32 path, tile size 128.
 //
-// Updates (UNMQR / TSMQR / TTMQR, Alg. 2) of one column slab with the full
-// 128 x 128 compact-WY factor T of the panel tile:
-//   Q^T C = C - V T^T V^T C,   Q C = C - V T V^T C,
-// as three products with M = 128 on the 5th-generation tensor cores:
-//   A: W  = V^T C_b  (+ C_t for TS/TT, whose V has an identity top block)
-//   B: W' = T^T W    (T W for Q)          then C_t -= W'   (TS/TT)
-//   C: D  = V W'                           then C_b -= D
+// Updates (UNMQR / TSMQR / TTMQR, Alg. 2) of a whole tile column (or of a
+// right-hand-side block) with the full 128 x 128 compact-WY factor T of the
+// panel tile, as products with M = 128 on the 5th-generation tensor cores:
+//   Q^T C = C - V T^T V^T C:  W = V^T C_b (+ C_t for TS/TT, whose V has an
+//     identity top block); C_t -= T^T W (TS/TT); C_b -= Y W, Y = V T^T
+//     precomputed by the panel task, so both updates come from the same W;
+//   Q C = C - V T V^T C:  W = V^T C_b (+ C_t); W' = T W; C_t -= W';
+//     C_b -= V W' (only factorizations that keep V and T apply Q).
 // Each product runs as kind::f16 MMAs on BF16 operands split three ways
 // ("BF16x3": x = b0 + b1 + b2 with b0 = bf16(x), b1 = bf16(x - b0), b2 =
 // bf16(x - b0 - b1), all rounded to nearest, |x - b0 - b1 - b2| <= 2^-27 |x|)
@@ -15,22 +16,25 @@
 // in tensor memory (one accumulator per K chunk of 32, summed in FP32 in the
 // epilogue). The updates thus keep FP32 accuracy, which the
 // corrected semi-normal-equation refinement needs, at the tensor-core cost
-// of three tf32 products.
+// of three tf32 products. With N = 128 columns per task an MMA runs at the
+// pipe's full rate (N <= 64 costs the same time per instruction).
 //
 // Operands sit in shared memory in the canonical K-major layout without
 // swizzle: core matrices of 8 rows x 16 bytes (8 bf16), element (row, k) at
 //   (row & 7) * 16 + (row >> 3) * SBO + (k & 7) * 2 + (k >> 3) * LBO.
 // A product streams its operands in 4 chunks of K = 32, each in its own
 // shared-memory stage; every thread loads its pieces of a chunk two chunks
-// ahead into registers (L2-only loads, so no stale L1 lines across tasks),
-// and the first chunks of the next product are requested while the current
-// one finishes. The intermediate W^T is resident (K = 128) with LBO = 144
-// bytes so that its transposed writes from tensor memory are free of bank
-// conflicts. Hand-off uses mbarriers: every thread arrives on a chunk's
-// barrier after writing it, one thread issues that chunk's MMAs, and one
-// commit signals the end of a product. The C slabs that the epilogues
-// update are fetched into shared memory by bulk copies while product A
-// runs. Every wait is bounded by the global timer.
+// ahead into registers (L2-only loads, so no stale L1 lines across tasks).
+// The operand images of the panel (V^T, T^T, Y, and V for Q) arrive by one
+// bulk copy per chunk; the next image is requested while the epilogue of the
+// previous product runs. The intermediate W^T is resident (K = 128) with
+// LBO = 144 bytes so that its transposed writes from tensor memory are free
+// of bank conflicts. The C tiles stay in global memory: the threads split
+// C_b^T into the stages from there, and the epilogues read and write C with
+// a warp's lanes on consecutive rows. Hand-off uses mbarriers: every thread
+// arrives on a chunk's barrier after writing it, one thread issues that
+// chunk's MMAs, and one commit signals the end of a product. Every wait is
+// bounded by the global timer.
 #pragma once
 
 #include <cstdint>
@@ -43,32 +47,29 @@ namespace hqr {
 namespace tc {
 
 constexpr int NB = 128;          // tile size of the tensor-core path
-constexpr int WMAX = 64;         // widest column slab of an update task
+constexpr int WMAX = 128;        // widest column slab of an update task (a whole tile)
 constexpr int KC = 32;           // K extent of one chunk (two MMA K steps of 16)
 constexpr int NCH = NB / KC;     // chunks per product (each in its own stage)
 constexpr int DT = 2;            // chunks loaded ahead in registers
 constexpr int NP = 3;            // BF16 pieces of an FP32 value
 constexpr int KS_ACC = 2;                  // MMA K steps (of 16) chained in one accumulator
 constexpr int NACC = NCH * (KC / 16) / KS_ACC;  // accumulators: one per K chunk of 32
-constexpr int TMEM_COLS = 2 * NACC * WMAX;  // 512 columns: two products' accumulators (all of the SM's)
+constexpr int TMEM_COLS = NACC * WMAX;  // 512 columns: one product's accumulators (all of the SM's)
 constexpr int NTHR = 256;
 
 constexpr uint32_t LBO_C = 128, SBO_C = (KC / 8) * 128;      // chunk buffers: 8-row groups of 512 B
 constexpr uint32_t A_PC = (NB / 8) * SBO_C;                  // one piece of a 128 x 32 chunk: 8192 B
-constexpr uint32_t B_PC = (WMAX / 8) * SBO_C;                // one piece of a 64 x 32 chunk: 4096 B
+constexpr uint32_t B_PC = (WMAX / 8) * SBO_C;                // one piece of a 128 x 32 chunk: 8192 B
 constexpr uint32_t LBO_W = 144, SBO_W = (NB / 8) * LBO_W;    // resident W^T (K = 128)
-constexpr uint32_t W_PC = (WMAX / 8) * SBO_W;                // one piece: 18432 B
+constexpr uint32_t W_PC = (WMAX / 8) * SBO_W;                // one piece: 36864 B
 constexpr uint32_t OFF_W = 0;
 constexpr uint32_t STAGE_A = NP * (A_PC + B_PC);             // product A stage: A pieces, B pieces
 constexpr uint32_t STAGE_BC = NP * A_PC;                     // products B, C: A pieces
 constexpr uint32_t OFF_RING_A = 0;                           // product A: W region is free
 constexpr uint32_t OFF_RING_BC = NP * W_PC;
-constexpr uint32_t SMEM_A = OFF_RING_A + NCH * STAGE_A;      // 147456
-constexpr uint32_t SMEM_BC = OFF_RING_BC + NCH * STAGE_BC;   // 153600
-constexpr uint32_t SLAB_BYTES = WMAX * NB * 4;                  // one C slab (64 columns of 128)
-constexpr uint32_t OFF_TOP = SMEM_A > SMEM_BC ? SMEM_A : SMEM_BC;  // C_t slab, column-major, ld 128
-constexpr uint32_t OFF_BOT = OFF_TOP + SLAB_BYTES;                 // C_b slab
-constexpr uint32_t SMEM_BYTES = OFF_BOT + SLAB_BYTES;              // 219136
+constexpr uint32_t SMEM_A = OFF_RING_A + NCH * STAGE_A;      // 196608
+constexpr uint32_t SMEM_BC = OFF_RING_BC + NCH * STAGE_BC;   // 208896
+constexpr uint32_t SMEM_BYTES = SMEM_A > SMEM_BC ? SMEM_A : SMEM_BC;  // 208896 (the C tiles stay in global memory)
 
 // Per panel tile (i, k, GEQRT or kill) the panel task stores a "T record":
 // the update operands already split into BF16 pieces in the chunk layout of
@@ -92,9 +93,7 @@ constexpr uint32_t T_RECORD = (REC_T32 + NB * NB * 4) / 4;       // with them: 1
 struct State {
   uint64_t full[NCH];   // chunk c staged by every thread
   uint64_t img[NCH];    // chunk c of an operand image arrived (bulk copy)
-  uint64_t sfree[NCH];  // the MMAs that read stage c of the second ring completed
   uint64_t done;        // every MMA of a product completed
-  uint64_t slab;        // the C slabs of an update arrived (bulk copies)
   uint32_t tmem;
   int pad;
 };
@@ -204,7 +203,7 @@ __device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity, volatil
 // Parity of the chunk barriers (all flip once per product) and of the done
 // barrier, tracked identically by every thread.
 struct Phases {
-  uint32_t full = 0, img = 0, done = 0, slab = 0, sfree = 0;
+  uint32_t full = 0, img = 0, done = 0;
 };
 
 // Element masks of the reflector block V at (row, reflector):
@@ -303,10 +302,10 @@ __device__ __forceinline__ void store_piece(const Src &s, const Piece &x, int c,
 }
 
 // Registers of a product's streamed operands: DT chunks, A (2 pieces per
-// thread and chunk) and B (1 piece, product A only).
+// thread and chunk) and B (2 pieces, product A only).
 struct Fetch {
   Piece a[DT][2];
-  Piece b[DT];
+  Piece b[DT][2];
 };
 
 __device__ __forceinline__ void fetch_a(const Src &s, int c, Piece (&r)[2]) {
@@ -318,10 +317,13 @@ __device__ __forceinline__ void fetch_a(const Src &s, int c, Piece (&r)[2]) {
   }
 }
 
-__device__ __forceinline__ void fetch_b(const Src &s, int c, Piece &r) {
-  int m, kg;
-  piece_coords(s, WMAX, 0, m, kg);
-  r = load_piece(s, c, m, kg);
+__device__ __forceinline__ void fetch_b(const Src &s, int c, Piece (&r)[2]) {
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    int m, kg;
+    piece_coords(s, WMAX, u, m, kg);
+    r[u] = load_piece(s, c, m, kg);
+  }
 }
 
 // The six BF16 products of one K step, small terms first, accumulating.
@@ -385,9 +387,12 @@ __device__ bool product(const Src &sa, const unsigned char *img, const Src *sb, 
       }
     }
     if (streamB) {
-      int m, kg;
-      piece_coords(*sb, WMAX, 0, m, kg);
-      store_piece(*sb, f.b[slot], c, m, kg, stage + NP * A_PC, B_PC);
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        int m, kg;
+        piece_coords(*sb, WMAX, u, m, kg);
+        store_piece(*sb, f.b[slot][u], c, m, kg, stage + NP * A_PC, B_PC);
+      }
     }
     if (c + DT < NCH) {
       if (!useImg) fetch_a(sa, c + DT, f.a[slot]);
@@ -444,21 +449,11 @@ __device__ __forceinline__ void tmem_sum16(uint32_t taddr, float (&v)[16]) {
   }
 }
 
-// Accumulator elements of this thread in the epilogues: lane m = 32 (warp
-// & 3) + laneid, columns 16 g .. 16 g + 15 for the column groups g = (warp >>
-// 2) + 2 e, e = 0, 1 (n <= 64). The C slabs sit in shared memory (column
-// col of a slab at col * 128 floats), fetched at the start of the task.
-
-// Request the slab's cw columns with one bulk copy on `bar`: in a tile (and a
-// right-hand-side block) the columns of a slab are contiguous (ld 128).
-__device__ __forceinline__ void fetch_slab(const float *c, int cw, float *dst, uint64_t *bar) {
-  ptx::bulk_g2s(dst, c, (uint32_t)cw * NB * 4, bar);
-}
-
-// Coalesced write-back of a slab from shared memory.
-__device__ __forceinline__ void store_slab(float *c, int cw, const float *src) {
-  for (int e = threadIdx.x; e < cw * NB; e += NTHR) __stcg(c + e, src[e]);
-}
+// Accumulator elements of this thread in the epilogues: row m = 32 (warp &
+// 3) + laneid (the tensor-memory lanes its warp may read), columns 16 g ..
+// 16 g + 15 for the column groups g = (warp >> 2) + 2 e, e = 0 .. 3 (n <= 128).
+// The C tiles stay in global memory (column col at col * 128 floats): a warp's
+// accesses to one column are 128 consecutive bytes.
 
 // Offset of element (n = column, k = reflector) in a piece of the resident
 // W^T buffer.
@@ -466,17 +461,23 @@ __device__ __forceinline__ uint32_t woff(int n, int k) {
   return (uint32_t)(n & 7) * 16 + (uint32_t)(n >> 3) * SBO_W + (uint32_t)(k & 7) * 2 + (uint32_t)(k >> 3) * LBO_W;
 }
 
-// Epilogue of products A and B: W = D (+ add), optionally sub -= W (slabs in
-// shared memory), and W^T (three BF16 pieces) to the resident buffer for the
+// Epilogue of products A and B: W = D (+ add), optionally sub -= W (C tiles in
+// global memory), and W^T (three BF16 pieces) to the resident buffer for the
 // next product.
 __device__ void epilogue_w(uint32_t tmem, int n, int cw, const float *add, float *sub, unsigned char *smem) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m = 32 * (warp & 3) + lane;
   const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-#pragma unroll
-  for (int e = 0; e < 2; ++e) {
+#pragma unroll 1
+  for (int e = 0; e < 4; ++e) {
     const int g = (warp >> 2) + 2 * e;
     if (g >= n / 16) continue;
+    float c0[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int col = 16 * g + q;
+      c0[q] = (col < cw && (add || sub)) ? __ldcg((add ? add : sub) + (size_t)col * NB + m) : 0.f;
+    }
     float v[16];
     tmem_sum16(tl + 16 * g, v);
 #pragma unroll
@@ -484,9 +485,8 @@ __device__ void epilogue_w(uint32_t tmem, int n, int cw, const float *add, float
       const int col = 16 * g + q;
       float x = 0.f;
       if (col < cw) {
-        x = v[q];
-        if (add) x += add[col * NB + m];
-        if (sub) sub[col * NB + m] -= x;
+        x = add ? v[q] + c0[q] : v[q];
+        if (sub) __stcg(sub + (size_t)col * NB + m, c0[q] - x);
       }
       uint32_t p0, p1, p2;
       split3(x, p0, p1, p2);
@@ -498,170 +498,106 @@ __device__ void epilogue_w(uint32_t tmem, int n, int cw, const float *add, float
   }
 }
 
-// Epilogue of product C: C_b -= D (slab in shared memory).
-__device__ void epilogue_c(uint32_t tmem, int n, int cw, float *cb) {
+// Epilogue of a product that updates a C tile: c -= D (global memory).
+__device__ void epilogue_c(uint32_t tmem, int n, int cw, float *c) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m = 32 * (warp & 3) + lane;
   const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-#pragma unroll
-  for (int e = 0; e < 2; ++e) {
+#pragma unroll 1
+  for (int e = 0; e < 4; ++e) {
     const int g = (warp >> 2) + 2 * e;
     if (g >= n / 16) continue;
+    float c0[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int col = 16 * g + q;
+      c0[q] = col < cw ? __ldcg(c + (size_t)col * NB + m) : 0.f;
+    }
     float v[16];
     tmem_sum16(tl + 16 * g, v);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int col = 16 * g + q;
-      if (col < cw) cb[col * NB + m] -= v[q];
+      if (col < cw) __stcg(c + (size_t)col * NB + m, c0[q] - v[q]);
     }
   }
 }
 
-// Second phase of a Q^T update from the resident W^T: D_top = T^T W (TS /
-// TT: `top`) into the accumulators at tmem, and D_bot = Y W (Y = V T^T) into
-// those at tmem + NACC * WMAX. The images stream through the four stages of
-// the second ring: the caller has issued the first image (T^T with `top`, else
-// Y); with `top`, stage c is refilled with Y's chunk c as soon as the MMAs
-// that read T^T's chunk c completed (one commit per stage). One thread issues
-// every MMA; all threads wait for the last. Returns false on a timeout.
-__device__ bool product_pair(const unsigned char *rec, bool top, unsigned char *smem, State &st, Phases &ph,
-                             uint32_t tmem, int n, volatile int *abort, long long limit_ns) {
-  const uint32_t idesc = idesc_bf16(n);
-  const uint32_t sbase = ptx::smem_addr(smem);
-  bool ok = true;
-  if (threadIdx.x == 0) {
-    const uint32_t pi = ph.img & 1u, pf = ph.sfree & 1u;
-    auto issue = [&](int c, uint32_t dbase) {
-      const uint32_t a = sbase + OFF_RING_BC + (uint32_t)c * STAGE_BC;
-#pragma unroll
-      for (int ks = 0; ks < KC / 16; ++ks) {
-        const int acc = (c * (KC / 16) + ks) / KS_ACC;
-        const bool first = (c * (KC / 16) + ks) % KS_ACC == 0;
-        issue_kstep(dbase + (uint32_t)acc * WMAX, idesc, a + (uint32_t)ks * 2 * LBO_C, A_PC,
-                    sbase + OFF_W + (uint32_t)(c * KC / 8 + ks * 2) * LBO_W, W_PC, LBO_W, SBO_W, first);
-      }
-    };
-    const uint32_t dbot = tmem + (uint32_t)(NACC * WMAX);
-    if (top) {
-      for (int c = 0; c < NCH && ok; ++c) {
-        if (!wait_bar(&st.img[c], pi, abort, limit_ns)) ok = false;
-        tc_fence_after();
-        if (ok) {
-          issue(c, tmem);
-          mma_commit(&st.sfree[c]);
-        }
-      }
-      for (int c = 0; c < NCH && ok; ++c) {  // refill each stage once its T^T chunk is consumed
-        if (!wait_bar(&st.sfree[c], pf, abort, limit_ns)) ok = false;
-        if (ok) {
-          ptx::mbar_arrive_expect_tx(&st.img[c], NP * A_PC);
-          ptx::bulk_g2s(smem + OFF_RING_BC + (uint32_t)c * STAGE_BC, rec + REC_Y + (size_t)c * NP * A_PC, NP * A_PC,
-                        &st.img[c]);
-        }
-      }
-      for (int c = 0; c < NCH && ok; ++c) {
-        if (!wait_bar(&st.img[c], pi ^ 1u, abort, limit_ns)) ok = false;
-        tc_fence_after();
-        if (ok) issue(c, dbot);
-      }
-    } else {
-      for (int c = 0; c < NCH && ok; ++c) {
-        if (!wait_bar(&st.img[c], pi, abort, limit_ns)) ok = false;
-        tc_fence_after();
-        if (ok) issue(c, dbot);
-      }
-    }
-    if (ok) mma_commit(&st.done);
-  }
-  if (top) {
-    ph.sfree ^= 1u;  // T^T then Y: every image barrier completed twice
-  } else {
-    ph.img ^= 1u;
-  }
-  if (!wait_bar(&st.done, ph.done & 1u, abort, limit_ns)) ok = false;
-  ph.done ^= 1u;
+// Order the epilogue's tensor-memory reads and shared-memory writes before
+// the next product's MMAs (all threads).
+__device__ __forceinline__ void between_products() {
+  tc_fence_before();
+  fence_async_smem();
+  __syncthreads();
   tc_fence_after();
-  return ok && !*abort;
 }
 
-// One update task on a column slab of cw <= 64 columns.
+// One update task on a column slab of cw <= 128 columns (a whole tile, or a
+// right-hand-side block).
 //  mode: 1 UNMQR (V unit lower in tile V), 0 TSMQR (V = [I; V2], V2 the full
 //        tile), 2 TTMQR (V2 the upper triangle of the tile)
 //  trans: 1 applies Q^T, 0 applies Q
 //  ct: top block (TS/TT; nullptr for UNMQR), cb: bottom block (or the
 //      UNMQR target); both column-major with leading dimension 128, at the
-//      slab's first column
-//  V: the reflector tile, Trec: the T record of the panel tile (the FP32 T
-//     and the split operand images written by the panel task)
+//      slab's first column, in global memory
+//  V: the reflector tile, Trec: the T record of the panel tile (the split
+//     operand images written by the panel task, and the FP32 T when kept)
+// Q^T (the direction of factorizations, least-squares plans and the server):
+//   W = V^T C_b (+ C_t); C_t -= T^T W (TS / TT); C_b -= Y W with Y = V T^T
+// from the panel's images. Q: W = V^T C_b (+ C_t); W' = T W; C_t -= W';
+// C_b -= V W'.
 // Returns false on a timeout.
 __device__ bool update(int mode, int trans, const float *V, const float *Trec, float *ct, float *cb, int cw,
                        unsigned char *smem, State &st, Phases &ph, volatile int *abort, long long limit_ns) {
   const int n = (cw + 15) & ~15;
   const uint32_t tmem = st.tmem;
   const unsigned char *rec = reinterpret_cast<const unsigned char *>(Trec);
-  float *top = reinterpret_cast<float *>(smem + OFF_TOP), *bot = reinterpret_cast<float *>(smem + OFF_BOT);
   const Src sva{V, NB, 0, NB, mode == 0 ? -1 : mode, 0};  // V^T (reflector, row): image REC_VA
-  const Src scb{bot, NB, 0, cw, -1, 1};                    // C_b^T (column, row) from the staged slab
-  const Src stt{Trec + REC_T32 / 4, NB, 1, NB, -1, 0};     // T (Q): gathered; T^T (Q^T): image REC_TB
-  const Src svc{V, NB, 1, NB, mode == 0 ? -1 : mode, 0};  // V (row, reflector): image REC_VC
-  fence_async_smem();  // earlier generic accesses of the stages and slabs before the bulk copies
+  const Src scb{cb, NB, 0, cw, -1, 0};                     // C_b^T (column, row), from global memory
+  const Src stt{Trec + REC_T32 / 4, NB, 1, NB, -1, 0};     // T (Q): gathered
+  const Src svc{V, NB, 1, NB, mode == 0 ? -1 : mode, 0};  // V (row, reflector): image REC_VC (Q)
+  fence_async_smem();  // earlier generic accesses of the stages before the bulk copies
   __syncthreads();
-  if (threadIdx.x < 32) {  // the slabs and product A's V^T image, all in flight at once
-    if (threadIdx.x == 0) ptx::mbar_arrive_expect_tx(&st.slab, (uint32_t)((ct ? 2 : 1) * cw * NB * 4));
-    __syncwarp();
-    if (ct && threadIdx.x == 1) fetch_slab(ct, cw, top, &st.slab);
-    if (threadIdx.x == 2) fetch_slab(cb, cw, bot, &st.slab);
-    if (threadIdx.x == 0) issue_image(rec + REC_VA, smem, OFF_RING_A, STAGE_A, st);
-  }
-  if (!wait_bar(&st.slab, ph.slab & 1u, abort, limit_ns)) return false;
-  ph.slab ^= 1u;
+  if (threadIdx.x == 0) issue_image(rec + REC_VA, smem, OFF_RING_A, STAGE_A, st);
   Fetch f;
 #pragma unroll
   for (int c = 0; c < DT; ++c) fetch_b(scb, c, f.b[c]);
   if (!product(sva, rec + REC_VA, &scb, trans ? nullptr : &stt, f, smem, st, ph, tmem, n, abort, limit_ns, true))
     return false;
   if (trans) {
-    // Q^T: C_t -= T^T W and C_b -= Y W with W = V^T C_b (+ C_t), the two products from the
-    // same W^T; the first image (T^T, or Y for UNMQR) is requested while W^T is written
+    // the next image (T^T, or Y for UNMQR) is requested while W^T is written; for TS / TT the
+    // Y image follows into the same stages once the MMAs that read T^T completed
     fence_async_smem();
     __syncthreads();  // product A's stages are free (its MMAs completed) before the copies
     if (threadIdx.x == 0) issue_image(rec + (ct ? REC_TB : REC_Y), smem, OFF_RING_BC, STAGE_BC, st);
-    epilogue_w(tmem, n, cw, ct ? top : nullptr, nullptr, smem);
+    epilogue_w(tmem, n, cw, ct, nullptr, smem);
+    between_products();
+    if (ct) {
+      if (!product(sva, rec + REC_TB, nullptr, nullptr, f, smem, st, ph, tmem, n, abort, limit_ns, true))
+        return false;
+      fence_async_smem();
+      __syncthreads();
+      if (threadIdx.x == 0) issue_image(rec + REC_Y, smem, OFF_RING_BC, STAGE_BC, st);
+      epilogue_c(tmem, n, cw, ct);
+      between_products();
+    }
+    if (!product(sva, rec + REC_Y, nullptr, nullptr, f, smem, st, ph, tmem, n, abort, limit_ns, true)) return false;
+    epilogue_c(tmem, n, cw, cb);
     tc_fence_before();
-    fence_async_smem();
     __syncthreads();
     tc_fence_after();
-    if (!product_pair(rec, ct != nullptr, smem, st, ph, tmem, n, abort, limit_ns)) return false;
-    if (ct) epilogue_c(tmem, n, cw, top);
-    epilogue_c(tmem + (uint32_t)(NACC * WMAX), n, cw, bot);
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (ct) store_slab(ct, cw, top);
-    store_slab(cb, cw, bot);
-    __syncthreads();
     return true;
   }
-  epilogue_w(tmem, n, cw, ct ? top : nullptr, nullptr, smem);
-  tc_fence_before();
-  fence_async_smem();
-  __syncthreads();
-  tc_fence_after();
-  if (!product(stt, trans ? rec + REC_TB : nullptr, nullptr, nullptr, f, smem, st, ph, tmem, n, abort, limit_ns))
-    return false;
-  epilogue_w(tmem, n, cw, nullptr, ct ? top : nullptr, smem);
-  tc_fence_before();
-  fence_async_smem();
-  __syncthreads();
-  tc_fence_after();
-  if (ct) store_slab(ct, cw, top);
+  epilogue_w(tmem, n, cw, ct, nullptr, smem);
+  between_products();
+  if (!product(stt, nullptr, nullptr, nullptr, f, smem, st, ph, tmem, n, abort, limit_ns)) return false;
+  epilogue_w(tmem, n, cw, nullptr, ct, smem);
+  between_products();
   if (!product(svc, rec + REC_VC, nullptr, nullptr, f, smem, st, ph, tmem, n, abort, limit_ns)) return false;
-  epilogue_c(tmem, n, cw, bot);
+  epilogue_c(tmem, n, cw, cb);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  store_slab(cb, cw, bot);
-  __syncthreads();
   return true;
 }
 
