@@ -163,10 +163,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr)
       : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ float4 ldcg4(const float *p) { return __ldcg(reinterpret_cast<const float4 *>(p)); }
 
@@ -301,11 +302,12 @@ __device__ __forceinline__ void store_piece(const Src &s, const Piece &x, int c,
     *reinterpret_cast<uint4 *>(buf + q * piece_bytes + off) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
 }
 
-// Registers of a product's streamed operands: DT chunks, A (2 pieces per
-// thread and chunk) and B (2 pieces, product A only).
+// Registers of a product's streamed operands: A, DT chunks ahead (2 pieces
+// per thread and chunk), and B (product A only: all NCH chunks, requested at
+// task start so that a single L2 round trip precedes the MMAs).
 struct Fetch {
   Piece a[DT][2];
-  Piece b[DT][2];
+  Piece b[NCH][2];
 };
 
 __device__ __forceinline__ void fetch_a(const Src &s, int c, Piece (&r)[2]) {
@@ -360,7 +362,7 @@ __device__ __forceinline__ void issue_image(const unsigned char *img, unsigned c
 
 __device__ bool product(const Src &sa, const unsigned char *img, const Src *sb, const Src *next, Fetch &f,
                         unsigned char *smem, State &st, Phases &ph, uint32_t tmem, int n, volatile int *abort,
-                        long long limit_ns, bool img_issued = false) {
+                        long long limit_ns, bool img_issued = false, bool wait = true) {
   const int tid = threadIdx.x;
   const bool streamB = sb != nullptr, useImg = img != nullptr;
   const bool threadsWrite = !useImg || streamB;  // chunk hand-off through the "full" barriers
@@ -391,12 +393,11 @@ __device__ bool product(const Src &sa, const unsigned char *img, const Src *sb, 
       for (int u = 0; u < 2; ++u) {
         int m, kg;
         piece_coords(*sb, WMAX, u, m, kg);
-        store_piece(*sb, f.b[slot][u], c, m, kg, stage + NP * A_PC, B_PC);
+        store_piece(*sb, f.b[c][u], c, m, kg, stage + NP * A_PC, B_PC);
       }
     }
     if (c + DT < NCH) {
       if (!useImg) fetch_a(sa, c + DT, f.a[slot]);
-      if (streamB) fetch_b(*sb, c + DT, f.b[slot]);
     } else if (next && !useImg) {
       fetch_a(*next, c + DT - NCH, f.a[slot]);
     }
@@ -428,7 +429,16 @@ __device__ bool product(const Src &sa, const unsigned char *img, const Src *sb, 
   if (threadsWrite) ph.full ^= 1u;
   if (useImg) ph.img ^= 1u;
   if (tid == 0) mma_commit(&st.done);
+  if (!wait) return ok && !*abort;
   if (!wait_bar(&st.done, ph.done & 1u, abort, limit_ns)) ok = false;
+  ph.done ^= 1u;
+  tc_fence_after();
+  return ok && !*abort;
+}
+
+// Completion of a product issued with wait = false (every thread).
+__device__ __forceinline__ bool product_wait(State &st, Phases &ph, volatile int *abort, long long limit_ns) {
+  const bool ok = wait_bar(&st.done, ph.done & 1u, abort, limit_ns);
   ph.done ^= 1u;
   tc_fence_after();
   return ok && !*abort;
@@ -439,13 +449,16 @@ __device__ bool product(const Src &sa, const unsigned char *img, const Src *sb, 
 // accumulator takes the MMAs of KS_ACC K steps only, which keeps the
 // accumulation error of the tensor cores over a short chain.
 __device__ __forceinline__ void tmem_sum16(uint32_t taddr, float (&v)[16]) {
-  tmem_ld16(taddr, v);
+  float w[NACC][16];
 #pragma unroll
-  for (int c = 1; c < NACC; ++c) {
-    float w[16];
-    tmem_ld16(taddr + (uint32_t)c * WMAX, w);
+  for (int c = 0; c < NACC; ++c) tmem_ld16(taddr + (uint32_t)c * WMAX, w[c]);
+  tmem_wait_ld();
 #pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] += w[q];
+  for (int q = 0; q < 16; ++q) {
+    float x = w[0][q];
+#pragma unroll
+    for (int c = 1; c < NACC; ++c) x += w[c][q];
+    v[q] = x;
   }
 }
 
@@ -453,7 +466,24 @@ __device__ __forceinline__ void tmem_sum16(uint32_t taddr, float (&v)[16]) {
 // 3) + laneid (the tensor-memory lanes its warp may read), columns 16 g ..
 // 16 g + 15 for the column groups g = (warp >> 2) + 2 e, e = 0 .. 3 (n <= 128).
 // The C tiles stay in global memory (column col at col * 128 floats): a warp's
-// accesses to one column are 128 consecutive bytes.
+// accesses to one column are 128 consecutive bytes. A thread's 64 elements of
+// a C tile in this layout ("C registers") are loaded ahead of the epilogue
+// that needs them, while the tensor cores run the product before it.
+typedef float CRegs[4][16];
+
+__device__ __forceinline__ void load_c(const float *c, int cw, CRegs &r) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m = 32 * (warp & 3) + lane;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int g = (warp >> 2) + 2 * e;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int col = 16 * g + q;
+      r[e][q] = (c && col < cw) ? __ldcg(c + (size_t)col * NB + m) : 0.f;
+    }
+  }
+}
 
 // Offset of element (n = column, k = reflector) in a piece of the resident
 // W^T buffer.
@@ -461,23 +491,17 @@ __device__ __forceinline__ uint32_t woff(int n, int k) {
   return (uint32_t)(n & 7) * 16 + (uint32_t)(n >> 3) * SBO_W + (uint32_t)(k & 7) * 2 + (uint32_t)(k >> 3) * LBO_W;
 }
 
-// Epilogue of products A and B: W = D (+ add), optionally sub -= W (C tiles in
-// global memory), and W^T (three BF16 pieces) to the resident buffer for the
-// next product.
-__device__ void epilogue_w(uint32_t tmem, int n, int cw, const float *add, float *sub, unsigned char *smem) {
+// Epilogue of products A and B: W = D (+ cr when add), optionally sub -= W
+// with cr holding sub's elements (C tiles in global memory), and W^T (three
+// BF16 pieces) to the resident buffer for the next product.
+__device__ void epilogue_w(uint32_t tmem, int n, int cw, const CRegs &cr, bool add, float *sub, unsigned char *smem) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m = 32 * (warp & 3) + lane;
   const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-#pragma unroll 1
+#pragma unroll
   for (int e = 0; e < 4; ++e) {
     const int g = (warp >> 2) + 2 * e;
     if (g >= n / 16) continue;
-    float c0[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int col = 16 * g + q;
-      c0[q] = (col < cw && (add || sub)) ? __ldcg((add ? add : sub) + (size_t)col * NB + m) : 0.f;
-    }
     float v[16];
     tmem_sum16(tl + 16 * g, v);
 #pragma unroll
@@ -485,8 +509,8 @@ __device__ void epilogue_w(uint32_t tmem, int n, int cw, const float *add, float
       const int col = 16 * g + q;
       float x = 0.f;
       if (col < cw) {
-        x = add ? v[q] + c0[q] : v[q];
-        if (sub) __stcg(sub + (size_t)col * NB + m, c0[q] - x);
+        x = add ? v[q] + cr[e][q] : v[q];
+        if (sub) __stcg(sub + (size_t)col * NB + m, cr[e][q] - x);
       }
       uint32_t p0, p1, p2;
       split3(x, p0, p1, p2);
@@ -498,27 +522,22 @@ __device__ void epilogue_w(uint32_t tmem, int n, int cw, const float *add, float
   }
 }
 
-// Epilogue of a product that updates a C tile: c -= D (global memory).
-__device__ void epilogue_c(uint32_t tmem, int n, int cw, float *c) {
+// Epilogue of a product that updates a C tile: c -= D (global memory), with
+// cr holding c's elements.
+__device__ void epilogue_c(uint32_t tmem, int n, int cw, float *c, const CRegs &cr) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m = 32 * (warp & 3) + lane;
   const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-#pragma unroll 1
+#pragma unroll
   for (int e = 0; e < 4; ++e) {
     const int g = (warp >> 2) + 2 * e;
     if (g >= n / 16) continue;
-    float c0[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int col = 16 * g + q;
-      c0[q] = col < cw ? __ldcg(c + (size_t)col * NB + m) : 0.f;
-    }
     float v[16];
     tmem_sum16(tl + 16 * g, v);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int col = 16 * g + q;
-      if (col < cw) __stcg(c + (size_t)col * NB + m, c0[q] - v[q]);
+      if (col < cw) __stcg(c + (size_t)col * NB + m, cr[e][q] - v[q]);
     }
   }
 }
@@ -561,16 +580,20 @@ __device__ bool update(int mode, int trans, const float *V, const float *Trec, f
   if (threadIdx.x == 0) issue_image(rec + REC_VA, smem, OFF_RING_A, STAGE_A, st);
   Fetch f;
 #pragma unroll
-  for (int c = 0; c < DT; ++c) fetch_b(scb, c, f.b[c]);
-  if (!product(sva, rec + REC_VA, &scb, trans ? nullptr : &stt, f, smem, st, ph, tmem, n, abort, limit_ns, true))
+  for (int c = 0; c < NCH; ++c) fetch_b(scb, c, f.b[c]);
+  if (!product(sva, rec + REC_VA, &scb, trans ? nullptr : &stt, f, smem, st, ph, tmem, n, abort, limit_ns, true,
+               false))
     return false;
+  CRegs cr;
+  load_c(ct, cw, cr);  // C_t (zeros for UNMQR) while product A's MMAs run
+  if (!product_wait(st, ph, abort, limit_ns)) return false;
   if (trans) {
     // the next image (T^T, or Y for UNMQR) is requested while W^T is written; for TS / TT the
     // Y image follows into the same stages once the MMAs that read T^T completed
     fence_async_smem();
     __syncthreads();  // product A's stages are free (its MMAs completed) before the copies
     if (threadIdx.x == 0) issue_image(rec + (ct ? REC_TB : REC_Y), smem, OFF_RING_BC, STAGE_BC, st);
-    epilogue_w(tmem, n, cw, ct, nullptr, smem);
+    epilogue_w(tmem, n, cw, cr, ct != nullptr, nullptr, smem);
     between_products();
     if (ct) {
       if (!product(sva, rec + REC_TB, nullptr, nullptr, f, smem, st, ph, tmem, n, abort, limit_ns, true))
@@ -578,23 +601,29 @@ __device__ bool update(int mode, int trans, const float *V, const float *Trec, f
       fence_async_smem();
       __syncthreads();
       if (threadIdx.x == 0) issue_image(rec + REC_Y, smem, OFF_RING_BC, STAGE_BC, st);
-      epilogue_c(tmem, n, cw, ct);
+      epilogue_c(tmem, n, cw, ct, cr);  // C_t stayed in registers since epilogue A
       between_products();
     }
-    if (!product(sva, rec + REC_Y, nullptr, nullptr, f, smem, st, ph, tmem, n, abort, limit_ns, true)) return false;
-    epilogue_c(tmem, n, cw, cb);
+    if (!product(sva, rec + REC_Y, nullptr, nullptr, f, smem, st, ph, tmem, n, abort, limit_ns, true, false))
+      return false;
+    load_c(cb, cw, cr);  // C_b while the last product's MMAs run
+    if (!product_wait(st, ph, abort, limit_ns)) return false;
+    epilogue_c(tmem, n, cw, cb, cr);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     return true;
   }
-  epilogue_w(tmem, n, cw, ct, nullptr, smem);
+  epilogue_w(tmem, n, cw, cr, ct != nullptr, nullptr, smem);
   between_products();
   if (!product(stt, nullptr, nullptr, nullptr, f, smem, st, ph, tmem, n, abort, limit_ns)) return false;
-  epilogue_w(tmem, n, cw, nullptr, ct, smem);
+  epilogue_w(tmem, n, cw, cr, false, ct, smem);  // cr still holds C_t
   between_products();
-  if (!product(svc, rec + REC_VC, nullptr, nullptr, f, smem, st, ph, tmem, n, abort, limit_ns)) return false;
-  epilogue_c(tmem, n, cw, cb);
+  if (!product(svc, rec + REC_VC, nullptr, nullptr, f, smem, st, ph, tmem, n, abort, limit_ns, false, false))
+    return false;
+  load_c(cb, cw, cr);
+  if (!product_wait(st, ph, abort, limit_ns)) return false;
+  epilogue_c(tmem, n, cw, cb, cr);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
