@@ -1402,13 +1402,20 @@ __global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_sched(EngineParams p) {
   tc::tc_fence_after();
   uint32_t phase = 0;
   tc::Phases tph;
+  // Warp 1 claims the CTA's next task while warp 0 releases the successors
+  // of the last one. It also counts completed tasks (`pending`, flushed to
+  // the global done counter whenever the queues look empty or 64 have
+  // accumulated): a task counts as done once its results are written, before
+  // its successors are released, which cannot end the run early since the
+  // counter reaches the task count only when no task has unfinished
+  // successors.
   unsigned pending = 0;
+  if (threadIdx.x >= 32 && threadIdx.x < 64) {
+    const int v = pop_ready(p, pending);
+    if (threadIdx.x == 32) sh.task = v;
+  }
+  __syncthreads();
   while (true) {
-    if (threadIdx.x < 32) {
-      const int v = pop_ready(p, pending);
-      if (threadIdx.x == 0) sh.task = v;
-    }
-    __syncthreads();
     const int tid = sh.task;
     if (tid < 0) break;
     const Task t = p.tasks[tid];
@@ -1438,12 +1445,16 @@ __global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_sched(EngineParams p) {
       }
       __syncwarp();
       if (threadIdx.x == 0) sh.norelease = 0;
-      if (threadIdx.x == 0 && ++pending >= 64) {
+    } else if (threadIdx.x < 64) {  // warp 1 claims the next task meanwhile
+      if (threadIdx.x == 32 && ++pending >= 64) {
         __threadfence();
         atomicAdd(&p.ctl->done.v, pending);
         pending = 0;
       }
+      const int v = sh.abort ? -1 : pop_ready(p, pending);
+      if (threadIdx.x == 32) sh.task = v;
     }
+    __syncthreads();
     if (sh.abort) break;
   }
   // a bulk copy that outlived its wait must land before the CTA exits
