@@ -647,9 +647,10 @@ namespace tc {
 // partial sums meet in shared memory (double-buffered by step parity) and
 // every thread finishes them in the same fixed order. The same products give
 // the trailing-update coefficients (columns > j) and the Gram entries
-// G(l, j) = v_l^T v_j (columns < j). T then follows from G by recursive
-// doubling: T([A B], [A B]) has T_AB = -T_A G_AB T_B (the compact-WY merge of
-// two reflector blocks).
+// G(l, j) = v_l^T v_j (columns < j). T then follows from G: column by column
+// within each 32 x 32 diagonal block (one warp per block, no CTA barrier),
+// then by recursive doubling over the blocks: T([A B], [A B]) has T_AB =
+// -T_A G_AB T_B (the compact-WY merge of two reflector blocks).
 //
 // Modes: 1 GE (the tile itself), 0 TS (R = upper triangle of the killer
 // tile, X = the killed tile), 2 TT (X = upper triangle of the killed tile).
@@ -711,14 +712,15 @@ __device__ void write_image(unsigned char *dst, F value) {
 // Y(m, k) = sum over l >= k of V(m, l) T(k, l), V the masked reflectors of
 // the factored tile `sv` (column l at l * LDT), T the upper triangle of `tg`
 // (T(k, l) at k + l * LDT). Thread block: rows lane + 32 a (a < 4: the lanes
-// of a warp read consecutive words) x 8 reflectors (four pieces of the
-// image), in FP32 with the terms in ascending l.
+// of a warp read consecutive words) x 8 reflectors; warp w takes the
+// reflector groups w and 15 - w (the same number of terms for every warp).
+// FP32, with the terms in ascending l.
 __device__ void write_y_image(int mode, const float *sv, const float *tg, unsigned char *dst) {
   constexpr int RB = 4;
 #pragma unroll 1
   for (int u = 0; u < (NB / RB) * (NB / 8) / NTHR; ++u) {
-    const int p = threadIdx.x + NTHR * u;
-    const int m0 = p & 31, kg = p >> 5;  // rows m0 + 32 a; warps: k groups
+    const int m0 = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int kg = u == 0 ? w : 15 - w;  // rows m0 + 32 a; warps: k groups w and 15 - w
     const int k0 = 8 * kg;
     float acc[RB][8];
 #pragma unroll
@@ -757,6 +759,95 @@ __device__ void write_y_image(int mode, const float *sv, const float *tg, unsign
         __stcg(reinterpret_cast<uint4 *>(dst + off + (uint32_t)q * A_PC),
                make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]));
     }
+  }
+}
+
+// T of the 32 x 32 diagonal block d of the panel (warp d, d < 4), column by
+// column: T(i, j) = -tau_j sum over i <= l < j of T(i, l) G(l, j), T(j, j) =
+// tau_j, with G(l, j) = v_l^T v_j at (j, l) of `tg` and tau on its diagonal.
+// Lane i keeps row i of the block in registers; the result replaces the
+// block's upper triangle. These are the first five levels of the doubling
+// (blocks of 1 .. 16 merged) without a CTA barrier.
+__device__ __noinline__ void t_diag_block(float *tg) {
+  const int d = threadIdx.x >> 5, i = threadIdx.x & 31, o = 32 * d;
+  float tr[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const float tau = tg[(o + j) * (LDT + 1)];
+    float acc = 0.f;
+#pragma unroll
+    for (int l = 0; l < j; ++l)
+      if (l >= i) acc = fmaf(tr[l], tg[(o + j) + (o + l) * LDT], acc);
+    tr[j] = i < j ? -tau * acc : (i == j ? tau : 0.f);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < 32; ++j)
+    if (j >= i) tg[(o + i) + (o + j) * LDT] = tr[j];
+}
+
+// The remaining levels of the doubling (blocks of 32 and 64 merged): T_AB =
+// -T_A (G_AB T_B), 4 x 4 output blocks per thread, T upper and G lower in
+// `tg` as for t_diag_block. All threads; ends with a CTA barrier.
+__device__ __noinline__ void t_merge_blocks(float *tg) {
+  const int tid = threadIdx.x;
+  for (int s = 32; s < NB; s *= 2) {
+    const int nbk = s / 4, per = nbk * nbk, nblocks = (NB / (2 * s)) * per;
+    const bool act = tid < nblocks;
+    int a = 0, l0 = 0, j0 = 0;
+    if (act) {
+      const int pr = tid / per, rem = tid - pr * per;
+      a = pr * 2 * s;
+      l0 = a + (rem % nbk) * 4;
+      j0 = a + s + (rem / nbk) * 4;
+    }
+    float acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+    if (act)  // X = G_AB T_B (T_B upper triangular: m <= j)
+      for (int m = a + s; m <= j0 + 3; ++m) {
+        float gv[4], tv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) gv[u] = tg[m + (l0 + u) * LDT];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) tv[v] = m <= j0 + v ? tg[m + (j0 + v) * LDT] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(gv[u], tv[v], acc[u][v]);
+      }
+    __syncthreads();
+    if (act)
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) tg[(l0 + u) + (j0 + v) * LDT] = acc[u][v];
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+    if (act)  // T_AB = -T_A X (T_A upper triangular: m >= l)
+      for (int m = l0; m < a + s; ++m) {
+        float ta[4], xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ta[u] = m >= l0 + u ? tg[(l0 + u) + m * LDT] : 0.f;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) xv[v] = tg[m + (j0 + v) * LDT];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(ta[u], xv[v], acc[u][v]);
+      }
+    __syncthreads();
+    if (act)
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) tg[(l0 + u) + (j0 + v) * LDT] = -acc[u][v];
+    __syncthreads();
   }
 }
 
@@ -957,119 +1048,9 @@ __device__ void panel(int mode, float *X, float *Rg, float *Tg, bool with_t32, u
   // ---- T from G by recursive doubling
   for (int e = tid; e < NB; e += NTHR) sm.tg[e * LDT + e] = sm.tau[e];
   __syncthreads();
-  for (int s = 1; s < NB; s *= 2) {
-    if (s >= 16) {  // 4 x 4 output blocks per thread: 16 FMAs per 8 shared loads
-      const int nbk = s / 4, per = nbk * nbk, nblocks = (NB / (2 * s)) * per;
-      const bool act = tid < nblocks;
-      int a = 0, l0 = 0, j0 = 0;
-      if (act) {
-        const int pr = tid / per, rem = tid - pr * per;
-        a = pr * 2 * s;
-        l0 = a + (rem % nbk) * 4;
-        j0 = a + s + (rem / nbk) * 4;
-      }
-      float acc[4][4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
-      if (act)  // X = G_AB T_B (T_B upper triangular: m <= j)
-        for (int m = a + s; m <= j0 + 3; ++m) {
-          float gv[4], tv[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) gv[u] = sm.tg[m + (l0 + u) * LDT];
-#pragma unroll
-          for (int v = 0; v < 4; ++v) tv[v] = m <= j0 + v ? sm.tg[m + (j0 + v) * LDT] : 0.f;
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(gv[u], tv[v], acc[u][v]);
-        }
-      __syncthreads();
-      if (act)
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) sm.tg[(l0 + u) + (j0 + v) * LDT] = acc[u][v];
-      __syncthreads();
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
-      if (act)  // T_AB = -T_A X (T_A upper triangular: m >= l)
-        for (int m = l0; m < a + s; ++m) {
-          float ta[4], xv[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) ta[u] = m >= l0 + u ? sm.tg[(l0 + u) + m * LDT] : 0.f;
-#pragma unroll
-          for (int v = 0; v < 4; ++v) xv[v] = sm.tg[m + (j0 + v) * LDT];
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(ta[u], xv[v], acc[u][v]);
-        }
-      __syncthreads();
-      if (act)
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) sm.tg[(l0 + u) + (j0 + v) * LDT] = -acc[u][v];
-      __syncthreads();
-      continue;
-    }
-    const int per = s * s, total = (NB / (2 * s)) * per;  // outputs: (pairs) x s x s
-    float acc[2];  // s < 16: at most 2 outputs per thread
-    // X = G_AB T_B (rows l in A, columns j in B)
-    int nout = 0;
-    for (int o = tid; o < total; o += NTHR, ++nout) {
-      const int pr = o / per, rem = o - pr * per;
-      const int a = pr * 2 * s, l = a + rem % s, jj = a + s + rem / s;
-      float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
-      const float *gl = sm.tg + l * LDT, *tj = sm.tg + jj * LDT;
-      int m = a + s;
-      for (; m + 3 <= jj; m += 4) {
-        v0 = fmaf(gl[m], tj[m], v0);
-        v1 = fmaf(gl[m + 1], tj[m + 1], v1);
-        v2 = fmaf(gl[m + 2], tj[m + 2], v2);
-        v3 = fmaf(gl[m + 3], tj[m + 3], v3);
-      }
-      for (; m <= jj; ++m) v0 = fmaf(gl[m], tj[m], v0);
-      acc[nout] = (v0 + v1) + (v2 + v3);
-    }
-    __syncthreads();
-    nout = 0;
-    for (int o = tid; o < total; o += NTHR, ++nout) {
-      const int pr = o / per, rem = o - pr * per;
-      const int a = pr * 2 * s, l = a + rem % s, jj = a + s + rem / s;
-      sm.tg[l + jj * LDT] = acc[nout];
-    }
-    __syncthreads();
-    // T_AB = -T_A X
-    nout = 0;
-    for (int o = tid; o < total; o += NTHR, ++nout) {
-      const int pr = o / per, rem = o - pr * per;
-      const int a = pr * 2 * s, l = a + rem % s, jj = a + s + rem / s;
-      float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
-      const float *tj = sm.tg + jj * LDT;
-      int m = l;
-      for (; m + 3 < a + s; m += 4) {
-        v0 = fmaf(sm.tg[l + m * LDT], tj[m], v0);
-        v1 = fmaf(sm.tg[l + (m + 1) * LDT], tj[m + 1], v1);
-        v2 = fmaf(sm.tg[l + (m + 2) * LDT], tj[m + 2], v2);
-        v3 = fmaf(sm.tg[l + (m + 3) * LDT], tj[m + 3], v3);
-      }
-      for (; m < a + s; ++m) v0 = fmaf(sm.tg[l + m * LDT], tj[m], v0);
-      acc[nout] = -((v0 + v1) + (v2 + v3));
-    }
-    __syncthreads();
-    nout = 0;
-    for (int o = tid; o < total; o += NTHR, ++nout) {
-      const int pr = o / per, rem = o - pr * per;
-      const int a = pr * 2 * s, l = a + rem % s, jj = a + s + rem / s;
-      sm.tg[l + jj * LDT] = acc[nout];
-    }
-    __syncthreads();
-  }
+  if (warp < NB / 32) t_diag_block(sm.tg);
+  __syncthreads();
+  t_merge_blocks(sm.tg);
   // ---- the factored tile (V / R) to shared memory
 #pragma unroll
   for (int i = 0; i < 16; ++i)
