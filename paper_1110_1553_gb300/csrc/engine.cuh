@@ -421,6 +421,9 @@ __device__ void gemm_tn(Real *W, int ldw, const Real *V, int ldv, const Real *Cm
 }
 
 // C(k,j) -= sum_{i<Mi} V(k,i) W(i,j), k < K, j < Nj. Threads run along k.
+// The FP64 version accumulates into C itself (C = fma(-V, W, C), terms in
+// ascending i): a separate subtraction per output would cost the FP64 pipe
+// as much as a DFMA, one extra operation per Mi (as few as 8) DFMAs.
 template <typename Real>
 __device__ void gemm_nn_sub(Real *Cm, int ldc, const Real *V, int ldv, const Real *W, int ldw, int K, int Mi,
                             int Nj) {
@@ -435,17 +438,17 @@ __device__ void gemm_nn_sub(Real *Cm, int ldc, const Real *V, int ldv, const Rea
     const int j0 = jc * 8, jn = min(8, Nj - j0);
     Real acc[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = 0;
+    for (int q = 0; q < 8; ++q) acc[q] = q < jn ? Cm[k + (size_t)(j0 + q) * ldc] : Real(0);
     for (int i = 0; i < Mi; ++i) {
       const Real v = V[k + (size_t)i * ldv];
       const Real *w = W + i + (size_t)j0 * ldw;
 #pragma unroll
       for (int q = 0; q < 8; ++q)
-        if (q < jn) acc[q] = fma(v, w[(size_t)q * ldw], acc[q]);
+        if (q < jn) acc[q] = fma(-v, w[(size_t)q * ldw], acc[q]);
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q)
-      if (q < jn) Cm[k + (size_t)(j0 + q) * ldc] -= acc[q];
+      if (q < jn) Cm[k + (size_t)(j0 + q) * ldc] = acc[q];
   }
   __syncthreads();
 }
