@@ -624,21 +624,32 @@ __device__ void shape_v(Real *V, int ld, int L, int ncols, int mode, int coff, i
 
 // ------------------------------------------------------------- task bodies --
 
+template <typename Real>
+__host__ __device__ inline size_t engine_smem_bytes(int nb, int ib, int w, int wt, int vc);
+
 // Updates UNMQR / TSMQR / TTMQR of one column slab (also used for Q and Q^T
-// applied to right-hand-side blocks).
+// applied to right-hand-side blocks). V is staged in chunks of columns; the
+// chunk buffer comes last in shared memory and may use what the panel tasks
+// need beyond the updates: in FP64, a block of L reflector rows (GE and TT
+// blocks get shorter towards one end of the tile) takes chunks as wide as
+// fit (8, 16 or 32 columns, column stride L + pad), so a short block needs
+// fewer staging rounds, and none for its second product when one chunk
+// holds all of it.
 template <typename Real>
 __device__ void task_update(const EngineParams &p, const Geo<Real> &g, const Task &t, Shared<Real> &sh,
                             Real *dyn, uint32_t &phase) {
   const int nb = g.nb, ib = g.ib, lds = g.lds, cw = t.cw;
   const int wmax = t.tgt == 0 ? g.w : g.wb;
   const int VC = g.vc;
-  const int nchunk = ib / VC;
   Real *C1 = dyn;
   Real *C2 = C1 + (size_t)lds * wmax;
-  Real *Vc = C2 + (size_t)lds * wmax;
-  Real *Tq = Vc + (size_t)lds * VC;
+  Real *Tq = C2 + (size_t)lds * wmax;
   Real *W = Tq + (size_t)ib * ib;
   Real *scr = W + (size_t)ib * wmax;
+  const size_t su = (sizeof(Real) == 4 ? 4 : 1) * (size_t)(((VC + 3) / 4) * ((wmax + 3) / 4) * 16);
+  Real *Vc = scr + (su > (size_t)NT ? su : (size_t)NT);
+  const size_t vcap = engine_smem_bytes<Real>(nb, ib, g.w > g.wb ? g.w : g.wb, g.wt, VC) / sizeof(Real) -
+                      (size_t)(Vc - dyn);
   const int op = t.op;
   const bool pair = op != OP_UNMQR;
   const int mode = op == OP_UNMQR ? PANEL_GE : (op == OP_TSMQR ? PANEL_TS : PANEL_TT);
@@ -659,24 +670,30 @@ __device__ void task_update(const EngineParams &p, const Geo<Real> &g, const Tas
     const int L = (mode == PANEL_GE) ? nb - q0 : (mode == PANEL_TS ? nb : q0 + ib);
     Real *Cb = (mode == PANEL_GE) ? C1 + q0 : C2;
     Real *Ct = C1 + q0;
+    int vq = VC, ldv = lds;
+    if constexpr (sizeof(Real) == 8) {
+      ldv = L + smem_pad<Real>();
+      while (2 * vq <= ib && ib % (2 * vq) == 0 && (size_t)ldv * 2 * vq <= vcap) vq *= 2;
+    }
+    const int nchunk = ib / vq;
     for (int c = 0; c < nchunk; ++c) {
       __syncthreads();
-      Copy<Real> cp[2] = {{Vc, lds, Vt + (size_t)(q0 + c * VC) * nb + vr0, nb, L, VC},
+      Copy<Real> cp[2] = {{Vc, ldv, Vt + (size_t)(q0 + c * vq) * nb + vr0, nb, L, vq},
                           {Tq, ib, Tt + (size_t)q * ib * ib, ib, c == 0 ? ib : 0, ib}};
       stage(p, sh, cp, 2, phase);
-      shape_v(Vc, lds, L, VC, mode, c * VC, q0);
-      gemm_tn(W + c * VC, ib, Vc, lds, Cb, lds, L, VC, cw, pair ? Ct + c * VC : nullptr, lds, scr);
+      shape_v(Vc, ldv, L, vq, mode, c * vq, q0);
+      gemm_tn(W + c * vq, ib, Vc, ldv, Cb, lds, L, vq, cw, pair ? Ct + c * vq : nullptr, lds, scr);
     }
     trmm_tw(W, ib, Tq, ib, cw, t.trans);
     if (pair) sub_top(Ct, lds, W, ib, ib, cw);
     for (int c = 0; c < nchunk; ++c) {
       if (nchunk > 1) {
         __syncthreads();
-        Copy<Real> cp[1] = {{Vc, lds, Vt + (size_t)(q0 + c * VC) * nb + vr0, nb, L, VC}};
+        Copy<Real> cp[1] = {{Vc, ldv, Vt + (size_t)(q0 + c * vq) * nb + vr0, nb, L, vq}};
         stage(p, sh, cp, 1, phase);
-        shape_v(Vc, lds, L, VC, mode, c * VC, q0);
+        shape_v(Vc, ldv, L, vq, mode, c * vq, q0);
       }
-      gemm_nn_sub(Cb, lds, Vc, lds, W + c * VC, ib, L, VC, cw);
+      gemm_nn_sub(Cb, lds, Vc, ldv, W + c * vq, ib, L, vq, cw);
     }
   }
   store_cols(g1, nb, C1, lds, nb, cw, 0, 0);
@@ -1714,13 +1731,15 @@ inline size_t engine_smem_bytes_tc() {
 
 // Shared memory (bytes) of the scheduler kernel for a problem configuration.
 template <typename Real>
-inline size_t engine_smem_bytes(int nb, int ib, int w, int wt, int vc) {
+__host__ __device__ inline size_t engine_smem_bytes(int nb, int ib, int w, int wt, int vc) {
   const int lds = nb + smem_pad<Real>(), ldt = ib + smem_pad<Real>();
   // scratch: FP32 GEMMs keep up to 4 K-groups of partial output blocks
   const size_t fac = sizeof(Real) == 4 ? 4 : 1;
-  const size_t scr_u = std::max<size_t>({(size_t)NT, fac * (((vc + 3) / 4) * ((w + 3) / 4) * 16)});
-  const size_t scr_p = std::max<size_t>({(size_t)NT, fac * (((ib + 3) / 4) * ((wt + 3) / 4) * 16),
-                                         fac * (((ib + 3) / 4) * ((ib + 3) / 4) * 16)});
+  const size_t su = fac * (((vc + 3) / 4) * ((w + 3) / 4) * 16);
+  const size_t scr_u = su > (size_t)NT ? su : (size_t)NT;
+  const size_t sp1 = fac * (((ib + 3) / 4) * ((wt + 3) / 4) * 16), sp2 = fac * (((ib + 3) / 4) * ((ib + 3) / 4) * 16);
+  const size_t sp = sp1 > sp2 ? sp1 : sp2;
+  const size_t scr_p = sp > (size_t)NT ? sp : (size_t)NT;
   const size_t upd = (size_t)lds * (2 * w + vc) + (size_t)ib * ib + (size_t)ib * w + scr_u;
   const size_t cbg = (size_t)(lds * wt > ib * ib ? lds * wt : ib * ib);
   const size_t pan = (size_t)lds * ib + (size_t)ldt * (ib + wt) + (size_t)ib * ib + cbg +
