@@ -453,28 +453,68 @@ __device__ void gemm_nn_sub(Real *Cm, int ldc, const Real *V, int ldv, const Rea
   __syncthreads();
 }
 
-// W <- T^T W (trans) or T W in place, T an ib x ib upper triangle (ld ib), ib <= 32: each warp takes
-// 32 / ib columns of W at a time, lane group g holding column j0 + g (lane i of the group: W(i, j))
-// and forming its outputs from the group's values by shuffles. Lane i walks the terms from its own
-// offset, so the lanes of a group read T from different shared-memory banks.
+// W <- T^T W (trans) or T W in place, T an ib x ib upper triangle (leading
+// dimension ldq), ib even and <= 32. FP64: a group of ib / 2 lanes takes one
+// column of W: lane h holds rows h and ib - 1 - h and forms both outputs from
+// the group's values by shuffles, (h + 1) + (ib - h) = ib + 1 terms, one
+// useful FMA per step (a lane per row would idle through half of its steps,
+// and an idle FP64 step costs the FP64 pipe as much as a used one); terms of
+// each output in ascending order.
 template <typename Real>
-__device__ void trmm_tw(Real *W, int ldw, const Real *Tq, int ib, int Nj, int trans) {
+__device__ void trmm_tw(Real *W, int ldw, const Real *Tq, int ldq, int ib, int Nj, int trans) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int G = 32 / ib, grp = lane / ib, i = lane - grp * ib;
+  if constexpr (sizeof(Real) == 4) {
+    // FP32 (idle FMA steps are cheap there): one row per lane, lane i walking
+    // the terms from its own offset so that a group's lanes read T from
+    // different banks
+    const int G = 32 / ib, grp = lane / ib, i = lane - grp * ib;
+    for (int j0 = warp * G; j0 < Nj; j0 += NWARP * G) {
+      const int j = j0 + grp;
+      const bool on = grp < G && j < Nj;
+      Real *w = W + (size_t)j * ldw;
+      const Real wl = on ? w[i] : Real(0);
+      Real s = 0;
+      for (int u = 0; u < ib; ++u) {
+        int l = i + u;
+        if (l >= ib) l -= ib;
+        const Real wv = __shfl_sync(0xffffffffu, wl, (grp * ib + l) & 31);
+        if (on && (trans ? l <= i : l >= i)) s = fma(trans ? Tq[l + (size_t)i * ldq] : Tq[i + (size_t)l * ldq], wv, s);
+      }
+      __syncwarp();
+      if (on) w[i] = s;
+    }
+    __syncthreads();
+    return;
+  }
+  const int hb = ib / 2, G = 32 / hb, grp = lane / hb, h = lane - grp * hb;
+  const int ra = h, rb = ib - 1 - h;
   for (int j0 = warp * G; j0 < Nj; j0 += NWARP * G) {
     const int j = j0 + grp;
     const bool on = grp < G && j < Nj;
     Real *w = W + (size_t)j * ldw;
-    const Real wl = on ? w[i] : Real(0);
-    Real s = 0;
-    for (int u = 0; u < ib; ++u) {
-      int l = i + u;
-      if (l >= ib) l -= ib;
-      const Real wv = __shfl_sync(0xffffffffu, wl, (grp * ib + l) & 31);
-      if (on && (trans ? l <= i : l >= i)) s = fma(trans ? Tq[l + (size_t)i * ib] : Tq[i + (size_t)l * ib], wv, s);
+    const Real wa = on ? w[ra] : Real(0), wb = on ? w[rb] : Real(0);
+    Real sa = 0, sb = 0;
+    for (int u = 0; u <= ib; ++u) {
+      // output row r of this step and its source row l (trans: l <= r; else l >= r)
+      const bool first = trans ? u <= h : u < ib - h;
+      const int l = trans ? (first ? u : u - h - 1) : (first ? h + u : u - 1);
+      const int r = first ? ra : rb;
+      const int src = grp * hb + (l < hb ? l : ib - 1 - l);
+      const Real xa = __shfl_sync(0xffffffffu, wa, src & 31);
+      const Real xb = __shfl_sync(0xffffffffu, wb, src & 31);
+      const Real c = trans ? Tq[l + (size_t)r * ldq] : Tq[r + (size_t)l * ldq];
+      Real acc = first ? sa : sb;
+      acc = fma(c, l < hb ? xa : xb, acc);
+      if (first)
+        sa = acc;
+      else
+        sb = acc;
     }
     __syncwarp();
-    if (on) w[i] = s;
+    if (on) {
+      w[ra] = sa;
+      w[rb] = sb;
+    }
   }
   __syncthreads();
 }
@@ -585,17 +625,17 @@ __device__ void factor_block(int mode, Real *P, int ld, int L, int ib, Real *Rt,
 
 // T of a block from the Gram matrix G = V^T V (only G(l, j), l < j, used).
 template <typename Real>
-__device__ void build_t(Real *Tq, const Real *G, int ib, const Shared<Real> &sh) {
-  for (int e = threadIdx.x; e < ib * ib; e += NT) Tq[e] = 0;
+__device__ void build_t(Real *Tq, int ldq, const Real *G, int ib, const Shared<Real> &sh) {
+  for (int e = threadIdx.x; e < ib * ldq; e += NT) Tq[e] = 0;
   __syncthreads();
   for (int jj = 0; jj < ib; ++jj) {
     const int tid = threadIdx.x;
     if (tid < jj) {
       Real y = 0;
-      for (int l = tid; l < jj; ++l) y = fma(Tq[tid + (size_t)l * ib], G[l + (size_t)jj * ib], y);
-      Tq[tid + (size_t)jj * ib] = -sh.tau[jj] * y;
+      for (int l = tid; l < jj; ++l) y = fma(Tq[tid + (size_t)l * ldq], G[l + (size_t)jj * ib], y);
+      Tq[tid + (size_t)jj * ldq] = -sh.tau[jj] * y;
     } else if (tid == jj) {
-      Tq[jj + (size_t)jj * ib] = sh.tau[jj];
+      Tq[jj + (size_t)jj * ldq] = sh.tau[jj];
     }
     __syncthreads();
   }
@@ -643,8 +683,9 @@ __device__ void task_update(const EngineParams &p, const Geo<Real> &g, const Tas
   const int VC = g.vc;
   Real *C1 = dyn;
   Real *C2 = C1 + (size_t)lds * wmax;
+  const int ldq = sizeof(Real) == 8 ? g.ldt : ib;  // T of the block (FP64: padded for the paired trmm)
   Real *Tq = C2 + (size_t)lds * wmax;
-  Real *W = Tq + (size_t)ib * ib;
+  Real *W = Tq + (size_t)ib * ldq;
   Real *scr = W + (size_t)ib * wmax;
   const size_t su = (sizeof(Real) == 4 ? 4 : 1) * (size_t)(((VC + 3) / 4) * ((wmax + 3) / 4) * 16);
   Real *Vc = scr + (su > (size_t)NT ? su : (size_t)NT);
@@ -679,12 +720,12 @@ __device__ void task_update(const EngineParams &p, const Geo<Real> &g, const Tas
     for (int c = 0; c < nchunk; ++c) {
       __syncthreads();
       Copy<Real> cp[2] = {{Vc, ldv, Vt + (size_t)(q0 + c * vq) * nb + vr0, nb, L, vq},
-                          {Tq, ib, Tt + (size_t)q * ib * ib, ib, c == 0 ? ib : 0, ib}};
+                          {Tq, ldq, Tt + (size_t)q * ib * ib, ib, c == 0 ? ib : 0, ib}};
       stage(p, sh, cp, 2, phase);
       shape_v(Vc, ldv, L, vq, mode, c * vq, q0);
       gemm_tn(W + c * vq, ib, Vc, ldv, Cb, lds, L, vq, cw, pair ? Ct + c * vq : nullptr, lds, scr);
     }
-    trmm_tw(W, ib, Tq, ib, cw, t.trans);
+    trmm_tw(W, ib, Tq, ldq, ib, cw, t.trans);
     if (pair) sub_top(Ct, lds, W, ib, ib, cw);
     for (int c = 0; c < nchunk; ++c) {
       if (nchunk > 1) {
@@ -708,8 +749,9 @@ __device__ void task_panel(const EngineParams &p, const Geo<Real> &g, const Task
   const int mode = t.op == OP_GEQRT ? PANEL_GE : (t.op == OP_TSQRT ? PANEL_TS : PANEL_TT);
   Real *P = dyn;
   Real *Rt = P + (size_t)lds * ib;
+  const int ldq = sizeof(Real) == 8 ? ldt : ib;  // T of the block (FP64: padded for the paired trmm)
   Real *Tq = Rt + (size_t)ldt * ib;
-  Real *Ct = Tq + (size_t)ib * ib;
+  Real *Ct = Tq + (size_t)ib * ldq;
   Real *Cb = Ct + (size_t)ldt * wt;
   Real *G = Cb;  // the Gram matrix is dead before the trailing slabs use Cb
   Real *W = Cb + (size_t)(lds * wt > ib * ib ? lds * wt : ib * ib);
@@ -749,8 +791,8 @@ __device__ void task_panel(const EngineParams &p, const Geo<Real> &g, const Task
     __syncthreads();
     if (mode == PANEL_GE) shape_v(P, lds, L, ib, PANEL_GE, 0, 0);
     gemm_tn(G, ib, P, lds, P, lds, L, ib, ib, (const Real *)nullptr, 0, scr);
-    build_t(Tq, G, ib, sh);
-    store_cols(Tg + (size_t)q * ib * ib, ib, Tq, ib, ib, ib, 0, 0);
+    build_t(Tq, ldq, G, ib, sh);
+    store_cols(Tg + (size_t)q * ib * ib, ib, Tq, ldq, ib, ib, 0, 0);
     if (t.blk > 0) break;
     // trailing columns of the tile(s): block reflector applied with Q^T
     for (int c0 = q0 + ib; c0 < nb; c0 += wt) {
@@ -760,7 +802,7 @@ __device__ void task_panel(const EngineParams &p, const Geo<Real> &g, const Task
         Copy<Real> cp[1] = {{Cb, lds, XB + (size_t)c0 * nb + q0, nb, L, wc}};
         stage(p, sh, cp, 1, phase);
         gemm_tn(W, ib, P, lds, Cb, lds, L, ib, wc, (const Real *)nullptr, 0, scr);
-        trmm_tw(W, ib, Tq, ib, wc, 1);
+        trmm_tw(W, ib, Tq, ldq, ib, wc, 1);
         gemm_nn_sub(Cb, lds, P, lds, W, ib, L, ib, wc);
         store_cols(XB + (size_t)c0 * nb + q0, nb, Cb, lds, L, wc, 0, 0);
       } else {
@@ -768,7 +810,7 @@ __device__ void task_panel(const EngineParams &p, const Geo<Real> &g, const Task
                             {Cb, lds, XB + (size_t)c0 * nb, nb, L, wc}};
         stage(p, sh, cp, 2, phase);
         gemm_tn(W, ib, P, lds, Cb, lds, L, ib, wc, (const Real *)Ct, ldt, scr);
-        trmm_tw(W, ib, Tq, ib, wc, 1);
+        trmm_tw(W, ib, Tq, ldq, ib, wc, 1);
         sub_top(Ct, ldt, W, ib, ib, wc);
         gemm_nn_sub(Cb, lds, P, lds, W, ib, L, ib, wc);
         store_cols(XR + (size_t)c0 * nb + q0, nb, Ct, ldt, ib, wc, 0, 0);
@@ -1740,9 +1782,10 @@ __host__ __device__ inline size_t engine_smem_bytes(int nb, int ib, int w, int w
   const size_t sp1 = fac * (((ib + 3) / 4) * ((wt + 3) / 4) * 16), sp2 = fac * (((ib + 3) / 4) * ((ib + 3) / 4) * 16);
   const size_t sp = sp1 > sp2 ? sp1 : sp2;
   const size_t scr_p = sp > (size_t)NT ? sp : (size_t)NT;
-  const size_t upd = (size_t)lds * (2 * w + vc) + (size_t)ib * ib + (size_t)ib * w + scr_u;
+  const int ldq = sizeof(Real) == 8 ? ldt : ib;  // T of a block
+  const size_t upd = (size_t)lds * (2 * w + vc) + (size_t)ib * ldq + (size_t)ib * w + scr_u;
   const size_t cbg = (size_t)(lds * wt > ib * ib ? lds * wt : ib * ib);
-  const size_t pan = (size_t)lds * ib + (size_t)ldt * (ib + wt) + (size_t)ib * ib + cbg +
+  const size_t pan = (size_t)lds * ib + (size_t)ldt * (ib + wt) + (size_t)ib * ldq + cbg +
                      (size_t)ib * wt + scr_p;
   const size_t vec = (size_t)(2 * NT + 256) * sizeof(double);  // FP64 vector tasks
   const size_t tiles = sizeof(Real) * (upd > pan ? upd : pan);
