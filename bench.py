@@ -471,7 +471,7 @@ def serving_sustainable(torch, hqr, dev, peaks, seconds=3.0):
     least 97 % of the requests completed within the window plus 50 %, with
     p50 / p99 latency at that rate."""
     out = {"criterion": "completed >= 97 %% of the offered requests within 1.5x the %g s arrival window" % seconds}
-    for label, rates in (("mixed_tc", (250.0, 400.0, 600.0)), ("fp64", (80.0, 110.0, 140.0))):
+    for label, rates in (("mixed_tc", (400.0, 600.0, 750.0, 900.0)), ("fp64", (110.0, 140.0, 170.0))):
         best = None
         for rate in rates:
             r = serving(torch, hqr, dev, rate=rate, seconds=seconds, peaks=peaks, labels=(label,), stop_factor=2.0)[label]

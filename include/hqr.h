@@ -630,6 +630,15 @@ void hqr_set_timeout_ms(int64_t ms);
  * roofline; the paper has no counterpart. Synchronizes the device. */
 int hqr_fp64_pipe_rates(double *dfma_tflops, double *dmma_tflops);
 
+/* hqr_widen_f32 -- y[i] = x[i] widened exactly from FP32 to FP64, i < n, on
+ * `stream` (device pointers; asynchronous). The same integer-pipe widening
+ * the refinement kernels apply to FP32 matrices (A, R) before their FP64
+ * products: the FP32 -> FP64 conversion instruction runs at the FP64 rate
+ * on this GPU. Equal bit for bit to the conversion instruction, except that a
+ * signalling NaN stays signalling. Returns -1 / -2 for a null x / y with
+ * n > 0, -3 for n < 0, HQR_ERR_CUDA if the launch fails. */
+int hqr_widen_f32(const float *x, double *y, long long n, void *stream);
+
 /* hqr_strerror -- static text of a status code. */
 const char *hqr_strerror(int status);
 

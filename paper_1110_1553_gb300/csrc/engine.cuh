@@ -866,7 +866,7 @@ __device__ __forceinline__ double tile_dot(const M *m, int ld, bool transposed, 
     int k = K > 0 ? (o & 31) % K : 0;
     auto term = [&](double acc) {
       const int q = q0 + k * step;
-      acc = fma((double)col[q], g[q], acc);
+      acc = fma(ptx::to_f64(col[q]), g[q], acc);
       if (++k == K) k = 0;
       return acc;
     };
@@ -885,12 +885,12 @@ __device__ __forceinline__ double tile_dot(const M *m, int ld, bool transposed, 
     const double *gq = g + q0;
     int c = 0;
     for (; c + 3 < K; c += 4, p += 4 * qs, gq += 4 * step) {
-      a0 = fma((double)p[0], gq[0], a0);
-      a1 = fma((double)p[qs], gq[step], a1);
-      a2 = fma((double)p[2 * qs], gq[2 * step], a2);
-      a3 = fma((double)p[3 * qs], gq[3 * step], a3);
+      a0 = fma(ptx::to_f64(p[0]), gq[0], a0);
+      a1 = fma(ptx::to_f64(p[qs]), gq[step], a1);
+      a2 = fma(ptx::to_f64(p[2 * qs]), gq[2 * step], a2);
+      a3 = fma(ptx::to_f64(p[3 * qs]), gq[3 * step], a3);
     }
-    for (; c < K; ++c, p += qs, gq += step) a0 = fma((double)p[0], gq[0], a0);
+    for (; c < K; ++c, p += qs, gq += step) a0 = fma(ptx::to_f64(p[0]), gq[0], a0);
   }
   return (a0 + a1) + (a2 + a3);
 }
@@ -902,7 +902,10 @@ __device__ __forceinline__ bool aligned16(const void *p) { return ((uintptr_t)p 
 constexpr uint32_t kVecStageOff = 4096;
 static_assert((128 + NT) * 8 <= kVecStageOff, "vector scratch overlaps the staged tiles");
 
-template <typename Real>
+// KU: elements of A each thread keeps in flight in the residual and A^T r
+// loops (16 in the one-CTA-per-SM tensor-core kernel, 8 where two CTAs share
+// an SM's registers).
+template <typename Real, int KU>
 __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<Real> &g, const Task &t,
                             double *sm, Shared<Real> &sh, uint32_t &phase) {
   const int nb = g.nb, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -948,30 +951,64 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
         const Real *arow = A0 + r0 + rr;
         double s1 = 0.0, s2 = 0.0, s3 = 0.0;
         int j = clo + gi;
-        for (; j + 3 * G < chi; j += 4 * G) {
-          s = fma((double)__ldcg(arow + (long long)j * P.lda0), __ldcg(P.x + j), s);
-          s1 = fma((double)__ldcg(arow + (long long)(j + G) * P.lda0), __ldcg(P.x + j + G), s1);
-          s2 = fma((double)__ldcg(arow + (long long)(j + 2 * G) * P.lda0), __ldcg(P.x + j + 2 * G), s2);
-          s3 = fma((double)__ldcg(arow + (long long)(j + 3 * G) * P.lda0), __ldcg(P.x + j + 3 * G), s3);
+        // KU columns in flight per thread (the loads of A are the latency to hide); each chain
+        // takes its terms in the same order as one step at a time
+        for (; j + (KU - 1) * G < chi; j += KU * G) {
+          Real a[KU];
+          double xv[KU];
+#pragma unroll
+          for (int u = 0; u < KU; ++u) {
+            a[u] = __ldcg(arow + (long long)(j + u * G) * P.lda0);
+            xv[u] = __ldcg(P.x + j + u * G);
+          }
+#pragma unroll
+          for (int u = 0; u < KU; u += 4) {
+            s = fma(ptx::to_f64(a[u]), xv[u], s);
+            s1 = fma(ptx::to_f64(a[u + 1]), xv[u + 1], s1);
+            s2 = fma(ptx::to_f64(a[u + 2]), xv[u + 2], s2);
+            s3 = fma(ptx::to_f64(a[u + 3]), xv[u + 3], s3);
+          }
         }
-        for (; j < chi; j += G) s = fma((double)__ldcg(arow + (long long)j * P.lda0), __ldcg(P.x + j), s);
+        for (; j + 3 * G < chi; j += 4 * G) {
+          s = fma(ptx::to_f64(__ldcg(arow + (long long)j * P.lda0)), __ldcg(P.x + j), s);
+          s1 = fma(ptx::to_f64(__ldcg(arow + (long long)(j + G) * P.lda0)), __ldcg(P.x + j + G), s1);
+          s2 = fma(ptx::to_f64(__ldcg(arow + (long long)(j + 2 * G) * P.lda0)), __ldcg(P.x + j + 2 * G), s2);
+          s3 = fma(ptx::to_f64(__ldcg(arow + (long long)(j + 3 * G) * P.lda0)), __ldcg(P.x + j + 3 * G), s3);
+        }
+        for (; j < chi; j += G) s = fma(ptx::to_f64(__ldcg(arow + (long long)j * P.lda0)), __ldcg(P.x + j), s);
         s = (s + s1) + (s2 + s3);
       } else if (rr < nr && gi < G) {
         // four independent compensated sums (more FP64 work in flight), merged in a fixed order
         const Real *arow = A0 + r0 + rr;
         double s1 = 0.0, c1 = 0.0, s2 = 0.0, c2 = 0.0, s3 = 0.0, c3 = 0.0;
         int j = clo + gi;
+        for (; j + (KU - 1) * G < chi; j += KU * G) {  // KU columns in flight, the same order per sum
+          Real a[KU];
+          double xv[KU];
+#pragma unroll
+          for (int u = 0; u < KU; ++u) {
+            a[u] = __ldcg(arow + (long long)(j + u * G) * P.lda0);
+            xv[u] = __ldcg(P.x + j + u * G);
+          }
+#pragma unroll
+          for (int u = 0; u < KU; u += 4) {
+            dot2_step(ptx::to_f64(a[u]), xv[u], s, c);
+            dot2_step(ptx::to_f64(a[u + 1]), xv[u + 1], s1, c1);
+            dot2_step(ptx::to_f64(a[u + 2]), xv[u + 2], s2, c2);
+            dot2_step(ptx::to_f64(a[u + 3]), xv[u + 3], s3, c3);
+          }
+        }
         for (; j + 3 * G < chi; j += 4 * G) {
-          const double a0 = (double)__ldcg(arow + (long long)j * P.lda0);
-          const double a1 = (double)__ldcg(arow + (long long)(j + G) * P.lda0);
-          const double a2 = (double)__ldcg(arow + (long long)(j + 2 * G) * P.lda0);
-          const double a3 = (double)__ldcg(arow + (long long)(j + 3 * G) * P.lda0);
+          const double a0 = ptx::to_f64(__ldcg(arow + (long long)j * P.lda0));
+          const double a1 = ptx::to_f64(__ldcg(arow + (long long)(j + G) * P.lda0));
+          const double a2 = ptx::to_f64(__ldcg(arow + (long long)(j + 2 * G) * P.lda0));
+          const double a3 = ptx::to_f64(__ldcg(arow + (long long)(j + 3 * G) * P.lda0));
           dot2_step(a0, __ldcg(P.x + j), s, c);
           dot2_step(a1, __ldcg(P.x + j + G), s1, c1);
           dot2_step(a2, __ldcg(P.x + j + 2 * G), s2, c2);
           dot2_step(a3, __ldcg(P.x + j + 3 * G), s3, c3);
         }
-        for (; j < chi; j += G) dot2_step((double)__ldcg(arow + (long long)j * P.lda0), __ldcg(P.x + j), s, c);
+        for (; j < chi; j += G) dot2_step(ptx::to_f64(__ldcg(arow + (long long)j * P.lda0)), __ldcg(P.x + j), s, c);
         dot2_merge(s, c, s1, c1);
         dot2_merge(s2, c2, s3, c3);
         dot2_merge(s, c, s2, c2);
@@ -1041,13 +1078,29 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
         double s = 0.0, c = 0.0, s1 = 0.0, c1 = 0.0, s2 = 0.0, c2 = 0.0, s3 = 0.0, c3 = 0.0;
         int i = rlo + lane;
         if (!comp) {  // plain FP64 round: FMA chains, then a plain warp sum
-          for (; i + 96 < rhi; i += 128) {
-            s = fma((double)__ldcg(acol + i), __ldcg(P.r + i), s);
-            s1 = fma((double)__ldcg(acol + i + 32), __ldcg(P.r + i + 32), s1);
-            s2 = fma((double)__ldcg(acol + i + 64), __ldcg(P.r + i + 64), s2);
-            s3 = fma((double)__ldcg(acol + i + 96), __ldcg(P.r + i + 96), s3);
+          for (; i + 32 * (KU - 1) < rhi; i += 32 * KU) {  // KU rows in flight, the same order per chain
+            Real a[KU];
+            double rv[KU];
+#pragma unroll
+            for (int u = 0; u < KU; ++u) {
+              a[u] = __ldcg(acol + i + 32 * u);
+              rv[u] = __ldcg(P.r + i + 32 * u);
+            }
+#pragma unroll
+            for (int u = 0; u < KU; u += 4) {
+              s = fma(ptx::to_f64(a[u]), rv[u], s);
+              s1 = fma(ptx::to_f64(a[u + 1]), rv[u + 1], s1);
+              s2 = fma(ptx::to_f64(a[u + 2]), rv[u + 2], s2);
+              s3 = fma(ptx::to_f64(a[u + 3]), rv[u + 3], s3);
+            }
           }
-          for (; i < rhi; i += 32) s = fma((double)__ldcg(acol + i), __ldcg(P.r + i), s);
+          for (; i + 96 < rhi; i += 128) {
+            s = fma(ptx::to_f64(__ldcg(acol + i)), __ldcg(P.r + i), s);
+            s1 = fma(ptx::to_f64(__ldcg(acol + i + 32)), __ldcg(P.r + i + 32), s1);
+            s2 = fma(ptx::to_f64(__ldcg(acol + i + 64)), __ldcg(P.r + i + 64), s2);
+            s3 = fma(ptx::to_f64(__ldcg(acol + i + 96)), __ldcg(P.r + i + 96), s3);
+          }
+          for (; i < rhi; i += 32) s = fma(ptx::to_f64(__ldcg(acol + i)), __ldcg(P.r + i), s);
           s = warp_sum((s + s1) + (s2 + s3));
           if (lane == 0) {
             P.gp[2 * ((size_t)t.i * np + c0 + cc)] = s;
@@ -1055,15 +1108,31 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
           }
           continue;
         }
+        for (; i + 32 * (KU - 1) < rhi; i += 32 * KU) {  // KU rows in flight, the same order per sum
+          Real a[KU];
+          double rv[KU];
+#pragma unroll
+          for (int u = 0; u < KU; ++u) {
+            a[u] = __ldcg(acol + i + 32 * u);
+            rv[u] = __ldcg(P.r + i + 32 * u);
+          }
+#pragma unroll
+          for (int u = 0; u < KU; u += 4) {
+            dot2_step(ptx::to_f64(a[u]), rv[u], s, c);
+            dot2_step(ptx::to_f64(a[u + 1]), rv[u + 1], s1, c1);
+            dot2_step(ptx::to_f64(a[u + 2]), rv[u + 2], s2, c2);
+            dot2_step(ptx::to_f64(a[u + 3]), rv[u + 3], s3, c3);
+          }
+        }
         for (; i + 96 < rhi; i += 128) {  // four independent compensated sums, merged in a fixed order
-          const double a0 = (double)__ldcg(acol + i), a1 = (double)__ldcg(acol + i + 32);
-          const double a2 = (double)__ldcg(acol + i + 64), a3 = (double)__ldcg(acol + i + 96);
+          const double a0 = ptx::to_f64(__ldcg(acol + i)), a1 = ptx::to_f64(__ldcg(acol + i + 32));
+          const double a2 = ptx::to_f64(__ldcg(acol + i + 64)), a3 = ptx::to_f64(__ldcg(acol + i + 96));
           dot2_step(a0, __ldcg(P.r + i), s, c);
           dot2_step(a1, __ldcg(P.r + i + 32), s1, c1);
           dot2_step(a2, __ldcg(P.r + i + 64), s2, c2);
           dot2_step(a3, __ldcg(P.r + i + 96), s3, c3);
         }
-        for (; i < rhi; i += 32) dot2_step((double)__ldcg(acol + i), __ldcg(P.r + i), s, c);
+        for (; i < rhi; i += 32) dot2_step(ptx::to_f64(__ldcg(acol + i)), __ldcg(P.r + i), s, c);
         dot2_merge(s, c, s1, c1);
         dot2_merge(s2, c2, s3, c3);
         dot2_merge(s, c, s2, c2);
@@ -1490,7 +1559,7 @@ __global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_sched(EngineParams p) {
     else if (t.op <= OP_TTMQR)
       task_update(p, g, t, sh, dyn, phase);
     else
-      task_vector(p, p.probs[t.pid], g, t, reinterpret_cast<double *>(dyn_raw), sh, phase);
+      task_vector<Real, TC ? 16 : 8>(p, p.probs[t.pid], g, t, reinterpret_cast<double *>(dyn_raw), sh, phase);
     __syncthreads();
     if (threadIdx.x < 32) {  // warp 0 releases the successors, 32 at a time (most critical first)
       if (threadIdx.x == 0 && p.trace) {
@@ -1729,7 +1798,7 @@ __global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_serve(ServeParams sp) {
     else if (t.op <= OP_TTMQR)
       task_update(p, g, t, sh, dyn, phase);
     else
-      task_vector(p, P, g, t, reinterpret_cast<double *>(dyn_raw), sh, phase);
+      task_vector<Real, TC ? 16 : 8>(p, P, g, t, reinterpret_cast<double *>(dyn_raw), sh, phase);
     __syncthreads();
     if (threadIdx.x < 32) {  // warp 0 releases the successors, 32 at a time
       ptx::fence_proxy_async();

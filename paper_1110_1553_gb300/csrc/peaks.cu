@@ -8,6 +8,7 @@
 #include <cstdint>
 
 #include "../../include/hqr.h"
+#include "ptx.cuh"
 
 namespace {
 
@@ -45,7 +46,22 @@ __global__ void fp64_dmma_loop(int iters, double seed, double *sink) {
   if (s == 12345.678) sink[threadIdx.x] = s;
 }
 
+__global__ void widen_f32(const float *x, double *y, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = hqr::ptx::to_f64(x[i]);
+}
+
 }  // namespace
+
+extern "C" int hqr_widen_f32(const float *x, double *y, long long n, void *stream) {
+  if (n < 0) return -3;
+  if (n == 0) return HQR_SUCCESS;
+  if (!x) return -1;
+  if (!y) return -2;
+  const long long blocks = (n + 255) / 256;
+  widen_f32<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, (cudaStream_t)stream>>>(x, y, n);
+  return cudaGetLastError() == cudaSuccess ? HQR_SUCCESS : HQR_ERR_CUDA;
+}
 
 extern "C" int hqr_fp64_pipe_rates(double *dfma_tflops, double *dmma_tflops) {
   if (!dfma_tflops) return -1;

@@ -31,7 +31,7 @@ EXPORTS = ["hqr_elim_list", "hqr_elim_list_domino", "hqr_validate_list", "hqr_ta
            "hqr_status", "hqr_get_r", "hqr_get_tiles", "hqr_get_t", "hqr_factors_info", "hqr_kernel_ms", "hqr_kernel_times", "hqr_trace", "hqr_apply_q",
            "hqr_gels", "hqr_gels_qr", "hqr_geqrf_r_noalloc", "hqr_ls_plan_create", "hqr_ls_plan_create_tol",
            "hqr_ls_plan_refine_info", "hqr_critical_path", "hqr_set_split_launch", "hqr_fp64_pipe_rates",
-           "hqr_ls_plan_run",
+           "hqr_widen_f32", "hqr_ls_plan_run",
            "hqr_ls_plan_capture", "hqr_ls_plan_status", "hqr_ls_plan_correction", "hqr_ls_plan_info", "hqr_ls_plan_config",
            "hqr_ls_plan_free", "hqr_ls_plan_trace", "hqr_set_tuning", "hqr_autotune", "hqr_server_create", "hqr_server_start",
            "hqr_server_submit", "hqr_server_poll", "hqr_server_stats", "hqr_server_progress", "hqr_server_counters", "hqr_server_stop", "hqr_server_free", "hqr_debug_block_task", "hqr_factors_free", "hqr_set_timeout_ms", "hqr_strerror", "hqr_last_error", "hqr_set_slab_widths",
@@ -128,6 +128,7 @@ def load(build_if_missing=False):
     lib.hqr_set_panel_split.argtypes = [i32]
     lib.hqr_set_split_launch.argtypes = [i32]
     lib.hqr_fp64_pipe_rates.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.hqr_widen_f32.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p]
     lib.hqr_set_timeout_ms.argtypes = [i64]
     lib.hqr_set_timeout_ms.restype = None
     lib.hqr_strerror.argtypes = [i32]
@@ -233,6 +234,16 @@ def fp64_pipe_rates():
     a, b = ctypes.c_double(0), ctypes.c_double(0)
     _check(load().hqr_fp64_pipe_rates(ctypes.byref(a), ctypes.byref(b)), "hqr_fp64_pipe_rates")
     return a.value, b.value
+
+
+def widen_f32(x, y, stream=None):
+    """y <- x widened exactly from FP32 to FP64 (contiguous CUDA tensors of
+    the same length), the refinement kernels' integer-pipe widening
+    (hqr_widen_f32); asynchronous on `stream`."""
+    if x.numel() != y.numel() or not (x.is_contiguous() and y.is_contiguous()):
+        raise ValueError("x and y: contiguous, same length")
+    _check(load().hqr_widen_f32(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), x.numel(),
+                                _stream_ptr(stream)), "hqr_widen_f32")
 
 
 def set_split_launch(on):
