@@ -439,8 +439,9 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
 // Estimated cost of a task in units of b^3/3 (Sec. 2 weights), updates scaled by slab width;
 // the FP64 vector tasks of least-squares graphs by their relative durations (a compensated
 // residual or A^T r chunk costs about a GEQRT, a plain one a fifth of it, a triangular-solve
-// step a few percent), so that the solve chains keep their place ahead of the next round's
-// residuals.
+// step a few percent, twice that when it also applies the next diagonal inverse), so that the
+// solve chains keep their place ahead of the next round's residuals and the step that carries
+// the chain is its predecessor's most critical successor.
 static double task_cost(const Task &t, int nb) {
   const double slab = t.cw > 0 ? (double)t.cw / nb : 1.0;
   // a block task of a split panel: about one block's share of its panel (or of one update slab)
@@ -458,7 +459,7 @@ static double task_cost(const Task &t, int nb) {
     case OP_TRSV_TD:
     case OP_TRSV_TU:
     case OP_TRSV_D:
-    case OP_TRSV_U: return 0.2;
+    case OP_TRSV_U: return t.tgt ? 0.4 : 0.2;  // a fused step also applies the next inverse
     default: return 0.1;
   }
 }

@@ -137,6 +137,9 @@ struct Shared {
   int abort;
   int vskip, vcomp;  // vector tasks of tolerance-stopped rounds: skip the task, compensated sums
   int norelease;     // the task released none of its successors (a gate that cancelled its rounds)
+  int kept;          // a successor the last task made ready and this CTA runs next (-1: none)
+  int popped;        // the task warp 1 claimed meanwhile (-1: none or finished, -2: stopped)
+  int deferred;      // a claimed task that waits for the kept one (-1: none)
   Real red[2 * NWARP];
   Real tau[IBMAX];
   Real wv[IBMAX];
@@ -1425,17 +1428,19 @@ __device__ __forceinline__ int take_slot(const EngineParams &p, int *slot) {
   return v - 1;
 }
 
-// Claim the next ready task (warp 0, all lanes; the result in every lane).
-// -1: finished or failed. `pending` (lane 0's) counts tasks this CTA
-// completed but has not yet added to the global done counter; it is
-// flushed whenever the queues look empty.
-__device__ int pop_ready(const EngineParams &p, unsigned &pending) {
+// Claim the next ready task (one warp, all lanes; the result in every lane).
+// -1: finished or failed; -2: `stop` (if given) turned non-negative first
+// (the CTA has its next task already). `pending` (lane 0's) counts tasks
+// this CTA completed but has not yet added to the global done counter; it
+// is flushed whenever the queues look empty.
+__device__ int pop_ready(const EngineParams &p, unsigned &pending, const volatile int *stop = nullptr) {
   const int lane = threadIdx.x & 31;
   const uint64_t t0 = ptx::globaltimer();
   const int cap = shard_cap(p.ntasks);
   unsigned sleep_ns = 32;
   while (true) {
     if (__shfl_sync(0xffffffffu, lane == 0 ? ptx::ld_relaxed((const int *)&p.ctl->status.v) : 0, 0) != 0) return -1;
+    if (stop && __shfl_sync(0xffffffffu, lane == 0 ? *stop : -1, 0) >= 0) return -2;
     unsigned h = 0;
     const int qs = warp_claim<kNumQueues>(p.ctl->head, p.ctl->tail, h);
     if (qs >= 0) {
@@ -1539,8 +1544,19 @@ __global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_sched(EngineParams p) {
   // accumulated): a task counts as done once its results are written, before
   // its successors are released, which cannot end the run early since the
   // counter reaches the task count only when no task has unfinished
-  // successors.
+  // successors. Seven warps release the successors (a solve step has up to
+  // one per tile of the vector). The most critical successor that the release
+  // makes ready (successors are listed by decreasing bottom level) stays with this CTA
+  // and runs next without a trip through the queues: a chain of dependent
+  // tasks (a triangular solve, a panel column) then pays neither the push nor
+  // another CTA's claim per step. Warp 1 stops claiming once warp 0 keeps a
+  // task; a task it claimed before that runs right after the kept one.
   unsigned pending = 0;
+  if (threadIdx.x == 0) {
+    sh.kept = -1;
+    sh.popped = -1;
+    sh.deferred = -1;
+  }
   if (threadIdx.x >= 32 && threadIdx.x < 64) {
     const int v = pop_ready(p, pending);
     if (threadIdx.x == 32) sh.task = v;
@@ -1561,7 +1577,8 @@ __global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_sched(EngineParams p) {
     else
       task_vector<Real, TC ? 32 : 8>(p, p.probs[t.pid], g, t, reinterpret_cast<double *>(dyn_raw), sh, phase);
     __syncthreads();
-    if (threadIdx.x < 32) {  // warp 0 releases the successors, 32 at a time (most critical first)
+    const int warp = threadIdx.x >> 5;
+    if (warp != 1) {  // warps 0, 2 .. 7 release the successors, warp 0 the most critical 32
       if (threadIdx.x == 0 && p.trace) {
         p.trace[3 * (size_t)tid + 0] = t_start;
         p.trace[3 * (size_t)tid + 1] = ptx::globaltimer();
@@ -1569,21 +1586,56 @@ __global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_sched(EngineParams p) {
       }
       ptx::fence_proxy_async();
       __threadfence();
+      const int rw = warp == 0 ? 0 : warp - 1;  // release slot of this warp
       const int e_end = sh.norelease ? t.succ_begin : t.succ_end;
-      for (int e = t.succ_begin + (int)threadIdx.x; e < e_end; e += 32) {
-        const int s = p.succ[e];
-        if (atomicSub(&p.indeg[s], 1) == 1) push_ready(p, s);
+      const bool may_keep = warp == 0 && sh.deferred < 0;
+      for (int e0 = t.succ_begin + 32 * rw; e0 < e_end; e0 += 32 * (NWARP - 1)) {
+        const int e = e0 + (threadIdx.x & 31);
+        int s = -1;
+        bool ready = false;
+        if (e < e_end) {
+          s = p.succ[e];
+          ready = atomicSub(&p.indeg[s], 1) == 1;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, ready);
+        const int keeper = (e0 == t.succ_begin && may_keep && m) ? __ffs(m) - 1 : -1;
+        if (ready) {
+          if ((int)(threadIdx.x & 31) == keeper)
+            *(volatile int *)&sh.kept = s;
+          else
+            push_ready(p, s);
+        }
       }
       __syncwarp();
-      if (threadIdx.x == 0) sh.norelease = 0;
-    } else if (threadIdx.x < 64) {  // warp 1 claims the next task meanwhile
+      // a kept task's other predecessors published their results before their own decrements
+      // (fence, then atomic): this fence orders its reads after the decrement that made it ready,
+      // as take_slot does for a claimed task
+      __threadfence();
+    } else {  // warp 1 claims the next task meanwhile
       if (threadIdx.x == 32 && ++pending >= 64) {
         __threadfence();
         atomicAdd(&p.ctl->done.v, pending);
         pending = 0;
       }
-      const int v = sh.abort ? -1 : pop_ready(p, pending);
-      if (threadIdx.x == 32) sh.task = v;
+      const int v = (sh.abort || sh.deferred >= 0) ? -1 : pop_ready(p, pending, &sh.kept);
+      if (threadIdx.x == 32) sh.popped = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {  // the next task: the kept one, else one waiting, else the claimed one
+      int next;
+      if (sh.kept >= 0) {
+        next = sh.kept;
+        if (sh.popped >= 0) sh.deferred = sh.popped;
+      } else if (sh.deferred >= 0) {
+        next = sh.deferred;
+        sh.deferred = -1;
+      } else {
+        next = sh.popped;
+      }
+      sh.task = next;
+      sh.kept = -1;
+      sh.popped = -1;
+      sh.norelease = 0;
     }
     __syncthreads();
     if (sh.abort) break;
