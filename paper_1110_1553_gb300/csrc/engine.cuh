@@ -906,8 +906,8 @@ constexpr uint32_t kVecStageOff = 4096;
 static_assert((128 + NT) * 8 <= kVecStageOff, "vector scratch overlaps the staged tiles");
 
 // KU: elements of A each thread keeps in flight in the residual and A^T r
-// loops (32 in the one-CTA-per-SM tensor-core kernel, 8 where two CTAs share
-// an SM's registers); the vector they multiply sits in shared memory.
+// loops (16 in the one-CTA-per-SM tensor-core kernel, 8 where two CTAs share
+// an SM's registers).
 template <typename Real, int KU>
 __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<Real> &g, const Task &t,
                             double *sm, Shared<Real> &sh, uint32_t &phase) {
@@ -949,40 +949,36 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
       const int clo = t.j * kResChunk * nb, chi = min(P.N, clo + kResChunk * nb);
       const int G = NT / nb;  // column groups
       const int rr = tid % nb, gi = tid / nb;
-      // the chunk's x in shared memory (read by every row), where the launch has room
-      double *xs = sm + 2 * NT;
-      const bool xsm = (size_t)(2 * NT + chi - clo) * sizeof(double) <= ptx::dynamic_smem_bytes();
-      if (xsm) {
-        for (int q = tid; q < chi - clo; q += NT) xs[q] = __ldcg(P.x + clo + q);
-        __syncthreads();
-      }
-      const double *xb = xsm ? xs - clo : P.x;  // x(j) at xb[j]
       double s = 0.0, c = 0.0;
       if (rr < nr && gi < G && !comp) {  // plain FP64 round: four independent FMA chains
         const Real *arow = A0 + r0 + rr;
         double s1 = 0.0, s2 = 0.0, s3 = 0.0;
         int j = clo + gi;
-        // KU columns of A in flight per thread (their loads are the latency to hide); each
-        // chain takes its terms in the same order as one step at a time
+        // KU columns in flight per thread (the loads of A are the latency to hide); each chain
+        // takes its terms in the same order as one step at a time
         for (; j + (KU - 1) * G < chi; j += KU * G) {
           Real a[KU];
+          double xv[KU];
 #pragma unroll
-          for (int u = 0; u < KU; ++u) a[u] = __ldcg(arow + (long long)(j + u * G) * P.lda0);
+          for (int u = 0; u < KU; ++u) {
+            a[u] = __ldcg(arow + (long long)(j + u * G) * P.lda0);
+            xv[u] = __ldcg(P.x + j + u * G);
+          }
 #pragma unroll
           for (int u = 0; u < KU; u += 4) {
-            s = fma(ptx::to_f64(a[u]), xb[j + u * G], s);
-            s1 = fma(ptx::to_f64(a[u + 1]), xb[j + (u + 1) * G], s1);
-            s2 = fma(ptx::to_f64(a[u + 2]), xb[j + (u + 2) * G], s2);
-            s3 = fma(ptx::to_f64(a[u + 3]), xb[j + (u + 3) * G], s3);
+            s = fma(ptx::to_f64(a[u]), xv[u], s);
+            s1 = fma(ptx::to_f64(a[u + 1]), xv[u + 1], s1);
+            s2 = fma(ptx::to_f64(a[u + 2]), xv[u + 2], s2);
+            s3 = fma(ptx::to_f64(a[u + 3]), xv[u + 3], s3);
           }
         }
         for (; j + 3 * G < chi; j += 4 * G) {
-          s = fma(ptx::to_f64(__ldcg(arow + (long long)j * P.lda0)), xb[j], s);
-          s1 = fma(ptx::to_f64(__ldcg(arow + (long long)(j + G) * P.lda0)), xb[j + G], s1);
-          s2 = fma(ptx::to_f64(__ldcg(arow + (long long)(j + 2 * G) * P.lda0)), xb[j + 2 * G], s2);
-          s3 = fma(ptx::to_f64(__ldcg(arow + (long long)(j + 3 * G) * P.lda0)), xb[j + 3 * G], s3);
+          s = fma(ptx::to_f64(__ldcg(arow + (long long)j * P.lda0)), __ldcg(P.x + j), s);
+          s1 = fma(ptx::to_f64(__ldcg(arow + (long long)(j + G) * P.lda0)), __ldcg(P.x + j + G), s1);
+          s2 = fma(ptx::to_f64(__ldcg(arow + (long long)(j + 2 * G) * P.lda0)), __ldcg(P.x + j + 2 * G), s2);
+          s3 = fma(ptx::to_f64(__ldcg(arow + (long long)(j + 3 * G) * P.lda0)), __ldcg(P.x + j + 3 * G), s3);
         }
-        for (; j < chi; j += G) s = fma(ptx::to_f64(__ldcg(arow + (long long)j * P.lda0)), xb[j], s);
+        for (; j < chi; j += G) s = fma(ptx::to_f64(__ldcg(arow + (long long)j * P.lda0)), __ldcg(P.x + j), s);
         s = (s + s1) + (s2 + s3);
       } else if (rr < nr && gi < G) {
         // four independent compensated sums (more FP64 work in flight), merged in a fixed order
@@ -991,14 +987,18 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
         int j = clo + gi;
         for (; j + (KU - 1) * G < chi; j += KU * G) {  // KU columns in flight, the same order per sum
           Real a[KU];
+          double xv[KU];
 #pragma unroll
-          for (int u = 0; u < KU; ++u) a[u] = __ldcg(arow + (long long)(j + u * G) * P.lda0);
+          for (int u = 0; u < KU; ++u) {
+            a[u] = __ldcg(arow + (long long)(j + u * G) * P.lda0);
+            xv[u] = __ldcg(P.x + j + u * G);
+          }
 #pragma unroll
           for (int u = 0; u < KU; u += 4) {
-            dot2_step(ptx::to_f64(a[u]), xb[j + u * G], s, c);
-            dot2_step(ptx::to_f64(a[u + 1]), xb[j + (u + 1) * G], s1, c1);
-            dot2_step(ptx::to_f64(a[u + 2]), xb[j + (u + 2) * G], s2, c2);
-            dot2_step(ptx::to_f64(a[u + 3]), xb[j + (u + 3) * G], s3, c3);
+            dot2_step(ptx::to_f64(a[u]), xv[u], s, c);
+            dot2_step(ptx::to_f64(a[u + 1]), xv[u + 1], s1, c1);
+            dot2_step(ptx::to_f64(a[u + 2]), xv[u + 2], s2, c2);
+            dot2_step(ptx::to_f64(a[u + 3]), xv[u + 3], s3, c3);
           }
         }
         for (; j + 3 * G < chi; j += 4 * G) {
@@ -1006,12 +1006,12 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
           const double a1 = ptx::to_f64(__ldcg(arow + (long long)(j + G) * P.lda0));
           const double a2 = ptx::to_f64(__ldcg(arow + (long long)(j + 2 * G) * P.lda0));
           const double a3 = ptx::to_f64(__ldcg(arow + (long long)(j + 3 * G) * P.lda0));
-          dot2_step(a0, xb[j], s, c);
-          dot2_step(a1, xb[j + G], s1, c1);
-          dot2_step(a2, xb[j + 2 * G], s2, c2);
-          dot2_step(a3, xb[j + 3 * G], s3, c3);
+          dot2_step(a0, __ldcg(P.x + j), s, c);
+          dot2_step(a1, __ldcg(P.x + j + G), s1, c1);
+          dot2_step(a2, __ldcg(P.x + j + 2 * G), s2, c2);
+          dot2_step(a3, __ldcg(P.x + j + 3 * G), s3, c3);
         }
-        for (; j < chi; j += G) dot2_step(ptx::to_f64(__ldcg(arow + (long long)j * P.lda0)), xb[j], s, c);
+        for (; j < chi; j += G) dot2_step(ptx::to_f64(__ldcg(arow + (long long)j * P.lda0)), __ldcg(P.x + j), s, c);
         dot2_merge(s, c, s1, c1);
         dot2_merge(s2, c2, s3, c3);
         dot2_merge(s, c, s2, c2);
@@ -1076,14 +1076,6 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
       const int c0 = t.j * nb, nc = min(nb, P.N - c0);
       const int rlo = t.i * kAtrChunk * nb, rhi = min(P.M, rlo + kAtrChunk * nb);
       const size_t np = (size_t)g.n * nb;
-      // the chunk's r in shared memory (read by every column), where the launch has room
-      double *rsh = sm + 2 * NT;
-      const bool rsm = (size_t)(2 * NT + rhi - rlo) * sizeof(double) <= ptx::dynamic_smem_bytes();
-      if (rsm) {
-        for (int q = tid; q < rhi - rlo; q += NT) rsh[q] = __ldcg(P.r + rlo + q);
-        __syncthreads();
-      }
-      const double *rb = rsm ? rsh - rlo : P.r;  // r(i) at rb[i]
       for (int cc = warp; cc < nc; cc += NWARP) {
         const Real *acol = A0 + (long long)(c0 + cc) * P.lda0;
         double s = 0.0, c = 0.0, s1 = 0.0, c1 = 0.0, s2 = 0.0, c2 = 0.0, s3 = 0.0, c3 = 0.0;
@@ -1091,23 +1083,27 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
         if (!comp) {  // plain FP64 round: FMA chains, then a plain warp sum
           for (; i + 32 * (KU - 1) < rhi; i += 32 * KU) {  // KU rows in flight, the same order per chain
             Real a[KU];
+            double rv[KU];
 #pragma unroll
-            for (int u = 0; u < KU; ++u) a[u] = __ldcg(acol + i + 32 * u);
+            for (int u = 0; u < KU; ++u) {
+              a[u] = __ldcg(acol + i + 32 * u);
+              rv[u] = __ldcg(P.r + i + 32 * u);
+            }
 #pragma unroll
             for (int u = 0; u < KU; u += 4) {
-              s = fma(ptx::to_f64(a[u]), rb[i + 32 * u], s);
-              s1 = fma(ptx::to_f64(a[u + 1]), rb[i + 32 * (u + 1)], s1);
-              s2 = fma(ptx::to_f64(a[u + 2]), rb[i + 32 * (u + 2)], s2);
-              s3 = fma(ptx::to_f64(a[u + 3]), rb[i + 32 * (u + 3)], s3);
+              s = fma(ptx::to_f64(a[u]), rv[u], s);
+              s1 = fma(ptx::to_f64(a[u + 1]), rv[u + 1], s1);
+              s2 = fma(ptx::to_f64(a[u + 2]), rv[u + 2], s2);
+              s3 = fma(ptx::to_f64(a[u + 3]), rv[u + 3], s3);
             }
           }
           for (; i + 96 < rhi; i += 128) {
-            s = fma(ptx::to_f64(__ldcg(acol + i)), rb[i], s);
-            s1 = fma(ptx::to_f64(__ldcg(acol + i + 32)), rb[i + 32], s1);
-            s2 = fma(ptx::to_f64(__ldcg(acol + i + 64)), rb[i + 64], s2);
-            s3 = fma(ptx::to_f64(__ldcg(acol + i + 96)), rb[i + 96], s3);
+            s = fma(ptx::to_f64(__ldcg(acol + i)), __ldcg(P.r + i), s);
+            s1 = fma(ptx::to_f64(__ldcg(acol + i + 32)), __ldcg(P.r + i + 32), s1);
+            s2 = fma(ptx::to_f64(__ldcg(acol + i + 64)), __ldcg(P.r + i + 64), s2);
+            s3 = fma(ptx::to_f64(__ldcg(acol + i + 96)), __ldcg(P.r + i + 96), s3);
           }
-          for (; i < rhi; i += 32) s = fma(ptx::to_f64(__ldcg(acol + i)), rb[i], s);
+          for (; i < rhi; i += 32) s = fma(ptx::to_f64(__ldcg(acol + i)), __ldcg(P.r + i), s);
           s = warp_sum((s + s1) + (s2 + s3));
           if (lane == 0) {
             P.gp[2 * ((size_t)t.i * np + c0 + cc)] = s;
@@ -1117,25 +1113,29 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
         }
         for (; i + 32 * (KU - 1) < rhi; i += 32 * KU) {  // KU rows in flight, the same order per sum
           Real a[KU];
+          double rv[KU];
 #pragma unroll
-          for (int u = 0; u < KU; ++u) a[u] = __ldcg(acol + i + 32 * u);
+          for (int u = 0; u < KU; ++u) {
+            a[u] = __ldcg(acol + i + 32 * u);
+            rv[u] = __ldcg(P.r + i + 32 * u);
+          }
 #pragma unroll
           for (int u = 0; u < KU; u += 4) {
-            dot2_step(ptx::to_f64(a[u]), rb[i + 32 * u], s, c);
-            dot2_step(ptx::to_f64(a[u + 1]), rb[i + 32 * (u + 1)], s1, c1);
-            dot2_step(ptx::to_f64(a[u + 2]), rb[i + 32 * (u + 2)], s2, c2);
-            dot2_step(ptx::to_f64(a[u + 3]), rb[i + 32 * (u + 3)], s3, c3);
+            dot2_step(ptx::to_f64(a[u]), rv[u], s, c);
+            dot2_step(ptx::to_f64(a[u + 1]), rv[u + 1], s1, c1);
+            dot2_step(ptx::to_f64(a[u + 2]), rv[u + 2], s2, c2);
+            dot2_step(ptx::to_f64(a[u + 3]), rv[u + 3], s3, c3);
           }
         }
         for (; i + 96 < rhi; i += 128) {  // four independent compensated sums, merged in a fixed order
           const double a0 = ptx::to_f64(__ldcg(acol + i)), a1 = ptx::to_f64(__ldcg(acol + i + 32));
           const double a2 = ptx::to_f64(__ldcg(acol + i + 64)), a3 = ptx::to_f64(__ldcg(acol + i + 96));
-          dot2_step(a0, rb[i], s, c);
-          dot2_step(a1, rb[i + 32], s1, c1);
-          dot2_step(a2, rb[i + 64], s2, c2);
-          dot2_step(a3, rb[i + 96], s3, c3);
+          dot2_step(a0, __ldcg(P.r + i), s, c);
+          dot2_step(a1, __ldcg(P.r + i + 32), s1, c1);
+          dot2_step(a2, __ldcg(P.r + i + 64), s2, c2);
+          dot2_step(a3, __ldcg(P.r + i + 96), s3, c3);
         }
-        for (; i < rhi; i += 32) dot2_step(ptx::to_f64(__ldcg(acol + i)), rb[i], s, c);
+        for (; i < rhi; i += 32) dot2_step(ptx::to_f64(__ldcg(acol + i)), __ldcg(P.r + i), s, c);
         dot2_merge(s, c, s1, c1);
         dot2_merge(s2, c2, s3, c3);
         dot2_merge(s, c, s2, c2);
@@ -1575,7 +1575,7 @@ __global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_sched(EngineParams p) {
     else if (t.op <= OP_TTMQR)
       task_update(p, g, t, sh, dyn, phase);
     else
-      task_vector<Real, TC ? 32 : 8>(p, p.probs[t.pid], g, t, reinterpret_cast<double *>(dyn_raw), sh, phase);
+      task_vector<Real, TC ? 16 : 8>(p, p.probs[t.pid], g, t, reinterpret_cast<double *>(dyn_raw), sh, phase);
     __syncthreads();
     const int warp = threadIdx.x >> 5;
     if (warp != 1) {  // warps 0, 2 .. 7 release the successors, warp 0 the most critical 32
@@ -1850,7 +1850,7 @@ __global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_serve(ServeParams sp) {
     else if (t.op <= OP_TTMQR)
       task_update(p, g, t, sh, dyn, phase);
     else
-      task_vector<Real, TC ? 32 : 8>(p, P, g, t, reinterpret_cast<double *>(dyn_raw), sh, phase);
+      task_vector<Real, TC ? 16 : 8>(p, P, g, t, reinterpret_cast<double *>(dyn_raw), sh, phase);
     __syncthreads();
     if (threadIdx.x < 32) {  // warp 0 releases the successors, 32 at a time
       ptx::fence_proxy_async();
