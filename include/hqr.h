@@ -349,8 +349,10 @@ int hqr_debug_block_task(hqr_factors *F, int64_t task, int extra);
  * panel tasks (no split panels); the arithmetic of each task is the same.
  * An invalid list returns -7 (argument 7, as every -k code names argument k).
  * No cudaMalloc, cudaFree or other allocating call is made. The first call
- * on each device looks up that device's scratch address (a one-time set-up);
- * make that first call before any stream capture. All calls share the one
+ * on each device looks up that device's scratch address (a one-time set-up).
+ * The call cannot be part of a CUDA graph: it copies its task graph from
+ * static host memory and synchronizes `stream`, so a stream that is being
+ * captured returns -11 (argument 11) before any work. All calls share the one
  * scratch array and the library's static host staging, so calls that
  * overlap (on the GPU, or from several host threads) race; the array keeps
  * the last call's contents and every call rewrites all it reads. The call

@@ -2691,6 +2691,13 @@ extern "C" int hqr_geqrf_r_noalloc(const void *dA, int M, int N, int lda, int nb
   if (m > kNaMaxM || n > kNaMaxN || m * n > kNaMaxTiles) return HQR_ERR_TOO_LARGE;
   if (!na_list_valid(m, n, list, count)) return -7;
   cudaStream_t s = (cudaStream_t)stream;
+  {  // the call stages from host memory and synchronizes the stream: it cannot be captured
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+      cudaGetLastError();
+      return -11;
+    }
+  }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return HQR_ERR_CUDA;
   if (dev < 0 || dev >= kNaMaxDevices) return HQR_ERR_TOO_LARGE;

@@ -77,3 +77,25 @@ def test_noalloc_layout_over_the_scratch_size_then_a_normal_call():
     assert hqr.geqrf_r_noalloc(A, nb, ib, recs, R) == 0
     Rref = hqr.geqrf(A, nb, ib, recs).R()
     assert ((R - Rref).abs().max() / torch.linalg.norm(A)).item() <= R_TOL
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    """The call stages its task graph from host memory and synchronizes its
+    stream, so it cannot be captured: on a stream under capture it returns -11
+    (the stream argument) before any work, and the capture stays usable."""
+    import ctypes
+    nb, ib, M, N = 64, 16, 256, 128
+    recs = hqr.elim_list(M // nb, N // nb, 2, 1, "greedy", "greedy")
+    arr = np.ascontiguousarray(hqr.to_array(recs), dtype=hqr.ELIM_DTYPE)
+    A = torch.from_numpy(inputs.gaussian(M, N, seed=33)).cuda()
+    R = hqr.empty_colmajor(N, N)
+    lib = hqr.load()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        st = lib.hqr_geqrf_r_noalloc(ctypes.c_void_p(A.data_ptr()), M, N, M, nb, ib, ctypes.c_void_p(arr.ctypes.data),
+                                     len(arr), ctypes.c_void_p(R.data_ptr()), N, ctypes.c_void_p(s.cuda_stream))
+        R.add_(0.0)  # the capture goes on after the refused call
+    assert st == -11
+    torch.cuda.synchronize()
+    assert hqr.geqrf_r_noalloc(A, nb, ib, recs, R) == 0  # and a normal call after it works
