@@ -159,7 +159,9 @@ int hqr_validate_list(int m, int n, const hqr_elim_t *list, size_t count);
  *            q + 1: block q of a split panel), i, r, k, j, c0, cw, trans,
  *            tgt (fields of the device task record); tasks are in a
  *            topological order.
- *   succ_ptr caller array of ntasks + 1 offsets into succ (CSR successors).
+ *   succ_ptr caller array of ntasks + 1 offsets into succ (CSR successors;
+ *            with priority policy 1, each task's successors in the order the
+ *            device graph lists them: decreasing bottom level).
  *   succ     caller array of nedges successor ids.
  * With tasks == NULL only *ntasks and *nedges are set (HQR_ERR_CAPACITY
  * when buffers were given but are too small). Returns

@@ -523,6 +523,10 @@ int hqr_task_graph(int m, int n, int nb, int ib, int prec, const hqr_elim_t *lis
     g = build_ls_graph(ops, m, n, nb, P.w, param, 0, kind == 4, split_ib_for(prec, P), kind == 5);
   else
     g = build_apply_graph(ops, m, param, P.wb, kind == 1 ? 1 : 0);
+  // successor lists in the order the device copy of the same graph gets them (plans merge their
+  // problems' graphs and order them with the tensor-core tile size as the reference)
+  if (g_priority_policy == 1 && (kind == 0 || kind >= 3))
+    critical_path_priorities(g, (kind == 3 || kind == 5) ? 128 : nb);
   *ntasks = (int64_t)g.tasks.size();
   *nedges = (int64_t)g.succ.size();
   if (!tasks) return HQR_SUCCESS;

@@ -459,3 +459,34 @@ def test_noalloc_graph_limits():
     with pytest.raises(hqr.HQRError) as e:
         hqr.task_graph(65, 1, 16, 4, recs, kind="noalloc")
     assert e.value.status == hqr.ERR_TOO_LARGE
+
+
+@pytest.mark.parametrize("kind", ["ls", "ls_tol"])
+def test_fused_solve_steps_lead_their_predecessors_successors(kind):
+    """The scheduler lets a CTA keep the first successor (in list order) that a
+    finished triangular-solve step makes ready and run it next. Successor
+    lists are sorted by decreasing bottom level, and the cost model weights a
+    fused step (an update that also applies the next diagonal inverse) twice a
+    plain one, so the step that carries each solve chain is listed first among
+    the successors of the previous fused step."""
+    m = n = 9
+    nb, ib = 64, 16
+    tasks, ptr, succ = hqr.task_graph(m, n, nb, ib, hqr_elim_list(m, n, 2, 1, GREEDY, FIBONACCI), kind=kind,
+                                      param=3)
+    ops, ii, jj, tgt = tasks[:, 0], tasks[:, 2], tasks[:, 5], tasks[:, 9]
+    checked = 0
+    for op in (TRSV_TU, TRSV_U):
+        step = 1 if op == TRSV_TU else -1
+        fused = np.where((ops == op) & (tgt == 1))[0]
+        by_pos = {(int(ii[q]), int(jj[q]), int(q)): q for q in fused}
+        for q in fused:
+            # the next fused step of the same chain: row i + step, applying the inverse of tile j + step
+            nxt = [r for (i, j, r) in by_pos if i == ii[q] + step and j == jj[q] + step and r > q]
+            if not nxt:
+                continue
+            r = min(nxt)  # the same round: the first such step after q
+            lst = succ[ptr[q]:ptr[q + 1]]
+            assert r in lst, (op, q, r)
+            assert lst[0] == r, (op, int(q), int(r), [int(x) for x in lst[:4]])
+            checked += 1
+    assert checked >= 2 * 3 * (n - 2)  # every round's two chains
