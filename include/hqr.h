@@ -149,7 +149,8 @@ int hqr_validate_list(int m, int n, const hqr_elim_t *list, size_t count);
  *            server request (packing tasks first); 5: a problem of a plan
  *            from hqr_ls_plan_create_tol with at most `param` rounds (round
  *            tasks carry trans = 2 and k = the round; op 18 is a round's
- *            convergence check, op 19 a round's gate); 6: the graph of
+ *            convergence check, op 19 a round's gate; op 20 joins a round's
+ *            residual rows before its A^T r tasks); 6: the graph of
  *            hqr_geqrf_r_noalloc (FP64 only, its limits apply:
  *            HQR_ERR_TOO_LARGE beyond them; built in the static storage that
  *            entry point uses, so not concurrently with it).

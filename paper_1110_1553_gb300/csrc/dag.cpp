@@ -262,6 +262,7 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
   nres += (size_t)m * nrc;
   const size_t ires0 = nres;  // inverses of the diagonal R tiles
   nres += (size_t)n;
+  const size_t jres = nres++;  // a round's residual join
   auto pres = [&](int c, int j) { return pres0 + (size_t)c * n + (size_t)j; };
   auto qres = [&](int i, int c) { return qres0 + (size_t)i * nrc + (size_t)c; };
   auto ires = [&](int i) { return ires0 + (size_t)i; };
@@ -418,9 +419,17 @@ Graph build_ls_graph(const std::vector<PanelOp> &ops, int m, int n, int nb, int 
       tr.write(rres(i), d);
       b.add(vtask(OP_RESR, i, i));
     }
+    // The round's join, after every residual row: its release hands out all A^T r tasks at once in
+    // decreasing bottom level (the row chunks of column tile 0 first, which the forward solve
+    // needs first), where each row chunk's last residual would release them chunk by chunk and
+    // column tile 0 would be complete only at the end.
+    for (int i = 0; i < m; ++i) tr.read(rres(i), d);
+    tr.write(jres, d);
+    b.add(vtask(OP_RJOIN, 0, 0));
     for (int j = 0; j < n; ++j) {
       for (int c = 0; c < nch; ++c) {
         for (int i = c * kAtrChunk; i < std::min(m, (c + 1) * kAtrChunk); ++i) tr.read(rres(i), d);
+        tr.read(jres, d);
         tr.write(pres(c, j), d);
         b.add(rtask(OP_ATR, c, j));
       }

@@ -138,8 +138,7 @@ struct Shared {
   int vskip, vcomp;  // vector tasks of tolerance-stopped rounds: skip the task, compensated sums
   int norelease;     // the task released none of its successors (a gate that cancelled its rounds)
   int kept;          // a successor the last task made ready and this CTA runs next (-1: none)
-  int popped;        // the task warp 1 claimed meanwhile (-1: none or finished, -2: stopped)
-  int deferred;      // a claimed task that waits for the kept one (-1: none)
+  int popped;        // the task warp 1 claimed (-1: none, or finished)
   Real red[2 * NWARP];
   Real tau[IBMAX];
   Real wv[IBMAX];
@@ -1350,6 +1349,7 @@ __device__ void task_vector(const EngineParams &p, const Problem &P, const Geo<R
       }
       break;
     }
+    case OP_RJOIN:  // a join of the round's residual rows: no work
     default:
       break;
   }
@@ -1429,18 +1429,16 @@ __device__ __forceinline__ int take_slot(const EngineParams &p, int *slot) {
 }
 
 // Claim the next ready task (one warp, all lanes; the result in every lane).
-// -1: finished or failed; -2: `stop` (if given) turned non-negative first
-// (the CTA has its next task already). `pending` (lane 0's) counts tasks
-// this CTA completed but has not yet added to the global done counter; it
-// is flushed whenever the queues look empty.
-__device__ int pop_ready(const EngineParams &p, unsigned &pending, const volatile int *stop = nullptr) {
+// -1: finished or failed. `pending` (lane 0's) counts tasks this CTA
+// completed but has not yet added to the global done counter; it is flushed
+// whenever the queues look empty.
+__device__ int pop_ready(const EngineParams &p, unsigned &pending) {
   const int lane = threadIdx.x & 31;
   const uint64_t t0 = ptx::globaltimer();
   const int cap = shard_cap(p.ntasks);
   unsigned sleep_ns = 32;
   while (true) {
     if (__shfl_sync(0xffffffffu, lane == 0 ? ptx::ld_relaxed((const int *)&p.ctl->status.v) : 0, 0) != 0) return -1;
-    if (stop && __shfl_sync(0xffffffffu, lane == 0 ? *stop : -1, 0) >= 0) return -2;
     unsigned h = 0;
     const int qs = warp_claim<kNumQueues>(p.ctl->head, p.ctl->tail, h);
     if (qs >= 0) {
@@ -1545,19 +1543,20 @@ __global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_sched(EngineParams p) {
   // its successors are released, which cannot end the run early since the
   // counter reaches the task count only when no task has unfinished
   // successors. Seven warps release the successors (a solve step has up to
-  // one per tile of the vector). After a triangular-solve step, the most
+  // one per tile of the vector). After a least-squares vector task, the most
   // critical successor that the release makes ready (successors are listed by
   // decreasing bottom level) stays with this CTA and runs next without a trip
-  // through the queues, so the solve chain pays neither the push nor another
-  // CTA's claim per step (measured: 7.0 -> 4.3 us between steps). Warp 1 stops
-  // claiming once warp 0 keeps a task; a task it claimed before that runs right
-  // after the kept one. (Keeping after factorization tasks as well cost the
-  // 512^2 FP64 latency case 2 %: a claimed task then waits behind the kept one.)
+  // through the queues: the solve chain pays neither the push nor another
+  // CTA's claim per step (measured: 7.0 -> 4.3 us between steps), and the sum
+  // of a column tile's A^T r partials, then the solve step that needs it, run as
+  // soon as the last partial is done instead of queuing behind the other
+  // columns' partials. After such a task warp 1 claims only if nothing was kept
+  // (after the release), so a kept task never meets a claimed one. (Keeping
+  // after factorization tasks as well cost the 512^2 FP64 latency case 2 %.)
   unsigned pending = 0;
   if (threadIdx.x == 0) {
     sh.kept = -1;
     sh.popped = -1;
-    sh.deferred = -1;
   }
   if (threadIdx.x >= 32 && threadIdx.x < 64) {
     const int v = pop_ready(p, pending);
@@ -1590,7 +1589,7 @@ __global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_sched(EngineParams p) {
       __threadfence();
       const int rw = warp == 0 ? 0 : warp - 1;  // release slot of this warp
       const int e_end = sh.norelease ? t.succ_begin : t.succ_end;
-      const bool may_keep = warp == 0 && sh.deferred < 0 && t.op >= OP_TRSV_TD && t.op <= OP_TRSV_U;
+      const bool may_keep = warp == 0 && t.op >= OP_RESID;
       for (int e0 = t.succ_begin + 32 * rw; e0 < e_end; e0 += 32 * (NWARP - 1)) {
         const int e = e0 + (threadIdx.x & 31);
         int s = -1;
@@ -1619,22 +1618,18 @@ __global__ void __launch_bounds__(NT, TC ? 1 : 2) hqr_sched(EngineParams p) {
         atomicAdd(&p.ctl->done.v, pending);
         pending = 0;
       }
-      const int v = (sh.abort || sh.deferred >= 0) ? -1 : pop_ready(p, pending, &sh.kept);
+      // after a vector task the claim waits for the release (a successor may be kept)
+      const int v = (sh.abort || t.op >= OP_RESID) ? -1 : pop_ready(p, pending);
       if (threadIdx.x == 32) sh.popped = v;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {  // the next task: the kept one, else one waiting, else the claimed one
-      int next;
-      if (sh.kept >= 0) {
-        next = sh.kept;
-        if (sh.popped >= 0) sh.deferred = sh.popped;
-      } else if (sh.deferred >= 0) {
-        next = sh.deferred;
-        sh.deferred = -1;
-      } else {
-        next = sh.popped;
-      }
-      sh.task = next;
+    if (t.op >= OP_RESID && sh.kept < 0 && !sh.abort && warp == 1) {  // nothing kept: claim now
+      const int v = pop_ready(p, pending);
+      if (threadIdx.x == 32) sh.popped = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {  // the next task: the kept one, else the claimed one
+      sh.task = sh.kept >= 0 ? sh.kept : sh.popped;
       sh.kept = -1;
       sh.popped = -1;
       sh.norelease = 0;

@@ -33,6 +33,7 @@ enum Op : int8_t {
   OP_RESR = 17,    // r_i = b_i - sum over column chunks of the OP_RESID partial sums
   OP_RCHK = 18,    // convergence check of one refinement round (tolerance-stopped plans)
   OP_RGATE = 19,   // gate of refinement round k >= 2 (tolerance-stopped plans): cancels rounds >= k
+  OP_RJOIN = 20,   // join of a round's residual rows before its A^T r tasks (no work)
 };
 
 // Refinement rounds of a least-squares graph at most.

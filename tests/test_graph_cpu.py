@@ -17,7 +17,7 @@ from oracle.elim_list import BINARY, FIBONACCI, FLAT, GREEDY, hqr_elim_list
 hqr = pytest.importorskip("paper_1110_1553_gb300.hqr")
 
 GEQRT, UNMQR, TSQRT, TSMQR, TTQRT, TTMQR = range(6)
-RESID, ATR, TRSV_TD, TRSV_TU, TRSV_D, TRSV_U, XUPD, BTOG, PACK, ATRR, TRINV, RESR, RCHK, RGATE = range(6, 20)
+RESID, ATR, TRSV_TD, TRSV_TU, TRSV_D, TRSV_U, XUPD, BTOG, PACK, ATRR, TRINV, RESR, RCHK, RGATE, RJOIN = range(6, 21)
 WEIGHT = {GEQRT: 4, UNMQR: 6, TSQRT: 6, TSMQR: 12, TTQRT: 2, TTMQR: 6}  # units of b^3 / 3 (Sec. 2)
 CHUNK = 8  # tiles per chunk of the residual / A^T r partial sums
 
@@ -68,6 +68,8 @@ def accesses(task, nb, ib, m=0, n=0):
             reads, writes = {("g", j)}, {("x", j)}
         elif op == RGATE:  # round k's gate: acts on the stop decisions of the checks up to round k - 2
             reads = {("conv", k - 2)}
+        elif op == RJOIN:  # a join of the round's residual rows: no data of its own
+            pass
         elif op == RCHK:  # round k's convergence check (tolerance plans): its stop decision ("conv", k)
             reads = {("stat", k), ("cval", k - 1), ("mode", k), ("mode", k + 1), ("conv", k - 1)}
             writes = {("conv", k), ("cval", k), ("mode", k + 2)}
@@ -353,7 +355,7 @@ def test_tolerance_graph_has_no_races(low, high, a, p, iters, split):
     ops, ks, trans = tasks[:, 0], tasks[:, 4], tasks[:, 8]
     assert (ops == RCHK).sum() == iters
     assert sorted(ks[ops == RCHK]) == list(range(iters))
-    rnd = np.isin(ops, [RESID, RESR, ATR, ATRR, TRSV_TD, TRSV_TU, TRSV_D, TRSV_U, XUPD, RCHK, RGATE])
+    rnd = np.isin(ops, [RESID, RESR, ATR, ATRR, TRSV_TD, TRSV_TU, TRSV_D, TRSV_U, XUPD, RCHK, RGATE, RJOIN])
     assert rnd[trans == 2].all()  # only round tasks are marked
     assert (trans[np.isin(ops, [RESID, RESR, ATR, ATRR, RCHK])] == 2).all()
     # the starting point x0 = R^{-1} (Q^T b)[0:N]: Q^T b, its first N entries, one backward solve
