@@ -552,8 +552,14 @@ __device__ void factor_block(int mode, Real *P, int ld, int L, int ib, Real *Rt,
     for (int k = r0 + tid; k < r1; k += NT) ss = fma(col[k], col[k], ss);
     ss = block_sum(ss, sh, nact);
     Real snorm;
-    if (ss > RealTraits<Real>::tiny && ss < RealTraits<Real>::huge) {
-      snorm = sqrt(ss);
+    const bool plain = ss > RealTraits<Real>::tiny && ss < RealTraits<Real>::huge;
+    if constexpr (sizeof(Real) == 8) {
+      // FP64: the norm only matters to thread 0 below, which forms ||(alpha, x)|| from ss itself
+      // (a warp-wide square root on every warp would occupy the FP64 pipe for nothing)
+      snorm = plain ? ss : Real(0);
+    }
+    if (plain) {
+      if constexpr (sizeof(Real) == 4) snorm = sqrt(ss);
     } else {
       Real am = 0;
       for (int k = r0 + tid; k < r1; k += NT) am = fmax(am, fabs(col[k]));
@@ -576,7 +582,12 @@ __device__ void factor_block(int mode, Real *P, int ld, int L, int ib, Real *Rt,
       const Real alpha = *diag;
       Real beta = alpha, t = 0, scale = 0;
       if (snorm != Real(0)) {
-        const Real h = hypot(alpha, snorm);
+        Real h;
+        if constexpr (sizeof(Real) == 8)  // unscaled: snorm holds ss; sqrt(alpha^2 + ss) cannot overflow
+          h = plain ? (fabs(alpha) < 1e150 ? sqrt(fma(alpha, alpha, ss)) : hypot(alpha, sqrt(ss)))
+                    : hypot(alpha, snorm);
+        else
+          h = hypot(alpha, snorm);
         beta = (alpha >= Real(0)) ? -h : h;
         t = (beta - alpha) / beta;
         scale = Real(1) / (alpha - beta);
