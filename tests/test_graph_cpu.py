@@ -355,6 +355,10 @@ def test_tolerance_graph_has_no_races(low, high, a, p, iters, split):
     ops, ks, trans = tasks[:, 0], tasks[:, 4], tasks[:, 8]
     assert (ops == RCHK).sum() == iters
     assert sorted(ks[ops == RCHK]) == list(range(iters))
+    assert sorted(ks[ops == RJOIN]) == list(range(iters))  # one join per round, before its A^T r tasks
+    for q in np.nonzero(ops == RJOIN)[0]:  # it releases every A^T r task of its round
+        atr = np.nonzero((ops == ATR) & (ks == ks[q]) & (trans == 2))[0]
+        assert len(atr) and set(atr.tolist()) <= set(succ[ptr[q]:ptr[q + 1]].tolist())
     rnd = np.isin(ops, [RESID, RESR, ATR, ATRR, TRSV_TD, TRSV_TU, TRSV_D, TRSV_U, XUPD, RCHK, RGATE, RJOIN])
     assert rnd[trans == 2].all()  # only round tasks are marked
     assert (trans[np.isin(ops, [RESID, RESR, ATR, ATRR, RCHK])] == 2).all()
