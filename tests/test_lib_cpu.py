@@ -89,6 +89,11 @@ def test_capacity_and_argument_errors(lib):
     assert lib.hqr_elim_list(4, 2, 1, 0, 0, 0, None, 0, ctypes.byref(cnt)) == -4
     assert lib.hqr_elim_list(4, 2, 1, 1, 7, 0, None, 0, ctypes.byref(cnt)) == -5
     assert lib.hqr_geqrf(None, 4, 4, 4, 0, 8, 4, None, 0, None, None) == -1
+    # the widening entry point checks its arguments before any device work
+    assert lib.hqr_widen_f32(None, None, -1, None) == -3
+    assert lib.hqr_widen_f32(None, None, 0, None) == 0
+    assert lib.hqr_widen_f32(None, ctypes.c_void_p(16), 4, None) == -1
+    assert lib.hqr_widen_f32(ctypes.c_void_p(16), None, 4, None) == -2
 
 
 def test_validator_agrees_with_oracle_on_mutations(lib):
